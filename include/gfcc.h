@@ -1,0 +1,157 @@
+/*
+ * gfcc.h - C ABI of the GB300 GFCCSD library (libgfcc.so).
+ *
+ * The library solves, for every frequency omega and orbital p, the shifted
+ * complex linear systems of the GFCCSD method (Peng et al., "GFCCLib",
+ * arXiv 2010.04768, Theory section, eq. xplin)
+ *
+ *     IP: (omega - i eta + Hbar_N) X_p |Phi> = a_p-bar |Phi>      (1h + 2h1p space, eq. xp)
+ *     EA: (omega + i eta - Hbar_N) Y_q |Phi> = a_q^+-bar |Phi>    (1p + 2p1h space, eq. yq)
+ *
+ * by GMRES (GFCC Workflow and Bottlenecks section), and forms the Green's
+ * function of eqs. gfxn2/gfxn3
+ *
+ *     G_pq(omega) = <Phi|(1+Lambda) a_q^+-bar X_p|Phi> + <Phi|(1+Lambda) a_p-bar Y_q|Phi>.
+ *
+ * Conventions (spin-orbital formalism, n = o + v orbitals, occupied first):
+ *   Hbar = e^-T H e^T with H = sum h_pq p^+q + 1/4 sum <pq||rs> p^+q^+sr,
+ *   <pq||rs> = (pr|qs) - (ps|qr), (pr|qs) = sum_K L[K][p][r] L[K][q][s]
+ *   (the Cholesky representation of the Implementation Details section), and
+ *   h = fock - sum_j <pj||qj> so that the reference Fock matrix is `fock`.
+ *   The operator of eq. xplin is taken in commutator form <mu|[Hbar, R]|Phi>.
+ *
+ * All arrays are row-major float64 (IEEE binary64).  Unless stated otherwise,
+ * pointers are HOST pointers; the library copies what it needs and never keeps
+ * a caller pointer after a call returns.  A context owns all the device memory
+ * it allocates and one CUDA stream (settable); it is not thread-safe.
+ *
+ * Return codes: 0 = success, > 0 = warning (results written), < 0 = error
+ * (nothing written).  No error aborts the process; gfcc_last_error() gives a
+ * message for the last failing call on the calling thread.
+ */
+#ifndef GFCC_H
+#define GFCC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GFCC_OK                    0
+#define GFCC_WARN_NOT_CONVERGED    1   /* G written; gfcc_last_stats says which columns missed tol     */
+#define GFCC_ERR_ARG             (-1)  /* bad size, ordering, symmetry, orbital index, eta/tol <= 0     */
+#define GFCC_ERR_OOM             (-2)  /* device allocation failed                                      */
+#define GFCC_ERR_CUDA            (-3)  /* a CUDA call or kernel launch failed                           */
+#define GFCC_ERR_TIMEOUT         (-4)  /* a bounded device wait gave up                                 */
+#define GFCC_ERR_STATE           (-5)  /* call not valid in the context's current state                 */
+
+/* Sectors (gfcc_set_option key GFCC_OPT_SECTOR). */
+#define GFCC_SECTOR_IP   1
+#define GFCC_SECTOR_EA   2
+#define GFCC_SECTOR_BOTH 3
+
+/* Precisions (key GFCC_OPT_PRECISION). */
+#define GFCC_PREC_FP64        0   /* every step in float64                                              */
+#define GFCC_PREC_MIXED_BF16  1   /* sigma product on bf16 tensor cores + fp64 iterative refinement    */
+
+/* Preconditioners (key GFCC_OPT_PRECOND). */
+#define GFCC_PRECOND_NONE  0      /* plain GMRES, as in the paper's runs                                */
+#define GFCC_PRECOND_DIAG  1      /* right preconditioning by the Fock-like diagonal of the operator    */
+
+/* Option keys for gfcc_set_option. */
+#define GFCC_OPT_SECTOR      1    /* GFCC_SECTOR_*; default BOTH (eq. gfxn3)                            */
+#define GFCC_OPT_PRECISION   2    /* GFCC_PREC_*; default FP64                                           */
+#define GFCC_OPT_RESTART     3    /* GMRES restart length m (1..64); default 30                          */
+#define GFCC_OPT_MAX_ITERS   4    /* max sigma products per system; default 1500                         */
+#define GFCC_OPT_PRECOND     5    /* GFCC_PRECOND_*; default DIAG                                        */
+#define GFCC_OPT_BATCH       6    /* systems solved together (0 = chosen from free memory); default 0   */
+#define GFCC_OPT_INNER_TOL   7    /* mixed precision: inner GMRES relative tolerance; default 1e-3       */
+
+/* Per-column status values reported by gfcc_last_stats. */
+#define GFCC_STATUS_CONVERGED      0
+#define GFCC_STATUS_NOT_CONVERGED  1
+
+typedef struct gfcc_ctx gfcc_ctx;
+
+/*
+ * gfcc_create - copy the problem to the device and build the Hbar elements.
+ *   o, v      : occupied / virtual orbital counts (o >= 1, v >= 1); L >= 1 Cholesky vectors.
+ *   fock      : n x n, symmetric (checked to 1e-12 relative).
+ *   chol      : L x n x n, chol[K][p][q] == chol[K][q][p] (checked).
+ *   t1        : o x v, t1[i][a] = t_i^a.
+ *   t2        : o x o x v x v, t2[i][j][a][b] = t_ij^ab, antisymmetric in (i,j) and (a,b) (checked).
+ *   lambda    : NULL for Lambda = T^dagger (lambda_a^i = t_i^a, lambda_ab^ij = t_ij^ab);
+ *               otherwise o*v values lambda1[i][a] followed by o*o*v*v values lambda2[i][j][a][b].
+ *   out       : receives the new context (NULL on error).
+ * The T1 part of T is applied to the integrals (L' = (1-t) L (1+t), an orbital
+ * rotation) and the T2 part gives the Hbar elements kept for the sigma product
+ * (Implementation Details section: constant intermediates of size <= O(O^2 V^2),
+ * plus the vvvv block when the EA sector is enabled).  Sector and precision
+ * are fixed at creation: call gfcc_create_ex to choose them, gfcc_create builds both
+ * sectors in FP64.
+ */
+int gfcc_create(int o, int v, int L, const double *fock, const double *chol,
+                const double *t1, const double *t2, const double *lambda, gfcc_ctx **out);
+
+/* gfcc_create_ex - gfcc_create with the sectors (GFCC_SECTOR_*) and precision (GFCC_PREC_*)
+ * to build intermediates for. */
+int gfcc_create_ex(int o, int v, int L, const double *fock, const double *chol,
+                   const double *t1, const double *t2, const double *lambda,
+                   int sectors, int precision, gfcc_ctx **out);
+
+/* gfcc_set_option - set one GFCC_OPT_* option (value cast from double).  Returns GFCC_ERR_ARG
+ * for an unknown key or a value out of range. */
+int gfcc_set_option(gfcc_ctx *ctx, int key, double value);
+
+/* gfcc_set_stream - run all of the context's work on `stream` (a cudaStream_t; NULL = the
+ * context's own stream). */
+int gfcc_set_stream(gfcc_ctx *ctx, void *stream);
+
+/*
+ * gfcc_solve - G(omega) for every omega in `omegas` and every (p, q) pair of `orbitals`.
+ *   omegas   : n_omega frequencies (Hartree).  eta > 0 broadening.  tol > 0: a column is
+ *              converged when ||b - A x||_2 <= tol ||b||_2 (true residual, packed coordinates).
+ *   orbitals : n_orb indices in [0, o+v); p and q both run over this list.
+ *   G        : out, complex128 interleaved (re, im), [n_omega][n_orb (p)][n_orb (q)], caller-allocated
+ *              host memory of 2*n_omega*n_orb*n_orb doubles; G = G^IP + G^EA for the enabled sectors.
+ * Returns GFCC_OK, GFCC_WARN_NOT_CONVERGED (G written, some columns missed tol), or an error.
+ */
+int gfcc_solve(gfcc_ctx *ctx, int n_omega, const double *omegas, double eta,
+               int n_orb, const int *orbitals, double tol, double *G);
+
+/* gfcc_solve_device - gfcc_solve with omegas, orbitals and G in DEVICE memory (same layouts);
+ * the call is asynchronous on the context's stream except for the per-iteration
+ * convergence checks, which synchronise it. */
+int gfcc_solve_device(gfcc_ctx *ctx, int n_omega, const double *omegas_dev, double eta,
+                      int n_orb, const int *orbitals_dev, double tol, double *G_dev);
+
+/*
+ * gfcc_last_stats - statistics of the last gfcc_solve, one entry per (sector, omega, orbital)
+ * in the order IP then EA, omega-major: `iters` sigma products, `relres` final true relative
+ * residual, `status` GFCC_STATUS_*.  Any pointer may be NULL; `count` (in/out) is the capacity
+ * on input and the number of entries on output.
+ */
+int gfcc_last_stats(gfcc_ctx *ctx, int *count, int *iters, double *relres, int *status);
+
+/*
+ * gfcc_sigma - apply the sigma product sigma(x) = <mu|[Hbar, X]|Phi> (the Hbar part of eq. xplin)
+ * to n_vec packed complex vectors.  sector GFCC_SECTOR_IP or GFCC_SECTOR_EA.
+ *   x, y : host, complex128 interleaved, [n_vec][dim]; dim = o + o(o-1)/2 * v (IP, packed
+ *          order: 1h i, then pairs i<j lexicographic with a fastest) or v + o * v(v-1)/2
+ *          (EA: 1p a, then i-major with pairs a<b lexicographic).
+ * Uses the FP64 sigma regardless of the precision option.
+ */
+int gfcc_sigma(gfcc_ctx *ctx, int sector, int n_vec, const double *x, double *y);
+
+/* gfcc_dims - packed dimensions of the IP and EA spaces of the context. */
+int gfcc_dims(gfcc_ctx *ctx, long long *dim_ip, long long *dim_ea);
+
+/* gfcc_destroy - free the context and all its device memory.  NULL is a no-op. */
+void gfcc_destroy(gfcc_ctx *ctx);
+
+/* gfcc_last_error - message of the last failing call on this thread ("" if none). */
+const char *gfcc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GFCC_H */

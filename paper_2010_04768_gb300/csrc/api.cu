@@ -1,0 +1,770 @@
+// The C ABI of libgfcc: context life cycle, option handling, the frequency x orbital
+// task loop of gfcc_solve (Algorithm 1 of the paper: all (omega, p) tasks of a level are
+// independent; here they are batched onto one GPU instead of process groups), the
+// right-hand sides, left vectors and overlaps of eqs. gfxn2/gfxn3.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "ctx.cuh"
+#include "gmres.cuh"
+#include "kernels.cuh"
+#include "sigma.cuh"
+
+namespace gfcc {
+
+static thread_local char g_err[1024] = "";
+
+namespace {
+struct AllocRec {
+  uintptr_t base;
+  size_t bytes;
+};
+std::mutex g_alloc_mu;
+std::vector<AllocRec> g_allocs;
+}  // namespace
+
+void reg_alloc(const void *p, size_t bytes) {
+  if (p == nullptr) return;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_allocs.push_back({reinterpret_cast<uintptr_t>(p), bytes});
+}
+
+void unreg_alloc(const void *p) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  for (size_t i = 0; i < g_allocs.size(); i++)
+    if (g_allocs[i].base == reinterpret_cast<uintptr_t>(p)) {
+      g_allocs[i] = g_allocs.back();
+      g_allocs.pop_back();
+      return;
+    }
+}
+
+int check_extent(const double *p, long long lo, long long hi, const char *what) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p + lo), b = reinterpret_cast<uintptr_t>(p + hi + 1);
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  for (const AllocRec &r : g_allocs)
+    if (a >= r.base && b <= r.base + r.bytes && lo <= hi) return GFCC_OK;
+  set_error("internal extent check failed for %s: offsets [%lld, %lld] are outside every device allocation", what,
+            lo, hi);
+  return GFCC_ERR_ARG;
+}
+
+cudaError_t dmalloc(void **p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) reg_alloc(*p, bytes);
+  return e;
+}
+
+void dfree(void *p) {
+  if (p == nullptr) return;
+  unreg_alloc(p);
+  cudaFree(p);
+}
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+namespace {
+
+// ---------------------------------------------------------------- input checks (device)
+__device__ __forceinline__ void atomic_max_abs(unsigned long long *dst, double v) {
+  // |v| as IEEE bits orders like an unsigned integer (NaN sorts above +inf)
+  const unsigned long long bits = __double_as_longlong(fabs(v)) & 0x7fffffffffffffffULL;
+  atomicMax(dst, bits);
+}
+
+// out[0] = max |x|; out[1] = max |x - sign * x^P| over the permutation given by (swap01, swap23) of a 4-index tensor
+__global__ void symmetry_kernel(const double *x, long long d0, long long d1, long long d2, long long d3, int swap01,
+                                int swap23, double sign, unsigned long long *out) {
+  const long long tot = d0 * d1 * d2 * d3;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    long long r = t;
+    const long long k3 = r % d3; r /= d3;
+    const long long k2 = r % d2; r /= d2;
+    const long long k1 = r % d1;
+    const long long k0 = r / d1;
+    long long p0 = k0, p1 = k1, p2 = k2, p3 = k3;
+    if (swap01) { p0 = k1; p1 = k0; }
+    if (swap23) { p2 = k3; p3 = k2; }
+    const double a = x[t];
+    const double b = x[((p0 * d1 + p1) * d2 + p2) * d3 + p3];
+    atomic_max_abs(out, a);
+    atomic_max_abs(out + 1, a - sign * b);
+  }
+}
+
+// ---------------------------------------------------------------- right-hand sides
+// IP b_p: p occupied: unit 1h vector; p = o + b virtual: r1 = t1[:, b], r2[i<j, a] = t2[i][j][b][a]
+__global__ void rhs_ip_kernel(double *B, long long n, int nsys, const int *porb, int o, int v, const double *t1,
+                              const double *t2) {
+  const long long tot = n * nsys;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(t / n);
+    const long long mu = t - (long long)s * n;
+    const int p = porb[s];
+    double val = 0.0;
+    if (mu < o) {
+      val = p < o ? (mu == p ? 1.0 : 0.0) : t1[mu * v + (p - o)];
+    } else if (p >= o) {
+      const long long r = mu - o;
+      const long long a = r % v;
+      long long i, j;
+      pair_decode(r / v, o, i, j);
+      val = t2[((i * o + j) * v + (p - o)) * v + a];
+    }
+    B[2 * t] = val;
+    B[2 * t + 1] = 0.0;
+  }
+}
+
+// EA b_q: q virtual: unit 1p vector; q = m occupied: y1 = -t1[m, :], y2[i, a<b] = -t2[m][i][a][b]
+__global__ void rhs_ea_kernel(double *B, long long n, int nsys, const int *qorb, int o, int v, long long Pv,
+                              const double *t1, const double *t2) {
+  const long long tot = n * nsys;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(t / n);
+    const long long mu = t - (long long)s * n;
+    const int q = qorb[s];
+    double val = 0.0;
+    if (mu < v) {
+      val = q >= o ? (mu == q - o ? 1.0 : 0.0) : -t1[(long long)q * v + mu];
+    } else if (q < o) {
+      const long long r = mu - v;
+      const long long i = r / Pv;
+      long long a, b;
+      pair_decode(r % Pv, v, a, b);
+      val = -t2[(((long long)q * o + i) * v + a) * v + b];
+    }
+    B[2 * t] = val;
+    B[2 * t + 1] = 0.0;
+  }
+}
+
+// ---------------------------------------------------------------- left vectors (real), C[q][mu]
+// IP c_q(mu) = <Phi|(1+Lambda) a_q^+-bar |mu>:
+//   q = o + b: c(k) = l1[k][b], c(i<j, a) = l2[i][j][b][a]
+//   q = m    : c(k) = d_mk - t1[m].l1[k] - 1/2 t2[m][l][c][d] l2[k][l][c][d];
+//              c(i<j, a) = d_mi l1[j][a] - d_mj l1[i][a] - t1[m][c] l2[i][j][c][a]
+__global__ void left_ip_2h1p_kernel(double *C, long long n, int nq, const int *qorb, int o, int v, const double *t1,
+                                    const double *l1, const double *l2) {
+  const long long n2 = n - o;
+  const long long tot = n2 * nq;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int qi = (int)(t / n2);
+    const long long r = t - (long long)qi * n2;
+    const int q = qorb[qi];
+    const long long a = r % v;
+    long long i, j;
+    pair_decode(r / v, o, i, j);
+    double val;
+    if (q >= o) {
+      val = l2[((i * o + j) * v + (q - o)) * v + a];
+    } else {
+      const int m = q;
+      val = (m == i ? l1[j * v + a] : 0.0) - (m == j ? l1[i * v + a] : 0.0);
+      for (int c = 0; c < v; c++) val -= t1[(long long)m * v + c] * l2[((i * o + j) * v + c) * v + a];
+    }
+    C[(long long)qi * n + o + r] = val;
+  }
+}
+
+__global__ void left_ip_1h_kernel(double *C, long long n, int nq, const int *qorb, int o, int v, const double *t1,
+                                  const double *t2, const double *l1, const double *l2) {
+  __shared__ double2 sh[32];
+  const int qi = blockIdx.x / o, k = blockIdx.x % o;
+  const int q = qorb[qi];
+  double val;
+  if (q >= o) {
+    val = l1[(long long)k * v + (q - o)];
+  } else {
+    const int m = q;
+    const long long ovv = (long long)o * v * v;
+    double acc = 0.0;
+    for (long long x = threadIdx.x; x < ovv; x += blockDim.x)   // x = (l, c, d)
+      acc += t2[(long long)m * ovv + x] * l2[(long long)k * ovv + x];
+    double acc1 = 0.0;
+    for (int c = threadIdx.x; c < v; c += blockDim.x) acc1 += t1[(long long)m * v + c] * l1[(long long)k * v + c];
+    double2 sum = make_double2(acc, acc1);
+    for (int off = 16; off > 0; off >>= 1) {
+      sum.x += __shfl_down_sync(0xffffffffu, sum.x, off);
+      sum.y += __shfl_down_sync(0xffffffffu, sum.y, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = sum;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    sum = make_double2(0.0, 0.0);
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      sum.x += sh[w].x;
+      sum.y += sh[w].y;
+    }
+    val = (m == k ? 1.0 : 0.0) - sum.y - 0.5 * sum.x;
+  }
+  if (threadIdx.x == 0) C[(long long)qi * n + k] = val;
+}
+
+// EA c_p(mu) = <Phi|(1+Lambda) a_p-bar |mu>:
+//   p = m    : c(c) = -l1[m][c], c(i, c<d) = l2[i][m][c][d]
+//   p = o + e: c(c) = d_ec - t1[k][e] l1[k][c] + 1/2 t2[k][l][e][d] l2[k][l][d][c];
+//              c(i, c<d) = d_ec l1[i][d] - d_ed l1[i][c] + t1[k][e] l2[i][k][c][d]
+__global__ void left_ea_2p1h_kernel(double *C, long long n, int np, const int *porb, int o, int v, long long Pv,
+                                    const double *t1, const double *l1, const double *l2) {
+  const long long n2 = n - v;
+  const long long tot = n2 * np;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int pi = (int)(t / n2);
+    const long long r = t - (long long)pi * n2;
+    const int p = porb[pi];
+    const long long i = r / Pv;
+    long long c, d;
+    pair_decode(r % Pv, v, c, d);
+    double val;
+    if (p < o) {
+      val = l2[((i * o + p) * v + c) * v + d];
+    } else {
+      const long long e = p - o;
+      val = (e == c ? l1[i * v + d] : 0.0) - (e == d ? l1[i * v + c] : 0.0);
+      for (int k = 0; k < o; k++) val += t1[(long long)k * v + e] * l2[((i * o + k) * v + c) * v + d];
+    }
+    C[(long long)pi * n + v + r] = val;
+  }
+}
+
+__global__ void left_ea_1p_kernel(double *C, long long n, int np, const int *porb, int o, int v, const double *t1,
+                                  const double *t2, const double *l1, const double *l2) {
+  __shared__ double2 sh[32];
+  const int pi = blockIdx.x / v, c = blockIdx.x % v;
+  const int p = porb[pi];
+  double val;
+  if (p < o) {
+    val = -l1[(long long)p * v + c];
+  } else {
+    const long long e = p - o;
+    const long long oov = (long long)o * o * v;
+    double acc = 0.0;
+    for (long long x = threadIdx.x; x < oov; x += blockDim.x) {   // x = (k, l, d)
+      const long long kl = x / v, d = x % v;
+      acc += t2[(kl * v + e) * v + d] * l2[(kl * v + d) * v + c];
+    }
+    double acc1 = 0.0;
+    for (int k = threadIdx.x; k < o; k += blockDim.x) acc1 += t1[(long long)k * v + e] * l1[(long long)k * v + c];
+    double2 sum = make_double2(acc, acc1);
+    for (int off = 16; off > 0; off >>= 1) {
+      sum.x += __shfl_down_sync(0xffffffffu, sum.x, off);
+      sum.y += __shfl_down_sync(0xffffffffu, sum.y, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = sum;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    sum = make_double2(0.0, 0.0);
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      sum.x += sh[w].x;
+      sum.y += sh[w].y;
+    }
+    val = (e == c ? 1.0 : 0.0) - sum.y + 0.5 * sum.x;
+  }
+  if (threadIdx.x == 0) C[(long long)pi * n + c] = val;
+}
+
+// ---------------------------------------------------------------- overlaps
+// part[z][(s,t)][q] summed over z -> G: IP row (w_s, a_s) gets columns q; EA column (w_s, a_s) gets rows q
+__global__ void overlap_scatter_kernel(const double *part, int nsplit, int nsys, int nq, const int *tw, const int *ta,
+                                       int is_ip, double *G) {
+  const long long tot = (long long)nsys * nq;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(t / nq), q = (int)(t % nq);
+    double re = 0.0, im = 0.0;
+    const long long zs = 2LL * nsys * nq;
+    for (int z = 0; z < nsplit; z++) {
+      re += part[z * zs + (2LL * s) * nq + q];
+      im += part[z * zs + (2LL * s + 1) * nq + q];
+    }
+    const long long w = tw[s], a = ta[s];
+    const long long idx = is_ip ? (w * nq + a) * nq + q : (w * nq + q) * nq + a;
+    G[2 * idx] += re;
+    G[2 * idx + 1] += im;
+  }
+}
+
+__global__ void gather_omega_kernel(const double *om, const int *tw, int nsys, double *out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < nsys) out[s] = om[tw[s]];
+}
+
+__global__ void gather_orb_kernel(const int *orbs, const int *ta, int nsys, int *out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < nsys) out[s] = orbs[ta[s]];
+}
+
+int check_tensor(cudaStream_t st, const double *x, long long d0, long long d1, long long d2, long long d3, int s01,
+                 int s23, double sign, double rel, const char *name) {
+  unsigned long long *d, h[2];
+  GFCC_CUDA(cudaMalloc(&d, 2 * sizeof(unsigned long long)));
+  cudaMemsetAsync(d, 0, 2 * sizeof(unsigned long long), st);
+  symmetry_kernel<<<grid1d(d0 * d1 * d2 * d3), 256, 0, st>>>(x, d0, d1, d2, d3, s01, s23, sign, d);
+  cudaError_t e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    set_error("input check of %s: %s", name, cudaGetErrorString(e));
+    return GFCC_ERR_CUDA;
+  }
+  double mx, dev;
+  memcpy(&mx, &h[0], sizeof(double));
+  memcpy(&dev, &h[1], sizeof(double));
+  if (!std::isfinite(mx) || !std::isfinite(dev)) {
+    set_error("%s contains non-finite values", name);
+    return GFCC_ERR_ARG;
+  }
+  if (dev > rel * std::max(1.0, mx)) {
+    set_error("%s violates its permutation symmetry (max deviation %.3e, max |value| %.3e)", name, dev, mx);
+    return GFCC_ERR_ARG;
+  }
+  return GFCC_OK;
+}
+
+int upload(gfcc_ctx *c, double **dst, const double *src, long long count) {
+  GFCC_TRY(dev_alloc(c, dst, count));
+  GFCC_CUDA(cudaMemcpyAsync(*dst, src, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
+  return GFCC_OK;
+}
+
+int create_impl(int o, int v, int L, const double *fock, const double *chol, const double *t1, const double *t2,
+                const double *lambda, int sectors, int precision, gfcc_ctx **out) {
+  if (out == nullptr) {
+    set_error("gfcc_create: out is NULL");
+    return GFCC_ERR_ARG;
+  }
+  *out = nullptr;
+  if (o < 1 || v < 1 || L < 1 || fock == nullptr || chol == nullptr || t1 == nullptr || t2 == nullptr) {
+    set_error("gfcc_create: need o >= 1, v >= 1, L >= 1 and non-NULL fock, chol, t1, t2");
+    return GFCC_ERR_ARG;
+  }
+  if (sectors < 1 || sectors > 3 || (precision != GFCC_PREC_FP64 && precision != GFCC_PREC_MIXED_BF16)) {
+    set_error("gfcc_create: bad sectors (%d) or precision (%d)", sectors, precision);
+    return GFCC_ERR_ARG;
+  }
+  gfcc_ctx *c = new gfcc_ctx();
+  c->o = o; c->v = v; c->L = L; c->n = o + v;
+  c->Po = (long long)o * (o - 1) / 2;
+  c->Pv = (long long)v * (v - 1) / 2;
+  c->dim_ip = o + c->Po * v;
+  c->dim_ea = v + (long long)o * c->Pv;
+  c->sectors = sectors;
+  c->precision = precision;
+  int s = GFCC_OK;
+  auto fail = [&](int code) {
+    gfcc_destroy(c);
+    return code;
+  };
+  if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("gfcc_create: cannot create a CUDA stream (no usable GPU?)");
+    return fail(GFCC_ERR_CUDA);
+  }
+  c->stream = c->own_stream;
+  const long long n = c->n, nn = n * n, ov = (long long)o * v, oovv = ov * ov;
+  double *d_fock = nullptr, *d_chol = nullptr;
+  if ((s = dev_alloc_tmp(&d_fock, nn)) < 0) return fail(s);
+  if ((s = dev_alloc_tmp(&d_chol, (long long)L * nn)) < 0) {
+    dfree(d_fock);
+    return fail(s);
+  }
+  auto free_tmp = [&]() {
+    dfree(d_fock);
+    dfree(d_chol);
+  };
+  if (cudaMemcpyAsync(d_fock, fock, sizeof(double) * nn, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(d_chol, chol, sizeof(double) * L * nn, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+    set_error("gfcc_create: host-to-device copy failed: %s", cudaGetErrorString(cudaGetLastError()));
+    free_tmp();
+    return fail(GFCC_ERR_CUDA);
+  }
+  if ((s = upload(c, &c->t1, t1, ov)) < 0 || (s = upload(c, &c->t2, t2, oovv)) < 0) {
+    free_tmp();
+    return fail(s);
+  }
+  if (lambda != nullptr) {
+    if ((s = upload(c, &c->l1, lambda, ov)) < 0 || (s = upload(c, &c->l2, lambda + ov, oovv)) < 0) {
+      free_tmp();
+      return fail(s);
+    }
+  } else {
+    c->l1 = c->t1;
+    c->l2 = c->t2;
+  }
+  // input checks: symmetric fock and Cholesky vectors, antisymmetric T2 / Lambda2, all finite
+  if ((s = check_tensor(c->stream, d_fock, 1, 1, n, n, 0, 1, 1.0, 1e-12, "fock")) < 0 ||
+      (s = check_tensor(c->stream, d_chol, 1, L, n, n, 0, 1, 1.0, 1e-12, "chol")) < 0 ||
+      (s = check_tensor(c->stream, c->t1, 1, 1, o, v, 0, 0, 1.0, 1e300, "t1")) < 0 ||
+      (s = check_tensor(c->stream, c->t2, o, o, v, v, 1, 0, -1.0, 1e-12, "t2 (i<->j)")) < 0 ||
+      (s = check_tensor(c->stream, c->t2, o, o, v, v, 0, 1, -1.0, 1e-12, "t2 (a<->b)")) < 0) {
+    free_tmp();
+    return fail(s);
+  }
+  if (lambda != nullptr &&
+      ((s = check_tensor(c->stream, c->l1, 1, 1, o, v, 0, 0, 1.0, 1e300, "lambda1")) < 0 ||
+       (s = check_tensor(c->stream, c->l2, o, o, v, v, 1, 0, -1.0, 1e-12, "lambda2 (i<->j)")) < 0 ||
+       (s = check_tensor(c->stream, c->l2, o, o, v, v, 0, 1, -1.0, 1e-12, "lambda2 (a<->b)")) < 0)) {
+    free_tmp();
+    return fail(s);
+  }
+  s = build_hbar(c, d_fock, d_chol);
+  free_tmp();
+  if (s < 0) return fail(s);
+  *out = c;
+  return GFCC_OK;
+}
+
+int choose_batch(gfcc_ctx *c, int sector, long long n, long long ntasks) {
+  if (c->batch > 0) return (int)std::min<long long>(c->batch, ntasks);
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    fr = 1ULL << 30;
+  }
+  const double per = 8.0 * (double)(gmres_work_doubles(c, sector, n, 2, c->restart) -
+                                   gmres_work_doubles(c, sector, n, 1, c->restart));
+  long long b = (long long)(0.6 * (double)fr / std::max(per, 1.0));
+  b = std::max<long long>(1, std::min<long long>(b, 256));
+  return (int)std::min<long long>(b, ntasks);
+}
+
+int grow_scratch(gfcc_ctx *c, size_t bytes) {
+  if (c->scratch_bytes >= bytes) return GFCC_OK;
+  if (c->scratch) dfree(c->scratch);
+  c->scratch = nullptr;
+  c->scratch_bytes = 0;
+  if (dmalloc(&c->scratch, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cannot allocate %.3f GB of solver workspace", bytes / 1e9);
+    return GFCC_ERR_OOM;
+  }
+  c->scratch_bytes = bytes;
+  return GFCC_OK;
+}
+
+int solve_impl(gfcc_ctx *c, int n_omega, const double *d_om, double eta, int n_orb, const int *d_orb,
+               const int *h_orb, double tol, double *d_G) {
+  cudaStream_t st = c->stream;
+  const int sectors[2] = {GFCC_SECTOR_IP, GFCC_SECTOR_EA};
+  const long long ntasks = (long long)n_omega * n_orb;
+  const int nsec = (c->sectors & GFCC_SECTOR_IP ? 1 : 0) + (c->sectors & GFCC_SECTOR_EA ? 1 : 0);
+  c->st_iters.assign(ntasks * nsec, 0);
+  c->st_status.assign(ntasks * nsec, GFCC_STATUS_NOT_CONVERGED);
+  c->st_relres.assign(ntasks * nsec, 0.0);
+  GFCC_CUDA(cudaMemsetAsync(d_G, 0, sizeof(double) * 2 * n_omega * n_orb * n_orb, st));
+  int sec_slot = 0;
+  bool all_ok = true;
+  (void)h_orb;
+  for (int sector : sectors) {
+    if (!(c->sectors & sector)) continue;
+    const bool ip = sector == GFCC_SECTOR_IP;
+    const long long n = ip ? c->dim_ip : c->dim_ea;
+    const int nsys = choose_batch(c, sector, n, ntasks);
+    const int m = c->restart;
+    const long long nsplit = (n + 8191) / 8192;
+    const long long work = gmres_work_doubles(c, sector, n, nsys, m) + (long long)n_orb * n +
+                           nsplit * 2LL * nsys * n_orb + 4LL * nsys + 64;
+    GFCC_TRY(grow_scratch(c, sizeof(double) * work));
+    double *base = static_cast<double *>(c->scratch);
+    Gmres gm;
+    GFCC_TRY(gm.init(c, sector, n, nsys, m, base));
+    double *Cl = base + gmres_work_doubles(c, sector, n, nsys, m);
+    double *part = Cl + (long long)n_orb * n;
+    int *d_tw = reinterpret_cast<int *>(part + nsplit * 2LL * nsys * n_orb);
+    int *d_ta = d_tw + nsys;
+    int *d_porb = d_ta + nsys;
+    gm.eta = eta;
+    gm.use_precond = c->precond == GFCC_PRECOND_DIAG;
+    // left vectors for all orbitals of the list
+    if (ip) {
+      left_ip_1h_kernel<<<n_orb * c->o, 256, 0, st>>>(Cl, n, n_orb, d_orb, c->o, c->v, c->t1, c->t2, c->l1, c->l2);
+      GFCC_LAUNCH_CHECK();
+      if (n > c->o) {
+        left_ip_2h1p_kernel<<<grid1d((n - c->o) * n_orb), 256, 0, st>>>(Cl, n, n_orb, d_orb, c->o, c->v, c->t1,
+                                                                          c->l1, c->l2);
+        GFCC_LAUNCH_CHECK();
+      }
+    } else {
+      left_ea_1p_kernel<<<n_orb * c->v, 256, 0, st>>>(Cl, n, n_orb, d_orb, c->o, c->v, c->t1, c->t2, c->l1, c->l2);
+      GFCC_LAUNCH_CHECK();
+      if (n > c->v) {
+        left_ea_2p1h_kernel<<<grid1d((n - c->v) * n_orb), 256, 0, st>>>(Cl, n, n_orb, d_orb, c->o, c->v, c->Pv, c->t1,
+                                                                          c->l1, c->l2);
+        GFCC_LAUNCH_CHECK();
+      }
+    }
+    std::vector<int> h_tw(nsys), h_ta(nsys), h_state(nsys), h_it(nsys);
+    std::vector<double> h_rel(nsys);
+    for (long long t0 = 0; t0 < ntasks; t0 += nsys) {
+      const int nb = (int)std::min<long long>(nsys, ntasks - t0);
+      // pad a short last batch by repeating its last task (results of the padding are dropped)
+      for (int s = 0; s < nsys; s++) {
+        const long long t = t0 + std::min(s, nb - 1);
+        h_tw[s] = (int)(t / n_orb);
+        h_ta[s] = (int)(t % n_orb);
+      }
+      GFCC_CUDA(cudaMemcpyAsync(d_tw, h_tw.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+      GFCC_CUDA(cudaMemcpyAsync(d_ta, h_ta.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+      gather_omega_kernel<<<cdiv(nsys, 128), 128, 0, st>>>(d_om, d_tw, nsys, gm.omega);
+      GFCC_LAUNCH_CHECK();
+      gather_orb_kernel<<<cdiv(nsys, 128), 128, 0, st>>>(d_orb, d_ta, nsys, d_porb);
+      GFCC_LAUNCH_CHECK();
+      if (ip) {
+        rhs_ip_kernel<<<grid1d(n * nsys), 256, 0, st>>>(gm.B, n, nsys, d_porb, c->o, c->v, c->t1, c->t2);
+      } else {
+        rhs_ea_kernel<<<grid1d(n * nsys), 256, 0, st>>>(gm.B, n, nsys, d_porb, c->o, c->v, c->Pv, c->t1, c->t2);
+      }
+      GFCC_LAUNCH_CHECK();
+      GFCC_TRY(gm.solve(tol, c->max_iters, h_state.data()));
+      // overlaps: part[z][(s,t)][q] = sum_{mu in chunk z} x_s[mu] C[q][mu]
+      Contract k;
+      k.A = gm.U; k.am = imap2(2, 1, 2 * n); k.ak = imap1(2);
+      k.B = Cl; k.bk = imap1(1); k.bn = imap1(n);
+      k.C = part; k.cm = imap1(n_orb); k.cn = imap1(1);
+      k.M = 2LL * nsys; k.N = n_orb; k.K = n;
+      k.nsplit = nsplit; k.kchunk = 8192; k.scz = 2LL * nsys * n_orb;
+      GFCC_TRY(contract_f64(k, st));
+      overlap_scatter_kernel<<<grid1d((long long)nb * n_orb), 256, 0, st>>>(part, (int)nsplit, nb, n_orb, d_tw, d_ta,
+                                                                             ip ? 1 : 0, d_G);
+      GFCC_LAUNCH_CHECK();
+      GFCC_CUDA(cudaMemcpyAsync(h_it.data(), gm.iters, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
+      GFCC_CUDA(cudaMemcpyAsync(h_rel.data(), gm.relres, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
+      GFCC_CUDA(cudaMemcpyAsync(h_state.data(), gm.state, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
+      GFCC_CUDA(cudaStreamSynchronize(st));
+      for (int s = 0; s < nb; s++) {
+        const long long idx = sec_slot * ntasks + t0 + s;
+        c->st_iters[idx] = h_it[s];
+        c->st_relres[idx] = h_rel[s];
+        c->st_status[idx] = h_state[s] == 3 ? GFCC_STATUS_CONVERGED : GFCC_STATUS_NOT_CONVERGED;
+        all_ok &= h_state[s] == 3;
+      }
+    }
+    sec_slot++;
+  }
+  return all_ok ? GFCC_OK : GFCC_WARN_NOT_CONVERGED;
+}
+
+int check_solve_args(gfcc_ctx *c, int n_omega, double eta, int n_orb, double tol) {
+  if (c == nullptr) {
+    set_error("gfcc_solve: ctx is NULL");
+    return GFCC_ERR_ARG;
+  }
+  if (n_omega < 0 || n_orb < 0 || !(eta > 0.0) || !(tol > 0.0)) {
+    set_error("gfcc_solve: need n_omega >= 0, n_orb >= 0, eta > 0, tol > 0");
+    return GFCC_ERR_ARG;
+  }
+  return GFCC_OK;
+}
+
+}  // namespace
+}  // namespace gfcc
+
+using namespace gfcc;
+
+extern "C" {
+
+int gfcc_create(int o, int v, int L, const double *fock, const double *chol, const double *t1, const double *t2,
+                const double *lambda, gfcc_ctx **out) {
+  return create_impl(o, v, L, fock, chol, t1, t2, lambda, GFCC_SECTOR_BOTH, GFCC_PREC_FP64, out);
+}
+
+int gfcc_create_ex(int o, int v, int L, const double *fock, const double *chol, const double *t1, const double *t2,
+                   const double *lambda, int sectors, int precision, gfcc_ctx **out) {
+  return create_impl(o, v, L, fock, chol, t1, t2, lambda, sectors, precision, out);
+}
+
+int gfcc_set_option(gfcc_ctx *c, int key, double value) {
+  if (c == nullptr) {
+    set_error("gfcc_set_option: ctx is NULL");
+    return GFCC_ERR_ARG;
+  }
+  const int iv = (int)value;
+  switch (key) {
+    case GFCC_OPT_SECTOR:
+      if (iv < 1 || iv > 3 || (iv & ~c->sectors)) {
+        set_error("gfcc_set_option: sector %d not built in this context", iv);
+        return GFCC_ERR_ARG;
+      }
+      c->sectors = iv;
+      return GFCC_OK;
+    case GFCC_OPT_PRECISION:
+      if (iv != GFCC_PREC_FP64 && iv != GFCC_PREC_MIXED_BF16) break;
+      c->precision = iv;
+      return GFCC_OK;
+    case GFCC_OPT_RESTART:
+      if (iv < 1 || iv > 64) break;
+      c->restart = iv;
+      return GFCC_OK;
+    case GFCC_OPT_MAX_ITERS:
+      if (iv < 1) break;
+      c->max_iters = iv;
+      return GFCC_OK;
+    case GFCC_OPT_PRECOND:
+      if (iv != GFCC_PRECOND_NONE && iv != GFCC_PRECOND_DIAG) break;
+      c->precond = iv;
+      return GFCC_OK;
+    case GFCC_OPT_BATCH:
+      if (iv < 0 || iv > 4096) break;
+      c->batch = iv;
+      return GFCC_OK;
+    case GFCC_OPT_INNER_TOL:
+      if (!(value > 0.0 && value < 1.0)) break;
+      c->inner_tol = value;
+      return GFCC_OK;
+    default:
+      set_error("gfcc_set_option: unknown key %d", key);
+      return GFCC_ERR_ARG;
+  }
+  set_error("gfcc_set_option: value %g out of range for key %d", value, key);
+  return GFCC_ERR_ARG;
+}
+
+int gfcc_set_stream(gfcc_ctx *c, void *stream) {
+  if (c == nullptr) {
+    set_error("gfcc_set_stream: ctx is NULL");
+    return GFCC_ERR_ARG;
+  }
+  c->stream = stream ? static_cast<cudaStream_t>(stream) : c->own_stream;
+  return GFCC_OK;
+}
+
+int gfcc_solve_device(gfcc_ctx *c, int n_omega, const double *omegas_dev, double eta, int n_orb,
+                      const int *orbitals_dev, double tol, double *G_dev) {
+  GFCC_TRY(check_solve_args(c, n_omega, eta, n_orb, tol));
+  if (n_omega == 0 || n_orb == 0) return GFCC_OK;
+  // orbital range check on a host copy
+  std::vector<int> h_orb(n_orb);
+  GFCC_CUDA(cudaMemcpyAsync(h_orb.data(), orbitals_dev, sizeof(int) * n_orb, cudaMemcpyDeviceToHost, c->stream));
+  GFCC_CUDA(cudaStreamSynchronize(c->stream));
+  for (int x : h_orb)
+    if (x < 0 || x >= c->n) {
+      set_error("gfcc_solve: orbital index %d out of range [0, %d)", x, c->n);
+      return GFCC_ERR_ARG;
+    }
+  return solve_impl(c, n_omega, omegas_dev, eta, n_orb, orbitals_dev, h_orb.data(), tol, G_dev);
+}
+
+int gfcc_solve(gfcc_ctx *c, int n_omega, const double *omegas, double eta, int n_orb, const int *orbitals, double tol,
+               double *G) {
+  GFCC_TRY(check_solve_args(c, n_omega, eta, n_orb, tol));
+  if (n_omega == 0 || n_orb == 0) return GFCC_OK;
+  if (omegas == nullptr || orbitals == nullptr || G == nullptr) {
+    set_error("gfcc_solve: NULL omegas, orbitals or G");
+    return GFCC_ERR_ARG;
+  }
+  for (int a = 0; a < n_orb; a++)
+    if (orbitals[a] < 0 || orbitals[a] >= c->n) {
+      set_error("gfcc_solve: orbital index %d out of range [0, %d)", orbitals[a], c->n);
+      return GFCC_ERR_ARG;
+    }
+  for (int w = 0; w < n_omega; w++)
+    if (!std::isfinite(omegas[w])) {
+      set_error("gfcc_solve: omega[%d] is not finite", w);
+      return GFCC_ERR_ARG;
+    }
+  double *d_om = nullptr, *d_G = nullptr;
+  int *d_orb = nullptr;
+  const size_t gbytes = sizeof(double) * 2 * (size_t)n_omega * n_orb * n_orb;
+  if (dmalloc((void **)&d_om, sizeof(double) * n_omega) != cudaSuccess ||
+      dmalloc((void **)&d_orb, sizeof(int) * n_orb) != cudaSuccess || dmalloc((void **)&d_G, gbytes) != cudaSuccess) {
+    cudaGetLastError();
+    dfree(d_om);
+    dfree(d_orb);
+    dfree(d_G);
+    set_error("gfcc_solve: cannot allocate the frequency / orbital / G buffers");
+    return GFCC_ERR_OOM;
+  }
+  int s = GFCC_OK;
+  if (cudaMemcpyAsync(d_om, omegas, sizeof(double) * n_omega, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(d_orb, orbitals, sizeof(int) * n_orb, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+    set_error("gfcc_solve: host-to-device copy failed");
+    s = GFCC_ERR_CUDA;
+  }
+  if (s == GFCC_OK) s = solve_impl(c, n_omega, d_om, eta, n_orb, d_orb, orbitals, tol, d_G);
+  if (s >= 0) {
+    if (cudaMemcpyAsync(G, d_G, gbytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      set_error("gfcc_solve: device-to-host copy of G failed");
+      s = GFCC_ERR_CUDA;
+    }
+  }
+  dfree(d_om);
+  dfree(d_orb);
+  dfree(d_G);
+  return s;
+}
+
+int gfcc_last_stats(gfcc_ctx *c, int *count, int *iters, double *relres, int *status) {
+  if (c == nullptr || count == nullptr) {
+    set_error("gfcc_last_stats: NULL argument");
+    return GFCC_ERR_ARG;
+  }
+  const int total = (int)c->st_iters.size();
+  const int cap = *count;
+  const int nout = std::min(cap, total);
+  for (int i = 0; i < nout; i++) {
+    if (iters) iters[i] = c->st_iters[i];
+    if (relres) relres[i] = c->st_relres[i];
+    if (status) status[i] = c->st_status[i];
+  }
+  *count = total;
+  return GFCC_OK;
+}
+
+int gfcc_sigma(gfcc_ctx *c, int sector, int n_vec, const double *x, double *y) {
+  if (c == nullptr || x == nullptr || y == nullptr || n_vec < 0 ||
+      (sector != GFCC_SECTOR_IP && sector != GFCC_SECTOR_EA) || !(c->sectors & sector)) {
+    set_error("gfcc_sigma: bad arguments or sector not built");
+    return GFCC_ERR_ARG;
+  }
+  if (n_vec == 0) return GFCC_OK;
+  const long long n = sector == GFCC_SECTOR_IP ? c->dim_ip : c->dim_ea;
+  const long long work = sigma_work_doubles(c, sector, n_vec) + 4LL * n_vec * n;
+  GFCC_TRY(grow_scratch(c, sizeof(double) * work));
+  double *dx = static_cast<double *>(c->scratch);
+  double *dy = dx + 2LL * n_vec * n;
+  double *w = dy + 2LL * n_vec * n;
+  GFCC_CUDA(cudaMemcpyAsync(dx, x, sizeof(double) * 2 * n_vec * n, cudaMemcpyHostToDevice, c->stream));
+  SysBatch b;
+  b.nsys = n_vec;
+  b.x = dx; b.ldx = n;
+  b.y = dy; b.ldy = n;
+  GFCC_TRY(sector == GFCC_SECTOR_IP ? apply_ip(c, b, w) : apply_ea(c, b, w));
+  GFCC_CUDA(cudaMemcpyAsync(y, dy, sizeof(double) * 2 * n_vec * n, cudaMemcpyDeviceToHost, c->stream));
+  GFCC_CUDA(cudaStreamSynchronize(c->stream));
+  return GFCC_OK;
+}
+
+int gfcc_dims(gfcc_ctx *c, long long *dim_ip, long long *dim_ea) {
+  if (c == nullptr) {
+    set_error("gfcc_dims: ctx is NULL");
+    return GFCC_ERR_ARG;
+  }
+  if (dim_ip) *dim_ip = c->dim_ip;
+  if (dim_ea) *dim_ea = c->dim_ea;
+  return GFCC_OK;
+}
+
+void gfcc_destroy(gfcc_ctx *c) {
+  if (c == nullptr) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (void *p : c->allocs) dfree(p);
+  if (c->scratch) dfree(c->scratch);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete c;
+}
+
+const char *gfcc_last_error(void) { return g_err; }
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Shared device/host helpers of libgfcc (error propagation, index maps, launch helpers).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "../../include/gfcc.h"
+
+namespace gfcc {
+
+void set_error(const char *fmt, ...);
+
+// Registry of device allocations made by the library.  Every contraction / permutation
+// launch checks on the host that the address range its index maps can reach lies inside
+// one registered allocation, so a wrong map becomes an error return, not a device fault.
+void reg_alloc(const void *p, size_t bytes);
+void unreg_alloc(const void *p);
+// 0 if [p + lo*8, p + hi*8 + 8) lies inside a registered allocation, else GFCC_ERR_ARG (with message)
+int check_extent(const double *p, long long lo, long long hi, const char *what);
+cudaError_t dmalloc(void **p, size_t bytes);   // cudaMalloc + reg_alloc
+void dfree(void *p);                           // unreg_alloc + cudaFree
+
+// Evaluate a CUDA runtime call; on failure record the message and return GFCC_ERR_CUDA.
+#define GFCC_CUDA(call)                                                                 \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      ::gfcc::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+      return GFCC_ERR_CUDA;                                                             \
+    }                                                                                   \
+  } while (0)
+
+// Propagate a non-zero gfcc status.
+#define GFCC_TRY(expr)          \
+  do {                          \
+    int s_ = (expr);            \
+    if (s_ < 0) return s_;      \
+  } while (0)
+
+// Check the last kernel launch.
+#define GFCC_LAUNCH_CHECK() GFCC_CUDA(cudaGetLastError())
+
+// Index map of a flattened GEMM index x onto a tensor offset:
+//   d0 <= 0 : x * s0
+//   d0  > 0 : (x % d0) * s0 + (x / d0) * s1      (two tensor indices fused into one GEMM index)
+struct IMap {
+  long long d0, s0, s1;
+};
+static inline IMap imap1(long long s0) { return IMap{0, s0, 0}; }
+static inline IMap imap2(long long d0, long long s0, long long s1) { return IMap{d0, s0, s1}; }
+
+// Largest offset an IMap produces for x in [0, X) (all strides are non-negative).
+static inline long long imap_max(const IMap &m, long long X) {
+  if (X <= 0) return 0;
+  if (m.d0 <= 0) return (X - 1) * m.s0;
+  const long long r = (X < m.d0 ? X : m.d0) - 1;
+  return r * m.s0 + ((X - 1) / m.d0) * m.s1;
+}
+
+__device__ __forceinline__ long long imap_apply(const IMap &m, long long x) {
+  if (m.d0 <= 0) return x * m.s0;
+  long long q = x / m.d0;
+  return (x - q * m.d0) * m.s0 + q * m.s1;
+}
+
+// Pairs i < j < m in lexicographic order: index = pair_start(i) + (j - i - 1).
+__host__ __device__ __forceinline__ long long pair_start(long long i, long long m) { return i * m - i * (i + 1) / 2; }
+__host__ __device__ __forceinline__ long long pair_index(long long i, long long j, long long m) {
+  return pair_start(i, m) + (j - i - 1);
+}
+// Inverse of pair_index (closed form from the quadratic, then an exact integer correction).
+__device__ __forceinline__ void pair_decode(long long idx, long long m, long long &i, long long &j) {
+  const double b = 2.0 * (double)m - 1.0;
+  long long ii = (long long)((b - sqrt(fmax(b * b - 8.0 * (double)idx, 0.0))) * 0.5);
+  if (ii < 0) ii = 0;
+  if (ii > m - 2) ii = m - 2;
+  while (ii > 0 && pair_start(ii, m) > idx) ii--;
+  while (ii + 1 <= m - 2 && pair_start(ii + 1, m) <= idx) ii++;
+  i = ii;
+  j = idx - pair_start(ii, m) + ii + 1;
+}
+
+static inline unsigned int cdiv(long long a, long long b) { return (unsigned int)((a + b - 1) / b); }
+
+// Grid-stride 1-D launch size for `n` elements (capped to keep the grid modest).
+static inline unsigned int grid1d(long long n, int threads = 256) {
+  long long b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 152LL * 64) b = 152LL * 64;
+  return (unsigned int)b;
+}
+
+}  // namespace gfcc

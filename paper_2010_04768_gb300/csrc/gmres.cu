@@ -1,0 +1,479 @@
+// Batched restarted GMRES (Saad & Schultz 1986) for the GFCCSD linear systems, FP64.
+//
+// GFCC Workflow and Bottlenecks section: the systems (omega - i eta + Hbar_N) X = b
+// are solved by GMRES, whose residual norm decreases monotonically; its cost grows
+// as O(n^2 O^2 V) in the iteration count n, which is the Arnoldi work here.
+//
+// All systems of a batch advance in lock step through the Arnoldi steps of a
+// restart cycle.  Orthogonalisation is classical Gram-Schmidt applied twice
+// (CGS2): both passes are batched dot products / vector updates that stream the
+// Krylov basis once each, which suits HBM better than the sequential modified
+// Gram-Schmidt of the oracle and is as stable.  The (m+1) x m Hessenberg matrix
+// of each system is reduced by complex Givens rotations on the device, one thread
+// per system; a system leaves its cycle when the rotated residual estimate
+// reaches tol ||b|| (or on breakdown), and every cycle ends with the true
+// residual b - A x recomputed by the operator.
+#include <algorithm>
+#include <vector>
+
+#include "ctx.cuh"
+#include "gmres.cuh"
+#include "kernels.cuh"
+#include "sigma.cuh"
+
+namespace gfcc {
+
+namespace {
+
+constexpr int ST_PENDING = 0, ST_IN_CYCLE = 1, ST_CYCLE_DONE = 2, ST_CONVERGED = 3, ST_FAILED = 4;
+constexpr int DOT_THREADS = 256, DOT_PER_THREAD = 8, DOT_CHUNK = DOT_THREADS * DOT_PER_THREAD;
+
+__device__ __forceinline__ double2 ld2(const double *p, long long i) { return reinterpret_cast<const double2 *>(p)[i]; }
+__device__ __forceinline__ void st2(double *p, long long i, double2 v) { reinterpret_cast<double2 *>(p)[i] = v; }
+
+// Block-wide sum of a complex value; result valid in thread 0.
+__device__ __forceinline__ double2 block_sum(double2 v, double2 *sh) {
+  for (int off = 16; off > 0; off >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, off);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? sh[lane] : make_double2(0.0, 0.0);
+    for (int off = 16; off > 0; off >>= 1) {
+      v.x += __shfl_down_sync(0xffffffffu, v.x, off);
+      v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+    }
+  }
+  return v;
+}
+
+// partial[(s*NV + i)*nch + chunk] = sum_{mu in chunk} conj(Vs_i[mu]) w_s[mu]   (systems with state == want)
+__global__ __launch_bounds__(DOT_THREADS) void mdot_partial_kernel(const double *V, long long vs_stride,
+                                                                   long long vi_stride, int nv, const double *w,
+                                                                   long long ws_stride, long long n, int nch,
+                                                                   const int *state, int want, double *partial,
+                                                                   int NV) {
+  __shared__ double2 sh[32];
+  const int s = blockIdx.y, chunk = blockIdx.x;
+  if (state != nullptr && state[s] != want) return;
+  const long long base = (long long)chunk * DOT_CHUNK;
+  double2 wv[DOT_PER_THREAD];
+  const double *ws = w + 2 * s * ws_stride;
+#pragma unroll
+  for (int r = 0; r < DOT_PER_THREAD; r++) {
+    const long long mu = base + threadIdx.x + (long long)r * DOT_THREADS;
+    wv[r] = mu < n ? ld2(ws, mu) : make_double2(0.0, 0.0);
+  }
+  for (int i = 0; i < nv; i++) {
+    const double *vi = V + 2 * (s * vs_stride + i * vi_stride);
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int r = 0; r < DOT_PER_THREAD; r++) {
+      const long long mu = base + threadIdx.x + (long long)r * DOT_THREADS;
+      if (mu < n) {
+        const double2 a = ld2(vi, mu);
+        acc.x += a.x * wv[r].x + a.y * wv[r].y;
+        acc.y += a.x * wv[r].y - a.y * wv[r].x;
+      }
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) reinterpret_cast<double2 *>(partial)[((long long)s * NV + i) * nch + chunk] = acc;
+  }
+}
+
+// out[s*NV + i] (+)= sum_chunk partial  (one warp per (s, i))
+__global__ void mdot_final_kernel(const double *partial, int nsys, int nv, int NV, int nch, const int *state,
+                                  int want, double *out, int accumulate) {
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (gw >= nsys * nv) return;
+  const int s = gw / nv, i = gw % nv;
+  if (state != nullptr && state[s] != want) return;
+  double2 acc = make_double2(0.0, 0.0);
+  const double2 *p = reinterpret_cast<const double2 *>(partial) + ((long long)s * NV + i) * nch;
+  for (int c = lane; c < nch; c += 32) {
+    acc.x += p[c].x;
+    acc.y += p[c].y;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
+    acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
+  }
+  if (lane == 0) {
+    double2 *o = reinterpret_cast<double2 *>(out) + (long long)s * NV + i;
+    if (accumulate) {
+      o->x += acc.x;
+      o->y += acc.y;
+    } else {
+      *o = acc;
+    }
+  }
+}
+
+// w_s[mu] += sign * sum_{i<nv_s} coef[s*NV + i] Vs_i[mu]   (systems with state == want;
+// nv_s = nvs[s] when nvs != nullptr, else nv)
+__global__ void vupdate_kernel(const double *V, long long vs_stride, long long vi_stride, int nv, const int *nvs,
+                               const double *coef, int NV, double sign, double *w, long long ws_stride, long long n,
+                               int nsys, const int *state, int want) {
+  const long long tot = n * nsys;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(t / n);
+    const long long mu = t - (long long)s * n;
+    if (state != nullptr && state[s] != want) continue;
+    double2 acc = make_double2(0.0, 0.0);
+    const double2 *cf = reinterpret_cast<const double2 *>(coef) + (long long)s * NV;
+    const int nvv = nvs != nullptr ? nvs[s] : nv;
+    for (int i = 0; i < nvv; i++) {
+      const double2 a = ld2(V + 2 * (s * vs_stride + i * vi_stride), mu);
+      const double2 c = cf[i];
+      acc.x += c.x * a.x - c.y * a.y;
+      acc.y += c.x * a.y + c.y * a.x;
+    }
+    double2 x = ld2(w + 2 * s * ws_stride, mu);
+    x.x += sign * acc.x;
+    x.y += sign * acc.y;
+    st2(w + 2 * s * ws_stride, mu, x);
+  }
+}
+
+// w_s *= 1 / scale[s] (real scale stored as the real part of a complex entry scale[s*NV + idx])
+__global__ void vscale_kernel(double *w, long long ws_stride, long long n, int nsys, const double *nrm2, int NV,
+                              int idx, const int *state, int want) {
+  const long long tot = n * nsys;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(t / n);
+    const long long mu = t - (long long)s * n;
+    if (state != nullptr && state[s] != want) continue;
+    const double nn = nrm2[2 * ((long long)s * NV + idx)];
+    if (!(nn > 0.0)) continue;
+    const double inv = 1.0 / sqrt(nn);
+    double2 x = ld2(w + 2 * s * ws_stride, mu);
+    x.x *= inv;
+    x.y *= inv;
+    st2(w + 2 * s * ws_stride, mu, x);
+  }
+}
+
+// r_s = b_s - w_s for systems that are not finished
+__global__ void resid_form_kernel(const double *B, const double *W, double *R, long long r_stride, long long n,
+                                  int nsys, const int *state) {
+  const long long tot = n * nsys;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(t / n);
+    const long long mu = t - (long long)s * n;
+    if (state[s] != ST_PENDING) continue;
+    const double2 b = ld2(B, t), w = ld2(W, t);
+    st2(R + 2 * s * r_stride, mu, make_double2(b.x - w.x, b.y - w.y));
+  }
+}
+
+// Decide per system after the true residual: converged, failed (budget) or start a new cycle.
+__global__ void cycle_start_kernel(int nsys, const double *nrm2, int NV, const double *bnorm, double tol, int max_iters,
+                                   int m1, int *state, int *iters, double *relres, double *g, double *H) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys || state[s] != ST_PENDING) return;
+  const double beta = sqrt(fmax(nrm2[2 * ((long long)s * NV)], 0.0));
+  const double bn = bnorm[s];
+  relres[s] = bn > 0.0 ? beta / bn : 0.0;
+  if (bn == 0.0 || beta <= tol * bn) {
+    state[s] = ST_CONVERGED;
+    return;
+  }
+  if (iters[s] >= max_iters) {
+    state[s] = ST_FAILED;
+    return;
+  }
+  double2 *gs = reinterpret_cast<double2 *>(g) + (long long)s * m1;
+  for (int i = 0; i < m1; i++) gs[i] = make_double2(0.0, 0.0);
+  gs[0] = make_double2(beta, 0.0);
+  (void)H;
+  state[s] = ST_IN_CYCLE;
+}
+
+// Givens update of column k for systems in cycle.
+//   h[s*NV + i], i <= k: Gram-Schmidt coefficients (pass 1 + pass 2); h[s*NV + k+1]: ||w||^2 (real part)
+__global__ void givens_kernel(int nsys, int k, int m, const double *h, int NV, double *H, double *cs, double *sn,
+                              double *g, const double *bnorm, double tol, int *state, int *kcyc, int *iters,
+                              double *est) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys || state[s] != ST_IN_CYCLE) return;
+  const double2 *hs = reinterpret_cast<const double2 *>(h) + (long long)s * NV;
+  double2 *Hs = reinterpret_cast<double2 *>(H) + (long long)s * (m + 1) * m;   // column-major [col][row], ld m+1
+  double2 *css = reinterpret_cast<double2 *>(cs) + (long long)s * m;
+  double2 *sns = reinterpret_cast<double2 *>(sn) + (long long)s * m;
+  double2 *gs = reinterpret_cast<double2 *>(g) + (long long)s * (m + 1);
+  double2 col[65];
+  for (int i = 0; i <= k; i++) col[i] = hs[i];
+  const double hk1 = sqrt(fmax(hs[k + 1].x, 0.0));
+  col[k + 1] = make_double2(hk1, 0.0);
+  for (int i = 0; i < k; i++) {   // previous rotations: [c, s; -conj(s), conj(c)]
+    const double2 c = css[i], sv = sns[i], a = col[i], b = col[i + 1];
+    const double2 t = make_double2(c.x * a.x - c.y * a.y + sv.x * b.x - sv.y * b.y,
+                                   c.x * a.y + c.y * a.x + sv.x * b.y + sv.y * b.x);
+    const double2 u = make_double2(-(sv.x * a.x + sv.y * a.y) + (c.x * b.x + c.y * b.y),
+                                   -(sv.x * a.y - sv.y * a.x) + (c.x * b.y - c.y * b.x));
+    col[i] = t;
+    col[i + 1] = u;
+  }
+  const double2 a = col[k], b = col[k + 1];
+  const double den = sqrt(a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y);
+  double2 c, sv;
+  if (den > 0.0) {
+    c = make_double2(a.x / den, -a.y / den);    // conj(a) / den
+    sv = make_double2(b.x / den, -b.y / den);   // conj(b) / den
+  } else {
+    c = make_double2(1.0, 0.0);
+    sv = make_double2(0.0, 0.0);
+  }
+  css[k] = c;
+  sns[k] = sv;
+  col[k] = make_double2(den, 0.0);
+  col[k + 1] = make_double2(0.0, 0.0);
+  const double2 gk = gs[k];
+  gs[k + 1] = make_double2(-(sv.x * gk.x + sv.y * gk.y), -(sv.x * gk.y - sv.y * gk.x));   // -conj(s) g_k
+  gs[k] = make_double2(c.x * gk.x - c.y * gk.y, c.x * gk.y + c.y * gk.x);                  // c g_k
+  for (int i = 0; i <= k; i++) Hs[(long long)k * (m + 1) + i] = col[i];
+  iters[s] += 1;
+  const double res = sqrt(gs[k + 1].x * gs[k + 1].x + gs[k + 1].y * gs[k + 1].y);
+  est[s] = bnorm[s] > 0.0 ? res / bnorm[s] : 0.0;
+  const bool breakdown = !(hk1 > 1e-14 * den);
+  if (res <= tol * bnorm[s] || breakdown || k + 1 == m || den == 0.0) {
+    state[s] = ST_CYCLE_DONE;
+    kcyc[s] = k + 1;
+  }
+}
+
+// y = R^-1 g (back substitution on the rotated Hessenberg), stored in y[s*NV + i]
+__global__ void backsolve_kernel(int nsys, int m, const double *H, const double *g, const int *state, const int *kcyc,
+                                 double *y, int NV) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys || state[s] != ST_CYCLE_DONE) return;
+  const double2 *Hs = reinterpret_cast<const double2 *>(H) + (long long)s * (m + 1) * m;
+  const double2 *gs = reinterpret_cast<const double2 *>(g) + (long long)s * (m + 1);
+  double2 *ys = reinterpret_cast<double2 *>(y) + (long long)s * NV;
+  const int k = kcyc[s];
+  for (int i = k - 1; i >= 0; i--) {
+    double2 acc = gs[i];
+    for (int j = i + 1; j < k; j++) {
+      const double2 r = Hs[(long long)j * (m + 1) + i], yj = ys[j];
+      acc.x -= r.x * yj.x - r.y * yj.y;
+      acc.y -= r.x * yj.y + r.y * yj.x;
+    }
+    const double2 d = Hs[(long long)i * (m + 1) + i];
+    const double dd = d.x * d.x + d.y * d.y;
+    ys[i] = dd > 0.0 ? make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd)
+                     : make_double2(0.0, 0.0);
+  }
+  for (int i = k; i < NV; i++) ys[i] = make_double2(0.0, 0.0);
+}
+
+__global__ void coef_add_kernel(int nsys, int nv, double *h, const double *h2, int NV, const int *state, int want) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)nsys * nv) return;
+  const int s = (int)(t / nv), i = (int)(t % nv);
+  if (state[s] != want) return;
+  const long long q = 2 * ((long long)s * NV + i);
+  h[q] += h2[q];
+  h[q + 1] += h2[q + 1];
+}
+
+__global__ void set_state_kernel(int nsys, int *state, int from, int to) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < nsys && state[s] == from) state[s] = to;
+}
+
+// x_s = u_s / D_s (final solution from the preconditioned iterate)
+__global__ void unprecondition_kernel(double *U, long long n, int nsys, const double *omega, double eta, double zsign,
+                                      const double *diag, double dsign) {
+  const long long tot = n * nsys;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(t / n);
+    const long long mu = t - (long long)s * n;
+    const double dr = omega[s] + dsign * diag[mu], di = zsign * eta;
+    const double d2 = dr * dr + di * di;
+    const double2 u = ld2(U, t);
+    st2(U, t, make_double2((u.x * dr + u.y * di) / d2, (u.y * dr - u.x * di) / d2));
+  }
+}
+
+__global__ void norm_from_partial_kernel(int nsys, const double *nrm2, int NV, double *out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < nsys) out[s] = sqrt(fmax(nrm2[2 * (long long)s * NV], 0.0));
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------
+
+long long gmres_work_doubles(const gfcc_ctx *c, int sector, long long n, int nsys, int m) {
+  const long long NV = m + 2;
+  const long long nch = (n + DOT_CHUNK - 1) / DOT_CHUNK;
+  long long w = 0;
+  w += 2LL * nsys * (m + 1) * n;            // V
+  w += 3 * 2LL * nsys * n;                  // U, B, W
+  w += 2LL * nsys * NV * nch;               // dot partials
+  w += 2LL * nsys * NV * 4;                 // h, h2, y, nrm
+  w += 2LL * nsys * (m + 1) * m;            // H
+  w += 2LL * nsys * (2 * m + (m + 1));      // cs, sn, g
+  w += 7LL * nsys + 512;                    // bnorm, relres, est, omega, int state/kcyc/iters, alignment
+  w += sigma_work_doubles(c, sector, nsys);
+  return w;
+}
+
+int Gmres::init(gfcc_ctx *ctx, int sec, long long dim, int ns, int mm, double *work) {
+  c = ctx;
+  sector = sec;
+  n = dim;
+  nsys = ns;
+  m = mm;
+  NV = m + 2;
+  nch = (int)((n + DOT_CHUNK - 1) / DOT_CHUNK);
+  double *p = work;
+  auto take = [&](double *&dst, long long cnt) {
+    dst = p;
+    p += (cnt + 7) & ~7LL;
+  };
+  take(V, 2LL * nsys * (m + 1) * n);
+  take(U, 2LL * nsys * n);
+  take(B, 2LL * nsys * n);
+  take(W, 2LL * nsys * n);
+  take(partial, 2LL * nsys * NV * nch);
+  take(h, 2LL * nsys * NV);
+  take(h2, 2LL * nsys * NV);
+  take(y, 2LL * nsys * NV);
+  take(nrm, 2LL * nsys * NV);
+  take(H, 2LL * nsys * (m + 1) * m);
+  take(cs, 2LL * nsys * m);
+  take(sn, 2LL * nsys * m);
+  take(g, 2LL * nsys * (m + 1));
+  take(bnorm, nsys);
+  take(relres, nsys);
+  take(est, nsys);
+  take(omega, nsys);
+  double *ip;
+  take(ip, 3LL * nsys);
+  state = reinterpret_cast<int *>(ip);
+  kcyc = state + nsys;
+  iters = kcyc + nsys;
+  sigma_work = p;
+  const long long used = (p - work) + sigma_work_doubles(c, sector, nsys);
+  if (used > gmres_work_doubles(c, sector, n, nsys, m)) {
+    set_error("internal: GMRES workspace layout (%lld doubles) exceeds its size", used);
+    return GFCC_ERR_ARG;
+  }
+  return GFCC_OK;
+}
+
+int Gmres::op(const double *x, long long ldx, double *yout, long long ldy) {
+  SysBatch b;
+  b.nsys = nsys;
+  b.x = x;
+  b.ldx = ldx;
+  b.y = yout;
+  b.ldy = ldy;
+  b.omega = omega;
+  b.eta = eta;
+  b.diag = use_precond ? (sector == GFCC_SECTOR_IP ? c->diag_ip : c->diag_ea) : nullptr;
+  b.dsign = sector == GFCC_SECTOR_IP ? 1.0 : -1.0;
+  b.zsign = sector == GFCC_SECTOR_IP ? -1.0 : 1.0;
+  return sector == GFCC_SECTOR_IP ? apply_ip(c, b, sigma_work) : apply_ea(c, b, sigma_work);
+}
+
+// dots of vectors [0, nv) of each system's basis (V + s*vs + i*vi) with w (w + s*ws) -> out
+int Gmres::mdot(const double *Vb, long long vs, long long vi, int nv, const double *w, long long ws, double *out,
+                int want, int accumulate) {
+  cudaStream_t st = c->stream;
+  dim3 grid(nch, nsys);
+  mdot_partial_kernel<<<grid, DOT_THREADS, 0, st>>>(Vb, vs, vi, nv, w, ws, n, nch, state, want, partial, NV);
+  GFCC_LAUNCH_CHECK();
+  const int warps = nsys * nv;
+  mdot_final_kernel<<<cdiv(warps * 32LL, 256), 256, 0, st>>>(partial, nsys, nv, NV, nch, state, want, out, accumulate);
+  GFCC_LAUNCH_CHECK();
+  return GFCC_OK;
+}
+
+int Gmres::solve(double tol, int max_iters, int *h_state) {
+  cudaStream_t st = c->stream;
+  const long long vs = (long long)(m + 1) * n;   // basis stride per system (complex elements)
+  const int T = 256;
+  GFCC_CUDA(cudaMemsetAsync(U, 0, sizeof(double) * 2 * nsys * n, st));
+  GFCC_CUDA(cudaMemsetAsync(V, 0, sizeof(double) * 2 * nsys * (m + 1) * n, st));
+  GFCC_CUDA(cudaMemsetAsync(iters, 0, sizeof(int) * nsys, st));
+  GFCC_CUDA(cudaMemsetAsync(state, 0, sizeof(int) * nsys, st));   // ST_PENDING
+  // ||b||
+  GFCC_TRY(mdot(B, n, 0, 1, B, n, nrm, ST_PENDING, 0));
+  norm_from_partial_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, nrm, NV, bnorm);
+  GFCC_LAUNCH_CHECK();
+  bool first = true;
+  for (int cycle = 0;; cycle++) {
+    // true residual r = b - A x into V_0 (x = 0 on the first cycle)
+    if (first) {
+      GFCC_CUDA(cudaMemsetAsync(W, 0, sizeof(double) * 2 * nsys * n, st));
+    } else {
+      GFCC_TRY(op(U, n, W, n));
+    }
+    resid_form_kernel<<<grid1d(n * nsys), T, 0, st>>>(B, W, V, vs, n, nsys, state);
+    GFCC_LAUNCH_CHECK();
+    GFCC_TRY(mdot(V, vs, 0, 1, V, vs, nrm, ST_PENDING, 0));
+    cycle_start_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, nrm, NV, bnorm, tol, max_iters, m + 1, state, iters, relres,
+                                                    g, H);
+    GFCC_LAUNCH_CHECK();
+    vscale_kernel<<<grid1d(n * nsys), T, 0, st>>>(V, vs, n, nsys, nrm, NV, 0, state, ST_IN_CYCLE);
+    GFCC_LAUNCH_CHECK();
+    first = false;
+    GFCC_CUDA(cudaMemcpyAsync(h_state, state, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
+    GFCC_CUDA(cudaStreamSynchronize(st));
+    bool any = false;
+    for (int s = 0; s < nsys; s++) any |= h_state[s] == ST_IN_CYCLE;
+    if (!any) break;
+    // Arnoldi steps
+    for (int k = 0; k < m; k++) {
+      double *vk = V + 2 * (long long)k * n;
+      double *w = V + 2 * (long long)(k + 1) * n;
+      GFCC_TRY(op(vk, vs, w, vs));
+      // CGS2: h = V^H w, w -= V h, h2 = V^H w, w -= V h2, h += h2, then ||w||^2 into h[k+1]
+      GFCC_TRY(mdot(V, vs, n, k + 1, w, vs, h, ST_IN_CYCLE, 0));
+      vupdate_kernel<<<grid1d(n * nsys), T, 0, st>>>(V, vs, n, k + 1, nullptr, h, NV, -1.0, w, vs, n, nsys, state,
+                                                      ST_IN_CYCLE);
+      GFCC_LAUNCH_CHECK();
+      GFCC_TRY(mdot(V, vs, n, k + 1, w, vs, h2, ST_IN_CYCLE, 0));
+      vupdate_kernel<<<grid1d(n * nsys), T, 0, st>>>(V, vs, n, k + 1, nullptr, h2, NV, -1.0, w, vs, n, nsys, state,
+                                                      ST_IN_CYCLE);
+      GFCC_LAUNCH_CHECK();
+      coef_add_kernel<<<cdiv((long long)nsys * (k + 1), T), T, 0, st>>>(nsys, k + 1, h, h2, NV, state, ST_IN_CYCLE);
+      GFCC_LAUNCH_CHECK();
+      GFCC_TRY(mdot(w, vs, 0, 1, w, vs, h + 2 * (k + 1), ST_IN_CYCLE, 0));
+      vscale_kernel<<<grid1d(n * nsys), T, 0, st>>>(w, vs, n, nsys, h, NV, k + 1, state, ST_IN_CYCLE);
+      GFCC_LAUNCH_CHECK();
+      givens_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, k, m, h, NV, H, cs, sn, g, bnorm, tol, state, kcyc, iters, est);
+      GFCC_LAUNCH_CHECK();
+      GFCC_CUDA(cudaMemcpyAsync(h_state, state, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
+      GFCC_CUDA(cudaStreamSynchronize(st));
+      bool in_cycle = false;
+      for (int s = 0; s < nsys; s++) in_cycle |= h_state[s] == ST_IN_CYCLE;
+      if (!in_cycle) break;
+    }
+    // x += V y
+    backsolve_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, m, H, g, state, kcyc, y, NV);
+    GFCC_LAUNCH_CHECK();
+    vupdate_kernel<<<grid1d(n * nsys), T, 0, st>>>(V, vs, n, m, kcyc, y, NV, 1.0, U, n, n, nsys, state,
+                                                    ST_CYCLE_DONE);
+    GFCC_LAUNCH_CHECK();
+    set_state_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, state, ST_CYCLE_DONE, ST_PENDING);
+    GFCC_LAUNCH_CHECK();
+  }
+  if (use_precond) {
+    unprecondition_kernel<<<grid1d(n * nsys), T, 0, st>>>(
+        U, n, nsys, omega, eta, sector == GFCC_SECTOR_IP ? -1.0 : 1.0,
+        sector == GFCC_SECTOR_IP ? c->diag_ip : c->diag_ea, sector == GFCC_SECTOR_IP ? 1.0 : -1.0);
+    GFCC_LAUNCH_CHECK();
+  }
+  return GFCC_OK;
+}
+
+}  // namespace gfcc

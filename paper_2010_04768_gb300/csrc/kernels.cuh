@@ -1,0 +1,32 @@
+// Declarations of the device-side building blocks of libgfcc.
+#pragma once
+#include "common.cuh"
+
+namespace gfcc {
+
+// ---------------------------------------------------------------- generic FP64 contraction
+struct Contract {
+  const double *A = nullptr;
+  const double *B = nullptr;
+  double *C = nullptr;
+  long long M = 0, N = 0, K = 0;
+  IMap am{0, 0, 0}, ak{0, 0, 0}, bk{0, 0, 0}, bn{0, 0, 0}, cm{0, 0, 0}, cn{0, 0, 0};
+  long long batch = 1, sab = 0, sbb = 0, scb = 0;
+  double alpha = 1.0, beta = 0.0;
+  // split-K: nsplit partial products over K ranges of kchunk, partial z written at C + z * scz
+  long long nsplit = 1, kchunk = 0, scz = 0;
+};
+int contract_f64(const Contract &c, cudaStream_t st);
+int gemm_f64(cudaStream_t st, long long M, long long N, long long K, double alpha,
+             const double *A, IMap am, IMap ak, const double *B, IMap bk, IMap bn, double beta,
+             double *C, IMap cm, IMap cn, long long batch = 1, long long sab = 0, long long sbb = 0,
+             long long scb = 0);
+
+// ---------------------------------------------------------------- elementwise helpers
+// For every index (i0, i1, i2, i3) < d:
+//   out[sum i_k * os[k]] = alpha * in[sum i_k * is[k]] + beta * out[sum i_k * os[k]]
+int permute4(cudaStream_t st, const long long d[4], const double *in, const long long is[4], double *out,
+             const long long os[4], double alpha, double beta);
+int fill_f64(cudaStream_t st, double *p, long long n, double value);
+
+}  // namespace gfcc

@@ -1,0 +1,163 @@
+"""ctypes binding of libgfcc.so (argument marshalling only; all arithmetic runs in the CUDA library).
+
+The names follow the C ABI of include/gfcc.h.  The library is loaded from the
+package's lib/ directory; if it is missing, every entry point raises instead of
+falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libgfcc.so")
+
+OK = 0
+WARN_NOT_CONVERGED = 1
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = -1, -2, -3, -4, -5
+
+SECTOR_IP, SECTOR_EA, SECTOR_BOTH = 1, 2, 3
+PREC_FP64, PREC_MIXED_BF16 = 0, 1
+PRECOND_NONE, PRECOND_DIAG = 0, 1
+OPT_SECTOR, OPT_PRECISION, OPT_RESTART, OPT_MAX_ITERS, OPT_PRECOND, OPT_BATCH, OPT_INNER_TOL = 1, 2, 3, 4, 5, 6, 7
+
+_SECTORS = {"IP": SECTOR_IP, "EA": SECTOR_EA, "IP+EA": SECTOR_BOTH, "BOTH": SECTOR_BOTH}
+_PRECS = {"fp64": PREC_FP64, "mixed": PREC_MIXED_BF16, "bf16": PREC_MIXED_BF16}
+
+_lib = None
+
+
+class GFCCError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libgfcc error {code}: {msg}")
+        self.code = code
+
+
+def load():
+    """Load libgfcc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2010_04768_gb300/build.py "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.gfcc_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, ctypes.POINTER(P)]
+    lib.gfcc_create_ex.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, ctypes.c_int,
+                                   ctypes.c_int, ctypes.POINTER(P)]
+    lib.gfcc_set_option.argtypes = [P, ctypes.c_int, ctypes.c_double]
+    lib.gfcc_set_stream.argtypes = [P, P]
+    lib.gfcc_solve.argtypes = [P, ctypes.c_int, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.c_double, dp]
+    lib.gfcc_solve_device.argtypes = [P, ctypes.c_int, P, ctypes.c_double, ctypes.c_int, P, ctypes.c_double, P]
+    lib.gfcc_last_stats.argtypes = [P, ip, ip, dp, ip]
+    lib.gfcc_sigma.argtypes = [P, ctypes.c_int, ctypes.c_int, dp, dp]
+    lib.gfcc_dims.argtypes = [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    lib.gfcc_destroy.argtypes = [P]
+    lib.gfcc_destroy.restype = None
+    lib.gfcc_last_error.restype = ctypes.c_char_p
+    for name in ("gfcc_create", "gfcc_create_ex", "gfcc_set_option", "gfcc_set_stream", "gfcc_solve",
+                 "gfcc_solve_device", "gfcc_last_stats", "gfcc_sigma", "gfcc_dims"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(code):
+    if code < 0:
+        raise GFCCError(code, load().gfcc_last_error().decode())
+    return code
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class GFCC:
+    """One gfcc_ctx: the problem on the device with its Hbar elements."""
+
+    def __init__(self, problem, sectors: str = "IP+EA", precision: str = "fp64"):
+        lib = load()
+        self.o, self.v, self.L = problem.o, problem.v, problem.L
+        fock, chol, t1, t2 = (_f64(x) for x in (problem.fock, problem.chol, problem.t1, problem.t2))
+        lam = None
+        if problem.lam1 is not None:
+            lam = np.concatenate([_f64(problem.lam1).reshape(-1), _f64(problem.lam2).reshape(-1)])
+        h = ctypes.c_void_p()
+        _check(lib.gfcc_create_ex(self.o, self.v, self.L, _dp(fock), _dp(chol), _dp(t1), _dp(t2),
+                                  None if lam is None else _dp(lam), _SECTORS[sectors], _PRECS[precision],
+                                  ctypes.byref(h)))
+        self._h = h
+        self.sectors = sectors
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().gfcc_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, key: int, value: float):
+        _check(load().gfcc_set_option(self._h, key, float(value)))
+
+    def set_stream(self, stream_handle: int | None):
+        _check(load().gfcc_set_stream(self._h, ctypes.c_void_p(stream_handle or 0)))
+
+    def dims(self):
+        a, b = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(load().gfcc_dims(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def solve(self, omegas, eta: float, orbitals, tol: float):
+        """G[w][p][q] (complex128) and the return code (0 or WARN_NOT_CONVERGED)."""
+        om = _f64(omegas).reshape(-1)
+        orb = np.ascontiguousarray(orbitals, dtype=np.int32).reshape(-1)
+        G = np.zeros((om.size, orb.size, orb.size), dtype=np.complex128)
+        code = _check(load().gfcc_solve(self._h, om.size, _dp(om), float(eta), orb.size,
+                                        orb.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), float(tol),
+                                        G.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return G, code
+
+    def solve_device(self, omegas_ptr: int, n_omega: int, eta: float, orbitals_ptr: int, n_orb: int, tol: float,
+                     G_ptr: int):
+        """gfcc_solve_device on caller-owned device buffers (e.g. torch tensors' data_ptr())."""
+        return _check(load().gfcc_solve_device(self._h, n_omega, ctypes.c_void_p(omegas_ptr), float(eta), n_orb,
+                                               ctypes.c_void_p(orbitals_ptr), float(tol), ctypes.c_void_p(G_ptr)))
+
+    def stats(self):
+        lib = load()
+        cnt = ctypes.c_int(0)
+        _check(lib.gfcc_last_stats(self._h, ctypes.byref(cnt), None, None, None))
+        n = cnt.value
+        it = np.zeros(n, dtype=np.int32)
+        rr = np.zeros(n, dtype=np.float64)
+        stt = np.zeros(n, dtype=np.int32)
+        cnt = ctypes.c_int(n)
+        _check(lib.gfcc_last_stats(self._h, ctypes.byref(cnt), it.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                   _dp(rr), stt.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return it, rr, stt
+
+    def sigma(self, sector: str, X: np.ndarray) -> np.ndarray:
+        """sigma(x) for packed complex vectors X[n_vec][dim] (FP64)."""
+        X = np.ascontiguousarray(np.atleast_2d(X), dtype=np.complex128)
+        Y = np.zeros_like(X)
+        _check(load().gfcc_sigma(self._h, _SECTORS[sector], X.shape[0],
+                                 X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 Y.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return Y

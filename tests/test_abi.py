@@ -1,0 +1,50 @@
+"""The C ABI: the built library exports every entry point include/gfcc.h declares (CPU only, no compute)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2010_04768_gb300 import build as gbuild
+from paper_2010_04768_gb300 import gfcc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "gfcc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gfcc_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(gfcc.LIB_PATH):
+        gbuild.build()
+    return ctypes.CDLL(gfcc.LIB_PATH)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("gfcc_create", "gfcc_solve", "gfcc_destroy", "gfcc_set_option", "gfcc_last_stats"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_last_error_is_empty_string_initially(lib):
+    lib.gfcc_last_error.restype = ctypes.c_char_p
+    assert isinstance(lib.gfcc_last_error(), bytes)
+
+
+def test_null_arguments_are_rejected_without_a_gpu(lib):
+    # argument checks happen before any CUDA call
+    typed = gfcc.load()
+    h = ctypes.c_void_p()
+    assert typed.gfcc_create(0, 4, 4, None, None, None, None, None, ctypes.byref(h)) == gfcc.ERR_ARG
+    assert b"o >= 1" in typed.gfcc_last_error()
+    assert typed.gfcc_set_option(None, 1, 1.0) == gfcc.ERR_ARG
+    typed.gfcc_destroy(None)
