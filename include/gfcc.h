@@ -52,6 +52,7 @@ extern "C" {
 /* Precisions (key GFCC_OPT_PRECISION). */
 #define GFCC_PREC_FP64        0   /* every step in float64                                              */
 #define GFCC_PREC_MIXED_BF16  1   /* sigma product on bf16 tensor cores + fp64 iterative refinement    */
+#define GFCC_PREC_FP64_EMULATED 2 /* gfcc_sigma_ex only: FP64-accurate sigma from BF16 digit planes     */
 
 /* Preconditioners (key GFCC_OPT_PRECOND). */
 #define GFCC_PRECOND_NONE  0      /* plain GMRES, as in the paper's runs                                */
@@ -65,6 +66,11 @@ extern "C" {
 #define GFCC_OPT_PRECOND     5    /* GFCC_PRECOND_*; default DIAG                                        */
 #define GFCC_OPT_BATCH       6    /* systems solved together (0 = chosen from free memory); default 0   */
 #define GFCC_OPT_INNER_TOL   7    /* mixed precision: inner GMRES relative tolerance; default 1e-3       */
+#define GFCC_OPT_RESIDUAL    8    /* mixed precision refinement residual: 1 (default) FP64-accurate from
+                                     digit planes on the tensor cores, 0 the FP64 (DFMA) sigma          */
+#define GFCC_OPT_INNER_CYCLES 9   /* mixed precision: GMRES restart cycles per refinement step; default 1 */
+#define GFCC_OPT_EMU_LEVEL  10    /* digit pairs i + j <= level in the FP64-accurate products (8 digits of
+                                     6 bits per operand); default 9                                      */
 
 /* Per-column status values reported by gfcc_last_stats. */
 #define GFCC_STATUS_CONVERGED      0
@@ -142,8 +148,46 @@ int gfcc_last_stats(gfcc_ctx *ctx, int *count, int *iters, double *relres, int *
  */
 int gfcc_sigma(gfcc_ctx *ctx, int sector, int n_vec, const double *x, double *y);
 
+/* gfcc_sigma_ex - gfcc_sigma in a chosen precision: GFCC_PREC_FP64; GFCC_PREC_MIXED_BF16 (IP only,
+ * context created mixed): the couplings on the BF16 tensor cores with FP32 accumulation, the
+ * Fock-like diagonal in FP64; GFCC_PREC_FP64_EMULATED (IP only, context created mixed): the
+ * FP64-accurate sigma of the refinement residual (digit planes on the tensor cores). */
+int gfcc_sigma_ex(gfcc_ctx *ctx, int sector, int precision, int n_vec, const double *x, double *y);
+
 /* gfcc_dims - packed dimensions of the IP and EA spaces of the context. */
 int gfcc_dims(gfcc_ctx *ctx, long long *dim_ip, long long *dim_ea);
+
+/*
+ * Profiling.  gfcc_profile(ctx, 1) resets the counters and times every later solve phase with CUDA
+ * events on the context's stream (gfcc_profile(ctx, 0) stops).  gfcc_profile_read returns, for one
+ * phase, the summed device time in milliseconds, the number of timed regions and the algorithmic
+ * floating-point operations they performed (counted from the problem sizes, not measured).
+ * Phases: 0 setup (gfcc_create), 1 ring contraction of the sigma product, 2 EA vvvv contraction,
+ * 3 whole sigma products (contains 1 and 2), 4 Arnoldi orthogonalisation, 5 Givens / least squares,
+ * 6 right-hand sides, left vectors and overlaps, 7 whole gfcc_solve calls, 8 ring contraction on the
+ * BF16 tensor cores (mixed precision; phase 1 is the FP64 ring contraction).
+ */
+int gfcc_profile(gfcc_ctx *ctx, int enable);
+int gfcc_profile_read(gfcc_ctx *ctx, int phase, double *ms, long long *count, double *flops);
+
+/* gfcc_launch_count - number of CUDA kernels this library has launched in this process. */
+long long gfcc_launch_count(void);
+
+/*
+ * gfcc_selftest_gemm_bf16 - run the tensor-core contraction engine of the mixed-precision sigma
+ * product alone: D[M][N] = sum_k bf16(A[m][k]) bf16(B[n][k]) with FP32 accumulation.
+ * A (M x K), B (N x K) and D (M x N) are row-major FP32 HOST arrays; the inputs are rounded to
+ * BF16 (nearest even) on the host.  GFCC_ERR_TIMEOUT if a bounded device wait gave up.
+ */
+int gfcc_selftest_gemm_bf16(int M, int N, int K, const float *A, const float *B, float *D);
+
+/*
+ * gfcc_selftest_gemm_f64emu - the FP64-accurate product C[M][N] = sum_k A[m][k] B[n][k] computed from
+ * S base-64 digit planes per operand on the BF16 tensor cores, keeping digit pairs i + j <= P
+ * (Ozaki-Ogita-Oishi-Rump splitting; the error per term is about 2^-(6P-4) of the row scales).
+ * A (M x K), B (N x K), C (M x N): row-major FP64 HOST arrays.
+ */
+int gfcc_selftest_gemm_f64emu(int M, int N, int K, const double *A, const double *B, int S, int P, double *C);
 
 /* gfcc_destroy - free the context and all its device memory.  NULL is a no-op. */
 void gfcc_destroy(gfcc_ctx *ctx);

@@ -106,14 +106,14 @@ class Integrals:
         Y = np.eye(n) + t                     # e^-T1 a_q e^T1 = sum_y Y[q,y] a_y
         self.X, self.Y = X, Y
         # core Hamiltonian: reference Fock matrix of h with <pq||rs> is f
-        J = np.einsum("kpq,kjj->pq", chol, chol[:, :o, :o])
-        K = np.einsum("kpj,kjq->pq", chol[:, :, :o], chol[:, :o, :])
+        J = np.einsum("kpq,kjj->pq", chol, chol[:, :o, :o], optimize=True)
+        K = np.einsum("kpj,kjq->pq", chol[:, :, :o], chol[:, :o, :], optimize=True)
         h = fock - J + K
-        self.Lt = np.einsum("xp,kpq,qy->kxy", X, chol, Y)    # L'^K = X L^K Y
+        self.Lt = np.einsum("xp,kpq,qy->kxy", X, chol, Y, optimize=True)    # L'^K = X L^K Y
         hp = X @ h @ Y
         Lt = self.Lt
-        Jp = np.einsum("kpq,kjj->pq", Lt, Lt[:, :o, :o])
-        Kp = np.einsum("kpj,kjq->pq", Lt[:, :, :o], Lt[:, :o, :])
+        Jp = np.einsum("kpq,kjj->pq", Lt, Lt[:, :o, :o], optimize=True)
+        Kp = np.einsum("kpj,kjq->pq", Lt[:, :, :o], Lt[:, :o, :], optimize=True)
         self.f = hp + Jp - Kp                 # f'_pq = h'_pq + sum_j <pj||qj>'
 
     def sl(self, c):
@@ -144,16 +144,16 @@ class HbarIP:
         voovv = ints.eri("oovv")
         self.v_oovv = voovv
         self.Fov = f("ov").copy()
-        self.Foo = f("oo") + 0.5 * np.einsum("mnef,inef->mi", voovv, t2)
-        self.Fvv = f("vv") - 0.5 * np.einsum("mnef,mnaf->ae", voovv, t2)
-        self.Woooo = ints.eri("oooo") + 0.5 * np.einsum("mnef,ijef->mnij", voovv, t2)
+        self.Foo = f("oo") + 0.5 * np.einsum("mnef,inef->mi", voovv, t2, optimize=True)
+        self.Fvv = f("vv") - 0.5 * np.einsum("mnef,mnaf->ae", voovv, t2, optimize=True)
+        self.Woooo = ints.eri("oooo") + 0.5 * np.einsum("mnef,ijef->mnij", voovv, t2, optimize=True)
         self.Wooov = ints.eri("ooov")
-        self.Wovvo = ints.eri("ovvo") - np.einsum("mnef,jnfb->mbej", voovv, t2)
+        self.Wovvo = ints.eri("ovvo") - np.einsum("mnef,jnfb->mbej", voovv, t2, optimize=True)
         v_ooov = self.Wooov
-        tmp = np.einsum("mnie,jnbe->mbij", v_ooov, t2)
+        tmp = np.einsum("mnie,jnbe->mbij", v_ooov, t2, optimize=True)
         self.Wovoo = (ints.eri("ovoo")
-                      - np.einsum("me,ijbe->mbij", self.Fov, t2)
-                      + 0.5 * np.einsum("mbef,ijef->mbij", ints.eri("ovvv"), t2)
+                      - np.einsum("me,ijbe->mbij", self.Fov, t2, optimize=True)
+                      + 0.5 * np.einsum("mbef,ijef->mbij", ints.eri("ovvv"), t2, optimize=True)
                       + tmp - tmp.transpose(0, 1, 3, 2))
 
 
@@ -166,16 +166,16 @@ class HbarEA:
         voovv = ints.eri("oovv")
         self.v_oovv = voovv
         self.Fov = f("ov").copy()
-        self.Foo = f("oo") + 0.5 * np.einsum("mnef,inef->mi", voovv, t2)
-        self.Fvv = f("vv") - 0.5 * np.einsum("mnef,mnaf->ae", voovv, t2)
-        self.Wovvo = ints.eri("ovvo") - np.einsum("mnef,jnfb->mbej", voovv, t2)
+        self.Foo = f("oo") + 0.5 * np.einsum("mnef,inef->mi", voovv, t2, optimize=True)
+        self.Fvv = f("vv") - 0.5 * np.einsum("mnef,mnaf->ae", voovv, t2, optimize=True)
+        self.Wovvo = ints.eri("ovvo") - np.einsum("mnef,jnfb->mbej", voovv, t2, optimize=True)
         self.Wvovv = ints.eri("vovv")
-        self.Wvvvv = ints.eri("vvvv") + 0.5 * np.einsum("mnef,mnab->abef", voovv, t2)
+        self.Wvvvv = ints.eri("vvvv") + 0.5 * np.einsum("mnef,mnab->abef", voovv, t2, optimize=True)
         v_ovvv = ints.eri("ovvv")
-        tmp = np.einsum("mbef,miaf->abei", v_ovvv, t2)
+        tmp = np.einsum("mbef,miaf->abei", v_ovvv, t2, optimize=True)
         self.Wvvvo = (ints.eri("vvvo")
-                      - np.einsum("me,miab->abei", self.Fov, t2)
-                      + 0.5 * np.einsum("mnei,mnab->abei", ints.eri("oovo"), t2)
+                      - np.einsum("me,miab->abei", self.Fov, t2, optimize=True)
+                      + 0.5 * np.einsum("mnei,mnab->abei", ints.eri("oovo"), t2, optimize=True)
                       - tmp + tmp.transpose(1, 0, 2, 3))
 
 
@@ -187,36 +187,36 @@ class HbarEA:
 def ip_sigma_unpacked(hb: HbarIP, r1, r2):
     """IP-EOM-CCSD sigma in Hbar elements (1h and 2h1p projections of [Hbar, R]|Phi>)."""
     t2 = hb.t2
-    s1 = (-np.einsum("mi,m->i", hb.Foo, r1)
-          - np.einsum("me,mie->i", hb.Fov, r2)
-          + 0.5 * np.einsum("nmie,mne->i", hb.Wooov, r2))
-    s2 = np.einsum("maji,m->ija", hb.Wovoo, r1)
-    s2 = s2 + np.einsum("ae,ije->ija", hb.Fvv, r2)
-    tmp = np.einsum("mi,mja->ija", hb.Foo, r2)
+    s1 = (-np.einsum("mi,m->i", hb.Foo, r1, optimize=True)
+          - np.einsum("me,mie->i", hb.Fov, r2, optimize=True)
+          + 0.5 * np.einsum("nmie,mne->i", hb.Wooov, r2, optimize=True))
+    s2 = np.einsum("maji,m->ija", hb.Wovoo, r1, optimize=True)
+    s2 = s2 + np.einsum("ae,ije->ija", hb.Fvv, r2, optimize=True)
+    tmp = np.einsum("mi,mja->ija", hb.Foo, r2, optimize=True)
     s2 = s2 - tmp + tmp.transpose(1, 0, 2)
-    s2 = s2 + 0.5 * np.einsum("mnij,mna->ija", hb.Woooo, r2)
-    tmp = np.einsum("maei,mje->ija", hb.Wovvo, r2)
+    s2 = s2 + 0.5 * np.einsum("mnij,mna->ija", hb.Woooo, r2, optimize=True)
+    tmp = np.einsum("maei,mje->ija", hb.Wovvo, r2, optimize=True)
     s2 = s2 + tmp - tmp.transpose(1, 0, 2)
-    z = 0.5 * np.einsum("mnef,mnf->e", hb.v_oovv, r2)          # three-body term
-    s2 = s2 + np.einsum("e,ijae->ija", z, t2)
+    z = 0.5 * np.einsum("mnef,mnf->e", hb.v_oovv, r2, optimize=True)          # three-body term
+    s2 = s2 + np.einsum("e,ijae->ija", z, t2, optimize=True)
     return s1, s2
 
 
 def ea_sigma_unpacked(hb: HbarEA, y1, y2):
     """EA-EOM-CCSD sigma in Hbar elements (1p and 2p1h projections of [Hbar, Q]|Phi>)."""
     t2 = hb.t2
-    s1 = (np.einsum("ae,e->a", hb.Fvv, y1)
-          + np.einsum("me,mae->a", hb.Fov, y2)
-          + 0.5 * np.einsum("amef,mef->a", hb.Wvovv, y2))
-    s2 = np.einsum("abei,e->iab", hb.Wvvvo, y1)
-    s2 = s2 - np.einsum("mi,mab->iab", hb.Foo, y2)
-    tmp = np.einsum("be,iae->iab", hb.Fvv, y2)
+    s1 = (np.einsum("ae,e->a", hb.Fvv, y1, optimize=True)
+          + np.einsum("me,mae->a", hb.Fov, y2, optimize=True)
+          + 0.5 * np.einsum("amef,mef->a", hb.Wvovv, y2, optimize=True))
+    s2 = np.einsum("abei,e->iab", hb.Wvvvo, y1, optimize=True)
+    s2 = s2 - np.einsum("mi,mab->iab", hb.Foo, y2, optimize=True)
+    tmp = np.einsum("be,iae->iab", hb.Fvv, y2, optimize=True)
     s2 = s2 + tmp - tmp.transpose(0, 2, 1)
-    s2 = s2 + 0.5 * np.einsum("abef,ief->iab", hb.Wvvvv, y2)
-    tmp = np.einsum("mbei,mae->iab", hb.Wovvo, y2)
+    s2 = s2 + 0.5 * np.einsum("abef,ief->iab", hb.Wvvvv, y2, optimize=True)
+    tmp = np.einsum("mbei,mae->iab", hb.Wovvo, y2, optimize=True)
     s2 = s2 + tmp - tmp.transpose(0, 2, 1)
-    z = 0.5 * np.einsum("mnef,nef->m", hb.v_oovv, y2)          # three-body term
-    s2 = s2 - np.einsum("m,miab->iab", z, t2)
+    z = 0.5 * np.einsum("mnef,nef->m", hb.v_oovv, y2, optimize=True)          # three-body term
+    s2 = s2 - np.einsum("m,miab->iab", z, t2, optimize=True)
     return s1, s2
 
 
@@ -252,11 +252,12 @@ def ip_left(o, v, t1, t2, lam1, lam2, q):
         c2[:] = lam2[:, :, b, :]
     else:
         m = q
-        c1[:] = -np.einsum("c,kc->k", t1[m], lam1) - 0.5 * np.einsum("lcd,klcd->k", t2[m], lam2)
+        c1[:] = (-np.einsum("c,kc->k", t1[m], lam1, optimize=True)
+                 - 0.5 * np.einsum("lcd,klcd->k", t2[m], lam2, optimize=True))
         c1[m] += 1.0
         c2[m, :, :] += lam1
         c2[:, m, :] -= lam1
-        c2 -= np.einsum("c,ijca->ija", t1[m], lam2)
+        c2 -= np.einsum("c,ijca->ija", t1[m], lam2, optimize=True)
     return c1, c2
 
 
@@ -282,11 +283,12 @@ def ea_left(o, v, t1, t2, lam1, lam2, p):
         c2[:] = lam2[:, m, :, :]
     else:
         e = p - o
-        c1[:] = -np.einsum("k,kc->c", t1[:, e], lam1) + 0.5 * np.einsum("kld,kldc->c", t2[:, :, e, :], lam2)
+        c1[:] = (-np.einsum("k,kc->c", t1[:, e], lam1, optimize=True)
+                 + 0.5 * np.einsum("kld,kldc->c", t2[:, :, e, :], lam2, optimize=True))
         c1[e] += 1.0
         c2[:, e, :] += lam1
         c2[:, :, e] -= lam1
-        c2 += np.einsum("k,ikcd->icd", t1[:, e], lam2)
+        c2 += np.einsum("k,ikcd->icd", t1[:, e], lam2, optimize=True)
     return c1, c2
 
 

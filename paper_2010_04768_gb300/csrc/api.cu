@@ -3,6 +3,7 @@
 // independent; here they are batched onto one GPU instead of process groups), the
 // right-hand sides, left vectors and overlaps of eqs. gfxn2/gfxn3.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -13,6 +14,8 @@
 #include "gmres.cuh"
 #include "kernels.cuh"
 #include "sigma.cuh"
+#include "ozaki.cuh"
+#include "umma.cuh"
 
 namespace gfcc {
 
@@ -53,6 +56,15 @@ int check_extent(const double *p, long long lo, long long hi, const char *what) 
   return GFCC_ERR_ARG;
 }
 
+int check_extent_bytes(const void *p, long long bytes, const char *what) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p), b = a + (uintptr_t)bytes;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  for (const AllocRec &r : g_allocs)
+    if (a >= r.base && b <= r.base + r.bytes && bytes > 0) return GFCC_OK;
+  set_error("internal extent check failed for %s: %lld bytes are outside every device allocation", what, bytes);
+  return GFCC_ERR_ARG;
+}
+
 cudaError_t dmalloc(void **p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes);
   if (e == cudaSuccess) reg_alloc(*p, bytes);
@@ -63,6 +75,57 @@ void dfree(void *p) {
   if (p == nullptr) return;
   unreg_alloc(p);
   cudaFree(p);
+}
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static cudaEvent_t take_event(gfcc_ctx *c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+PhaseTimer::PhaseTimer(gfcc_ctx *ctx, int ph, double fl) : c(ctx), phase(ph), flops(fl) {
+  if (c->prof) {
+    a = take_event(c);
+    if (a) cudaEventRecord(a, c->stream);
+  }
+}
+
+PhaseTimer::~PhaseTimer() {
+  if (!c->prof || a == nullptr) return;
+  cudaEvent_t b = take_event(c);
+  if (b == nullptr) {
+    c->ev_pool.push_back(a);
+    return;
+  }
+  cudaEventRecord(b, c->stream);
+  c->pend.push_back({a, b, phase, flops});
+}
+
+void prof_resolve(gfcc_ctx *c) {
+  for (auto &p : c->pend) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->prof_ms[p.phase] += ms;
+      c->prof_n[p.phase] += 1;
+      c->prof_flops[p.phase] += p.flops;
+    } else {
+      cudaGetLastError();
+    }
+    c->ev_pool.push_back(p.a);
+    c->ev_pool.push_back(p.b);
+  }
+  c->pend.clear();
 }
 
 void set_error(const char *fmt, ...) {
@@ -418,22 +481,43 @@ int create_impl(int o, int v, int L, const double *fock, const double *chol, con
     free_tmp();
     return fail(s);
   }
-  s = build_hbar(c, d_fock, d_chol);
+  {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool timed = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+    if (timed) cudaEventRecord(e0, c->stream);
+    s = build_hbar(c, d_fock, d_chol);
+    if (timed) {
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+        c->prof_ms[PH_SETUP] = ms;
+        c->prof_n[PH_SETUP] = 1;
+      }
+    }
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
   free_tmp();
   if (s < 0) return fail(s);
   *out = c;
   return GFCC_OK;
 }
 
+int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, int n_orb, const int *d_orb,
+                     const int *h_orb, double tol, double *d_G);
+
 int choose_batch(gfcc_ctx *c, int sector, long long n, long long ntasks) {
   if (c->batch > 0) return (int)std::min<long long>(c->batch, ntasks);
+  const bool mixed = sector == GFCC_SECTOR_IP && c->precision == GFCC_PREC_MIXED_BF16;
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
     cudaGetLastError();
     fr = 1ULL << 30;
   }
-  const double per = 8.0 * (double)(gmres_work_doubles(c, sector, n, 2, c->restart) -
-                                   gmres_work_doubles(c, sector, n, 1, c->restart));
+  const double per = 8.0 * (double)(gmres_work_doubles(c, sector, n, 2, c->restart, mixed) -
+                                   gmres_work_doubles(c, sector, n, 1, c->restart, mixed));
   long long b = (long long)(0.6 * (double)fr / std::max(per, 1.0));
   b = std::max<long long>(1, std::min<long long>(b, 256));
   return (int)std::min<long long>(b, ntasks);
@@ -456,6 +540,21 @@ int grow_scratch(gfcc_ctx *c, size_t bytes) {
 int solve_impl(gfcc_ctx *c, int n_omega, const double *d_om, double eta, int n_orb, const int *d_orb,
                const int *h_orb, double tol, double *d_G) {
   cudaStream_t st = c->stream;
+  int rc;
+  {
+    PhaseTimer tm(c, PH_SOLVE);
+    rc = solve_impl_inner(c, n_omega, d_om, eta, n_orb, d_orb, h_orb, tol, d_G);
+  }
+  if (c->prof) {
+    GFCC_CUDA(cudaStreamSynchronize(st));
+    prof_resolve(c);
+  }
+  return rc;
+}
+
+int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, int n_orb, const int *d_orb,
+                     const int *h_orb, double tol, double *d_G) {
+  cudaStream_t st = c->stream;
   const int sectors[2] = {GFCC_SECTOR_IP, GFCC_SECTOR_EA};
   const long long ntasks = (long long)n_omega * n_orb;
   const int nsec = (c->sectors & GFCC_SECTOR_IP ? 1 : 0) + (c->sectors & GFCC_SECTOR_EA ? 1 : 0);
@@ -470,16 +569,18 @@ int solve_impl(gfcc_ctx *c, int n_omega, const double *d_om, double eta, int n_o
     if (!(c->sectors & sector)) continue;
     const bool ip = sector == GFCC_SECTOR_IP;
     const long long n = ip ? c->dim_ip : c->dim_ea;
+    // mixed precision covers the IP sector; EA systems of a mixed context are solved in FP64
+    const bool mixed = ip && c->precision == GFCC_PREC_MIXED_BF16;
     const int nsys = choose_batch(c, sector, n, ntasks);
     const int m = c->restart;
     const long long nsplit = (n + 8191) / 8192;
-    const long long work = gmres_work_doubles(c, sector, n, nsys, m) + (long long)n_orb * n +
-                           nsplit * 2LL * nsys * n_orb + 4LL * nsys + 64;
+    const long long gw = gmres_work_doubles(c, sector, n, nsys, m, mixed);
+    const long long work = gw + (long long)n_orb * n + nsplit * 2LL * nsys * n_orb + 4LL * nsys + 64;
     GFCC_TRY(grow_scratch(c, sizeof(double) * work));
     double *base = static_cast<double *>(c->scratch);
     Gmres gm;
-    GFCC_TRY(gm.init(c, sector, n, nsys, m, base));
-    double *Cl = base + gmres_work_doubles(c, sector, n, nsys, m);
+    GFCC_TRY(gm.init(c, sector, n, nsys, m, base, mixed));
+    double *Cl = base + gw;
     double *part = Cl + (long long)n_orb * n;
     int *d_tw = reinterpret_cast<int *>(part + nsplit * 2LL * nsys * n_orb);
     int *d_ta = d_tw + nsys;
@@ -487,6 +588,8 @@ int solve_impl(gfcc_ctx *c, int n_omega, const double *d_om, double eta, int n_o
     gm.eta = eta;
     gm.use_precond = c->precond == GFCC_PRECOND_DIAG;
     // left vectors for all orbitals of the list
+    {
+    PhaseTimer tleft(c, PH_OVERLAP);
     if (ip) {
       left_ip_1h_kernel<<<n_orb * c->o, 256, 0, st>>>(Cl, n, n_orb, d_orb, c->o, c->v, c->t1, c->t2, c->l1, c->l2);
       GFCC_LAUNCH_CHECK();
@@ -504,6 +607,7 @@ int solve_impl(gfcc_ctx *c, int n_omega, const double *d_om, double eta, int n_o
         GFCC_LAUNCH_CHECK();
       }
     }
+    }
     std::vector<int> h_tw(nsys), h_ta(nsys), h_state(nsys), h_it(nsys);
     std::vector<double> h_rel(nsys);
     for (long long t0 = 0; t0 < ntasks; t0 += nsys) {
@@ -520,14 +624,25 @@ int solve_impl(gfcc_ctx *c, int n_omega, const double *d_om, double eta, int n_o
       GFCC_LAUNCH_CHECK();
       gather_orb_kernel<<<cdiv(nsys, 128), 128, 0, st>>>(d_orb, d_ta, nsys, d_porb);
       GFCC_LAUNCH_CHECK();
+      {
+      PhaseTimer trhs(c, PH_OVERLAP);
       if (ip) {
         rhs_ip_kernel<<<grid1d(n * nsys), 256, 0, st>>>(gm.B, n, nsys, d_porb, c->o, c->v, c->t1, c->t2);
       } else {
         rhs_ea_kernel<<<grid1d(n * nsys), 256, 0, st>>>(gm.B, n, nsys, d_porb, c->o, c->v, c->Pv, c->t1, c->t2);
       }
       GFCC_LAUNCH_CHECK();
-      GFCC_TRY(gm.solve(tol, c->max_iters, h_state.data()));
+      }
+      if (mixed) {
+        GFCC_TRY(umma_error_reset(st));
+        GFCC_TRY(gm.solve_refined(tol, c->inner_tol, c->max_iters, h_state.data(), h_it.data()));
+        GFCC_TRY(umma_error_check(st));
+      } else {
+        GFCC_TRY(gm.solve(tol, c->max_iters, h_state.data()));
+      }
       // overlaps: part[z][(s,t)][q] = sum_{mu in chunk z} x_s[mu] C[q][mu]
+      {
+      PhaseTimer tov(c, PH_OVERLAP);
       Contract k;
       k.A = gm.U; k.am = imap2(2, 1, 2 * n); k.ak = imap1(2);
       k.B = Cl; k.bk = imap1(1); k.bn = imap1(n);
@@ -538,6 +653,7 @@ int solve_impl(gfcc_ctx *c, int n_omega, const double *d_om, double eta, int n_o
       overlap_scatter_kernel<<<grid1d((long long)nb * n_orb), 256, 0, st>>>(part, (int)nsplit, nb, n_orb, d_tw, d_ta,
                                                                              ip ? 1 : 0, d_G);
       GFCC_LAUNCH_CHECK();
+      }
       GFCC_CUDA(cudaMemcpyAsync(h_it.data(), gm.iters, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
       GFCC_CUDA(cudaMemcpyAsync(h_rel.data(), gm.relres, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
       GFCC_CUDA(cudaMemcpyAsync(h_state.data(), gm.state, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
@@ -617,6 +733,18 @@ int gfcc_set_option(gfcc_ctx *c, int key, double value) {
     case GFCC_OPT_BATCH:
       if (iv < 0 || iv > 4096) break;
       c->batch = iv;
+      return GFCC_OK;
+    case GFCC_OPT_INNER_CYCLES:
+      if (iv < 1 || iv > 1000) break;
+      c->inner_cycles = iv;
+      return GFCC_OK;
+    case GFCC_OPT_EMU_LEVEL:
+      if (iv < 2 || iv > 2 * c->emu_S) break;
+      c->emu_P = iv;
+      return GFCC_OK;
+    case GFCC_OPT_RESIDUAL:
+      if (iv != 0 && iv != 1) break;
+      c->residual_emulated = iv;
       return GFCC_OK;
     case GFCC_OPT_INNER_TOL:
       if (!(value > 0.0 && value < 1.0)) break;
@@ -723,14 +851,28 @@ int gfcc_last_stats(gfcc_ctx *c, int *count, int *iters, double *relres, int *st
 }
 
 int gfcc_sigma(gfcc_ctx *c, int sector, int n_vec, const double *x, double *y) {
+  return gfcc_sigma_ex(c, sector, GFCC_PREC_FP64, n_vec, x, y);
+}
+
+int gfcc_sigma_ex(gfcc_ctx *c, int sector, int precision, int n_vec, const double *x, double *y) {
   if (c == nullptr || x == nullptr || y == nullptr || n_vec < 0 ||
       (sector != GFCC_SECTOR_IP && sector != GFCC_SECTOR_EA) || !(c->sectors & sector)) {
     set_error("gfcc_sigma: bad arguments or sector not built");
     return GFCC_ERR_ARG;
   }
+  const bool mixed = precision == GFCC_PREC_MIXED_BF16;
+  const bool emu = precision == GFCC_PREC_FP64_EMULATED;
+  if ((precision != GFCC_PREC_FP64 && !mixed && !emu) ||
+      ((mixed || emu) && (sector != GFCC_SECTOR_IP || c->Wr_bf == nullptr))) {
+    set_error("gfcc_sigma_ex: mixed / emulated precision needs the IP sector of a context created with "
+              "GFCC_PREC_MIXED_BF16");
+    return GFCC_ERR_ARG;
+  }
   if (n_vec == 0) return GFCC_OK;
   const long long n = sector == GFCC_SECTOR_IP ? c->dim_ip : c->dim_ea;
-  const long long work = sigma_work_doubles(c, sector, n_vec) + 4LL * n_vec * n;
+  const long long ew = emu ? sigma_emu_work_doubles(c, std::min(n_vec, 16)) : 0;
+  const long long work = sigma_work_doubles(c, sector, n_vec) + 4LL * n_vec * n +
+                         (mixed ? sigma_mixed_work_doubles(c, n_vec) : 0) + ew;
   GFCC_TRY(grow_scratch(c, sizeof(double) * work));
   double *dx = static_cast<double *>(c->scratch);
   double *dy = dx + 2LL * n_vec * n;
@@ -740,7 +882,13 @@ int gfcc_sigma(gfcc_ctx *c, int sector, int n_vec, const double *x, double *y) {
   b.nsys = n_vec;
   b.x = dx; b.ldx = n;
   b.y = dy; b.ldy = n;
-  GFCC_TRY(sector == GFCC_SECTOR_IP ? apply_ip(c, b, w) : apply_ea(c, b, w));
+  if (mixed || emu) {
+    GFCC_TRY(umma_error_reset(c->stream));
+    GFCC_TRY(mixed ? apply_ip_mixed(c, b, w) : apply_ip_emu(c, b, w, ew));
+    GFCC_TRY(umma_error_check(c->stream));
+  } else {
+    GFCC_TRY(sector == GFCC_SECTOR_IP ? apply_ip(c, b, w) : apply_ea(c, b, w));
+  }
   GFCC_CUDA(cudaMemcpyAsync(y, dy, sizeof(double) * 2 * n_vec * n, cudaMemcpyDeviceToHost, c->stream));
   GFCC_CUDA(cudaStreamSynchronize(c->stream));
   return GFCC_OK;
@@ -759,6 +907,8 @@ int gfcc_dims(gfcc_ctx *c, long long *dim_ip, long long *dim_ea) {
 void gfcc_destroy(gfcc_ctx *c) {
   if (c == nullptr) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  prof_resolve(c);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (void *p : c->allocs) dfree(p);
   if (c->scratch) dfree(c->scratch);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -766,5 +916,122 @@ void gfcc_destroy(gfcc_ctx *c) {
 }
 
 const char *gfcc_last_error(void) { return g_err; }
+
+int gfcc_profile(gfcc_ctx *c, int enable) {
+  if (c == nullptr) {
+    set_error("gfcc_profile: ctx is NULL");
+    return GFCC_ERR_ARG;
+  }
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  prof_resolve(c);
+  for (int i = 0; i < PH_COUNT; i++) {
+    if (i == PH_SETUP) continue;   // the setup time of gfcc_create is kept
+    c->prof_ms[i] = 0.0;
+    c->prof_n[i] = 0;
+    c->prof_flops[i] = 0.0;
+  }
+  c->prof = enable != 0;
+  return GFCC_OK;
+}
+
+int gfcc_profile_read(gfcc_ctx *c, int phase, double *ms, long long *count, double *flops) {
+  if (c == nullptr || phase < 0 || phase >= PH_COUNT) {
+    set_error("gfcc_profile_read: bad ctx or phase");
+    return GFCC_ERR_ARG;
+  }
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  prof_resolve(c);
+  if (ms) *ms = c->prof_ms[phase];
+  if (count) *count = c->prof_n[phase];
+  if (flops) *flops = c->prof_flops[phase];
+  return GFCC_OK;
+}
+
+long long gfcc_launch_count(void) { return gfcc::g_launches.load(); }
+
+int gfcc_selftest_gemm_f64emu(int M, int N, int K, const double *A, const double *B, int S, int P, double *C) {
+  if (M <= 0 || N <= 0 || K <= 0 || S < 1 || S > 12 || P < 2 || A == nullptr || B == nullptr || C == nullptr) {
+    set_error("gfcc_selftest_gemm_f64emu: bad arguments");
+    return GFCC_ERR_ARG;
+  }
+  void *da = nullptr, *db = nullptr, *dc = nullptr, *sa = nullptr, *sb = nullptr, *w = nullptr;
+  cudaStream_t st = nullptr;
+  int s = GFCC_OK;
+  if (dmalloc(&da, sizeof(double) * M * K) != cudaSuccess || dmalloc(&db, sizeof(double) * N * K) != cudaSuccess ||
+      dmalloc(&dc, sizeof(double) * M * N) != cudaSuccess ||
+      dmalloc(&sa, emu_operand_bytes(M, K, S)) != cudaSuccess ||
+      dmalloc(&sb, emu_operand_bytes(N, K, S)) != cudaSuccess ||
+      dmalloc(&w, emu_gemm_work_bytes(M, N, K)) != cudaSuccess || cudaStreamCreate(&st) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("gfcc_selftest_gemm_f64emu: allocation failed");
+    s = GFCC_ERR_OOM;
+  }
+  if (s == GFCC_OK && (cudaMemcpy(da, A, sizeof(double) * M * K, cudaMemcpyHostToDevice) != cudaSuccess ||
+                       cudaMemcpy(db, B, sizeof(double) * N * K, cudaMemcpyHostToDevice) != cudaSuccess)) {
+    set_error("gfcc_selftest_gemm_f64emu: copy failed");
+    s = GFCC_ERR_CUDA;
+  }
+  EmuOperand ea, eb;
+  if (s == GFCC_OK) s = umma_error_reset(st);
+  if (s == GFCC_OK) s = emu_slice(st, static_cast<double *>(da), M, K, K, S, sa, ea);
+  if (s == GFCC_OK) s = emu_slice(st, static_cast<double *>(db), N, K, K, S, sb, eb);
+  if (s == GFCC_OK) s = emu_gemm(st, ea, eb, P, 1.0, 0.0, static_cast<double *>(dc), imap1(N), imap1(1), w);
+  if (s == GFCC_OK) s = umma_error_check(st);
+  if (s == GFCC_OK && cudaMemcpy(C, dc, sizeof(double) * M * N, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    set_error("gfcc_selftest_gemm_f64emu: copy back failed");
+    s = GFCC_ERR_CUDA;
+  }
+  for (void *p : {da, db, dc, sa, sb, w}) dfree(p);
+  if (st) cudaStreamDestroy(st);
+  return s;
+}
+
+int gfcc_selftest_gemm_bf16(int M, int N, int K, const float *A, const float *B, float *D) {
+  if (M <= 0 || N <= 0 || K <= 0 || A == nullptr || B == nullptr || D == nullptr) {
+    set_error("gfcc_selftest_gemm_bf16: bad arguments");
+    return GFCC_ERR_ARG;
+  }
+  const long long ld = (K + 7) / 8 * 8;
+  std::vector<unsigned short> ha((size_t)M * ld, 0), hb((size_t)N * ld, 0);
+  auto to_bf16 = [](float x) -> unsigned short {   // round to nearest even
+    unsigned u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (unsigned short)(u >> 16);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (unsigned short)(u >> 16);
+  };
+  for (long long i = 0; i < M; i++)
+    for (long long k = 0; k < K; k++) ha[i * ld + k] = to_bf16(A[i * K + k]);
+  for (long long i = 0; i < N; i++)
+    for (long long k = 0; k < K; k++) hb[i * ld + k] = to_bf16(B[i * K + k]);
+  void *da = nullptr, *db = nullptr, *dd = nullptr;
+  cudaStream_t st = nullptr;
+  int s = GFCC_OK;
+  if (dmalloc(&da, ha.size() * 2) != cudaSuccess || dmalloc(&db, hb.size() * 2) != cudaSuccess ||
+      dmalloc(&dd, (size_t)M * N * 4) != cudaSuccess || cudaStreamCreate(&st) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("gfcc_selftest_gemm_bf16: allocation failed");
+    s = GFCC_ERR_OOM;
+  }
+  if (s == GFCC_OK && (cudaMemcpy(da, ha.data(), ha.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+                       cudaMemcpy(db, hb.data(), hb.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)) {
+    set_error("gfcc_selftest_gemm_bf16: copy failed");
+    s = GFCC_ERR_CUDA;
+  }
+  if (s == GFCC_OK) s = umma_error_reset(st);
+  if (s == GFCC_OK)
+    s = gemm_bf16_tn(st, static_cast<const __nv_bfloat16 *>(da), ld, static_cast<const __nv_bfloat16 *>(db), ld,
+                     static_cast<float *>(dd), N, M, N, K, 1.0f, 0.0f);
+  if (s == GFCC_OK) s = umma_error_check(st);
+  if (s == GFCC_OK && cudaMemcpy(D, dd, (size_t)M * N * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    set_error("gfcc_selftest_gemm_bf16: copy back failed");
+    s = GFCC_ERR_CUDA;
+  }
+  dfree(da);
+  dfree(db);
+  dfree(dd);
+  if (st) cudaStreamDestroy(st);
+  return s;
+}
 
 }  // extern "C"

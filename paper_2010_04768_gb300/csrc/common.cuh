@@ -18,6 +18,8 @@ void reg_alloc(const void *p, size_t bytes);
 void unreg_alloc(const void *p);
 // 0 if [p + lo*8, p + hi*8 + 8) lies inside a registered allocation, else GFCC_ERR_ARG (with message)
 int check_extent(const double *p, long long lo, long long hi, const char *what);
+// 0 if [p, p + bytes) lies inside a registered allocation
+int check_extent_bytes(const void *p, long long bytes, const char *what);
 cudaError_t dmalloc(void **p, size_t bytes);   // cudaMalloc + reg_alloc
 void dfree(void *p);                           // unreg_alloc + cudaFree
 
@@ -38,8 +40,13 @@ void dfree(void *p);                           // unreg_alloc + cudaFree
     if (s_ < 0) return s_;      \
   } while (0)
 
-// Check the last kernel launch.
-#define GFCC_LAUNCH_CHECK() GFCC_CUDA(cudaGetLastError())
+// Check the last kernel launch (and count it: gfcc_launch_count reports the total).
+void count_launch();
+#define GFCC_LAUNCH_CHECK()   \
+  do {                        \
+    ::gfcc::count_launch();   \
+    GFCC_CUDA(cudaGetLastError()); \
+  } while (0)
 
 // Index map of a flattened GEMM index x onto a tensor offset:
 //   d0 <= 0 : x * s0

@@ -9,6 +9,8 @@
 // per 256-thread block with 4x4 outputs per thread keeps the pipe fed while the
 // tile loads stay in L1/L2.
 #include "common.cuh"
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace gfcc {
@@ -114,6 +116,24 @@ int contract_f64(const Contract &c, cudaStream_t st) {
   return GFCC_OK;
 }
 
+namespace {
+// C = alpha * sum_z part[z] + beta * C
+__global__ void splitk_reduce_kernel(const double *part, int nsplit, long long M, long long N, double alpha, double beta,
+                                     double *C, IMap cm, IMap cn) {
+  const long long tot = M * N;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < nsplit; z++) s += part[z * tot + t];
+    const long long m = t / N, n = t - m * N;
+    const long long off = imap_apply(cm, m) + imap_apply(cn, n);
+    C[off] = alpha * s + (beta != 0.0 ? beta * C[off] : 0.0);
+  }
+}
+
+double *g_splitk_buf = nullptr;
+long long g_splitk_cap = 0;
+}  // namespace
+
 int gemm_f64(cudaStream_t st, long long M, long long N, long long K, double alpha,
              const double *A, IMap am, IMap ak, const double *B, IMap bk, IMap bn, double beta,
              double *C, IMap cm, IMap cn, long long batch, long long sab, long long sbb, long long scb) {
@@ -123,6 +143,39 @@ int gemm_f64(cudaStream_t st, long long M, long long N, long long K, double alph
   c.am = am; c.ak = ak; c.bk = bk; c.bn = bn; c.cm = cm; c.cn = cn;
   c.batch = batch; c.sab = sab; c.sbb = sbb; c.scb = scb;
   c.alpha = alpha; c.beta = beta;
+  // Few output tiles and a long K would leave most SMs idle: split K into partial sums.
+  const long long tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN) * batch;
+  if (batch == 1 && tiles < 152 && K >= 8192) {
+    long long nsplit = std::min<long long>(std::max<long long>(1, 304 / tiles), K / 2048);
+    nsplit = std::min<long long>(nsplit, 512);
+    if (nsplit >= 2) {
+      const long long need = nsplit * M * N;
+      if (need > g_splitk_cap) {
+        if (g_splitk_buf) dfree(g_splitk_buf);
+        g_splitk_buf = nullptr;
+        g_splitk_cap = 0;
+        if (dmalloc((void **)&g_splitk_buf, sizeof(double) * need) != cudaSuccess) {
+          cudaGetLastError();
+          set_error("gemm_f64: cannot allocate %lld doubles of split-K workspace", need);
+          return GFCC_ERR_OOM;
+        }
+        g_splitk_cap = need;
+      }
+      Contract p = c;
+      p.C = g_splitk_buf;
+      p.cm = imap1(N);
+      p.cn = imap1(1);
+      p.alpha = 1.0;
+      p.beta = 0.0;
+      p.nsplit = nsplit;
+      p.kchunk = (K + nsplit - 1) / nsplit;
+      p.scz = M * N;
+      GFCC_TRY(contract_f64(p, st));
+      splitk_reduce_kernel<<<grid1d(M * N), 256, 0, st>>>(g_splitk_buf, (int)nsplit, M, N, alpha, beta, C, cm, cn);
+      GFCC_LAUNCH_CHECK();
+      return GFCC_OK;
+    }
+  }
   return contract_f64(c, st);
 }
 

@@ -1,8 +1,25 @@
 // The gfcc_ctx structure: problem sizes, options, device-resident inputs and Hbar elements.
 #pragma once
+#include <cuda_bf16.h>
+
 #include <vector>
 
 #include "common.cuh"
+#include "ozaki.cuh"
+
+// Profiling phases (gfcc_profile_read): CUDA-event timings on the context's stream.
+enum GfccPhase {
+  PH_SETUP = 0,       // gfcc_create: Hbar elements
+  PH_RING = 1,        // the (ov) x (ov) ring contraction of the FP64 sigma product
+  PH_VVVV = 2,        // EA vvvv contraction
+  PH_SIGMA = 3,       // a whole sigma product (contains phases 1 and 2)
+  PH_ARNOLDI = 4,     // Gram-Schmidt dots, updates, normalisation
+  PH_LSQ = 5,         // Givens rotations, back substitution, cycle bookkeeping
+  PH_OVERLAP = 6,     // right-hand sides, left vectors, G overlaps
+  PH_SOLVE = 7,       // a whole gfcc_solve
+  PH_RING_BF16 = 8,   // the ring contraction on the BF16 tensor cores (mixed precision)
+  PH_COUNT = 9
+};
 
 struct gfcc_ctx {
   // sizes: n = o + v orbitals; packed pair counts Po = o(o-1)/2, Pv = v(v-1)/2
@@ -17,6 +34,7 @@ struct gfcc_ctx {
   int precond = GFCC_PRECOND_DIAG;
   int batch = 0;
   double inner_tol = 1e-3;
+  int inner_cycles = 1;      // GMRES restart cycles per refinement step (each ends with an FP64-accurate residual)
 
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;
@@ -37,6 +55,22 @@ struct gfcc_ctx {
   double *U1 = nullptr;      // [i][(m,e,n)]    -d_in Fov[m,e] + 1/2 Wooov[n,m,i,e]
   double *diag_ip = nullptr; // packed Fock-like diagonal
 
+  // mixed-precision IP operands: BF16, K-major, row strides padded to multiples of 8.  The exact
+  // Fock-like diagonal d (diag_ip) is left out of them and applied in FP64 by the epilogue.
+  __nv_bfloat16 *Wr_bf = nullptr;  // [(i,a)][(m,e)]   ring core + off-diagonal Fbar folding, ld_ov
+  __nv_bfloat16 *Wq_bf = nullptr;  // [(i,j)][(m,n)]   1/2 Woooo[m,n,i,j], ld_o2
+  __nv_bfloat16 *W1_bf = nullptr;  // [(i,a,j)][m]     Wovoo[m,a,j,i], ld_o
+  __nv_bfloat16 *V3_bf = nullptr;  // [e][(m,f,n)]     1/2 <mn||ef>', ld_o2v
+  __nv_bfloat16 *T3_bf = nullptr;  // [(i,a,j)][e]     t2[i,j,a,e], ld_v
+  __nv_bfloat16 *U1_bf = nullptr;  // [i][(m,e,n) | m] U1 and the off-diagonal -Fbar_oo of the 1h row, ld_k1
+  long long ld_ov = 0, ld_o2 = 0, ld_o = 0, ld_o2v = 0, ld_v = 0, ld_k1 = 0;
+
+  // digit planes of the FP64 IP operands for the FP64-accurate residual on the tensor cores
+  // (full Fock folding, same GEMM roles as the BF16 operands; V3 padded to the K of U1x)
+  gfcc::EmuOperand eWr, eWq, eW1, eV3, eT3, eU1;
+  int emu_S = 8, emu_P = 9;
+  int residual_emulated = 1;   // 0: refinement residuals with the FP64 (DFMA) sigma
+
   // EA sigma operands
   double *Wr_ea = nullptr;   // [(i,b)][(m,e)]  Wovvo[m,b,e,i] + d_mi Fvv[b,e] - 1/2 d_be Foo[m,i]
   double *Wp = nullptr;      // [(a<b)][(e<f)]  Wvvvv[a,b,e,f]
@@ -52,12 +86,36 @@ struct gfcc_ctx {
   std::vector<int> st_iters, st_status;
   std::vector<double> st_relres;
 
+  // profiling (CUDA events on the context's stream)
+  bool prof = false;
+  struct PendingEv {
+    cudaEvent_t a, b;
+    int phase;
+    double flops;
+  };
+  std::vector<PendingEv> pend;
+  std::vector<cudaEvent_t> ev_pool;
+  double prof_ms[PH_COUNT] = {0};
+  long long prof_n[PH_COUNT] = {0};
+  double prof_flops[PH_COUNT] = {0};
+
   // scratch reused across solves (grown on demand)
   void *scratch = nullptr;
   size_t scratch_bytes = 0;
 };
 
 namespace gfcc {
+// Times the enclosed region on the context's stream when profiling is on.
+struct PhaseTimer {
+  gfcc_ctx *c;
+  int phase;
+  double flops;
+  cudaEvent_t a = nullptr;
+  PhaseTimer(gfcc_ctx *ctx, int ph, double fl = 0.0);
+  ~PhaseTimer();
+};
+void prof_resolve(gfcc_ctx *c);   // after a stream synchronisation: fold pending events into the totals
+
 int dev_alloc(gfcc_ctx *c, double **p, long long count);      // owned by the context
 int dev_alloc_tmp(double **p, long long count);                  // caller frees with cudaFree
 int build_hbar(gfcc_ctx *c, const double *d_fock, const double *d_chol);

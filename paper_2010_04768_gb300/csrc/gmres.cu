@@ -310,7 +310,7 @@ __global__ void norm_from_partial_kernel(int nsys, const double *nrm2, int NV, d
 // host side
 // ------------------------------------------------------------------------------------------
 
-long long gmres_work_doubles(const gfcc_ctx *c, int sector, long long n, int nsys, int m) {
+long long gmres_work_doubles(const gfcc_ctx *c, int sector, long long n, int nsys, int m, bool mixed) {
   const long long NV = m + 2;
   const long long nch = (n + DOT_CHUNK - 1) / DOT_CHUNK;
   long long w = 0;
@@ -322,11 +322,17 @@ long long gmres_work_doubles(const gfcc_ctx *c, int sector, long long n, int nsy
   w += 2LL * nsys * (2 * m + (m + 1));      // cs, sn, g
   w += 7LL * nsys + 512;                    // bnorm, relres, est, omega, int state/kcyc/iters, alignment
   w += sigma_work_doubles(c, sector, nsys);
+  if (mixed) {
+    w += 3 * 2LL * nsys * n + nsys + 64;     // X, R, B0, ||b0||
+    w += sigma_mixed_work_doubles(c, nsys);
+    if (c->eWr.dig != nullptr) w += sigma_emu_work_doubles(c, std::min(nsys, 16));
+  }
   return w;
 }
 
-int Gmres::init(gfcc_ctx *ctx, int sec, long long dim, int ns, int mm, double *work) {
+int Gmres::init(gfcc_ctx *ctx, int sec, long long dim, int ns, int mm, double *work, bool mx) {
   c = ctx;
+  mixed = mx;
   sector = sec;
   n = dim;
   nsys = ns;
@@ -360,13 +366,47 @@ int Gmres::init(gfcc_ctx *ctx, int sec, long long dim, int ns, int mm, double *w
   state = reinterpret_cast<int *>(ip);
   kcyc = state + nsys;
   iters = kcyc + nsys;
+  if (mixed) {
+    take(X, 2LL * nsys * n);
+    take(R, 2LL * nsys * n);
+    take(B0, 2LL * nsys * n);
+    take(b0norm, nsys);
+  }
   sigma_work = p;
-  const long long used = (p - work) + sigma_work_doubles(c, sector, nsys);
-  if (used > gmres_work_doubles(c, sector, n, nsys, m)) {
+  long long used = (p - work) + sigma_work_doubles(c, sector, nsys);
+  if (mixed) used += sigma_mixed_work_doubles(c, nsys) + 64;
+  if (used > gmres_work_doubles(c, sector, n, nsys, m, mixed)) {
     set_error("internal: GMRES workspace layout (%lld doubles) exceeds its size", used);
     return GFCC_ERR_ARG;
   }
   return GFCC_OK;
+}
+
+int Gmres::op_fp64(const double *x, long long ldx, double *yout, long long ldy) {
+  if (mixed && sector == GFCC_SECTOR_IP && c->residual_emulated && c->eWr.dig != nullptr) {
+    SysBatch b;
+    b.nsys = nsys;
+    b.x = x;
+    b.ldx = ldx;
+    b.y = yout;
+    b.ldy = ldy;
+    b.omega = omega;
+    b.eta = eta;
+    double *ew = sigma_work + sigma_work_doubles(c, sector, nsys) + sigma_mixed_work_doubles(c, nsys);
+    return apply_ip_emu(c, b, ew, sigma_emu_work_doubles(c, std::min(nsys, 16)));
+  }
+  SysBatch b;
+  b.nsys = nsys;
+  b.x = x;
+  b.ldx = ldx;
+  b.y = yout;
+  b.ldy = ldy;
+  b.omega = omega;
+  b.eta = eta;
+  b.diag = nullptr;
+  b.dsign = sector == GFCC_SECTOR_IP ? 1.0 : -1.0;
+  b.zsign = sector == GFCC_SECTOR_IP ? -1.0 : 1.0;
+  return sector == GFCC_SECTOR_IP ? apply_ip(c, b, sigma_work) : apply_ea(c, b, sigma_work);
 }
 
 int Gmres::op(const double *x, long long ldx, double *yout, long long ldy) {
@@ -381,6 +421,10 @@ int Gmres::op(const double *x, long long ldx, double *yout, long long ldy) {
   b.diag = use_precond ? (sector == GFCC_SECTOR_IP ? c->diag_ip : c->diag_ea) : nullptr;
   b.dsign = sector == GFCC_SECTOR_IP ? 1.0 : -1.0;
   b.zsign = sector == GFCC_SECTOR_IP ? -1.0 : 1.0;
+  if (mixed && sector == GFCC_SECTOR_IP) {
+    double *mw = sigma_work + sigma_work_doubles(c, sector, nsys);
+    return apply_ip_mixed(c, b, mw);
+  }
   return sector == GFCC_SECTOR_IP ? apply_ip(c, b, sigma_work) : apply_ea(c, b, sigma_work);
 }
 
@@ -389,15 +433,16 @@ int Gmres::mdot(const double *Vb, long long vs, long long vi, int nv, const doub
                 int want, int accumulate) {
   cudaStream_t st = c->stream;
   dim3 grid(nch, nsys);
-  mdot_partial_kernel<<<grid, DOT_THREADS, 0, st>>>(Vb, vs, vi, nv, w, ws, n, nch, state, want, partial, NV);
+  const int *filt = want < 0 ? nullptr : state;   // want < 0: every system
+  mdot_partial_kernel<<<grid, DOT_THREADS, 0, st>>>(Vb, vs, vi, nv, w, ws, n, nch, filt, want, partial, NV);
   GFCC_LAUNCH_CHECK();
   const int warps = nsys * nv;
-  mdot_final_kernel<<<cdiv(warps * 32LL, 256), 256, 0, st>>>(partial, nsys, nv, NV, nch, state, want, out, accumulate);
+  mdot_final_kernel<<<cdiv(warps * 32LL, 256), 256, 0, st>>>(partial, nsys, nv, NV, nch, filt, want, out, accumulate);
   GFCC_LAUNCH_CHECK();
   return GFCC_OK;
 }
 
-int Gmres::solve(double tol, int max_iters, int *h_state) {
+int Gmres::solve(double tol, int max_iters, int *h_state, int max_cycles) {
   cudaStream_t st = c->stream;
   const long long vs = (long long)(m + 1) * n;   // basis stride per system (complex elements)
   const int T = 256;
@@ -411,6 +456,12 @@ int Gmres::solve(double tol, int max_iters, int *h_state) {
   GFCC_LAUNCH_CHECK();
   bool first = true;
   for (int cycle = 0;; cycle++) {
+    if (max_cycles > 0 && cycle >= max_cycles) {
+      // cycle budget spent: the systems still pending keep their iterate (state 4)
+      set_state_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, state, ST_PENDING, ST_FAILED);
+      GFCC_LAUNCH_CHECK();
+      break;
+    }
     // true residual r = b - A x into V_0 (x = 0 on the first cycle)
     if (first) {
       GFCC_CUDA(cudaMemsetAsync(W, 0, sizeof(double) * 2 * nsys * n, st));
@@ -437,6 +488,8 @@ int Gmres::solve(double tol, int max_iters, int *h_state) {
       double *w = V + 2 * (long long)(k + 1) * n;
       GFCC_TRY(op(vk, vs, w, vs));
       // CGS2: h = V^H w, w -= V h, h2 = V^H w, w -= V h2, h += h2, then ||w||^2 into h[k+1]
+      {
+      PhaseTimer ta(c, PH_ARNOLDI);
       GFCC_TRY(mdot(V, vs, n, k + 1, w, vs, h, ST_IN_CYCLE, 0));
       vupdate_kernel<<<grid1d(n * nsys), T, 0, st>>>(V, vs, n, k + 1, nullptr, h, NV, -1.0, w, vs, n, nsys, state,
                                                       ST_IN_CYCLE);
@@ -450,8 +503,13 @@ int Gmres::solve(double tol, int max_iters, int *h_state) {
       GFCC_TRY(mdot(w, vs, 0, 1, w, vs, h + 2 * (k + 1), ST_IN_CYCLE, 0));
       vscale_kernel<<<grid1d(n * nsys), T, 0, st>>>(w, vs, n, nsys, h, NV, k + 1, state, ST_IN_CYCLE);
       GFCC_LAUNCH_CHECK();
-      givens_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, k, m, h, NV, H, cs, sn, g, bnorm, tol, state, kcyc, iters, est);
-      GFCC_LAUNCH_CHECK();
+      }
+      {
+        PhaseTimer tl(c, PH_LSQ);
+        givens_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, k, m, h, NV, H, cs, sn, g, bnorm, tol, state, kcyc, iters,
+                                                   est);
+        GFCC_LAUNCH_CHECK();
+      }
       GFCC_CUDA(cudaMemcpyAsync(h_state, state, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
       GFCC_CUDA(cudaStreamSynchronize(st));
       bool in_cycle = false;
@@ -473,6 +531,92 @@ int Gmres::solve(double tol, int max_iters, int *h_state) {
         sector == GFCC_SECTOR_IP ? c->diag_ip : c->diag_ea, sector == GFCC_SECTOR_IP ? 1.0 : -1.0);
     GFCC_LAUNCH_CHECK();
   }
+  return GFCC_OK;
+}
+
+namespace {
+// y = a - b (all systems, contiguous [s][n] complex)
+__global__ void sub_kernel(const double *a, const double *b, double *y, long long tot) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
+    y[t] = a[t] - b[t];
+}
+// x += d (all systems)
+__global__ void add_kernel(double *x, const double *d, long long tot) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
+    x[t] += d[t];
+}
+// per system: relres = ||r|| / ||b0||; done systems get r = 0 so that the inner solve leaves them alone
+__global__ void refine_check_kernel(int nsys, const double *nrm2, int NV, const double *b0norm, double tol, int *done,
+                                    double *relres) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys) return;
+  const double r = sqrt(fmax(nrm2[2 * (long long)s * NV], 0.0));
+  relres[s] = b0norm[s] > 0.0 ? r / b0norm[s] : 0.0;
+  done[s] = (b0norm[s] == 0.0 || r <= tol * b0norm[s]) ? 1 : 0;
+}
+__global__ void zero_done_kernel(double *R, long long n, int nsys, const int *done) {
+  const long long tot = n * nsys;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
+    if (done[t / n]) {
+      R[2 * t] = 0.0;
+      R[2 * t + 1] = 0.0;
+    }
+}
+}  // namespace
+
+int Gmres::solve_refined(double tol, double inner_tol, int max_iters, int *h_state, int *h_iters) {
+  cudaStream_t st = c->stream;
+  const long long tot = 2LL * nsys * n;
+  const int T = 256;
+  std::vector<int> h_done(nsys, 0), it(nsys, 0);
+  for (int s = 0; s < nsys; s++) h_iters[s] = 0;
+  GFCC_CUDA(cudaMemcpyAsync(B0, B, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
+  GFCC_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * tot, st));
+  // ||b0|| into est (a free per-system slot during refinement)
+  GFCC_TRY(mdot(B0, n, 0, 1, B0, n, nrm, -1, 0));
+  int *done = kcyc;   // reused: per-system done flags between inner solves
+  norm_from_partial_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, nrm, NV, b0norm);
+  GFCC_LAUNCH_CHECK();
+  const int max_outer = 400;
+  bool all_done = false;
+  for (int outer = 0; outer <= max_outer; outer++) {
+    if (outer == 0) {
+      GFCC_CUDA(cudaMemcpyAsync(R, B0, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
+    } else {
+      GFCC_TRY(op_fp64(X, n, W, n));
+      sub_kernel<<<grid1d(tot), T, 0, st>>>(B0, W, R, tot);
+      GFCC_LAUNCH_CHECK();
+    }
+    GFCC_TRY(mdot(R, n, 0, 1, R, n, nrm, -1, 0));
+    refine_check_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, nrm, NV, b0norm, tol, done, relres);
+    GFCC_LAUNCH_CHECK();
+    GFCC_CUDA(cudaMemcpyAsync(h_done.data(), done, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
+    GFCC_CUDA(cudaStreamSynchronize(st));
+    all_done = true;
+    bool any_active = false;
+    for (int s = 0; s < nsys; s++) {
+      all_done &= h_done[s] != 0;
+      // a system over its iteration budget stops here (not converged); the others go on
+      if (!h_done[s] && h_iters[s] >= max_iters) h_done[s] = 2;
+      any_active |= h_done[s] == 0;
+    }
+    if (all_done || !any_active || outer == max_outer) break;
+    GFCC_CUDA(cudaMemcpyAsync(done, h_done.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+    zero_done_kernel<<<grid1d(n * nsys), T, 0, st>>>(R, n, nsys, done);
+    GFCC_LAUNCH_CHECK();
+    GFCC_CUDA(cudaMemcpyAsync(B, R, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
+    GFCC_TRY(solve(inner_tol, max_iters, h_state, c->inner_cycles));
+    GFCC_CUDA(cudaMemcpyAsync(it.data(), iters, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
+    GFCC_CUDA(cudaStreamSynchronize(st));
+    for (int s = 0; s < nsys; s++) h_iters[s] += it[s];
+    add_kernel<<<grid1d(tot), T, 0, st>>>(X, U, tot);
+    GFCC_LAUNCH_CHECK();
+  }
+  // final state: converged where the FP64 residual met tol
+  for (int s = 0; s < nsys; s++) h_state[s] = h_done[s] == 1 ? 3 : 4;
+  GFCC_CUDA(cudaMemcpyAsync(state, h_state, sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+  GFCC_CUDA(cudaMemcpyAsync(U, X, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
+  GFCC_CUDA(cudaMemcpyAsync(iters, h_iters, sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
   return GFCC_OK;
 }
 

@@ -4,7 +4,7 @@
 
 namespace gfcc {
 
-long long gmres_work_doubles(const gfcc_ctx *c, int sector, long long n, int nsys, int m);
+long long gmres_work_doubles(const gfcc_ctx *c, int sector, long long n, int nsys, int m, bool mixed = false);
 
 // One batch of nsys systems of packed dimension n in one sector.  The caller fills B
 // (right-hand sides, complex interleaved, [s][n]) and omega, then calls solve(); the
@@ -17,6 +17,9 @@ struct Gmres {
   int nsys = 0, m = 30, NV = 32, nch = 1;
   double eta = 0.0;
   bool use_precond = false;
+  bool mixed = false;      // inner operator on the BF16 tensor cores (IP), FP64 residuals outside
+  double *X = nullptr, *R = nullptr, *B0 = nullptr;   // refinement: solution, residual, original rhs
+  double *b0norm = nullptr;
   double *V = nullptr, *U = nullptr, *B = nullptr, *W = nullptr;
   double *partial = nullptr, *h = nullptr, *h2 = nullptr, *y = nullptr, *nrm = nullptr;
   double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr;
@@ -24,11 +27,17 @@ struct Gmres {
   int *state = nullptr, *kcyc = nullptr, *iters = nullptr;
   double *sigma_work = nullptr;
 
-  int init(gfcc_ctx *ctx, int sector, long long n, int nsys, int m, double *work);
-  int op(const double *x, long long ldx, double *y, long long ldy);
+  int init(gfcc_ctx *ctx, int sector, long long n, int nsys, int m, double *work, bool mixed = false);
+  int op(const double *x, long long ldx, double *y, long long ldy);          // the inner operator
+  int op_fp64(const double *x, long long ldx, double *y, long long ldy);     // FP64, no preconditioner
   int mdot(const double *Vb, long long vs, long long vi, int nv, const double *w, long long ws, double *out, int want,
            int accumulate);
-  int solve(double tol, int max_iters, int *h_state);
+  // max_cycles > 0 bounds the number of restart cycles (systems left pending end in state 4)
+  int solve(double tol, int max_iters, int *h_state, int max_cycles = 0);
+  // iterative refinement: FP64 residual r = b - A x, inner GMRES on the mixed operator to
+  // inner_tol, x += d, until ||r|| <= tol ||b||.  Leaves x in U, the FP64 relative residual in
+  // relres, the summed inner iterations in h_iters and the final state (3 / 4) in h_state.
+  int solve_refined(double tol, double inner_tol, int max_iters, int *h_state, int *h_iters);
 };
 
 }  // namespace gfcc

@@ -1,0 +1,157 @@
+// FP64-accurate matrix products on the BF16 tensor cores by exact digit splitting
+// (the splitting scheme of Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 59 (2012), with
+// fixed-point digits per row).
+//
+// GB300 runs FP64 at about 1.1 TFLOP/s, three orders of magnitude below its BF16 tensor
+// rate.  A row r of an FP64 operand is scaled by a power of two 2^-e_r so that its entries
+// lie in (-1/2, 1/2), then written as S base-64 digits
+//     a = 2^e_r * sum_{i=1..S} d_i 64^-i + rem,   d_i integer, |d_i| <= 32, |rem| <= 2^e_r 64^-S / 2.
+// Digits are exact in BF16 (8 significant bits).  A digit product is an integer of magnitude
+// <= 2^10, so a sum of up to 2^14 of them is an integer of magnitude <= 2^24 and the FP32
+// accumulation of the tensor cores is exact.  The product of two operands is then
+//     sum_k A[m][k] B[n][k] = 2^(e_m + f_n) sum_{i,j} 64^-(i+j) sum_k dA_i[m][k] dB_j[n][k]
+// and the digit-pair products with i + j <= P are evaluated as BF16 GEMMs (K split into
+// chunks of 2^14 with separate FP32 partial sums) and combined in FP64.  The truncation
+// error per term is bounded by about 2^-(6P-4) of 2^(e_m + f_n); P = S + 1.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "ozaki.cuh"
+#include "umma.cuh"
+
+namespace gfcc {
+
+namespace {
+
+constexpr int KCHUNK_BLOCKS = (1 << 14) / 64;   // K blocks (of 64) per exact partial sum
+
+// e[r] such that max_k |A[r][k]| * 2^-e[r] lies in [1/4, 1/2); rows of zeros get 0
+__global__ void rowexp_kernel(const double *A, long long rows, long long K, long long lda, int *e) {
+  __shared__ double sh[32];
+  const long long r = blockIdx.x;
+  if (r >= rows) return;
+  double mx = 0.0;
+  for (long long k = threadIdx.x; k < K; k += blockDim.x) mx = fmax(mx, fabs(A[r * lda + k]));
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) mx = fmax(mx, sh[w]);
+    int E = 0;
+    if (mx > 0.0) frexp(mx, &E);   // mx = f 2^E, f in [1/2, 1)
+    e[r] = mx > 0.0 ? E + 1 : 0;
+  }
+}
+
+// dig[i][r][k] = i-th base-64 digit of A[r][k] 2^-e[r] (k < K), 0 for K <= k < ld
+__global__ void slice_kernel(const double *A, long long rows, long long K, long long lda, const int *e, int S,
+                             __nv_bfloat16 *dig, long long ld) {
+  const long long tot = rows * ld;
+  const long long plane = rows * ld;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long r = t / ld, k = t - r * ld;
+    double x = k < K ? scalbn(A[r * lda + k], -e[r]) : 0.0;
+    for (int i = 0; i < S; i++) {
+      const double y = x * 64.0;
+      const double d = rint(y);
+      x = y - d;
+      dig[i * plane + t] = __double2bfloat16(d);
+    }
+  }
+}
+
+// acc[t] += scale * sum_z part[z][t]
+__global__ void combine_kernel(const float *part, int nz, long long tot, double scale, double *acc, int first) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < nz; z++) s += (double)part[(long long)z * tot + t];
+    acc[t] = first ? scale * s : acc[t] + scale * s;
+  }
+}
+
+// C(m, n) = alpha * 2^(eA[m] + eB[n]) acc[m][n] + beta * C(m, n)
+__global__ void finalize_kernel(const double *acc, long long M, long long N, const int *eA, const int *eB, double alpha,
+                                double beta, double *C, IMap cm, IMap cn) {
+  const long long tot = M * N;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long m = t / N, n = t - m * N;
+    const long long off = imap_apply(cm, m) + imap_apply(cn, n);
+    const double v = alpha * scalbn(acc[t], eA[m] + eB[n]);
+    C[off] = beta != 0.0 ? v + beta * C[off] : v;
+  }
+}
+
+}  // namespace
+
+long long emu_operand_bytes(long long rows, long long K, int S) {
+  const long long ld = (K + 7) / 8 * 8;
+  return (long long)S * rows * ld * 2 + ((rows * 4 + 255) / 256) * 256 + 256;
+}
+
+int emu_slice(cudaStream_t st, const double *A, long long rows, long long K, long long lda, int S, void *mem,
+              EmuOperand &out) {
+  out.rows = rows;
+  out.K = K;
+  out.ld = (K + 7) / 8 * 8;
+  out.S = S;
+  unsigned char *p = static_cast<unsigned char *>(mem);
+  out.dig = reinterpret_cast<__nv_bfloat16 *>(p);
+  p += ((long long)S * rows * out.ld * 2 + 255) / 256 * 256;
+  out.exp2 = reinterpret_cast<int *>(p);
+  if (rows <= 0 || K <= 0) return GFCC_OK;
+  GFCC_TRY(check_extent(A, 0, (rows - 1) * lda + K - 1, "digit split input"));
+  GFCC_TRY(check_extent_bytes(mem, emu_operand_bytes(rows, K, S), "digit split output"));
+  if (rows > 0x7fffffffLL) {
+    set_error("emu_slice: too many rows (%lld)", rows);
+    return GFCC_ERR_ARG;
+  }
+  rowexp_kernel<<<(unsigned)rows, 256, 0, st>>>(A, rows, K, lda, out.exp2);
+  GFCC_LAUNCH_CHECK();
+  slice_kernel<<<grid1d(rows * out.ld), 256, 0, st>>>(A, rows, K, lda, out.exp2, S, out.dig, out.ld);
+  GFCC_LAUNCH_CHECK();
+  return GFCC_OK;
+}
+
+long long emu_gemm_work_bytes(long long M, long long N, long long K) {
+  const long long nk = (K + 63) / 64;
+  const long long nz = (nk + KCHUNK_BLOCKS - 1) / KCHUNK_BLOCKS;
+  return nz * M * N * 4 + M * N * 8 + 512;
+}
+
+int emu_gemm(cudaStream_t st, const EmuOperand &A, const EmuOperand &B, int P, double alpha, double beta, double *C,
+             IMap cm, IMap cn, void *work) {
+  const long long M = A.rows, N = B.rows, K = A.K;
+  if (M <= 0 || N <= 0) return GFCC_OK;
+  if (B.K != K || A.ld != B.ld) {
+    set_error("emu_gemm: operands disagree in K (%lld vs %lld)", A.K, B.K);
+    return GFCC_ERR_ARG;
+  }
+  const long long nk = (K + 63) / 64;
+  const int nz = (int)((nk + KCHUNK_BLOCKS - 1) / KCHUNK_BLOCKS);
+  float *part = static_cast<float *>(work);
+  double *acc = reinterpret_cast<double *>(static_cast<unsigned char *>(work) + ((nz * M * N * 4 + 255) / 256) * 256);
+  GFCC_TRY(check_extent_bytes(work, emu_gemm_work_bytes(M, N, K), "digit GEMM workspace"));
+  GFCC_TRY(check_extent(C, 0, imap_max(cm, M) + imap_max(cn, N), "digit GEMM output"));
+  const long long plA = A.rows * A.ld, plB = B.rows * B.ld;
+  bool first = true;
+  // smallest contributions first
+  for (int L = P; L >= 2; L--) {
+    for (int i = 1; i <= A.S; i++) {
+      const int j = L - i;
+      if (j < 1 || j > B.S) continue;
+      GFCC_TRY(gemm_bf16_tn(st, A.dig + (long long)(i - 1) * plA, A.ld, B.dig + (long long)(j - 1) * plB, B.ld, part,
+                            N, (int)M, (int)N, (int)K, 1.0f, 0.0f, nz, M * N));
+      combine_kernel<<<grid1d(M * N), 256, 0, st>>>(part, umma_splits((int)K, nz), M * N, scalbn(1.0, -6 * L), acc,
+                                                     first ? 1 : 0);
+      GFCC_LAUNCH_CHECK();
+      first = false;
+    }
+  }
+  if (first) GFCC_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * M * N, st));
+  finalize_kernel<<<grid1d(M * N), 256, 0, st>>>(acc, M, N, A.exp2, B.exp2, alpha, beta, C, cm, cn);
+  GFCC_LAUNCH_CHECK();
+  return GFCC_OK;
+}
+
+}  // namespace gfcc

@@ -1,0 +1,26 @@
+// FP64-accurate products from BF16 digit planes on the tensor cores (ozaki.cu).
+#pragma once
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace gfcc {
+
+// An FP64 matrix (rows x K, K-major) split into S base-64 digit planes with a power-of-two
+// scale per row: A[r][k] ~= 2^exp2[r] sum_i dig[i][r][k] 64^-(i+1).
+struct EmuOperand {
+  __nv_bfloat16 *dig = nullptr;   // [S][rows][ld]
+  int *exp2 = nullptr;            // [rows]
+  long long rows = 0, K = 0, ld = 0;
+  int S = 0;
+};
+
+long long emu_operand_bytes(long long rows, long long K, int S);
+int emu_slice(cudaStream_t st, const double *A, long long rows, long long K, long long lda, int S, void *mem,
+              EmuOperand &out);
+long long emu_gemm_work_bytes(long long M, long long N, long long K);
+// C(m, n) = alpha * sum_k A[m][k] B[n][k] + beta * C(m, n) with digit pairs i + j <= P
+int emu_gemm(cudaStream_t st, const EmuOperand &A, const EmuOperand &B, int P, double alpha, double beta, double *C,
+             IMap cm, IMap cn, void *work);
+
+}  // namespace gfcc

@@ -23,6 +23,7 @@
 
 #include "ctx.cuh"
 #include "kernels.cuh"
+#include "ozaki.cuh"
 
 namespace gfcc {
 
@@ -135,7 +136,37 @@ __global__ void diag_ea_kernel(const double *Foo, const double *Fvv, int o, int 
   }
 }
 
+// out[r][c] = bf16(scale * in[r * ld_in + c]) for c < cols (columns up to ld_out are zeroed)
+__global__ void to_bf16_kernel(const double *in, long long rows, long long cols, long long ld_in, double scale,
+                               __nv_bfloat16 *out, long long ld_out) {
+  const long long tot = rows * ld_out;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < tot; x += (long long)gridDim.x * blockDim.x) {
+    const long long r = x / ld_out, c = x - r * ld_out;
+    out[x] = __double2bfloat16(c < cols ? scale * in[r * ld_in + c] : 0.0);
+  }
+}
+
+// remove the Fock-like diagonal element of the folded ring matrix: Wr[(i,a)][(i,a)] -= cvv Fvv[a][a] + coo Foo[i][i]
+__global__ void ring_undiag_kernel(double *Wr, int o, int v, const double *Foo, const double *Fvv, double cvv,
+                                   double coo) {
+  const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long ov = (long long)o * v;
+  if (row >= ov) return;
+  const int i = (int)(row / v), a = (int)(row % v);
+  Wr[row * ov + row] -= cvv * Fvv[(long long)a * v + a] + coo * Foo[(long long)i * o + i];
+}
+
+// U1x[i][o2v + m] = -Foo[m][i] for m != i (the off-diagonal part of the 1h row)
+__global__ void u1_foo_kernel(double *U1x, int o, long long o2v, long long ld, const double *Foo) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= o * o) return;
+  const int i = t / o, m = t % o;
+  U1x[(long long)i * ld + o2v + m] = (m == i) ? 0.0 : -Foo[(long long)m * o + i];
+}
+
 }  // namespace
+
+static inline long long round8(long long x) { return (x + 7) / 8 * 8; }
 
 int permute4(cudaStream_t st, const long long d[4], const double *in, const long long is[4], double *out,
              const long long os[4], double alpha, double beta) {
@@ -189,6 +220,22 @@ int dev_alloc_tmp(double **p, long long count) {
 }
 
 namespace {
+
+int alloc_bf16(gfcc_ctx *c, __nv_bfloat16 **p, long long count) {
+  double *d = nullptr;
+  GFCC_TRY(dev_alloc(c, &d, (count + 3) / 4));
+  *p = reinterpret_cast<__nv_bfloat16 *>(d);
+  return GFCC_OK;
+}
+
+int to_bf16(cudaStream_t st, const double *in, long long rows, long long cols, long long ld_in, double scale,
+            __nv_bfloat16 *out, long long ld_out) {
+  GFCC_TRY(check_extent(in, 0, (rows - 1) * ld_in + cols - 1, "bf16 conversion input"));
+  GFCC_TRY(check_extent_bytes(out, rows * ld_out * 2, "bf16 conversion output"));
+  to_bf16_kernel<<<grid1d(rows * ld_out), 256, 0, st>>>(in, rows, cols, ld_in, scale, out, ld_out);
+  GFCC_LAUNCH_CHECK();
+  return GFCC_OK;
+}
 
 // RAII holder of setup temporaries.
 struct Tmp {
@@ -382,6 +429,7 @@ int build_hbar(gfcc_ctx *c, const double *d_fock, const double *d_chol) {
     GFCC_TRY(dev_alloc(c, &c->diag_ip, c->dim_ip));
     diag_ip_kernel<<<grid1d(c->dim_ip), 256, 0, st>>>(c->Foo, c->Fvv, o, v, c->diag_ip);
     GFCC_LAUNCH_CHECK();
+
   }
 
   if (want_ea) {
@@ -478,6 +526,92 @@ int build_hbar(gfcc_ctx *c, const double *d_fock, const double *d_chol) {
       const long long os[4] = {vv, ov2, 1, v};
       GFCC_TRY(permute4(st, d, vc, is, c->U1e + m0 * vv, os, -0.5, 1.0));
     }
+  }
+  // BF16 operands of the mixed-precision sigma, after every FP64 term is in place
+  if (want_ip && c->precision == GFCC_PREC_MIXED_BF16) {
+    // BF16 operands of the mixed-precision sigma (the Fock-like diagonal stays in FP64)
+    c->ld_ov = round8(ov);
+    c->ld_o2 = round8(oo);
+    c->ld_o = round8(o);
+    c->ld_o2v = round8(o2v);
+    c->ld_v = round8(v);
+    c->ld_k1 = round8(o2v + o);
+    double *t;
+    GFCC_TRY(tmp.get(&t, std::max(ov * ov, o * (o2v + o))));
+    GFCC_CUDA(cudaMemcpyAsync(t, wr_core, sizeof(double) * ov * ov, cudaMemcpyDeviceToDevice, st));
+    ring_diag_kernel<<<cdiv(ov, 128), 128, 0, st>>>(t, o, v, c->Foo, c->Fvv, 0.5, -1.0);
+    GFCC_LAUNCH_CHECK();
+    ring_undiag_kernel<<<cdiv(ov, 128), 128, 0, st>>>(t, o, v, c->Foo, c->Fvv, 0.5, -1.0);
+    GFCC_LAUNCH_CHECK();
+    GFCC_TRY(alloc_bf16(c, &c->Wr_bf, ov * c->ld_ov));
+    GFCC_TRY(to_bf16(st, t, ov, ov, ov, 1.0, c->Wr_bf, c->ld_ov));
+    // Wq[(i,j)][(m,n)] = 1/2 Woooo[m][n][i][j]
+    {
+      const long long d[4] = {o, o, o, o};          // (i, j, m, n)
+      const long long is[4] = {o, 1, o * oo, oo};
+      const long long os[4] = {o * oo, oo, o, 1};
+      GFCC_TRY(permute4(st, d, c->Woooo, is, t, os, 1.0, 0.0));
+    }
+    GFCC_TRY(alloc_bf16(c, &c->Wq_bf, oo * c->ld_o2));
+    GFCC_TRY(to_bf16(st, t, oo, oo, oo, 0.5, c->Wq_bf, c->ld_o2));
+    GFCC_TRY(alloc_bf16(c, &c->W1_bf, o2v * c->ld_o));
+    GFCC_TRY(to_bf16(st, c->W1, o2v, o, o, 1.0, c->W1_bf, c->ld_o));
+    GFCC_TRY(alloc_bf16(c, &c->V3_bf, v * c->ld_o2v));
+    GFCC_TRY(to_bf16(st, c->V3, v, o2v, o2v, 1.0, c->V3_bf, c->ld_o2v));
+    GFCC_TRY(alloc_bf16(c, &c->T3_bf, o2v * c->ld_v));
+    GFCC_TRY(to_bf16(st, c->T3, o2v, v, v, 1.0, c->T3_bf, c->ld_v));
+    // U1x[i] = [U1[i][(m,e,n)] | -Foo_offdiag[m][i]]
+    {
+      const long long d[4] = {1, 1, o, o2v};
+      const long long is[4] = {0, 0, o2v, 1};
+      const long long os[4] = {0, 0, o2v + o, 1};
+      GFCC_TRY(permute4(st, d, c->U1, is, t, os, 1.0, 0.0));
+    }
+    u1_foo_kernel<<<cdiv(oo, 128), 128, 0, st>>>(t, o, o2v, o2v + o, c->Foo);
+    GFCC_LAUNCH_CHECK();
+    GFCC_TRY(alloc_bf16(c, &c->U1_bf, o * c->ld_k1));
+    GFCC_TRY(to_bf16(st, t, o, o2v + o, o2v + o, 1.0, c->U1_bf, c->ld_k1));
+
+    // digit planes of the FP64 operands (full Fock folding) for the FP64-accurate residual
+    const int S = c->emu_S;
+    auto slice = [&](const double *A, long long rows, long long K, long long lda, EmuOperand &e) -> int {
+      double *mem;
+      GFCC_TRY(dev_alloc(c, &mem, emu_operand_bytes(rows, K, S) / 8 + 1));
+      return emu_slice(st, A, rows, K, lda, S, mem, e);
+    };
+    GFCC_TRY(slice(c->Wr_ip, ov, ov, ov, c->eWr));
+    {
+      const long long d[4] = {o, o, o, o};          // (i, j, m, n)
+      const long long is[4] = {o, 1, o * oo, oo};
+      const long long os[4] = {o * oo, oo, o, 1};
+      GFCC_TRY(permute4(st, d, c->Woooo, is, t, os, 0.5, 0.0));
+    }
+    GFCC_TRY(slice(t, oo, oo, oo, c->eWq));
+    GFCC_TRY(slice(c->W1, o2v, o, o, c->eW1));
+    GFCC_TRY(slice(c->T3, o2v, v, v, c->eT3));
+    double *t2x;
+    GFCC_TRY(tmp.get(&t2x, std::max(v, o) * (o2v + o)));
+    {
+      // [V3 | 0]: V3 padded to the K of the 1h row
+      GFCC_TRY(fill_f64(st, t2x, v * (o2v + o), 0.0));
+      const long long d[4] = {1, 1, v, o2v};
+      const long long is[4] = {0, 0, o2v, 1};
+      const long long os[4] = {0, 0, o2v + o, 1};
+      GFCC_TRY(permute4(st, d, c->V3, is, t2x, os, 1.0, 0.0));
+    }
+    GFCC_TRY(slice(t2x, v, o2v + o, o2v + o, c->eV3));
+    {
+      // [U1 | -Fbar_oo^T]: the 1h row with the full Fbar_oo
+      const long long d[4] = {1, 1, o, o2v};
+      const long long is[4] = {0, 0, o2v, 1};
+      const long long os[4] = {0, 0, o2v + o, 1};
+      GFCC_TRY(permute4(st, d, c->U1, is, t2x, os, 1.0, 0.0));
+      const long long d2[4] = {1, 1, o, o};             // (i, m): t2x[i][o2v + m] = -Foo[m][i]
+      const long long is2[4] = {0, 0, 1, o};
+      const long long os2[4] = {0, 0, o2v + o, 1};
+      GFCC_TRY(permute4(st, d2, c->Foo, is2, t2x + o2v, os2, -1.0, 0.0));
+    }
+    GFCC_TRY(slice(t2x, o, o2v + o, o2v + o, c->eU1));
   }
   GFCC_CUDA(cudaStreamSynchronize(st));
   return GFCC_OK;

@@ -200,6 +200,14 @@ __global__ void epilogue_ea_kernel(SysBatch b, int o, int v, long long Pv, long 
 
 }  // namespace
 
+int launch_epilogue_ip(gfcc_ctx *c, const SysBatch &b, const double *S1, const double *T, const double *Q,
+                       const double *U) {
+  const long long C2 = 2LL * b.nsys;
+  epilogue_ip_kernel<<<grid1d(c->dim_ip * b.nsys), 256, 0, c->stream>>>(b, c->o, c->v, C2, c->dim_ip, S1, T, Q, U);
+  GFCC_LAUNCH_CHECK();
+  return GFCC_OK;
+}
+
 long long sigma_work_doubles(const gfcc_ctx *c, int sector, int nsys) {
   const long long o = c->o, v = c->v, C2 = 2LL * nsys;
   if (sector == GFCC_SECTOR_IP) return (o + 4 * o * o * v + v + o) * C2 + 64;
@@ -217,11 +225,15 @@ int apply_ip(gfcc_ctx *c, const SysBatch &b, double *work) {
   double *U = Q + o * o * v * C2;
   double *Z = U + o * v * o * C2;
   double *S1 = Z + v * C2;
+  PhaseTimer tsig(c, PH_SIGMA);
   unpack_ip_kernel<<<grid1d((o * v * o + o) * b.nsys), 256, 0, st>>>(b, (int)o, (int)v, C2, r1u, r2u);
   GFCC_LAUNCH_CHECK();
   // ring + Fock terms: T[(i,a)][(j,c)] = Wr[(i,a)][(m,e)] r2u[(m,e)][(j,c)]
-  GFCC_TRY(gemm_f64(st, ov, o * C2, ov, 1.0, c->Wr_ip, imap1(ov), imap1(1), r2u, imap1(o * C2), imap1(1), 0.0, T,
-                    imap1(o * C2), imap1(1)));
+  {
+    PhaseTimer tr(c, PH_RING, 2.0 * (double)ov * (double)ov * (double)(o * C2));
+    GFCC_TRY(gemm_f64(st, ov, o * C2, ov, 1.0, c->Wr_ip, imap1(ov), imap1(1), r2u, imap1(o * C2), imap1(1), 0.0, T,
+                      imap1(o * C2), imap1(1)));
+  }
   // Q[(i,j)][(a,c)] = 1/2 sum_mn Woooo[m][n][i][j] r2u[m][a][n][c]
   GFCC_TRY(gemm_f64(st, o * o, v * C2, o * o, 0.5, c->Woooo, imap1(1), imap1(o * o), r2u,
                     imap2(o, C2, v * o * C2), imap2(C2, 1, o * C2), 0.0, Q, imap1(v * C2), imap1(1)));
@@ -253,14 +265,19 @@ int apply_ea(gfcc_ctx *c, const SysBatch &b, double *work) {
   double *Qp = y2p + Pv * o * C2;
   double *Z = Qp + Pv * o * C2;
   double *S1 = Z + o * C2;
+  PhaseTimer tsig(c, PH_SIGMA);
   unpack_ea_kernel<<<grid1d((o * v * v + Pv * o + v) * b.nsys), 256, 0, st>>>(b, (int)o, (int)v, Pv, C2, y1u, y2u,
                                                                               y2p);
   GFCC_LAUNCH_CHECK();
   // T[(i,b)][(a,c)] = Wr_ea[(i,b)][(m,e)] y2u[(m,e)][(a,c)]
-  GFCC_TRY(gemm_f64(st, ov, v * C2, ov, 1.0, c->Wr_ea, imap1(ov), imap1(1), y2u, imap1(v * C2), imap1(1), 0.0, T,
-                    imap1(v * C2), imap1(1)));
+  {
+    PhaseTimer tr(c, PH_RING, 2.0 * (double)ov * (double)ov * (double)(v * C2));
+    GFCC_TRY(gemm_f64(st, ov, v * C2, ov, 1.0, c->Wr_ea, imap1(ov), imap1(1), y2u, imap1(v * C2), imap1(1), 0.0, T,
+                      imap1(v * C2), imap1(1)));
+  }
   // Qp[(a<b)][(i,c)] = Wp[(ab)][(ef)] y2p[(ef)][(i,c)]
   if (Pv > 0) {
+    PhaseTimer tv(c, PH_VVVV, 2.0 * (double)Pv * (double)Pv * (double)(o * C2));
     GFCC_TRY(gemm_f64(st, Pv, o * C2, Pv, 1.0, c->Wp, imap1(Pv), imap1(1), y2p, imap1(o * C2), imap1(1), 0.0, Qp,
                       imap1(o * C2), imap1(1)));
   }

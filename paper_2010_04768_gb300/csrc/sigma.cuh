@@ -23,7 +23,17 @@ struct SysBatch {
 };
 
 long long sigma_work_doubles(const gfcc_ctx *c, int sector, int nsys);
+long long sigma_mixed_work_doubles(const gfcc_ctx *c, int nsys);
+// mixed precision (IP): BF16 tensor-core couplings + FP64 diagonal and shift (sigma_mixed.cu)
+int apply_ip_mixed(gfcc_ctx *c, const SysBatch &b, double *work);
 int apply_ip(gfcc_ctx *c, const SysBatch &b, double *work);
+// the FP64 epilogue of the IP operator on given S1 / T / Q / U (FP64, layouts of sigma.cu)
+int launch_epilogue_ip(gfcc_ctx *c, const SysBatch &b, const double *S1, const double *T, const double *Q,
+                       const double *U);
+// FP64-accurate IP operator from digit planes on the BF16 tensor cores (sigma_emu.cu); processes
+// the systems in sub-batches that fit its workspace
+long long sigma_emu_work_doubles(const gfcc_ctx *c, int nsub);
+int apply_ip_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_doubles);
 int apply_ea(gfcc_ctx *c, const SysBatch &b, double *work);
 
 }  // namespace gfcc

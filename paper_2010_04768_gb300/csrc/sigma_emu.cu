@@ -1,0 +1,238 @@
+// FP64-accurate IP operator y = (omega - i eta) x + sigma(x) evaluated from base-64 digit
+// planes on the BF16 tensor cores (ozaki.cu), for the residuals of the mixed-precision
+// refinement.  Same contractions and layouts as the BF16 operator of sigma_mixed.cu, but the
+// operator matrices carry the full Fock folding (the diagonal included) and every product is
+// FP64-accurate, so the refinement converges to the FP64 solution.
+//
+// Each vector plane (system s, re/im) shares one power-of-two scale: its packed entries are
+// written as digits of x 2^-e_c directly by the unpack kernels, so no FP64 copy of the
+// unpacked layouts is made.  Systems are processed in sub-batches that fit the workspace.
+#include <cuda_bf16.h>
+
+#include "ctx.cuh"
+#include "kernels.cuh"
+#include "ozaki.cuh"
+#include "sigma.cuh"
+#include "umma.cuh"
+
+namespace gfcc {
+
+namespace {
+
+// e[c] (c = 2 s + re/im) with max_mu |x_s| * 2^-e in [1/4, 1/2)
+__global__ void plane_exp_kernel(const double *x, long long ldx, long long n, int *e) {
+  __shared__ double sh[32];
+  const int c = blockIdx.x, s = c >> 1, t = c & 1;
+  double mx = 0.0;
+  for (long long mu = threadIdx.x; mu < n; mu += blockDim.x) mx = fmax(mx, fabs(x[2 * (s * ldx + mu) + t]));
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) mx = fmax(mx, sh[w]);
+    int E = 0;
+    if (mx > 0.0) frexp(mx, &E);
+    e[c] = mx > 0.0 ? E + 1 : 0;
+  }
+}
+
+__device__ __forceinline__ double packed_r2(const double *x, long long ldx, int o, int v, int c, int m, int j, int e) {
+  if (m == j) return 0.0;
+  const long long lo = m < j ? m : j, hi = m < j ? j : m;
+  const long long mu = o + pair_index(lo, hi, o) * v + e;
+  const double val = x[2 * ((long long)(c >> 1) * ldx + mu) + (c & 1)];
+  return m > j ? -val : val;
+}
+
+__device__ __forceinline__ void put_digits(double val, int ex, int S, __nv_bfloat16 *dst, long long plane) {
+  double r = scalbn(val, -ex);
+  for (int i = 0; i < S; i++) {
+    const double y = r * 64.0;
+    const double d = rint(y);
+    r = y - d;
+    dst[i * plane] = __double2bfloat16(d);
+  }
+}
+
+// digit planes of r2b[(j,c)][(m,e)] = r2[m,j,e]; exp2[row] = e_c
+__global__ void digits_ring_kernel(const double *x, long long ldx, int C2, int o, int v, const int *ec, int S,
+                                   long long ld, __nv_bfloat16 *dig, int *rexp) {
+  const long long K = (long long)o * v, rows = (long long)o * C2, plane = rows * ld;
+  const long long tot = rows * ld;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long row = t / ld, k = t - row * ld;
+    const int c = (int)(row % C2), j = (int)(row / C2);
+    double val = 0.0;
+    if (k < K) val = packed_r2(x, ldx, o, v, c, (int)(k / v), j, (int)(k % v));
+    put_digits(val, ec[c], S, dig + t, plane);
+    if (k == 0) rexp[row] = ec[c];
+  }
+}
+
+// digit planes of r2o[(a,c)][(m,n)] = r2[m,n,a]
+__global__ void digits_oooo_kernel(const double *x, long long ldx, int C2, int o, int v, const int *ec, int S,
+                                   long long ld, __nv_bfloat16 *dig, int *rexp) {
+  const long long K = (long long)o * o, rows = (long long)v * C2, plane = rows * ld;
+  const long long tot = rows * ld;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long row = t / ld, k = t - row * ld;
+    const int c = (int)(row % C2), a = (int)(row / C2);
+    double val = 0.0;
+    if (k < K) val = packed_r2(x, ldx, o, v, c, (int)(k / o), (int)(k % o), a);
+    put_digits(val, ec[c], S, dig + t, plane);
+    if (k == 0) rexp[row] = ec[c];
+  }
+}
+
+// digit planes of rk[c][(m,e,n) | m] = r2[m,n,e] | r1[m] and r1b[c][m] = r1[m]
+__global__ void digits_k_kernel(const double *x, long long ldx, int C2, int o, int v, const int *ec, int S,
+                                long long ldk, __nv_bfloat16 *digk, int *rexpk, long long ld1, __nv_bfloat16 *dig1,
+                                int *rexp1) {
+  const long long o2v = (long long)o * o * v, K = o2v + o;
+  const long long planek = (long long)C2 * ldk, plane1 = (long long)C2 * ld1;
+  const long long tot = (long long)C2 * ldk;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long k = t % ldk;
+    const int c = (int)(t / ldk);
+    double val = 0.0;
+    if (k < o2v) {
+      const int m = (int)(k / ((long long)v * o));
+      const long long r = k % ((long long)v * o);
+      val = packed_r2(x, ldx, o, v, c, m, (int)(r % o), (int)(r / o));
+    } else if (k < K) {
+      val = x[2 * ((long long)(c >> 1) * ldx + (k - o2v)) + (c & 1)];
+    }
+    put_digits(val, ec[c], S, digk + t, planek);
+    if (k >= o2v && k < K) put_digits(val, ec[c], S, dig1 + (long long)c * ld1 + (k - o2v), plane1);
+    if (k < ld1 && k >= o) {
+      // zero padding of r1b beyond o
+      for (int i = 0; i < S; i++) dig1[i * plane1 + (long long)c * ld1 + k] = __double2bfloat16(0.0);
+    }
+    if (k == 0) {
+      rexpk[c] = ec[c];
+      rexp1[c] = ec[c];
+    }
+  }
+}
+
+// Zt[c][e] = Z[e][c]
+__global__ void transpose_kernel(const double *Z, long long rows, long long cols, double *Zt) {
+  const long long tot = rows * cols;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long r = t / cols, c = t - r * cols;
+    Zt[c * rows + r] = Z[t];
+  }
+}
+
+struct EmuWork {
+  EmuOperand r2b, r2o, rk, r1b, Zo;
+  int *ec;
+  double *T, *Q, *U, *S1, *Z, *Zt;
+  void *gw;     // emu_gemm workspace
+  long long bytes;
+};
+
+EmuWork emu_layout(const gfcc_ctx *c, int nsub, void *base) {
+  const long long o = c->o, v = c->v, C2 = 2LL * nsub, S = c->emu_S;
+  const long long o2v = o * o * v;
+  EmuWork w;
+  unsigned char *p = static_cast<unsigned char *>(base);
+  auto take = [&](long long bytes) {
+    unsigned char *q = p;
+    p += (bytes + 255) / 256 * 256;
+    return q;
+  };
+  auto op = [&](EmuOperand &e, long long rows, long long K) {
+    e.rows = rows;
+    e.K = K;
+    e.ld = (K + 7) / 8 * 8;
+    e.S = (int)S;
+    e.dig = reinterpret_cast<__nv_bfloat16 *>(take(S * rows * e.ld * 2));
+    e.exp2 = reinterpret_cast<int *>(take(rows * 4));
+  };
+  op(w.r2b, o * C2, o * v);
+  op(w.r2o, v * C2, o * o);
+  op(w.rk, C2, o2v + o);
+  op(w.r1b, C2, o);
+  op(w.Zo, C2, v);
+  w.ec = reinterpret_cast<int *>(take(C2 * 4));
+  w.T = reinterpret_cast<double *>(take(o * v * o * C2 * 8));
+  w.Q = reinterpret_cast<double *>(take(o * o * v * C2 * 8));
+  w.U = reinterpret_cast<double *>(take(o * v * o * C2 * 8));
+  w.S1 = reinterpret_cast<double *>(take(o * C2 * 8));
+  w.Z = reinterpret_cast<double *>(take(v * C2 * 8));
+  w.Zt = reinterpret_cast<double *>(take(v * C2 * 8));
+  long long g = 0;
+  g = std::max(g, emu_gemm_work_bytes(o * v, o * C2, o * v));
+  g = std::max(g, emu_gemm_work_bytes(o * o, v * C2, o * o));
+  g = std::max(g, emu_gemm_work_bytes(o2v, C2, o));
+  g = std::max(g, emu_gemm_work_bytes(v, C2, o2v + o));
+  g = std::max(g, emu_gemm_work_bytes(o2v, C2, v));
+  g = std::max(g, emu_gemm_work_bytes(o, C2, o2v + o));
+  w.gw = take(g);
+  w.bytes = p - static_cast<unsigned char *>(base);
+  return w;
+}
+
+}  // namespace
+
+long long sigma_emu_work_doubles(const gfcc_ctx *c, int nsub) { return emu_layout(c, nsub, nullptr).bytes / 8 + 64; }
+
+int apply_ip_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_doubles) {
+  if (c->eWr.dig == nullptr) {
+    set_error("FP64-emulated residual requested but its digit planes were not built");
+    return GFCC_ERR_STATE;
+  }
+  cudaStream_t st = c->stream;
+  const long long o = c->o, v = c->v, oo = o * o, o2v = oo * v, n = c->dim_ip;
+  // largest sub-batch whose workspace fits
+  int nsub = b.nsys;
+  while (nsub > 1 && sigma_emu_work_doubles(c, nsub) > work_doubles) nsub = (nsub + 1) / 2;
+  if (sigma_emu_work_doubles(c, nsub) > work_doubles) {
+    set_error("apply_ip_emu: workspace too small for one system");
+    return GFCC_ERR_OOM;
+  }
+  const int S = c->emu_S, P = c->emu_P;
+  PhaseTimer tsig(c, PH_SIGMA);
+  for (int s0 = 0; s0 < b.nsys; s0 += nsub) {
+    const int ns = std::min(nsub, b.nsys - s0);
+    const int C2 = 2 * ns;
+    EmuWork w = emu_layout(c, ns, work);
+    const double *x = b.x + 2 * (long long)s0 * b.ldx;
+    plane_exp_kernel<<<C2, 256, 0, st>>>(x, b.ldx, n, w.ec);
+    GFCC_LAUNCH_CHECK();
+    digits_ring_kernel<<<grid1d(w.r2b.rows * w.r2b.ld), 256, 0, st>>>(x, b.ldx, C2, (int)o, (int)v, w.ec, S, w.r2b.ld,
+                                                                       w.r2b.dig, w.r2b.exp2);
+    GFCC_LAUNCH_CHECK();
+    digits_oooo_kernel<<<grid1d(w.r2o.rows * w.r2o.ld), 256, 0, st>>>(x, b.ldx, C2, (int)o, (int)v, w.ec, S, w.r2o.ld,
+                                                                       w.r2o.dig, w.r2o.exp2);
+    GFCC_LAUNCH_CHECK();
+    digits_k_kernel<<<grid1d((long long)C2 * w.rk.ld), 256, 0, st>>>(x, b.ldx, C2, (int)o, (int)v, w.ec, S, w.rk.ld,
+                                                                      w.rk.dig, w.rk.exp2, w.r1b.ld, w.r1b.dig,
+                                                                      w.r1b.exp2);
+    GFCC_LAUNCH_CHECK();
+    {
+      PhaseTimer tr(c, PH_RING, 2.0 * (double)(o * v) * (double)(o * v) * (double)(o * C2));
+      GFCC_TRY(emu_gemm(st, c->eWr, w.r2b, P, 1.0, 0.0, w.T, imap1(o * C2), imap1(1), w.gw));
+    }
+    GFCC_TRY(emu_gemm(st, c->eWq, w.r2o, P, 1.0, 0.0, w.Q, imap1(v * C2), imap1(1), w.gw));
+    GFCC_TRY(emu_gemm(st, c->eW1, w.r1b, P, 1.0, 0.0, w.U, imap1(C2), imap1(1), w.gw));
+    GFCC_TRY(emu_gemm(st, c->eV3, w.rk, P, 1.0, 0.0, w.Z, imap1(C2), imap1(1), w.gw));
+    transpose_kernel<<<grid1d(v * C2), 256, 0, st>>>(w.Z, v, C2, w.Zt);
+    GFCC_LAUNCH_CHECK();
+    GFCC_TRY(emu_slice(st, w.Zt, C2, v, v, S, w.Zo.dig, w.Zo));
+    GFCC_TRY(emu_gemm(st, c->eT3, w.Zo, P, 1.0, 1.0, w.U, imap1(C2), imap1(1), w.gw));
+    GFCC_TRY(emu_gemm(st, c->eU1, w.rk, P, 1.0, 0.0, w.S1, imap1(C2), imap1(1), w.gw));
+    SysBatch bb = b;
+    bb.nsys = ns;
+    bb.x = x;
+    bb.y = b.y + 2 * (long long)s0 * b.ldy;
+    bb.omega = b.omega ? b.omega + s0 : nullptr;
+    bb.diag = nullptr;
+    GFCC_TRY(launch_epilogue_ip(c, bb, w.S1, w.T, w.Q, w.U));
+  }
+  (void)o2v;
+  return GFCC_OK;
+}
+
+}  // namespace gfcc

@@ -1,0 +1,361 @@
+// BF16 x BF16 -> FP32 GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+//   D[m][n] = alpha * sum_k A[m][k] B[n][k] (+ beta * D[m][n])     (both operands K-major)
+//
+// This is the contraction engine of the mixed-precision sigma product: the ring
+// matrix Wbar_ovvo (and the other Hbar blocks) are stored once in BF16, the Krylov
+// vectors are rounded to BF16 when they are unpacked, products accumulate in FP32
+// in tensor memory (TMEM).
+//
+// Structure (one 128 x 256 output tile per CTA, 4 warps):
+//   * warp 0, one lane: TMA producer.  A tile 128 x 64 and B tile 256 x 64 (BF16,
+//     128-byte swizzle) per stage into a 4-stage shared-memory ring, completion
+//     tracked by mbarrier transaction counts.
+//   * warp 1, one lane: MMA issuer.  Four tcgen05.mma (M=128, N=256, K=16) per stage,
+//     accumulating in 256 TMEM columns; tcgen05.commit releases the stage.
+//   * all 4 warps: epilogue.  tcgen05.ld of the warp's 32 TMEM lanes, scale, store.
+// Every wait is bounded (about one second of %globaltimer); on time-out the CTA sets
+// the error flag, stops issuing work, drains what it issued and frees its TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "umma.cuh"
+
+namespace gfcc {
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4, THREADS = 128;
+constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+constexpr unsigned long long WAIT_NS = 1000000000ULL;   // bounded waits: 1 s
+
+__device__ unsigned int g_umma_error = 0;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned addr, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned addr, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(addr), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned addr, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of the given parity; false on time-out or abort.
+__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity, volatile int *abort_flag) {
+  if (mbar_try_wait(addr, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    if (mbar_try_wait(addr, parity)) return true;
+    if (*abort_flag) return false;
+    if (globaltimer() - t0 > WAIT_NS) {
+      *abort_flag = 1;
+      atomicOr(&g_umma_error, 1u);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap *map, unsigned mbar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(mbar), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ unsigned long long smem_desc(unsigned addr) {
+  unsigned long long d = 0;
+  d |= (unsigned long long)((addr & 0x3FFFF) >> 4);       // start address
+  d |= (unsigned long long)(16 >> 4) << 16;               // leading byte offset (unused for swizzled K-major)
+  d |= (unsigned long long)(1024 >> 4) << 32;             // stride byte offset
+  d |= 1ULL << 46;                                        // descriptor version
+  d |= 2ULL << 61;                                        // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B, FP32 accumulator, K-major A and B, M x N.
+__host__ __device__ constexpr unsigned idesc_bf16(int M, int N) {
+  return (1u << 4)                      // D format: F32
+         | (1u << 7)                    // A format: BF16
+         | (1u << 10)                   // B format: BF16
+         | ((unsigned)(N >> 3) << 17)   // N / 8
+         | ((unsigned)(M >> 4) << 24);  // M / 16
+}
+
+__device__ __forceinline__ void umma_bf16(unsigned d_tmem, unsigned long long a, unsigned long long b, unsigned idesc,
+                                          unsigned accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.u32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(unsigned mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_32(unsigned taddr, float (&v)[32]) {
+  unsigned r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    umma_bf16_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, float *D,
+                          long long ldd, int M, int N, int K, float alpha, float beta, int kb_per_split,
+                          long long split_stride) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + STAGES * STAGE_BYTES);
+  unsigned long long *full = bars, *empty = bars + STAGES, *done = bars + 2 * STAGES;
+  unsigned *tmem_slot = reinterpret_cast<unsigned *>(bars + 2 * STAGES + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  volatile int *issued = reinterpret_cast<volatile int *>(tmem_slot + 2);     // TMA stages issued
+  volatile int *consumed = reinterpret_cast<volatile int *>(tmem_slot + 3);   // stages the MMA warp waited for
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  // split-K: this CTA covers K blocks [kb0, kb1) and writes its partial sum to D + z * split_stride
+  const int nk_all = (K + BK - 1) / BK;
+  const int kb0 = blockIdx.z * kb_per_split;
+  const int kb1 = min(nk_all, kb0 + kb_per_split);
+  const int nk = kb1 - kb0;
+  D += (long long)blockIdx.z * split_stride;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; s++) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(done), 1);
+    *abort_flag = 0;
+    *issued = 0;
+    *consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {   // TMEM: 256 FP32 columns x 128 lanes for the accumulator
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    for (int kb = 0; kb < nk; kb++) {
+      const int s = kb % STAGES;
+      const unsigned ph = (kb / STAGES) & 1;
+      if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag)) break;
+      unsigned char *sa = smem + s * STAGE_BYTES;
+      unsigned char *sb = sa + A_BYTES;
+      mbar_expect_tx(smem_u32(&full[s]), STAGE_BYTES);
+      tma_load_2d(smem_u32(sa), &tmA, smem_u32(&full[s]), (kb0 + kb) * BK, m0);
+      tma_load_2d(smem_u32(sb), &tmB, smem_u32(&full[s]), (kb0 + kb) * BK, n0);
+      *issued = kb + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    const unsigned idesc = idesc_bf16(BM, BN);
+    bool ok = true;
+    for (int kb = 0; kb < nk && ok; kb++) {
+      const int s = kb % STAGES;
+      const unsigned ph = (kb / STAGES) & 1;
+      if (!mbar_wait(smem_u32(&full[s]), ph, abort_flag)) {
+        ok = false;
+        break;
+      }
+      *consumed = kb + 1;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const unsigned sa = smem_u32(smem + s * STAGE_BYTES);
+      const unsigned sb = sa + A_BYTES;
+#pragma unroll
+      for (int k = 0; k < BK / 16; k++) {
+        // advance 16 BF16 (32 bytes) along K inside the 128-byte swizzle atom
+        umma_bf16(tmem, smem_desc(sa + 32 * k), smem_desc(sb + 32 * k), idesc, (kb > 0 || k > 0) ? 1u : 0u);
+      }
+      umma_commit(smem_u32(&empty[s]));
+    }
+    umma_commit(smem_u32(done));   // arrives when every MMA issued above has completed
+  }
+  __syncwarp();
+
+  // ---------------- epilogue: all 4 warps
+  const bool ready = mbar_wait(smem_u32(done), 0, abort_flag);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // tcgen05.ld is warp-collective: take the decision per warp
+  if (__all_sync(0xffffffffu, ready && !*abort_flag)) {
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      float v[32];
+      tmem_ld_32(tmem + ((unsigned)(warp * 32) << 16) + c0, v);
+      if (row < M) {
+        float *dst = D + (long long)row * ldd + n0 + c0;
+        const int ncols = min(32, N - (n0 + c0));
+        if (ncols == 32 && beta == 0.0f && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+#pragma unroll
+          for (int i = 0; i < 32; i += 4)
+            *reinterpret_cast<float4 *>(dst + i) = make_float4(alpha * v[i], alpha * v[i + 1], alpha * v[i + 2],
+                                                               alpha * v[i + 3]);
+        } else {
+          for (int i = 0; i < ncols; i++) dst[i] = alpha * v[i] + (beta != 0.0f ? beta * dst[i] : 0.0f);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) {
+    // after a time-out: let the TMA copies this CTA issued land before its shared memory goes away
+    volatile int never = 0;
+    for (int kb = *consumed; kb < *issued; kb++) mbar_wait(smem_u32(&full[kb % STAGES]), (kb / STAGES) & 1, &never);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (fn == nullptr) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D K-major BF16 tensor map: rows x K (row stride ld elements), box 64 (K) x box_rows, 128-byte swizzle
+int make_map(CUtensorMap *map, const void *base, long long rows, long long K, long long ld, int box_rows) {
+  auto fn = encode_fn();
+  if (fn == nullptr) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return GFCC_ERR_CUDA;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d) for rows=%lld K=%lld ld=%lld", (int)r, rows, K, ld);
+    return GFCC_ERR_ARG;
+  }
+  return GFCC_OK;
+}
+
+}  // namespace
+
+int umma_splits(int K, int nsplit) {
+  const int nk = (K + BK - 1) / BK;
+  if (nsplit < 1) nsplit = 1;
+  if (nsplit > nk) nsplit = nk;
+  const int kbs = (nk + nsplit - 1) / nsplit;
+  return (nk + kbs - 1) / kbs;
+}
+
+int umma_error_reset(cudaStream_t st) {
+  const unsigned zero = 0;
+  GFCC_CUDA(cudaMemcpyToSymbolAsync(g_umma_error, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st));
+  return GFCC_OK;
+}
+
+int umma_error_check(cudaStream_t st) {
+  unsigned h = 0;
+  GFCC_CUDA(cudaMemcpyFromSymbolAsync(&h, g_umma_error, sizeof(h), 0, cudaMemcpyDeviceToHost, st));
+  GFCC_CUDA(cudaStreamSynchronize(st));
+  if (h != 0) {
+    set_error("a tensor-core GEMM wait timed out on the device");
+    return GFCC_ERR_TIMEOUT;
+  }
+  return GFCC_OK;
+}
+
+int gemm_bf16_tn(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const __nv_bfloat16 *B, long long ldb,
+                 float *D, long long ldd, int M, int N, int K, float alpha, float beta, int nsplit,
+                 long long split_stride) {
+  if (M <= 0 || N <= 0) return GFCC_OK;
+  const int nk = (K + BK - 1) / BK;
+  if (nsplit < 1) nsplit = 1;
+  if (nsplit > nk) nsplit = nk;
+  const int kbs = (nk + nsplit - 1) / nsplit;
+  nsplit = (nk + kbs - 1) / kbs;   // every split gets at least one K block
+  if (nsplit > 1 && (beta != 0.0f || split_stride < (long long)(M - 1) * ldd + N)) {
+    set_error("gemm_bf16_tn: split-K writes separate partial sums (beta must be 0, stride >= one output)");
+    return GFCC_ERR_ARG;
+  }
+  if (K <= 0 || (lda % 8) || (ldb % 8) || lda < K || ldb < K || ldd < N ||
+      (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15)) {
+    set_error("gemm_bf16_tn: need K > 0, 16-byte aligned operands and row strides that are multiples of 8 "
+              "(M=%d N=%d K=%d lda=%lld ldb=%lld)", M, N, K, lda, ldb);
+    return GFCC_ERR_ARG;
+  }
+  GFCC_TRY(check_extent_bytes(A, (long long)(M - 1) * lda * 2 + (long long)K * 2, "bf16 GEMM operand A"));
+  GFCC_TRY(check_extent_bytes(B, (long long)(N - 1) * ldb * 2 + (long long)K * 2, "bf16 GEMM operand B"));
+  GFCC_TRY(check_extent_bytes(D, ((long long)(M - 1) * ldd + N + (long long)(nsplit - 1) * split_stride) * 4,
+                              "bf16 GEMM output D"));
+  CUtensorMap ma, mb;
+  GFCC_TRY(make_map(&ma, A, M, K, lda, BM));
+  GFCC_TRY(make_map(&mb, B, N, K, ldb, BN));
+  static bool attr = false;
+  if (!attr) {
+    GFCC_CUDA(cudaFuncSetAttribute(umma_bf16_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    attr = true;
+  }
+  if ((N + BN - 1) / BN > 65535 || nsplit > 65535) {
+    set_error("gemm_bf16_tn: grid too large (N=%d, nsplit=%d)", N, nsplit);
+    return GFCC_ERR_ARG;
+  }
+  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, nsplit);
+  umma_bf16_gemm_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, D, ldd, M, N, K, alpha, beta, kbs, split_stride);
+  GFCC_LAUNCH_CHECK();
+  return GFCC_OK;
+}
+
+}  // namespace gfcc

@@ -19,12 +19,13 @@ WARN_NOT_CONVERGED = 1
 ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = -1, -2, -3, -4, -5
 
 SECTOR_IP, SECTOR_EA, SECTOR_BOTH = 1, 2, 3
-PREC_FP64, PREC_MIXED_BF16 = 0, 1
+PREC_FP64, PREC_MIXED_BF16, PREC_FP64_EMULATED = 0, 1, 2
 PRECOND_NONE, PRECOND_DIAG = 0, 1
 OPT_SECTOR, OPT_PRECISION, OPT_RESTART, OPT_MAX_ITERS, OPT_PRECOND, OPT_BATCH, OPT_INNER_TOL = 1, 2, 3, 4, 5, 6, 7
+OPT_RESIDUAL, OPT_INNER_CYCLES, OPT_EMU_LEVEL = 8, 9, 10
 
 _SECTORS = {"IP": SECTOR_IP, "EA": SECTOR_EA, "IP+EA": SECTOR_BOTH, "BOTH": SECTOR_BOTH}
-_PRECS = {"fp64": PREC_FP64, "mixed": PREC_MIXED_BF16, "bf16": PREC_MIXED_BF16}
+_PRECS = {"fp64": PREC_FP64, "mixed": PREC_MIXED_BF16, "bf16": PREC_MIXED_BF16, "fp64emu": PREC_FP64_EMULATED}
 
 _lib = None
 
@@ -56,15 +57,56 @@ def load():
     lib.gfcc_solve_device.argtypes = [P, ctypes.c_int, P, ctypes.c_double, ctypes.c_int, P, ctypes.c_double, P]
     lib.gfcc_last_stats.argtypes = [P, ip, ip, dp, ip]
     lib.gfcc_sigma.argtypes = [P, ctypes.c_int, ctypes.c_int, dp, dp]
+    lib.gfcc_sigma_ex.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
+    lib.gfcc_sigma_ex.restype = ctypes.c_int
     lib.gfcc_dims.argtypes = [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    lib.gfcc_profile.argtypes = [P, ctypes.c_int]
+    lib.gfcc_profile_read.argtypes = [P, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_longlong), dp]
+    lib.gfcc_launch_count.restype = ctypes.c_longlong
+    lib.gfcc_launch_count.argtypes = []
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.gfcc_selftest_gemm_bf16.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, fp, fp, fp]
+    lib.gfcc_selftest_gemm_bf16.restype = ctypes.c_int
+    lib.gfcc_selftest_gemm_f64emu.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int,
+                                              ctypes.c_int, dp]
+    lib.gfcc_selftest_gemm_f64emu.restype = ctypes.c_int
     lib.gfcc_destroy.argtypes = [P]
     lib.gfcc_destroy.restype = None
     lib.gfcc_last_error.restype = ctypes.c_char_p
     for name in ("gfcc_create", "gfcc_create_ex", "gfcc_set_option", "gfcc_set_stream", "gfcc_solve",
-                 "gfcc_solve_device", "gfcc_last_stats", "gfcc_sigma", "gfcc_dims"):
+                 "gfcc_solve_device", "gfcc_last_stats", "gfcc_sigma", "gfcc_dims", "gfcc_profile",
+                 "gfcc_profile_read"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
+
+
+def launch_count() -> int:
+    """Kernels launched by libgfcc in this process."""
+    return int(load().gfcc_launch_count())
+
+
+def selftest_gemm_bf16(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """D = bf16(A) @ bf16(B).T with FP32 accumulation on the tensor cores (A: M x K, B: N x K)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    M, K = A.shape
+    N = B.shape[0]
+    D = np.zeros((M, N), dtype=np.float32)
+    fp = ctypes.POINTER(ctypes.c_float)
+    _check(load().gfcc_selftest_gemm_bf16(M, N, K, A.ctypes.data_as(fp), B.ctypes.data_as(fp), D.ctypes.data_as(fp)))
+    return D
+
+
+def selftest_gemm_f64emu(A: np.ndarray, B: np.ndarray, S: int = 8, P: int = 9) -> np.ndarray:
+    """C = A @ B.T (FP64 inputs) from BF16 digit planes on the tensor cores."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    M, K = A.shape
+    N = B.shape[0]
+    C = np.zeros((M, N), dtype=np.float64)
+    _check(load().gfcc_selftest_gemm_f64emu(M, N, K, _dp(A), _dp(B), S, P, _dp(C)))
+    return C
 
 
 def _dp(a: np.ndarray):
@@ -153,11 +195,25 @@ class GFCC:
                                    _dp(rr), stt.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
         return it, rr, stt
 
-    def sigma(self, sector: str, X: np.ndarray) -> np.ndarray:
-        """sigma(x) for packed complex vectors X[n_vec][dim] (FP64)."""
+    PHASES = ("setup", "ring", "vvvv", "sigma", "arnoldi", "lsq", "overlap", "solve", "ring_bf16")
+
+    def profile(self, enable: bool = True):
+        _check(load().gfcc_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """{phase: (ms, count, flops)} for every profiling phase."""
+        out = {}
+        for k, name in enumerate(self.PHASES):
+            ms, n, fl = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+            _check(load().gfcc_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl)))
+            out[name] = (ms.value, n.value, fl.value)
+        return out
+
+    def sigma(self, sector: str, X: np.ndarray, precision: str = "fp64") -> np.ndarray:
+        """sigma(x) for packed complex vectors X[n_vec][dim]."""
         X = np.ascontiguousarray(np.atleast_2d(X), dtype=np.complex128)
         Y = np.zeros_like(X)
-        _check(load().gfcc_sigma(self._h, _SECTORS[sector], X.shape[0],
-                                 X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                 Y.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        _check(load().gfcc_sigma_ex(self._h, _SECTORS[sector], _PRECS[precision], X.shape[0],
+                                    X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    Y.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return Y

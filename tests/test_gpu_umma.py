@@ -1,0 +1,59 @@
+"""The tcgen05 BF16 contraction engine alone, through the C ABI (gfcc_selftest_gemm_bf16).
+
+Reference: the same BF16-rounded operands multiplied in float64; the kernel accumulates
+in FP32, so the bound is a few FP32 roundings per output relative to sum_k |a_k b_k|.
+"""
+import numpy as np
+import pytest
+
+from paper_2010_04768_gb300 import gfcc
+from paper_2010_04768_gb300.synthetic import normal
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16_round(x):
+    x32 = np.asarray(x, dtype=np.float32)
+    u = x32.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (128, 256, 256), (300, 520, 200), (1, 1, 8), (257, 100, 1000),
+                                   (512, 768, 4096)])
+def test_umma_bf16_gemm(M, N, K):
+    A = normal(1, 1, M * K).reshape(M, K).astype(np.float32)
+    B = normal(2, 1, N * K).reshape(N, K).astype(np.float32)
+    D = gfcc.selftest_gemm_bf16(A, B)
+    Ab, Bb = bf16_round(A), bf16_round(B)
+    ref = Ab @ Bb.T
+    scale = np.abs(Ab) @ np.abs(Bb).T
+    err = np.abs(D.astype(np.float64) - ref) / scale
+    assert err.max() <= 4 * K * 2.0**-24 + 1e-7
+
+
+def test_umma_integer_products_are_exact():
+    """Digit products |a b| <= 2^10 summed over K = 2^14 stay exact in the FP32 accumulator
+    (the property the FP64 emulation rests on)."""
+    M, N, K = 256, 256, 16384
+    rng = np.random.default_rng(5)
+    A = rng.integers(-32, 33, size=(M, K)).astype(np.float32)
+    B = rng.integers(-32, 33, size=(N, K)).astype(np.float32)
+    A[0, :] = 32
+    B[0, :] = 32                                   # one entry reaches exactly 2^24
+    D = gfcc.selftest_gemm_bf16(A, B)
+    ref = A.astype(np.int64) @ B.astype(np.int64).T
+    assert np.array_equal(D.astype(np.int64), ref)
+
+
+@pytest.mark.parametrize("M,N,K", [(200, 300, 700), (128, 256, 20000), (1, 5, 8)])
+def test_f64_emulation_accuracy(M, N, K):
+    rng = np.random.default_rng(M + N + K)
+    A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-3, 3, size=(M, 1)))
+    B = rng.standard_normal((N, K)) * np.exp(rng.uniform(-3, 3, size=(N, 1)))
+    ref = A @ B.T
+    scale = np.abs(A) @ np.abs(B).T
+    C = gfcc.selftest_gemm_f64emu(A, B, S=8, P=9)
+    assert (np.abs(C - ref) / scale).max() <= 1e-13
+    C6 = gfcc.selftest_gemm_f64emu(A, B, S=6, P=7)
+    assert (np.abs(C6 - ref) / scale).max() <= 3e-10
