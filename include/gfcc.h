@@ -165,7 +165,9 @@ int gfcc_dims(gfcc_ctx *ctx, long long *dim_ip, long long *dim_ea);
  * Phases: 0 setup (gfcc_create), 1 ring contraction of the sigma product, 2 EA vvvv contraction,
  * 3 whole sigma products (contains 1 and 2), 4 Arnoldi orthogonalisation, 5 Givens / least squares,
  * 6 right-hand sides, left vectors and overlaps, 7 whole gfcc_solve calls, 8 ring contraction on the
- * BF16 tensor cores (mixed precision; phase 1 is the FP64 ring contraction).
+ * BF16 tensor cores (mixed precision; phase 1 is the FP64 ring contraction), 9 FP64-accurate ring
+ * contraction of the refinement residual (digit planes; flops counted as tensor-core work), 10 expansion
+ * of packed vectors into contraction layouts.
  */
 int gfcc_profile(gfcc_ctx *ctx, int enable);
 int gfcc_profile_read(gfcc_ctx *ctx, int phase, double *ms, long long *count, double *flops);

@@ -485,7 +485,11 @@ int create_impl(int o, int v, int L, const double *fock, const double *chol, con
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool timed = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
     if (timed) cudaEventRecord(e0, c->stream);
+    // mixed-precision contexts build their large FP64 intermediates from digit planes on the
+    // tensor cores (FP64-accurate); FP64 contexts keep every contraction on the FP64 units
+    g_emulate_big = precision == GFCC_PREC_MIXED_BF16;
     s = build_hbar(c, d_fock, d_chol);
+    g_emulate_big = false;
     if (timed) {
       cudaEventRecord(e1, c->stream);
       cudaEventSynchronize(e1);

@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include "kernels.cuh"
+#include "ozaki.cuh"
 
 namespace gfcc {
 
@@ -134,6 +135,9 @@ double *g_splitk_buf = nullptr;
 long long g_splitk_cap = 0;
 }  // namespace
 
+thread_local bool g_emulate_big = false;
+double g_emulate_min_flops = 4e12;
+
 int gemm_f64(cudaStream_t st, long long M, long long N, long long K, double alpha,
              const double *A, IMap am, IMap ak, const double *B, IMap bk, IMap bn, double beta,
              double *C, IMap cm, IMap cn, long long batch, long long sab, long long sbb, long long scb) {
@@ -143,6 +147,10 @@ int gemm_f64(cudaStream_t st, long long M, long long N, long long K, double alph
   c.am = am; c.ak = ak; c.bk = bk; c.bn = bn; c.cm = cm; c.cn = cn;
   c.batch = batch; c.sab = sab; c.sbb = sbb; c.scb = scb;
   c.alpha = alpha; c.beta = beta;
+  // Large contractions (setup of big problems) go to the FP64-accurate digit-plane path on the
+  // tensor cores when enabled: at ~1 TFLOP/s of FP64 they would take minutes.
+  if (batch == 1 && g_emulate_big && 2.0 * (double)M * (double)N * (double)K >= g_emulate_min_flops)
+    return gemm_f64_emulated(st, M, N, K, alpha, A, am, ak, B, bk, bn, beta, C, cm, cn, 8, 9);
   // Few output tiles and a long K would leave most SMs idle: split K into partial sums.
   const long long tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN) * batch;
   if (batch == 1 && tiles < 152 && K >= 8192) {

@@ -18,7 +18,9 @@ enum GfccPhase {
   PH_OVERLAP = 6,     // right-hand sides, left vectors, G overlaps
   PH_SOLVE = 7,       // a whole gfcc_solve
   PH_RING_BF16 = 8,   // the ring contraction on the BF16 tensor cores (mixed precision)
-  PH_COUNT = 9
+  PH_RING_EMU = 9,    // the FP64-accurate ring contraction of the refinement residual (digit planes)
+  PH_UNPACK = 10,     // expansion of packed vectors into the contraction layouts (BF16 / digits)
+  PH_COUNT = 11
 };
 
 struct gfcc_ctx {

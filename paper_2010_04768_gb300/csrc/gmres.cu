@@ -280,6 +280,140 @@ __global__ void coef_add_kernel(int nsys, int nv, double *h, const double *h2, i
   h[q + 1] += h2[q + 1];
 }
 
+
+// ---------------------------------------------------------------- fused CGS2 passes
+// Each block handles one chunk of FUSED_CHUNK elements of one system; NVT >= nv is a compile-time
+// bound so that the per-thread basis values and dot accumulators stay in registers.
+constexpr int FUSED_THREADS = 256, FUSED_PER = 4, FUSED_CHUNK = FUSED_THREADS * FUSED_PER;
+
+template <int NVT>
+__device__ __forceinline__ void block_reduce_store(double2 (&acc)[NVT], int nv, double2 *sh, double *partial, int s,
+                                                   int NV, int nch, int chunk) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NVT; i++) {
+    if (i >= nv) break;
+    double2 v = acc[i];
+    for (int off = 16; off > 0; off >>= 1) {
+      v.x += __shfl_down_sync(0xffffffffu, v.x, off);
+      v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+    }
+    if (lane == 0) sh[warp * NVT + i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double2 t = make_double2(0.0, 0.0);
+    for (int w = 0; w < FUSED_THREADS / 32; w++) {
+      t.x += sh[w * NVT + threadIdx.x].x;
+      t.y += sh[w * NVT + threadIdx.x].y;
+    }
+    reinterpret_cast<double2 *>(partial)[((long long)s * NV + threadIdx.x) * nch + chunk] = t;
+  }
+}
+
+// pass 1: partial dots conj(V_i) . w
+template <int NVT>
+__global__ __launch_bounds__(FUSED_THREADS) void cgs_dots_kernel(const double *V, long long vs, long long vi, int nv,
+                                                                 const double *w, long long n, int nch,
+                                                                 const int *state, int want, double *partial, int NV) {
+  __shared__ double2 sh[(FUSED_THREADS / 32) * NVT];
+  const int s = blockIdx.y, chunk = blockIdx.x;
+  if (state[s] != want) return;
+  double2 acc[NVT];
+#pragma unroll
+  for (int i = 0; i < NVT; i++) acc[i] = make_double2(0.0, 0.0);
+  const double *ws = w + 2 * s * vs;
+  const double *Vs = V + 2 * s * vs;
+  for (int r = 0; r < FUSED_PER; r++) {
+    const long long mu = (long long)chunk * FUSED_CHUNK + threadIdx.x + (long long)r * FUSED_THREADS;
+    if (mu >= n) break;
+    const double2 x = ld2(ws, mu);
+#pragma unroll
+    for (int i = 0; i < NVT; i++) {
+      if (i >= nv) break;
+      const double2 a = ld2(Vs + 2 * i * vi, mu);
+      acc[i].x += a.x * x.x + a.y * x.y;
+      acc[i].y += a.x * x.y - a.y * x.x;
+    }
+  }
+  block_reduce_store<NVT>(acc, nv, sh, partial, s, NV, nch, chunk);
+}
+
+// pass 2: w -= V h1 (in place), then partial dots conj(V_i) . w  (each basis value read once)
+template <int NVT>
+__global__ __launch_bounds__(FUSED_THREADS) void cgs_update_dots_kernel(const double *V, long long vs, long long vi,
+                                                                        int nv, double *w, long long n, int nch,
+                                                                        const int *state, int want, const double *h1,
+                                                                        double *partial, int NV) {
+  __shared__ double2 sh[(FUSED_THREADS / 32) * NVT];
+  __shared__ double2 hh[NVT];
+  const int s = blockIdx.y, chunk = blockIdx.x;
+  if (state[s] != want) return;
+  if (threadIdx.x < nv) hh[threadIdx.x] = reinterpret_cast<const double2 *>(h1)[(long long)s * NV + threadIdx.x];
+  __syncthreads();
+  double2 acc[NVT];
+#pragma unroll
+  for (int i = 0; i < NVT; i++) acc[i] = make_double2(0.0, 0.0);
+  double *ws = w + 2 * s * vs;
+  const double *Vs = V + 2 * s * vs;
+  for (int r = 0; r < FUSED_PER; r++) {
+    const long long mu = (long long)chunk * FUSED_CHUNK + threadIdx.x + (long long)r * FUSED_THREADS;
+    if (mu >= n) break;
+    double2 x = ld2(ws, mu);
+#pragma unroll
+    for (int i = 0; i < NVT; i++) {
+      if (i >= nv) break;
+      const double2 a = ld2(Vs + 2 * i * vi, mu);
+      const double2 c = hh[i];
+      x.x -= c.x * a.x - c.y * a.y;
+      x.y -= c.x * a.y + c.y * a.x;
+    }
+    st2(ws, mu, x);
+    // second sweep over the same basis elements: served from L1
+#pragma unroll
+    for (int i = 0; i < NVT; i++) {
+      if (i >= nv) break;
+      const double2 a = ld2(Vs + 2 * i * vi, mu);
+      acc[i].x += a.x * x.x + a.y * x.y;
+      acc[i].y += a.x * x.y - a.y * x.x;
+    }
+  }
+  block_reduce_store<NVT>(acc, nv, sh, partial, s, NV, nch, chunk);
+}
+
+// pass 3: w -= V h2 (in place), then the partial squared norm of w
+template <int NVT>
+__global__ __launch_bounds__(FUSED_THREADS) void cgs_update_norm_kernel(const double *V, long long vs, long long vi,
+                                                                        int nv, double *w, long long n, int nch,
+                                                                        const int *state, int want, const double *h2,
+                                                                        double *partial, int NV) {
+  __shared__ double2 sh[(FUSED_THREADS / 32) * 1];
+  __shared__ double2 hh[NVT];
+  const int s = blockIdx.y, chunk = blockIdx.x;
+  if (state[s] != want) return;
+  if (threadIdx.x < nv) hh[threadIdx.x] = reinterpret_cast<const double2 *>(h2)[(long long)s * NV + threadIdx.x];
+  __syncthreads();
+  double2 acc[1] = {make_double2(0.0, 0.0)};
+  double *ws = w + 2 * s * vs;
+  const double *Vs = V + 2 * s * vs;
+  for (int r = 0; r < FUSED_PER; r++) {
+    const long long mu = (long long)chunk * FUSED_CHUNK + threadIdx.x + (long long)r * FUSED_THREADS;
+    if (mu >= n) break;
+    double2 x = ld2(ws, mu);
+#pragma unroll
+    for (int i = 0; i < NVT; i++) {
+      if (i >= nv) break;
+      const double2 a = ld2(Vs + 2 * i * vi, mu);
+      const double2 c = hh[i];
+      x.x -= c.x * a.x - c.y * a.y;
+      x.y -= c.x * a.y + c.y * a.x;
+    }
+    st2(ws, mu, x);
+    acc[0].x += x.x * x.x + x.y * x.y;
+  }
+  block_reduce_store<1>(acc, 1, sh, partial, s, NV, nch, chunk);
+}
+
 __global__ void set_state_kernel(int nsys, int *state, int from, int to) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s < nsys && state[s] == from) state[s] = to;
@@ -312,7 +446,7 @@ __global__ void norm_from_partial_kernel(int nsys, const double *nrm2, int NV, d
 
 long long gmres_work_doubles(const gfcc_ctx *c, int sector, long long n, int nsys, int m, bool mixed) {
   const long long NV = m + 2;
-  const long long nch = (n + DOT_CHUNK - 1) / DOT_CHUNK;
+  const long long nch = (n + FUSED_CHUNK - 1) / FUSED_CHUNK;   // the finer of the two chunkings
   long long w = 0;
   w += 2LL * nsys * (m + 1) * n;            // V
   w += 3 * 2LL * nsys * n;                  // U, B, W
@@ -339,6 +473,7 @@ int Gmres::init(gfcc_ctx *ctx, int sec, long long dim, int ns, int mm, double *w
   m = mm;
   NV = m + 2;
   nch = (int)((n + DOT_CHUNK - 1) / DOT_CHUNK);
+  const long long nch_alloc = (n + FUSED_CHUNK - 1) / FUSED_CHUNK;
   double *p = work;
   auto take = [&](double *&dst, long long cnt) {
     dst = p;
@@ -348,7 +483,7 @@ int Gmres::init(gfcc_ctx *ctx, int sec, long long dim, int ns, int mm, double *w
   take(U, 2LL * nsys * n);
   take(B, 2LL * nsys * n);
   take(W, 2LL * nsys * n);
-  take(partial, 2LL * nsys * NV * nch);
+  take(partial, 2LL * nsys * NV * nch_alloc);
   take(h, 2LL * nsys * NV);
   take(h2, 2LL * nsys * NV);
   take(y, 2LL * nsys * NV);
@@ -442,6 +577,56 @@ int Gmres::mdot(const double *Vb, long long vs, long long vi, int nv, const doub
   return GFCC_OK;
 }
 
+namespace {
+template <int NVT>
+void launch_cgs(int pass, dim3 grid, cudaStream_t st, const double *V, long long vs, int nv, double *w, long long n,
+                int nch, const int *state, const double *coef, double *partial, int NV) {
+  if (pass == 0)
+    cgs_dots_kernel<NVT><<<grid, FUSED_THREADS, 0, st>>>(V, vs, n, nv, w, n, nch, state, ST_IN_CYCLE, partial, NV);
+  else if (pass == 1)
+    cgs_update_dots_kernel<NVT><<<grid, FUSED_THREADS, 0, st>>>(V, vs, n, nv, w, n, nch, state, ST_IN_CYCLE, coef,
+                                                                 partial, NV);
+  else
+    cgs_update_norm_kernel<NVT><<<grid, FUSED_THREADS, 0, st>>>(V, vs, n, nv, w, n, nch, state, ST_IN_CYCLE, coef,
+                                                                 partial, NV);
+}
+}  // namespace
+
+int Gmres::cgs2(const double *Vb, long long vs, int nv, double *w, cudaStream_t st) {
+  const int nchf = (int)((n + FUSED_CHUNK - 1) / FUSED_CHUNK);   // partial is sized for this chunking
+  dim3 grid(nchf, nsys);
+  const int T = 256;
+  auto pass = [&](int p, const double *coef) -> int {
+    if (nv <= 8)
+      launch_cgs<8>(p, grid, st, Vb, vs, nv, w, n, nchf, state, coef, partial, NV);
+    else if (nv <= 16)
+      launch_cgs<16>(p, grid, st, Vb, vs, nv, w, n, nchf, state, coef, partial, NV);
+    else if (nv <= 32)
+      launch_cgs<32>(p, grid, st, Vb, vs, nv, w, n, nchf, state, coef, partial, NV);
+    else
+      launch_cgs<65>(p, grid, st, Vb, vs, nv, w, n, nchf, state, coef, partial, NV);
+    GFCC_LAUNCH_CHECK();
+    return GFCC_OK;
+  };
+  auto final = [&](int nvv, double *out) -> int {
+    mdot_final_kernel<<<cdiv(nsys * (long long)nvv * 32, 256), 256, 0, st>>>(partial, nsys, nvv, NV, nchf, state,
+                                                                             ST_IN_CYCLE, out, 0);
+    GFCC_LAUNCH_CHECK();
+    return GFCC_OK;
+  };
+  GFCC_TRY(pass(0, nullptr));
+  GFCC_TRY(final(nv, h));
+  GFCC_TRY(pass(1, h));
+  GFCC_TRY(final(nv, h2));
+  GFCC_TRY(pass(2, h2));
+  GFCC_TRY(final(1, h + 2 * nv));   // ||w||^2 into h[nv] (real part)
+  coef_add_kernel<<<cdiv((long long)nsys * nv, T), T, 0, st>>>(nsys, nv, h, h2, NV, state, ST_IN_CYCLE);
+  GFCC_LAUNCH_CHECK();
+  vscale_kernel<<<grid1d(n * nsys), T, 0, st>>>(w, vs, n, nsys, h, NV, nv, state, ST_IN_CYCLE);
+  GFCC_LAUNCH_CHECK();
+  return GFCC_OK;
+}
+
 int Gmres::solve(double tol, int max_iters, int *h_state, int max_cycles) {
   cudaStream_t st = c->stream;
   const long long vs = (long long)(m + 1) * n;   // basis stride per system (complex elements)
@@ -487,22 +672,11 @@ int Gmres::solve(double tol, int max_iters, int *h_state, int max_cycles) {
       double *vk = V + 2 * (long long)k * n;
       double *w = V + 2 * (long long)(k + 1) * n;
       GFCC_TRY(op(vk, vs, w, vs));
-      // CGS2: h = V^H w, w -= V h, h2 = V^H w, w -= V h2, h += h2, then ||w||^2 into h[k+1]
+      // CGS2 in three fused passes over the basis: h = V^H w; (w -= V h, h2 = V^H w);
+      // (w -= V h2, ||w||^2); then h += h2 and w /= ||w||
       {
-      PhaseTimer ta(c, PH_ARNOLDI);
-      GFCC_TRY(mdot(V, vs, n, k + 1, w, vs, h, ST_IN_CYCLE, 0));
-      vupdate_kernel<<<grid1d(n * nsys), T, 0, st>>>(V, vs, n, k + 1, nullptr, h, NV, -1.0, w, vs, n, nsys, state,
-                                                      ST_IN_CYCLE);
-      GFCC_LAUNCH_CHECK();
-      GFCC_TRY(mdot(V, vs, n, k + 1, w, vs, h2, ST_IN_CYCLE, 0));
-      vupdate_kernel<<<grid1d(n * nsys), T, 0, st>>>(V, vs, n, k + 1, nullptr, h2, NV, -1.0, w, vs, n, nsys, state,
-                                                      ST_IN_CYCLE);
-      GFCC_LAUNCH_CHECK();
-      coef_add_kernel<<<cdiv((long long)nsys * (k + 1), T), T, 0, st>>>(nsys, k + 1, h, h2, NV, state, ST_IN_CYCLE);
-      GFCC_LAUNCH_CHECK();
-      GFCC_TRY(mdot(w, vs, 0, 1, w, vs, h + 2 * (k + 1), ST_IN_CYCLE, 0));
-      vscale_kernel<<<grid1d(n * nsys), T, 0, st>>>(w, vs, n, nsys, h, NV, k + 1, state, ST_IN_CYCLE);
-      GFCC_LAUNCH_CHECK();
+        PhaseTimer ta(c, PH_ARNOLDI);
+        GFCC_TRY(cgs2(V, vs, k + 1, w, st));
       }
       {
         PhaseTimer tl(c, PH_LSQ);

@@ -34,6 +34,8 @@ struct Gmres {
            int accumulate);
   // max_cycles > 0 bounds the number of restart cycles (systems left pending end in state 4)
   int solve(double tol, int max_iters, int *h_state, int max_cycles = 0);
+  // one CGS2 orthogonalisation of w against basis vectors [0, nv) of every system in cycle
+  int cgs2(const double *Vb, long long vs, int nv, double *w, cudaStream_t st);
   // iterative refinement: FP64 residual r = b - A x, inner GMRES on the mixed operator to
   // inner_tol, x += d, until ||r|| <= tol ||b||.  Leaves x in U, the FP64 relative residual in
   // relres, the summed inner iterations in h_iters and the final state (3 / 4) in h_state.

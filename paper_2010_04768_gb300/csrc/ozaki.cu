@@ -15,6 +15,8 @@
 // error per term is bounded by about 2^-(6P-4) of 2^(e_m + f_n); P = S + 1.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "ozaki.cuh"
@@ -70,13 +72,13 @@ __global__ void combine_kernel(const float *part, int nz, long long tot, double 
   }
 }
 
-// C(m, n) = alpha * 2^(eA[m] + eB[n]) acc[m][n] + beta * C(m, n)
+// C(m, n0 + n) = alpha * 2^(eA[m] + eB[n]) acc[m][n] + beta * C(m, n0 + n)
 __global__ void finalize_kernel(const double *acc, long long M, long long N, const int *eA, const int *eB, double alpha,
-                                double beta, double *C, IMap cm, IMap cn) {
+                                double beta, double *C, IMap cm, IMap cn, long long n0) {
   const long long tot = M * N;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     const long long m = t / N, n = t - m * N;
-    const long long off = imap_apply(cm, m) + imap_apply(cn, n);
+    const long long off = imap_apply(cm, m) + imap_apply(cn, n0 + n);
     const double v = alpha * scalbn(acc[t], eA[m] + eB[n]);
     C[off] = beta != 0.0 ? v + beta * C[off] : v;
   }
@@ -120,7 +122,7 @@ long long emu_gemm_work_bytes(long long M, long long N, long long K) {
 }
 
 int emu_gemm(cudaStream_t st, const EmuOperand &A, const EmuOperand &B, int P, double alpha, double beta, double *C,
-             IMap cm, IMap cn, void *work) {
+             IMap cm, IMap cn, void *work, long long n0) {
   const long long M = A.rows, N = B.rows, K = A.K;
   if (M <= 0 || N <= 0) return GFCC_OK;
   if (B.K != K || A.ld != B.ld) {
@@ -132,7 +134,7 @@ int emu_gemm(cudaStream_t st, const EmuOperand &A, const EmuOperand &B, int P, d
   float *part = static_cast<float *>(work);
   double *acc = reinterpret_cast<double *>(static_cast<unsigned char *>(work) + ((nz * M * N * 4 + 255) / 256) * 256);
   GFCC_TRY(check_extent_bytes(work, emu_gemm_work_bytes(M, N, K), "digit GEMM workspace"));
-  GFCC_TRY(check_extent(C, 0, imap_max(cm, M) + imap_max(cn, N), "digit GEMM output"));
+  GFCC_TRY(check_extent(C, 0, imap_max(cm, M) + imap_max(cn, n0 + N), "digit GEMM output"));
   const long long plA = A.rows * A.ld, plB = B.rows * B.ld;
   bool first = true;
   // smallest contributions first
@@ -149,9 +151,70 @@ int emu_gemm(cudaStream_t st, const EmuOperand &A, const EmuOperand &B, int P, d
     }
   }
   if (first) GFCC_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * M * N, st));
-  finalize_kernel<<<grid1d(M * N), 256, 0, st>>>(acc, M, N, A.exp2, B.exp2, alpha, beta, C, cm, cn);
+  finalize_kernel<<<grid1d(M * N), 256, 0, st>>>(acc, M, N, A.exp2, B.exp2, alpha, beta, C, cm, cn, n0);
   GFCC_LAUNCH_CHECK();
   return GFCC_OK;
+}
+
+namespace {
+// G[r][k] = X[imap(rm, r) + imap(km, k)] for k < K, 0 for K <= k < ld
+__global__ void gather_kernel(const double *X, long long rows, long long K, long long ld, IMap rm, IMap km, long long r0,
+                              double *G) {
+  const long long tot = rows * ld;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long r = t / ld, k = t - r * ld;
+    G[t] = k < K ? X[imap_apply(rm, r0 + r) + imap_apply(km, k)] : 0.0;
+  }
+}
+}  // namespace
+
+int gemm_f64_emulated(cudaStream_t st, long long M, long long N, long long K, double alpha, const double *A, IMap am,
+                      IMap ak, const double *B, IMap bk, IMap bn, double beta, double *C, IMap cm, IMap cn, int S,
+                      int P) {
+  if (M <= 0 || N <= 0) return GFCC_OK;
+  GFCC_TRY(check_extent(A, 0, imap_max(am, M) + imap_max(ak, K), "emulated contraction operand A"));
+  GFCC_TRY(check_extent(B, 0, imap_max(bk, K) + imap_max(bn, N), "emulated contraction operand B"));
+  GFCC_TRY(check_extent(C, 0, imap_max(cm, M) + imap_max(cn, N), "emulated contraction output C"));
+  const long long ld = (K + 7) / 8 * 8;
+  // column blocks of B / C sized so that one pass stays within about 12 GB of temporaries
+  const long long budget = 12LL << 30;
+  const long long nk = (K + 63) / 64, nz = (nk + KCHUNK_BLOCKS - 1) / KCHUNK_BLOCKS;
+  const long long per_col = ld * 8 + (long long)S * ld * 2 + nz * M * 4 + M * 8;
+  long long nb = std::max<long long>(256, budget / std::max<long long>(per_col, 1));
+  nb = std::min(nb, N);
+  void *ag = nullptr, *adig = nullptr, *bg = nullptr, *bdig = nullptr, *w = nullptr;
+  int s = GFCC_OK;
+  if (dmalloc(&ag, sizeof(double) * M * ld) != cudaSuccess || dmalloc(&adig, emu_operand_bytes(M, K, S)) != cudaSuccess ||
+      dmalloc(&bg, sizeof(double) * nb * ld) != cudaSuccess || dmalloc(&bdig, emu_operand_bytes(nb, K, S)) != cudaSuccess ||
+      dmalloc(&w, emu_gemm_work_bytes(M, nb, K)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("emulated contraction: cannot allocate its temporaries (M=%lld N-block=%lld K=%lld)", M, nb, K);
+    s = GFCC_ERR_OOM;
+  }
+  EmuOperand ea, eb;
+  if (s == GFCC_OK) {
+    gather_kernel<<<grid1d(M * ld), 256, 0, st>>>(A, M, K, ld, am, ak, 0, static_cast<double *>(ag));
+    if (cudaGetLastError() != cudaSuccess) s = GFCC_ERR_CUDA;
+    count_launch();
+  }
+  if (s == GFCC_OK) s = emu_slice(st, static_cast<double *>(ag), M, K, ld, S, adig, ea);
+  for (long long n0 = 0; n0 < N && s == GFCC_OK; n0 += nb) {
+    const long long cols = std::min(nb, N - n0);
+    gather_kernel<<<grid1d(cols * ld), 256, 0, st>>>(B, cols, K, ld, bn, bk, n0, static_cast<double *>(bg));
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) {
+      s = GFCC_ERR_CUDA;
+      break;
+    }
+    s = emu_slice(st, static_cast<double *>(bg), cols, K, ld, S, bdig, eb);
+    if (s == GFCC_OK) s = emu_gemm(st, ea, eb, P, alpha, beta, C, cm, cn, w, n0);
+  }
+  if (s == GFCC_OK && cudaStreamSynchronize(st) != cudaSuccess) {
+    set_error("emulated contraction failed: %s", cudaGetErrorString(cudaGetLastError()));
+    s = GFCC_ERR_CUDA;
+  }
+  for (void *p : {ag, adig, bg, bdig, w}) dfree(p);
+  return s;
 }
 
 }  // namespace gfcc

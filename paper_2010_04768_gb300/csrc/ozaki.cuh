@@ -20,7 +20,13 @@ int emu_slice(cudaStream_t st, const double *A, long long rows, long long K, lon
               EmuOperand &out);
 long long emu_gemm_work_bytes(long long M, long long N, long long K);
 // C(m, n) = alpha * sum_k A[m][k] B[n][k] + beta * C(m, n) with digit pairs i + j <= P
+// (the output column index of B's row n is n0 + n)
 int emu_gemm(cudaStream_t st, const EmuOperand &A, const EmuOperand &B, int P, double alpha, double beta, double *C,
-             IMap cm, IMap cn, void *work);
+             IMap cm, IMap cn, void *work, long long n0 = 0);
+// A strided FP64 contraction (the index maps of gemm_f64) evaluated from digit planes: operands are
+// gathered K-major, split into S digits, multiplied pairwise (i + j <= P) and combined in FP64.
+int gemm_f64_emulated(cudaStream_t st, long long M, long long N, long long K, double alpha, const double *A, IMap am,
+                      IMap ak, const double *B, IMap bk, IMap bn, double beta, double *C, IMap cm, IMap cn, int S,
+                      int P);
 
 }  // namespace gfcc

@@ -208,6 +208,14 @@ int launch_epilogue_ip(gfcc_ctx *c, const SysBatch &b, const double *S1, const d
   return GFCC_OK;
 }
 
+double sigma_flops(const gfcc_ctx *c, int sector) {
+  const double o = c->o, v = c->v;
+  if (sector == GFCC_SECTOR_IP)
+    return 2.0 * (2 * o * o * o * v * v + 0.5 * o * o * o * o * v + 3 * o * o * v * v + 4 * o * o * o * v +
+                  2 * o * o * v + 2 * o * o);
+  return 2.0 * (2 * o * o * v * v * v + 0.5 * o * v * v * v * v + 3 * o * v * v * v + 3 * o * o * v * v);
+}
+
 long long sigma_work_doubles(const gfcc_ctx *c, int sector, int nsys) {
   const long long o = c->o, v = c->v, C2 = 2LL * nsys;
   if (sector == GFCC_SECTOR_IP) return (o + 4 * o * o * v + v + o) * C2 + 64;
@@ -225,7 +233,7 @@ int apply_ip(gfcc_ctx *c, const SysBatch &b, double *work) {
   double *U = Q + o * o * v * C2;
   double *Z = U + o * v * o * C2;
   double *S1 = Z + v * C2;
-  PhaseTimer tsig(c, PH_SIGMA);
+  PhaseTimer tsig(c, PH_SIGMA, b.nsys * sigma_flops(c, GFCC_SECTOR_IP));
   unpack_ip_kernel<<<grid1d((o * v * o + o) * b.nsys), 256, 0, st>>>(b, (int)o, (int)v, C2, r1u, r2u);
   GFCC_LAUNCH_CHECK();
   // ring + Fock terms: T[(i,a)][(j,c)] = Wr[(i,a)][(m,e)] r2u[(m,e)][(j,c)]
@@ -265,7 +273,7 @@ int apply_ea(gfcc_ctx *c, const SysBatch &b, double *work) {
   double *Qp = y2p + Pv * o * C2;
   double *Z = Qp + Pv * o * C2;
   double *S1 = Z + o * C2;
-  PhaseTimer tsig(c, PH_SIGMA);
+  PhaseTimer tsig(c, PH_SIGMA, b.nsys * sigma_flops(c, GFCC_SECTOR_EA));
   unpack_ea_kernel<<<grid1d((o * v * v + Pv * o + v) * b.nsys), 256, 0, st>>>(b, (int)o, (int)v, Pv, C2, y1u, y2u,
                                                                               y2p);
   GFCC_LAUNCH_CHECK();

@@ -23,6 +23,8 @@ struct SysBatch {
 };
 
 long long sigma_work_doubles(const gfcc_ctx *c, int sector, int nsys);
+// algorithmic flops of one complex sigma product (two real vectors)
+double sigma_flops(const gfcc_ctx *c, int sector);
 long long sigma_mixed_work_doubles(const gfcc_ctx *c, int nsys);
 // mixed precision (IP): BF16 tensor-core couplings + FP64 diagonal and shift (sigma_mixed.cu)
 int apply_ip_mixed(gfcc_ctx *c, const SysBatch &b, double *work);

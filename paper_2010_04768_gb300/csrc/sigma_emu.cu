@@ -69,46 +69,69 @@ __global__ void digits_ring_kernel(const double *x, long long ldx, int C2, int o
   }
 }
 
-// digit planes of r2o[(a,c)][(m,n)] = r2[m,n,a]
+// digit planes of r2o[(a,c)][(m,n)] = r2[m,n,a]: 32 x 32 tile transpose (reads along a, writes
+// along (m,n)); grid (ld/32, v/32, C2), block (32, 8); exp2[row] = e_c
 __global__ void digits_oooo_kernel(const double *x, long long ldx, int C2, int o, int v, const int *ec, int S,
                                    long long ld, __nv_bfloat16 *dig, int *rexp) {
+  __shared__ double tile[32][33];
   const long long K = (long long)o * o, rows = (long long)v * C2, plane = rows * ld;
-  const long long tot = rows * ld;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const long long row = t / ld, k = t - row * ld;
-    const int c = (int)(row % C2), a = (int)(row / C2);
-    double val = 0.0;
-    if (k < K) val = packed_r2(x, ldx, o, v, c, (int)(k / o), (int)(k % o), a);
-    put_digits(val, ec[c], S, dig + t, plane);
-    if (k == 0) rexp[row] = ec[c];
+  const int c = blockIdx.z;
+  const long long k0 = (long long)blockIdx.x * 32;
+  const int a0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const long long k = k0 + r;
+    const int a = a0 + threadIdx.x;
+    tile[r][threadIdx.x] = (k < K && a < v) ? packed_r2(x, ldx, o, v, c, (int)(k / o), (int)(k % o), a) : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int a = a0 + r;
+    const long long k = k0 + threadIdx.x;
+    if (a < v && k < ld) {
+      const long long row = (long long)a * C2 + c;
+      put_digits(tile[threadIdx.x][r], ec[c], S, dig + row * ld + k, plane);
+      if (k == 0) rexp[row] = ec[c];
+    }
   }
 }
 
-// digit planes of rk[c][(m,e,n) | m] = r2[m,n,e] | r1[m] and r1b[c][m] = r1[m]
-__global__ void digits_k_kernel(const double *x, long long ldx, int C2, int o, int v, const int *ec, int S,
-                                long long ldk, __nv_bfloat16 *digk, int *rexpk, long long ld1, __nv_bfloat16 *dig1,
-                                int *rexp1) {
-  const long long o2v = (long long)o * o * v, K = o2v + o;
+// digit planes of rk[c][(m,e,n)] = r2[m,n,e] (tile transpose over (e, n) for fixed m, c);
+// grid (o/32, v/32, o * C2), block (32, 8)
+__global__ void digits_k2_kernel(const double *x, long long ldx, int C2, int o, int v, const int *ec, int S,
+                                 long long ldk, __nv_bfloat16 *digk) {
+  __shared__ double tile[32][33];
+  const long long planek = (long long)C2 * ldk;
+  const int c = blockIdx.z % C2, m = blockIdx.z / C2;
+  const int n0 = blockIdx.x * 32, e0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int n = n0 + r, e = e0 + threadIdx.x;
+    tile[r][threadIdx.x] = (n < o && e < v) ? packed_r2(x, ldx, o, v, c, m, n, e) : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int e = e0 + r, n = n0 + threadIdx.x;
+    if (e < v && n < o)
+      put_digits(tile[threadIdx.x][r], ec[c], S, digk + (long long)c * ldk + ((long long)m * v + e) * o + n, planek);
+  }
+}
+
+// digit planes of the r1 part: rk[c][o2v + m] (and the zero padding of rk up to ldk), r1b[c][m]
+// (zero up to ld1); exponents of both operands
+__global__ void digits_k1_kernel(const double *x, long long ldx, int C2, int o, int v, const int *ec, int S,
+                                 long long ldk, __nv_bfloat16 *digk, int *rexpk, long long ld1, __nv_bfloat16 *dig1,
+                                 int *rexp1) {
+  const long long o2v = (long long)o * o * v;
   const long long planek = (long long)C2 * ldk, plane1 = (long long)C2 * ld1;
-  const long long tot = (long long)C2 * ldk;
+  const long long tail = ldk - o2v;   // r1 values plus padding
+  const long long tot = (long long)C2 * (tail > ld1 ? tail : ld1);
+  const long long span = tail > ld1 ? tail : ld1;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const long long k = t % ldk;
-    const int c = (int)(t / ldk);
-    double val = 0.0;
-    if (k < o2v) {
-      const int m = (int)(k / ((long long)v * o));
-      const long long r = k % ((long long)v * o);
-      val = packed_r2(x, ldx, o, v, c, m, (int)(r % o), (int)(r / o));
-    } else if (k < K) {
-      val = x[2 * ((long long)(c >> 1) * ldx + (k - o2v)) + (c & 1)];
-    }
-    put_digits(val, ec[c], S, digk + t, planek);
-    if (k >= o2v && k < K) put_digits(val, ec[c], S, dig1 + (long long)c * ld1 + (k - o2v), plane1);
-    if (k < ld1 && k >= o) {
-      // zero padding of r1b beyond o
-      for (int i = 0; i < S; i++) dig1[i * plane1 + (long long)c * ld1 + k] = __double2bfloat16(0.0);
-    }
-    if (k == 0) {
+    const int c = (int)(t / span);
+    const long long q = t % span;
+    const double val = q < o ? x[2 * ((long long)(c >> 1) * ldx + q) + (c & 1)] : 0.0;
+    if (q < tail) put_digits(val, ec[c], S, digk + (long long)c * ldk + o2v + q, planek);
+    if (q < ld1) put_digits(val, ec[c], S, dig1 + (long long)c * ld1 + q, plane1);
+    if (q == 0) {
       rexpk[c] = ec[c];
       rexp1[c] = ec[c];
     }
@@ -193,26 +216,36 @@ int apply_ip_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_do
     return GFCC_ERR_OOM;
   }
   const int S = c->emu_S, P = c->emu_P;
-  PhaseTimer tsig(c, PH_SIGMA);
+  PhaseTimer tsig(c, PH_SIGMA, b.nsys * sigma_flops(c, GFCC_SECTOR_IP));
   for (int s0 = 0; s0 < b.nsys; s0 += nsub) {
     const int ns = std::min(nsub, b.nsys - s0);
     const int C2 = 2 * ns;
     EmuWork w = emu_layout(c, ns, work);
     const double *x = b.x + 2 * (long long)s0 * b.ldx;
+    {
+    PhaseTimer tu(c, PH_UNPACK);
     plane_exp_kernel<<<C2, 256, 0, st>>>(x, b.ldx, n, w.ec);
     GFCC_LAUNCH_CHECK();
     digits_ring_kernel<<<grid1d(w.r2b.rows * w.r2b.ld), 256, 0, st>>>(x, b.ldx, C2, (int)o, (int)v, w.ec, S, w.r2b.ld,
                                                                        w.r2b.dig, w.r2b.exp2);
     GFCC_LAUNCH_CHECK();
-    digits_oooo_kernel<<<grid1d(w.r2o.rows * w.r2o.ld), 256, 0, st>>>(x, b.ldx, C2, (int)o, (int)v, w.ec, S, w.r2o.ld,
-                                                                       w.r2o.dig, w.r2o.exp2);
+    digits_oooo_kernel<<<dim3(cdiv(w.r2o.ld, 32), cdiv(v, 32), C2), dim3(32, 8), 0, st>>>(
+        x, b.ldx, C2, (int)o, (int)v, w.ec, S, w.r2o.ld, w.r2o.dig, w.r2o.exp2);
     GFCC_LAUNCH_CHECK();
-    digits_k_kernel<<<grid1d((long long)C2 * w.rk.ld), 256, 0, st>>>(x, b.ldx, C2, (int)o, (int)v, w.ec, S, w.rk.ld,
-                                                                      w.rk.dig, w.rk.exp2, w.r1b.ld, w.r1b.dig,
-                                                                      w.r1b.exp2);
+    digits_k2_kernel<<<dim3(cdiv(o, 32), cdiv(v, 32), o * C2), dim3(32, 8), 0, st>>>(x, b.ldx, C2, (int)o, (int)v,
+                                                                                    w.ec, S, w.rk.ld, w.rk.dig);
     GFCC_LAUNCH_CHECK();
+    digits_k1_kernel<<<grid1d((long long)C2 * std::max(w.rk.ld - o2v, w.r1b.ld)), 256, 0, st>>>(
+        x, b.ldx, C2, (int)o, (int)v, w.ec, S, w.rk.ld, w.rk.dig, w.rk.exp2, w.r1b.ld, w.r1b.dig, w.r1b.exp2);
+    GFCC_LAUNCH_CHECK();
+    }
     {
-      PhaseTimer tr(c, PH_RING, 2.0 * (double)(o * v) * (double)(o * v) * (double)(o * C2));
+      // tensor-core work: one BF16 GEMM per digit pair (i, j), i + j <= P
+      int pairs = 0;
+      for (int L = 2; L <= P; L++)
+        for (int i = 1; i <= S; i++)
+          if (L - i >= 1 && L - i <= S) pairs++;
+      PhaseTimer tr(c, PH_RING_EMU, pairs * 2.0 * (double)(o * v) * (double)(o * v) * (double)(o * C2));
       GFCC_TRY(emu_gemm(st, c->eWr, w.r2b, P, 1.0, 0.0, w.T, imap1(o * C2), imap1(1), w.gw));
     }
     GFCC_TRY(emu_gemm(st, c->eWq, w.r2o, P, 1.0, 0.0, w.Q, imap1(v * C2), imap1(1), w.gw));
@@ -231,7 +264,6 @@ int apply_ip_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_do
     bb.diag = nullptr;
     GFCC_TRY(launch_epilogue_ip(c, bb, w.S1, w.T, w.Q, w.U));
   }
-  (void)o2v;
   return GFCC_OK;
 }
 

@@ -69,43 +69,68 @@ __global__ void unpack_ring_kernel(SysBatch b, int o, int v, long long ld, __nv_
   }
 }
 
-// r2o[(a, c)][(m, n)] = r2[m, n, a]
+// r2o[(a, c)][(m, n)] = r2[m, n, a]: a 32 x 32 tile transpose through shared memory (reads
+// coalesced along a, writes coalesced along (m, n)).  grid (K/32, v/32, C2), block (32, 8).
 __global__ void unpack_oooo_kernel(SysBatch b, int o, int v, long long ld, __nv_bfloat16 *out) {
-  const int ns = b.nsys;
+  __shared__ float tile[32][33];
+  const int C2 = 2 * b.nsys;
   const long long K = (long long)o * o;
-  const long long tot = (long long)v * 2 * ns * K;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const long long k = t % K, row = t / K;
-    const int c = (int)(row % (2 * ns)), a = (int)(row / (2 * ns));
-    const int m = (int)(k / o), n = (int)(k % o);
-    const Cz u = r2_at(b, o, v, c >> 1, m, n, a);
-    out[row * ld + k] = __double2bfloat16((c & 1) ? u.i : u.r);
+  const int c = blockIdx.z, s = c >> 1;
+  const long long k0 = (long long)blockIdx.x * 32;
+  const int a0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const long long k = k0 + r;
+    const int a = a0 + threadIdx.x;
+    float val = 0.f;
+    if (k < K && a < v) {
+      const Cz u = r2_at(b, o, v, s, (int)(k / o), (int)(k % o), a);
+      val = (float)((c & 1) ? u.i : u.r);
+    }
+    tile[r][threadIdx.x] = val;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int a = a0 + r;
+    const long long k = k0 + threadIdx.x;
+    if (a < v && k < K) out[((long long)a * C2 + c) * ld + k] = __float2bfloat16(tile[threadIdx.x][r]);
   }
 }
 
-// rk[c][(m, e, n)] = r2[m, n, e];  rk[c][o2v + m] = r1[m];  r1b[c][m] = r1[m]
-__global__ void unpack_k_kernel(SysBatch b, int o, int v, long long ldk, __nv_bfloat16 *rk, long long ld1,
-                                __nv_bfloat16 *r1b) {
-  const int ns = b.nsys;
-  const long long o2v = (long long)o * o * v;
-  const long long K = o2v + o;
-  const long long tot = 2LL * ns * K;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const long long k = t % K;
-    const int c = (int)(t / K);
-    Cz u;
-    if (k < o2v) {
-      const int m = (int)(k / ((long long)v * o));
-      const long long r = k % ((long long)v * o);
-      const int e = (int)(r / o), n = (int)(r % o);
-      u = r2_at(b, o, v, c >> 1, m, n, e);
-    } else {
-      u = load_u(b, c >> 1, k - o2v);
+// rk[c][(m, e, n)] = r2[m, n, e] (tile transpose over (e, n) for fixed m, c: reads coalesced along
+// e, writes along n); grid (o/32, v/32, o * C2), block (32, 8)
+__global__ void unpack_k_tiled_kernel(SysBatch b, int o, int v, long long ldk, __nv_bfloat16 *rk) {
+  __shared__ float tile[32][33];
+  const int C2 = 2 * b.nsys;
+  const int c = blockIdx.z % C2, m = blockIdx.z / C2, s = c >> 1;
+  const int n0 = blockIdx.x * 32, e0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int n = n0 + r, e = e0 + threadIdx.x;
+    float val = 0.f;
+    if (n < o && e < v) {
+      const Cz u = r2_at(b, o, v, s, m, n, e);
+      val = (float)((c & 1) ? u.i : u.r);
     }
-    const __nv_bfloat16 h = __double2bfloat16((c & 1) ? u.i : u.r);
-    rk[(long long)c * ldk + k] = h;
-    if (k >= o2v) r1b[(long long)c * ld1 + (k - o2v)] = h;
+    tile[r][threadIdx.x] = val;
   }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int e = e0 + r, n = n0 + threadIdx.x;
+    if (e < v && n < o) rk[(long long)c * ldk + ((long long)m * v + e) * o + n] = __float2bfloat16(tile[threadIdx.x][r]);
+  }
+}
+
+// rk[c][o2v + m] = r1[m] and r1b[c][m] = r1[m]
+__global__ void unpack_r1_kernel(SysBatch b, int o, int v, long long ldk, __nv_bfloat16 *rk, long long ld1,
+                                 __nv_bfloat16 *r1b) {
+  const long long o2v = (long long)o * o * v;
+  const int C2 = 2 * b.nsys;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= C2 * o) return;
+  const int c = t / o, m = t % o;
+  const Cz u = load_u(b, c >> 1, m);
+  const __nv_bfloat16 h = __double2bfloat16((c & 1) ? u.i : u.r);
+  rk[(long long)c * ldk + o2v + m] = h;
+  r1b[(long long)c * ld1 + m] = h;
 }
 
 // out[r][c] = sum_z part[z][r][c] (in place into part[0]); optional BF16 transposed copy outT[c][r]
@@ -208,13 +233,20 @@ int apply_ip_mixed(gfcc_ctx *c, const SysBatch &b, double *work) {
   cudaStream_t st = c->stream;
   const long long o = c->o, v = c->v, ov = o * v, oo = o * o, o2v = oo * v, C2 = 2LL * b.nsys;
   MixedWork w = layout(c, b.nsys, work);
-  PhaseTimer tsig(c, PH_SIGMA);
+  PhaseTimer tsig(c, PH_SIGMA, b.nsys * sigma_flops(c, GFCC_SECTOR_IP));
+  {
+  PhaseTimer tu(c, PH_UNPACK);
   unpack_ring_kernel<<<grid1d(o * C2 * ov), 256, 0, st>>>(b, (int)o, (int)v, c->ld_ov, w.r2b);
   GFCC_LAUNCH_CHECK();
-  unpack_oooo_kernel<<<grid1d(v * C2 * oo), 256, 0, st>>>(b, (int)o, (int)v, c->ld_o2, w.r2o);
+  unpack_oooo_kernel<<<dim3(cdiv(oo, 32), cdiv(v, 32), C2), dim3(32, 8), 0, st>>>(b, (int)o, (int)v, c->ld_o2,
+                                                                                   w.r2o);
   GFCC_LAUNCH_CHECK();
-  unpack_k_kernel<<<grid1d(C2 * (o2v + o)), 256, 0, st>>>(b, (int)o, (int)v, c->ld_k1, w.rk, c->ld_o, w.r1b);
+  unpack_k_tiled_kernel<<<dim3(cdiv(o, 32), cdiv(v, 32), o * C2), dim3(32, 8), 0, st>>>(b, (int)o, (int)v, c->ld_k1,
+                                                                                        w.rk);
   GFCC_LAUNCH_CHECK();
+  unpack_r1_kernel<<<cdiv(C2 * o, 128), 128, 0, st>>>(b, (int)o, (int)v, c->ld_k1, w.rk, c->ld_o, w.r1b);
+  GFCC_LAUNCH_CHECK();
+  }
   {
     PhaseTimer tr(c, PH_RING_BF16, 2.0 * (double)ov * (double)ov * (double)(o * C2));
     GFCC_TRY(gemm_bf16_tn(st, c->Wr_bf, c->ld_ov, w.r2b, c->ld_ov, w.T, o * C2, (int)ov, (int)(o * C2), (int)ov, 1.0f,

@@ -195,7 +195,8 @@ class GFCC:
                                    _dp(rr), stt.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
         return it, rr, stt
 
-    PHASES = ("setup", "ring", "vvvv", "sigma", "arnoldi", "lsq", "overlap", "solve", "ring_bf16")
+    PHASES = ("setup", "ring", "vvvv", "sigma", "arnoldi", "lsq", "overlap", "solve", "ring_bf16", "ring_emu",
+              "unpack")
 
     def profile(self, enable: bool = True):
         _check(load().gfcc_profile(self._h, 1 if enable else 0))
