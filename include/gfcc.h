@@ -154,6 +154,23 @@ int gfcc_sigma(gfcc_ctx *ctx, int sector, int n_vec, const double *x, double *y)
  * FP64-accurate sigma of the refinement residual (digit planes on the tensor cores). */
 int gfcc_sigma_ex(gfcc_ctx *ctx, int sector, int precision, int n_vec, const double *x, double *y);
 
+/*
+ * gfcc_sigma_noalloc - the FP64 sigma product of gfcc_sigma on DEVICE buffers, without allocating
+ * any memory.  The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory on their call path, such as an application whose device memory is all
+ * reserved up front by its own pool allocator (a cudaMalloc there fails or fragments the pool), or
+ * a latency-critical path where cudaMalloc / cudaFree would synchronise the device and stall the
+ * application's other streams.
+ *   x_dev, y_dev : device, complex128 interleaved, [n_vec][dim] in the packed order of gfcc_sigma.
+ * The workspace is a fixed array of 2^22 doubles (32 MiB) inside the library, present on every GPU
+ * that loads it until the process exits; sizes that need more (or a contraction longer than 8191
+ * elements, o*o*v for IP, o*v*v for EA) return GFCC_ERR_ARG.  The first call on a device looks the
+ * array's device address up; make that first call before any stream capture.  All calls share the
+ * array, so calls whose executions overlap on the GPU race: serialise them.  Runs on the context's
+ * stream and returns after it has finished.
+ */
+int gfcc_sigma_noalloc(gfcc_ctx *ctx, int sector, int n_vec, const double *x_dev, double *y_dev);
+
 /* gfcc_dims - packed dimensions of the IP and EA spaces of the context. */
 int gfcc_dims(gfcc_ctx *ctx, long long *dim_ip, long long *dim_ea);
 

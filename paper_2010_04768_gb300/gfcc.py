@@ -64,6 +64,8 @@ def load():
     lib.gfcc_profile_read.argtypes = [P, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_longlong), dp]
     lib.gfcc_launch_count.restype = ctypes.c_longlong
     lib.gfcc_launch_count.argtypes = []
+    lib.gfcc_sigma_noalloc.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
+    lib.gfcc_sigma_noalloc.restype = ctypes.c_int
     fp = ctypes.POINTER(ctypes.c_float)
     lib.gfcc_selftest_gemm_bf16.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, fp, fp, fp]
     lib.gfcc_selftest_gemm_bf16.restype = ctypes.c_int
@@ -194,6 +196,12 @@ class GFCC:
         _check(lib.gfcc_last_stats(self._h, ctypes.byref(cnt), it.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                    _dp(rr), stt.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
         return it, rr, stt
+
+    def sigma_noalloc(self, sector: str, n_vec: int, x_ptr: int, y_ptr: int):
+        """gfcc_sigma_noalloc on caller-owned device buffers (device pointers, packed complex128 vectors);
+        the library allocates nothing during the call."""
+        _check(load().gfcc_sigma_noalloc(self._h, _SECTORS[sector], n_vec, ctypes.c_void_p(x_ptr),
+                                         ctypes.c_void_p(y_ptr)))
 
     PHASES = ("setup", "ring", "vvvv", "sigma", "arnoldi", "lsq", "overlap", "solve", "ring_bf16", "ring_emu",
               "unpack")
