@@ -88,6 +88,37 @@ __device__ __forceinline__ void pair_decode(long long idx, long long m, long lon
   j = idx - pair_start(ii, m) + ii + 1;
 }
 
+// FP64 -> FP32 by bit manipulation on the integer units (truncating the mantissa; values below the
+// FP32 normal range flush to zero, values above it saturate to infinity).  GB300 issues about two
+// FP64 operations per SM and clock, so kernels that only need FP32 accuracy avoid the FP64 pipe.
+__device__ __forceinline__ float d2f_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  if (e <= 0) return __int_as_float((int)sign);
+  if (e >= 255) return __int_as_float((int)(sign | 0x7f800000u));
+  return __int_as_float((int)(sign | ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7fffff)));
+}
+
+// Balanced base-64 digits of y = x 2^-ex (|y| < 1/2), S of them (S <= 10), with integer arithmetic:
+// Y = round(y 2^(6S)) from the FP64 bit pattern, then d_i = round(Y / 2^(6(S-i))) successively.
+__device__ __forceinline__ long long fixed_point(double x, int ex, int bits) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ff);
+  if (E == 0) return 0;   // zero (and subnormals, far below any digit)
+  const long long m = (long long)((b & 0xfffffffffffffULL) | 0x10000000000000ULL);
+  const int sh = E - 1075 - ex + bits;   // Y = m 2^sh
+  long long Y;
+  if (sh >= 0) {
+    Y = sh < 11 ? (m << sh) : 0;          // cannot happen for |y| < 1/2 and bits <= 60
+  } else if (sh > -63) {
+    Y = (m + (1LL << (-sh - 1))) >> (-sh);
+  } else {
+    Y = 0;
+  }
+  return (b >> 63) ? -Y : Y;
+}
+
 static inline unsigned int cdiv(long long a, long long b) { return (unsigned int)((a + b - 1) / b); }
 
 // Grid-stride 1-D launch size for `n` elements (capped to keep the grid modest).

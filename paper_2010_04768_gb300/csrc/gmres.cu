@@ -311,7 +311,7 @@ __device__ __forceinline__ void block_reduce_store(double2 (&acc)[NVT], int nv, 
   }
 }
 
-// pass 1: partial dots conj(V_i) . w
+// pass 1: partial dots conj(V_i) . w (i < nv) and, in slot nv, the squared norm of w
 template <int NVT>
 __global__ __launch_bounds__(FUSED_THREADS) void cgs_dots_kernel(const double *V, long long vs, long long vi, int nv,
                                                                  const double *w, long long n, int nch,
@@ -335,8 +335,11 @@ __global__ __launch_bounds__(FUSED_THREADS) void cgs_dots_kernel(const double *V
       acc[i].x += a.x * x.x + a.y * x.y;
       acc[i].y += a.x * x.y - a.y * x.x;
     }
+#pragma unroll
+    for (int i = 0; i < NVT; i++)
+      if (i == nv) acc[i].x += x.x * x.x + x.y * x.y;
   }
-  block_reduce_store<NVT>(acc, nv, sh, partial, s, NV, nch, chunk);
+  block_reduce_store<NVT>(acc, nv + 1, sh, partial, s, NV, nch, chunk);
 }
 
 // pass 2: w -= V h1 (in place), then partial dots conj(V_i) . w  (each basis value read once)
@@ -414,6 +417,35 @@ __global__ __launch_bounds__(FUSED_THREADS) void cgs_update_norm_kernel(const do
   block_reduce_store<1>(acc, 1, sh, partial, s, NV, nch, chunk);
 }
 
+// Selective reorthogonalisation (Daniel, Gragg, Kaufman & Stewart 1976): a second Gram-Schmidt
+// pass only where the first one cancelled more than half of w (||w'||^2 < ||w||^2 / 2).
+__global__ void reorth_flag_kernel(int nsys, const int *state, int want, const double *h, const double *w2, int NV,
+                                   int nv, int *flag) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys) return;
+  const double before = h[2 * ((long long)s * NV + nv)];    // ||w||^2 from the first pass
+  const double after = w2[2 * ((long long)s * NV)];          // ||w'||^2
+  flag[s] = (state[s] == want && after < 0.5 * before) ? 1 : 0;
+}
+
+// h[s][i] += h2[s][i] (i < nv) and h[s][nv] = ||w||^2 for the flagged systems; copy the final norm
+__global__ void reorth_merge_kernel(int nsys, int nv, double *h, const double *h2, const double *n1, const double *n2,
+                                    int NV, const int *state, int want, const int *flag) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys || state[s] != want) return;
+  double2 *hs = reinterpret_cast<double2 *>(h) + (long long)s * NV;
+  const double2 *h2s = reinterpret_cast<const double2 *>(h2) + (long long)s * NV;
+  if (flag[s]) {
+    for (int i = 0; i < nv; i++) {
+      hs[i].x += h2s[i].x;
+      hs[i].y += h2s[i].y;
+    }
+    hs[nv] = make_double2(n2[2 * (long long)s * NV], 0.0);
+  } else {
+    hs[nv] = make_double2(n1[2 * (long long)s * NV], 0.0);
+  }
+}
+
 __global__ void set_state_kernel(int nsys, int *state, int from, int to) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s < nsys && state[s] == from) state[s] = to;
@@ -451,7 +483,7 @@ long long gmres_work_doubles(const gfcc_ctx *c, int sector, long long n, int nsy
   w += 2LL * nsys * (m + 1) * n;            // V
   w += 3 * 2LL * nsys * n;                  // U, B, W
   w += 2LL * nsys * NV * nch;               // dot partials
-  w += 2LL * nsys * NV * 4;                 // h, h2, y, nrm
+  w += 2LL * nsys * NV * 5;                 // h, h2, y, nrm (two slots)
   w += 2LL * nsys * (m + 1) * m;            // H
   w += 2LL * nsys * (2 * m + (m + 1));      // cs, sn, g
   w += 7LL * nsys + 512;                    // bnorm, relres, est, omega, int state/kcyc/iters, alignment
@@ -487,7 +519,7 @@ int Gmres::init(gfcc_ctx *ctx, int sec, long long dim, int ns, int mm, double *w
   take(h, 2LL * nsys * NV);
   take(h2, 2LL * nsys * NV);
   take(y, 2LL * nsys * NV);
-  take(nrm, 2LL * nsys * NV);
+  take(nrm, 2LL * 2 * nsys * NV);
   take(H, 2LL * nsys * (m + 1) * m);
   take(cs, 2LL * nsys * m);
   take(sn, 2LL * nsys * m);
@@ -497,10 +529,11 @@ int Gmres::init(gfcc_ctx *ctx, int sec, long long dim, int ns, int mm, double *w
   take(est, nsys);
   take(omega, nsys);
   double *ip;
-  take(ip, 3LL * nsys);
+  take(ip, 4LL * nsys);
   state = reinterpret_cast<int *>(ip);
   kcyc = state + nsys;
   iters = kcyc + nsys;
+  rflag = iters + nsys;
   if (mixed) {
     take(X, 2LL * nsys * n);
     take(R, 2LL * nsys * n);
@@ -580,15 +613,13 @@ int Gmres::mdot(const double *Vb, long long vs, long long vi, int nv, const doub
 namespace {
 template <int NVT>
 void launch_cgs(int pass, dim3 grid, cudaStream_t st, const double *V, long long vs, int nv, double *w, long long n,
-                int nch, const int *state, const double *coef, double *partial, int NV) {
+                int nch, const int *filt, const double *coef, double *partial, int NV, int want) {
   if (pass == 0)
-    cgs_dots_kernel<NVT><<<grid, FUSED_THREADS, 0, st>>>(V, vs, n, nv, w, n, nch, state, ST_IN_CYCLE, partial, NV);
+    cgs_dots_kernel<NVT><<<grid, FUSED_THREADS, 0, st>>>(V, vs, n, nv, w, n, nch, filt, want, partial, NV);
   else if (pass == 1)
-    cgs_update_dots_kernel<NVT><<<grid, FUSED_THREADS, 0, st>>>(V, vs, n, nv, w, n, nch, state, ST_IN_CYCLE, coef,
-                                                                 partial, NV);
+    cgs_update_dots_kernel<NVT><<<grid, FUSED_THREADS, 0, st>>>(V, vs, n, nv, w, n, nch, filt, want, coef, partial, NV);
   else
-    cgs_update_norm_kernel<NVT><<<grid, FUSED_THREADS, 0, st>>>(V, vs, n, nv, w, n, nch, state, ST_IN_CYCLE, coef,
-                                                                 partial, NV);
+    cgs_update_norm_kernel<NVT><<<grid, FUSED_THREADS, 0, st>>>(V, vs, n, nv, w, n, nch, filt, want, coef, partial, NV);
 }
 }  // namespace
 
@@ -596,31 +627,41 @@ int Gmres::cgs2(const double *Vb, long long vs, int nv, double *w, cudaStream_t 
   const int nchf = (int)((n + FUSED_CHUNK - 1) / FUSED_CHUNK);   // partial is sized for this chunking
   dim3 grid(nchf, nsys);
   const int T = 256;
-  auto pass = [&](int p, const double *coef) -> int {
-    if (nv <= 8)
-      launch_cgs<8>(p, grid, st, Vb, vs, nv, w, n, nchf, state, coef, partial, NV);
-    else if (nv <= 16)
-      launch_cgs<16>(p, grid, st, Vb, vs, nv, w, n, nchf, state, coef, partial, NV);
-    else if (nv <= 32)
-      launch_cgs<32>(p, grid, st, Vb, vs, nv, w, n, nchf, state, coef, partial, NV);
+  // pass p over the systems whose filter array equals `want`
+  auto pass = [&](int p, int nvt, const double *coef, const int *filt, int want) -> int {
+    if (nvt <= 8)
+      launch_cgs<8>(p, grid, st, Vb, vs, nv, w, n, nchf, filt, coef, partial, NV, want);
+    else if (nvt <= 16)
+      launch_cgs<16>(p, grid, st, Vb, vs, nv, w, n, nchf, filt, coef, partial, NV, want);
+    else if (nvt <= 33)
+      launch_cgs<33>(p, grid, st, Vb, vs, nv, w, n, nchf, filt, coef, partial, NV, want);
     else
-      launch_cgs<65>(p, grid, st, Vb, vs, nv, w, n, nchf, state, coef, partial, NV);
+      launch_cgs<66>(p, grid, st, Vb, vs, nv, w, n, nchf, filt, coef, partial, NV, want);
     GFCC_LAUNCH_CHECK();
     return GFCC_OK;
   };
-  auto final = [&](int nvv, double *out) -> int {
-    mdot_final_kernel<<<cdiv(nsys * (long long)nvv * 32, 256), 256, 0, st>>>(partial, nsys, nvv, NV, nchf, state,
-                                                                             ST_IN_CYCLE, out, 0);
+  auto final = [&](int nvv, double *out, const int *filt, int want) -> int {
+    mdot_final_kernel<<<cdiv(nsys * (long long)nvv * 32, 256), 256, 0, st>>>(partial, nsys, nvv, NV, nchf, filt, want,
+                                                                             out, 0);
     GFCC_LAUNCH_CHECK();
     return GFCC_OK;
   };
-  GFCC_TRY(pass(0, nullptr));
-  GFCC_TRY(final(nv, h));
-  GFCC_TRY(pass(1, h));
-  GFCC_TRY(final(nv, h2));
-  GFCC_TRY(pass(2, h2));
-  GFCC_TRY(final(1, h + 2 * nv));   // ||w||^2 into h[nv] (real part)
-  coef_add_kernel<<<cdiv((long long)nsys * nv, T), T, 0, st>>>(nsys, nv, h, h2, NV, state, ST_IN_CYCLE);
+  int *flag = rflag;
+  // pass 1: h = V^H w and ||w||^2 (slot nv)
+  GFCC_TRY(pass(0, nv + 1, nullptr, state, ST_IN_CYCLE));
+  GFCC_TRY(final(nv + 1, h, state, ST_IN_CYCLE));
+  // pass 2: w -= V h, ||w'||^2
+  GFCC_TRY(pass(2, nv, h, state, ST_IN_CYCLE));
+  GFCC_TRY(final(1, nrm, state, ST_IN_CYCLE));
+  // passes 3-4 only where the first pass cancelled most of w
+  reorth_flag_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, state, ST_IN_CYCLE, h, nrm, NV, nv, flag);
+  GFCC_LAUNCH_CHECK();
+  GFCC_TRY(pass(0, nv + 1, nullptr, flag, 1));
+  GFCC_TRY(final(nv, h2, flag, 1));
+  GFCC_TRY(pass(2, nv, h2, flag, 1));
+  GFCC_TRY(final(1, nrm + 2 * NV * (long long)nsys, flag, 1));
+  reorth_merge_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, nv, h, h2, nrm, nrm + 2 * NV * (long long)nsys, NV, state,
+                                                   ST_IN_CYCLE, flag);
   GFCC_LAUNCH_CHECK();
   vscale_kernel<<<grid1d(n * nsys), T, 0, st>>>(w, vs, n, nsys, h, NV, nv, state, ST_IN_CYCLE);
   GFCC_LAUNCH_CHECK();
@@ -672,8 +713,8 @@ int Gmres::solve(double tol, int max_iters, int *h_state, int max_cycles) {
       double *vk = V + 2 * (long long)k * n;
       double *w = V + 2 * (long long)(k + 1) * n;
       GFCC_TRY(op(vk, vs, w, vs));
-      // CGS2 in three fused passes over the basis: h = V^H w; (w -= V h, h2 = V^H w);
-      // (w -= V h2, ||w||^2); then h += h2 and w /= ||w||
+      // Gram-Schmidt against the basis: one classical pass (dots with ||w||^2, then update with
+      // ||w'||^2), a second pass only where needed, then w /= ||w||
       {
         PhaseTimer ta(c, PH_ARNOLDI);
         GFCC_TRY(cgs2(V, vs, k + 1, w, st));

@@ -24,7 +24,7 @@ struct Gmres {
   double *partial = nullptr, *h = nullptr, *h2 = nullptr, *y = nullptr, *nrm = nullptr;
   double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr;
   double *bnorm = nullptr, *relres = nullptr, *est = nullptr, *omega = nullptr;
-  int *state = nullptr, *kcyc = nullptr, *iters = nullptr;
+  int *state = nullptr, *kcyc = nullptr, *iters = nullptr, *rflag = nullptr;
   double *sigma_work = nullptr;
 
   int init(gfcc_ctx *ctx, int sector, long long n, int nsys, int m, double *work, bool mixed = false);

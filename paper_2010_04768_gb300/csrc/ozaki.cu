@@ -53,33 +53,45 @@ __global__ void slice_kernel(const double *A, long long rows, long long K, long 
   const long long plane = rows * ld;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     const long long r = t / ld, k = t - r * ld;
-    double x = k < K ? scalbn(A[r * lda + k], -e[r]) : 0.0;
+    long long Y = k < K ? fixed_point(A[r * lda + k], e[r], 6 * S) : 0;
     for (int i = 0; i < S; i++) {
-      const double y = x * 64.0;
-      const double d = rint(y);
-      x = y - d;
-      dig[i * plane + t] = __double2bfloat16(d);
+      const int sh = 6 * (S - 1 - i);
+      const long long d = sh > 0 ? (Y + (1LL << (sh - 1))) >> sh : Y;
+      Y -= d << sh;
+      dig[i * plane + t] = __float2bfloat16((float)(int)d);
     }
   }
 }
 
-// acc[t] += scale * sum_z part[z][t]
-__global__ void combine_kernel(const float *part, int nz, long long tot, double scale, double *acc, int first) {
+// Exact integer accumulation of digit-pair products: the FP32 partial sums are integers of
+// magnitude <= 2^24, so they convert to int32 exactly; a pair of level L adds (sum_z part) shifted
+// by 6 (Lhi - L) into the high accumulator (levels <= Lsplit) or by 6 (P - L) into the low one.
+// acc[2t] = high, acc[2t + 1] = low (int64).  No FP64 arithmetic.
+__global__ void combine_int_kernel(const float *part, int nz, long long tot, int shift, int which, long long *acc,
+                                   int first) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int z = 0; z < nz; z++) s += (double)part[(long long)z * tot + t];
-    acc[t] = first ? scale * s : acc[t] + scale * s;
+    long long s = 0;
+    for (int z = 0; z < nz; z++) s += (long long)__float2int_rn(part[(long long)z * tot + t]);
+    s <<= shift;
+    if (first) {
+      acc[2 * t] = which == 0 ? s : 0;
+      acc[2 * t + 1] = which == 1 ? s : 0;
+    } else {
+      acc[2 * t + which] += s;
+    }
   }
 }
 
-// C(m, n0 + n) = alpha * 2^(eA[m] + eB[n]) acc[m][n] + beta * C(m, n0 + n)
-__global__ void finalize_kernel(const double *acc, long long M, long long N, const int *eA, const int *eB, double alpha,
-                                double beta, double *C, IMap cm, IMap cn, long long n0) {
+// C(m, n0 + n) = alpha * 2^(eA[m] + eB[n]) (hi 64^-Lhi + lo 64^-P) + beta * C(m, n0 + n)
+__global__ void finalize_kernel(const long long *acc, long long M, long long N, const int *eA, const int *eB,
+                                int Lhi, int P, double alpha, double beta, double *C, IMap cm, IMap cn, long long n0) {
   const long long tot = M * N;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     const long long m = t / N, n = t - m * N;
     const long long off = imap_apply(cm, m) + imap_apply(cn, n0 + n);
-    const double v = alpha * scalbn(acc[t], eA[m] + eB[n]);
+    const int ex = eA[m] + eB[n];
+    const double val = scalbn((double)acc[2 * t], ex - 6 * Lhi) + scalbn((double)acc[2 * t + 1], ex - 6 * P);
+    const double v = alpha * val;
     C[off] = beta != 0.0 ? v + beta * C[off] : v;
   }
 }
@@ -118,7 +130,7 @@ int emu_slice(cudaStream_t st, const double *A, long long rows, long long K, lon
 long long emu_gemm_work_bytes(long long M, long long N, long long K) {
   const long long nk = (K + 63) / 64;
   const long long nz = (nk + KCHUNK_BLOCKS - 1) / KCHUNK_BLOCKS;
-  return nz * M * N * 4 + M * N * 8 + 512;
+  return nz * M * N * 4 + M * N * 16 + 512;
 }
 
 int emu_gemm(cudaStream_t st, const EmuOperand &A, const EmuOperand &B, int P, double alpha, double beta, double *C,
@@ -132,26 +144,35 @@ int emu_gemm(cudaStream_t st, const EmuOperand &A, const EmuOperand &B, int P, d
   const long long nk = (K + 63) / 64;
   const int nz = (int)((nk + KCHUNK_BLOCKS - 1) / KCHUNK_BLOCKS);
   float *part = static_cast<float *>(work);
-  double *acc = reinterpret_cast<double *>(static_cast<unsigned char *>(work) + ((nz * M * N * 4 + 255) / 256) * 256);
+  long long *acc =
+      reinterpret_cast<long long *>(static_cast<unsigned char *>(work) + ((nz * M * N * 4 + 255) / 256) * 256);
   GFCC_TRY(check_extent_bytes(work, emu_gemm_work_bytes(M, N, K), "digit GEMM workspace"));
   GFCC_TRY(check_extent(C, 0, imap_max(cm, M) + imap_max(cn, n0 + N), "digit GEMM output"));
   const long long plA = A.rows * A.ld, plB = B.rows * B.ld;
+  // two exact int64 accumulators: levels 2..Lhi (weights 64^(Lhi-L)) and Lhi+1..P (64^(P-L));
+  // a level sum is below (pairs * nz) 2^24 < 2^33, so 4 levels of 6-bit shifts stay below 2^63
+  const int Lhi = std::min(P, 5);
+  if (P - Lhi > 4 || nz > (1 << 16)) {
+    set_error("emu_gemm: level %d or K %lld beyond the exact integer accumulation", P, K);
+    return GFCC_ERR_ARG;
+  }
   bool first = true;
-  // smallest contributions first
   for (int L = P; L >= 2; L--) {
     for (int i = 1; i <= A.S; i++) {
       const int j = L - i;
       if (j < 1 || j > B.S) continue;
       GFCC_TRY(gemm_bf16_tn(st, A.dig + (long long)(i - 1) * plA, A.ld, B.dig + (long long)(j - 1) * plB, B.ld, part,
                             N, (int)M, (int)N, (int)K, 1.0f, 0.0f, nz, M * N));
-      combine_kernel<<<grid1d(M * N), 256, 0, st>>>(part, umma_splits((int)K, nz), M * N, scalbn(1.0, -6 * L), acc,
-                                                     first ? 1 : 0);
+      const int which = L <= Lhi ? 0 : 1;
+      const int shift = which == 0 ? 6 * (Lhi - L) : 6 * (P - L);
+      combine_int_kernel<<<grid1d(M * N), 256, 0, st>>>(part, umma_splits((int)K, nz), M * N, shift, which, acc,
+                                                         first ? 1 : 0);
       GFCC_LAUNCH_CHECK();
       first = false;
     }
   }
-  if (first) GFCC_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * M * N, st));
-  finalize_kernel<<<grid1d(M * N), 256, 0, st>>>(acc, M, N, A.exp2, B.exp2, alpha, beta, C, cm, cn, n0);
+  if (first) GFCC_CUDA(cudaMemsetAsync(acc, 0, sizeof(long long) * 2 * M * N, st));
+  finalize_kernel<<<grid1d(M * N), 256, 0, st>>>(acc, M, N, A.exp2, B.exp2, Lhi, P, alpha, beta, C, cm, cn, n0);
   GFCC_LAUNCH_CHECK();
   return GFCC_OK;
 }

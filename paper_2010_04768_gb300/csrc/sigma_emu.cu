@@ -45,12 +45,12 @@ __device__ __forceinline__ double packed_r2(const double *x, long long ldx, int 
 }
 
 __device__ __forceinline__ void put_digits(double val, int ex, int S, __nv_bfloat16 *dst, long long plane) {
-  double r = scalbn(val, -ex);
+  long long Y = fixed_point(val, ex, 6 * S);
   for (int i = 0; i < S; i++) {
-    const double y = r * 64.0;
-    const double d = rint(y);
-    r = y - d;
-    dst[i * plane] = __double2bfloat16(d);
+    const int sh = 6 * (S - 1 - i);
+    const long long d = sh > 0 ? (Y + (1LL << (sh - 1))) >> sh : Y;
+    Y -= d << sh;
+    dst[i * plane] = __float2bfloat16((float)(int)d);
   }
 }
 

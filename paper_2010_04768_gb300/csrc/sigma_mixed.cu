@@ -28,23 +28,26 @@ namespace gfcc {
 
 namespace {
 
+// The BF16 operands only need FP32 accuracy: the vector (and the preconditioner division) is
+// handled in FP32 on the FP32 pipe.
 struct Cz {
-  double r, i;
+  float r, i;
 };
 
 __device__ __forceinline__ Cz load_u(const SysBatch &b, int s, long long mu) {
-  Cz u{b.x[2 * (s * b.ldx + mu)], b.x[2 * (s * b.ldx + mu) + 1]};
+  Cz u{d2f_trunc(b.x[2 * (s * b.ldx + mu)]), d2f_trunc(b.x[2 * (s * b.ldx + mu) + 1])};
   if (b.diag != nullptr && b.omega != nullptr) {
-    const double dr = b.omega[s] + b.dsign * b.diag[mu], di = b.zsign * b.eta;
-    const double dd = dr * dr + di * di;
-    u = {(u.r * dr + u.i * di) / dd, (u.i * dr - u.r * di) / dd};
+    const float dr = d2f_trunc(b.omega[s]) + (float)b.dsign * d2f_trunc(b.diag[mu]);
+    const float di = (float)b.zsign * d2f_trunc(b.eta);
+    const float inv = 1.0f / (dr * dr + di * di);
+    u = {(u.r * dr + u.i * di) * inv, (u.i * dr - u.r * di) * inv};
   }
   return u;
 }
 
 // r2[m, j, e] of system s as (re, im); zero on the diagonal m == j
 __device__ __forceinline__ Cz r2_at(const SysBatch &b, int o, int v, int s, int m, int j, int e) {
-  if (m == j) return {0.0, 0.0};
+  if (m == j) return {0.0f, 0.0f};
   const long long lo = m < j ? m : j, hi = m < j ? j : m;
   const long long mu = o + pair_index(lo, hi, o) * v + e;
   Cz u = load_u(b, s, mu);
@@ -65,7 +68,7 @@ __global__ void unpack_ring_kernel(SysBatch b, int o, int v, long long ld, __nv_
     const int c = (int)(row % (2 * ns)), j = (int)(row / (2 * ns));
     const int m = (int)(k / v), e = (int)(k % v);
     const Cz u = r2_at(b, o, v, c >> 1, m, j, e);
-    out[row * ld + k] = __double2bfloat16((c & 1) ? u.i : u.r);
+    out[row * ld + k] = __float2bfloat16((c & 1) ? u.i : u.r);
   }
 }
 
@@ -84,7 +87,7 @@ __global__ void unpack_oooo_kernel(SysBatch b, int o, int v, long long ld, __nv_
     float val = 0.f;
     if (k < K && a < v) {
       const Cz u = r2_at(b, o, v, s, (int)(k / o), (int)(k % o), a);
-      val = (float)((c & 1) ? u.i : u.r);
+      val = (c & 1) ? u.i : u.r;
     }
     tile[r][threadIdx.x] = val;
   }
@@ -108,7 +111,7 @@ __global__ void unpack_k_tiled_kernel(SysBatch b, int o, int v, long long ldk, _
     float val = 0.f;
     if (n < o && e < v) {
       const Cz u = r2_at(b, o, v, s, m, n, e);
-      val = (float)((c & 1) ? u.i : u.r);
+      val = (c & 1) ? u.i : u.r;
     }
     tile[r][threadIdx.x] = val;
   }
@@ -128,7 +131,7 @@ __global__ void unpack_r1_kernel(SysBatch b, int o, int v, long long ldk, __nv_b
   if (t >= C2 * o) return;
   const int c = t / o, m = t % o;
   const Cz u = load_u(b, c >> 1, m);
-  const __nv_bfloat16 h = __double2bfloat16((c & 1) ? u.i : u.r);
+  const __nv_bfloat16 h = __float2bfloat16((c & 1) ? u.i : u.r);
   rk[(long long)c * ldk + o2v + m] = h;
   r1b[(long long)c * ld1 + m] = h;
 }

@@ -27,9 +27,15 @@ namespace gfcc {
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4, THREADS = 128;
-constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+constexpr int BM = 128, BK = 64, THREADS = 128;
+// BN (the N extent of a tile and of the TMEM accumulator) is a template parameter: 256 for wide
+// operands, 128 / 64 when the contraction has few columns (a tile wider than N wastes MMA work).
+template <int BN>
+struct Tile {
+  static constexpr int STAGES = BN == 256 ? 4 : 6;
+  static constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+};
 constexpr unsigned long long WAIT_NS = 1000000000ULL;   // bounded waits: 1 s
 
 __device__ unsigned int g_umma_error = 0;
@@ -136,10 +142,12 @@ __device__ __forceinline__ void tmem_ld_32(unsigned taddr, float (&v)[32]) {
   for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
 }
 
+template <int BN>
 __global__ void __launch_bounds__(THREADS, 1)
     umma_bf16_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, float *D,
                           long long ldd, int M, int N, int K, float alpha, float beta, int kb_per_split,
                           long long split_stride) {
+  constexpr int STAGES = Tile<BN>::STAGES, A_BYTES = Tile<BN>::A_BYTES, STAGE_BYTES = Tile<BN>::STAGE_BYTES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + STAGES * STAGE_BYTES);
@@ -317,6 +325,32 @@ int umma_error_check(cudaStream_t st) {
   return GFCC_OK;
 }
 
+namespace {
+template <int BN>
+int launch_umma(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const __nv_bfloat16 *B, long long ldb,
+                float *D, long long ldd, int M, int N, int K, float alpha, float beta, int nsplit, int kbs,
+                long long split_stride) {
+  CUtensorMap ma, mb;
+  GFCC_TRY(make_map(&ma, A, M, K, lda, BM));
+  GFCC_TRY(make_map(&mb, B, N, K, ldb, BN));
+  static bool attr = false;
+  if (!attr) {
+    GFCC_CUDA(cudaFuncSetAttribute(umma_bf16_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   Tile<BN>::SMEM_BYTES));
+    attr = true;
+  }
+  if ((N + BN - 1) / BN > 65535 || nsplit > 65535) {
+    set_error("gemm_bf16_tn: grid too large (N=%d, nsplit=%d)", N, nsplit);
+    return GFCC_ERR_ARG;
+  }
+  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, nsplit);
+  umma_bf16_gemm_kernel<BN><<<grid, THREADS, Tile<BN>::SMEM_BYTES, st>>>(ma, mb, D, ldd, M, N, K, alpha, beta, kbs,
+                                                                         split_stride);
+  GFCC_LAUNCH_CHECK();
+  return GFCC_OK;
+}
+}  // namespace
+
 int gemm_bf16_tn(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const __nv_bfloat16 *B, long long ldb,
                  float *D, long long ldd, int M, int N, int K, float alpha, float beta, int nsplit,
                  long long split_stride) {
@@ -340,22 +374,10 @@ int gemm_bf16_tn(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const _
   GFCC_TRY(check_extent_bytes(B, (long long)(N - 1) * ldb * 2 + (long long)K * 2, "bf16 GEMM operand B"));
   GFCC_TRY(check_extent_bytes(D, ((long long)(M - 1) * ldd + N + (long long)(nsplit - 1) * split_stride) * 4,
                               "bf16 GEMM output D"));
-  CUtensorMap ma, mb;
-  GFCC_TRY(make_map(&ma, A, M, K, lda, BM));
-  GFCC_TRY(make_map(&mb, B, N, K, ldb, BN));
-  static bool attr = false;
-  if (!attr) {
-    GFCC_CUDA(cudaFuncSetAttribute(umma_bf16_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    attr = true;
-  }
-  if ((N + BN - 1) / BN > 65535 || nsplit > 65535) {
-    set_error("gemm_bf16_tn: grid too large (N=%d, nsplit=%d)", N, nsplit);
-    return GFCC_ERR_ARG;
-  }
-  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, nsplit);
-  umma_bf16_gemm_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, D, ldd, M, N, K, alpha, beta, kbs, split_stride);
-  GFCC_LAUNCH_CHECK();
-  return GFCC_OK;
+  // narrowest tile that covers N (wide N keeps the 256-column tile)
+  if (N <= 64) return launch_umma<64>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
+  if (N <= 128) return launch_umma<128>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
+  return launch_umma<256>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
 }
 
 }  // namespace gfcc
