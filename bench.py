@@ -255,7 +255,9 @@ def main():
         barrier()
         ev0.record(stream)
         for k in range(args.steps):
+            torch.cuda.nvtx.range_push("step")   # lets a profiler select the timed steps
             c, _ = device_step(k)
+            torch.cuda.nvtx.range_pop()
             converged += c
         ev1.record(stream)
         barrier()

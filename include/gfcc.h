@@ -71,6 +71,24 @@ extern "C" {
 #define GFCC_OPT_INNER_CYCLES 9   /* mixed precision: GMRES restart cycles per refinement step; default 1 */
 #define GFCC_OPT_EMU_LEVEL  10    /* digit pairs i + j <= level in the FP64-accurate products (8 digits of
                                      6 bits per operand); default 9                                      */
+#define GFCC_OPT_GUESS      11    /* GFCC_GUESS_*: initial iterate of each GMRES solve; default ZERO     */
+#define GFCC_OPT_KEEP_SOLUTIONS 12 /* 1: keep the converged solutions of the last sector solved after
+                                     gfcc_solve (for gfcc_mlp_collect); default 0                        */
+
+/* Initial guesses (Algorithm 1, "compute initial guess").  With a guess other than ZERO, gfcc_solve
+ * keeps every converged solution X_p(omega) (FP32 complex, n_omega * n_orb * dim * 8 bytes of device
+ * memory per sector), solves the frequencies in a spread-out order (the two ends first, then always
+ * the frequency farthest from those already taken) and starts each system (omega, p) from a
+ * combination x0 = sum_k c_k X_p(omega_k) of the converged solutions of the same orbital at the 8
+ * nearest frequencies solved in earlier batches.  Because A(omega) X_k = b + (omega - omega_k) X_k,
+ * the residual of x0 is known from the 9 x 9 Gram matrix of (b, (omega - omega_k) X_k) without a
+ * sigma product; a guess whose predicted residual is not below ||b|| is replaced by zero.  The
+ * converged G does not depend on the guess (to the solver tolerance). */
+#define GFCC_GUESS_ZERO     0     /* x0 = 0                                                              */
+#define GFCC_GUESS_LEARNED  1     /* c from the model attached with gfcc_set_guess_model (needs all 8
+                                     neighbours, otherwise zero)                                         */
+#define GFCC_GUESS_MINRES   2     /* c minimising the predicted residual over the available neighbours
+                                     (normal equations with a relative shift of 1e-12)                   */
 
 /* Per-column status values reported by gfcc_last_stats. */
 #define GFCC_STATUS_CONVERGED      0
@@ -184,7 +202,7 @@ int gfcc_dims(gfcc_ctx *ctx, long long *dim_ip, long long *dim_ea);
  * 6 right-hand sides, left vectors and overlaps, 7 whole gfcc_solve calls, 8 ring contraction on the
  * BF16 tensor cores (mixed precision; phase 1 is the FP64 ring contraction), 9 FP64-accurate ring
  * contraction of the refinement residual (digit planes; flops counted as tensor-core work), 10 expansion
- * of packed vectors into contraction layouts.
+ * of packed vectors into contraction layouts, 11 initial guesses (Gram matrices, model, combination).
  */
 int gfcc_profile(gfcc_ctx *ctx, int enable);
 int gfcc_profile_read(gfcc_ctx *ctx, int phase, double *ms, long long *count, double *flops);
@@ -207,6 +225,78 @@ int gfcc_selftest_gemm_bf16(int M, int N, int K, const float *A, const float *B,
  * A (M x K), B (N x K), C (M x N): row-major FP64 HOST arrays.
  */
 int gfcc_selftest_gemm_f64emu(int M, int N, int K, const double *A, const double *B, int S, int P, double *C);
+
+/*
+ * gfcc_guess_stats - initial-guess statistics of the last gfcc_solve, in the entry order of
+ * gfcc_last_stats: `kind` the GFCC_GUESS_* actually used, `pred` the predicted
+ * ||b - A x0||^2 / ||b||^2 from the Gram matrix (1 for a zero guess), `relres0` the measured
+ * ||b - A x0|| / ||b|| of the first true residual (FP64).  Pointers may be NULL; `count` as in
+ * gfcc_last_stats.
+ */
+int gfcc_guess_stats(gfcc_ctx *ctx, int *count, int *kind, double *pred, double *relres0);
+
+/*
+ * The learned-guess model: a 3-layer perceptron with ReLU activations,
+ *     x^ = (x - mu) / sd,  h1 = relu(W1 x^ + b1),  h2 = relu(W2 h1 + b2),  y = W3 h2 + b3,
+ * from the 27 features of a system (omega, eta, p / n, delta_k = omega - omega_k for the 8
+ * neighbours nearest first, then Re and Im of <b|X_k> * eta / ||b||^2) to its 8 complex mixing
+ * coefficients c_k = y_2k + i y_2k+1.  It is trained on the method's own converged solutions:
+ * the loss of a sample is the predicted relative residual a^H Gm a / Gm_00 of its combination,
+ * with a = (sum_k c_k - 1, c_1, ..., c_8) and Gm the 9 x 9 Gram matrix of
+ * (b, delta_1 X_1, ..., delta_8 X_8) (complex, Gm[j][l] = <u_j, u_l>, conjugate-linear in the
+ * first argument).  Optimiser: Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * Parameter layout (doubles, row-major): W1 [hidden][27], b1 [hidden], W2 [hidden][hidden],
+ * b2 [hidden], W3 [16][hidden], b3 [16], mu [27], sd [27] (mu, sd are not trained).
+ * A model lives on the device current at creation; calls on one model must not overlap, and a
+ * model attached to a context must not be trained while that context solves.
+ */
+#define GFCC_MLP_FP32  0          /* FP32 master weights and training; FP16 weights for inference         */
+#define GFCC_MLP_FP64  1          /* FP64 throughout (gradient checks)                                     */
+#define GFCC_MLP_FEATURES 27
+#define GFCC_MLP_OUTPUTS  16
+
+typedef struct gfcc_mlp gfcc_mlp;
+
+/* gfcc_mlp_create - new model with `hidden` (1..256) units per hidden layer.  init_params: host,
+ * gfcc_mlp_num_params doubles in the layout above (the caller draws the initial weights; the mu /
+ * sd entries are ignored and set from the samples at the first gfcc_mlp_train). */
+int gfcc_mlp_create(int hidden, int precision, const double *init_params, gfcc_mlp **out);
+void gfcc_mlp_destroy(gfcc_mlp *m);
+long long gfcc_mlp_num_params(const gfcc_mlp *m);
+/* gfcc_mlp_get_params / gfcc_mlp_set_params - host copies of all parameters (set also fixes mu, sd;
+ * every sd must be non-zero). */
+int gfcc_mlp_get_params(gfcc_mlp *m, double *params);
+int gfcc_mlp_set_params(gfcc_mlp *m, const double *params);
+/* gfcc_mlp_forward - y [nb][16] of features [nb][27] (host arrays) with the inference weights. */
+int gfcc_mlp_forward(gfcc_mlp *m, int nb, const double *features, double *y);
+/* gfcc_mlp_loss_grad - mean loss over a batch (features [nb][27], gram [nb][9][9] complex
+ * interleaved; host) and its gradient with respect to every parameter (grad: host,
+ * gfcc_mlp_num_params doubles; zero for mu, sd), in the training precision. */
+int gfcc_mlp_loss_grad(gfcc_mlp *m, int nb, const double *features, const double *gram, double *loss, double *grad);
+/* gfcc_mlp_train_batch - one Adam step with learning rate lr on the given batch; *loss = the
+ * batch's mean loss before the step. */
+int gfcc_mlp_train_batch(gfcc_mlp *m, int nb, const double *features, const double *gram, double lr, double *loss);
+/* gfcc_mlp_collect - add training samples from the kept solutions of a context (after a gfcc_solve
+ * with GFCC_OPT_KEEP_SOLUTIONS or a guess): for every converged (omega, p), samples_per_system
+ * samples whose neighbours are the 8 nearest among a random subset of the other converged
+ * frequencies (keep probability drawn in [0.15, 1) per sample; `seed` drives the draws).
+ * *added = samples added (systems with fewer than 8 neighbours in the subset give none). */
+int gfcc_mlp_collect(gfcc_mlp *m, gfcc_ctx *ctx, int samples_per_system, unsigned long long seed, long long *added);
+long long gfcc_mlp_num_samples(const gfcc_mlp *m);
+/* gfcc_mlp_get_samples - host copies of collected samples [start, start + count): features
+ * [count][27] and Gram matrices [count][9][9] complex interleaved (either pointer may be NULL).
+ * A sample's neighbours are identified by its features: omega_k = omega - delta_k, p = (p/n) n. */
+int gfcc_mlp_get_samples(gfcc_mlp *m, long long start, int count, double *features, double *gram);
+/* gfcc_mlp_train - `steps` Adam steps on minibatches of the collected samples (drawn with
+ * replacement from `seed`).  *loss = mean minibatch loss over the last (up to) 50 steps. */
+int gfcc_mlp_train(gfcc_mlp *m, int steps, int minibatch, double lr, unsigned long long seed, double *loss);
+/* gfcc_mlp_eval - over the collected samples, with the inference weights: out[0] mean model loss,
+ * out[1] mean loss after the zero-guess fallback (min(loss, 1)), out[2] mean loss of the
+ * minimal-residual coefficients (clamped to [0, 1]), out[3] fraction of samples where the model
+ * beats the zero guess. */
+int gfcc_mlp_eval(gfcc_mlp *m, double *out);
+/* gfcc_set_guess_model - model used by GFCC_GUESS_LEARNED (not owned; NULL detaches). */
+int gfcc_set_guess_model(gfcc_ctx *ctx, gfcc_mlp *m);
 
 /* gfcc_destroy - free the context and all its device memory.  NULL is a no-op. */
 void gfcc_destroy(gfcc_ctx *ctx);

@@ -16,6 +16,8 @@
 #include "sigma.cuh"
 #include "ozaki.cuh"
 #include "umma.cuh"
+#include "guess.cuh"
+#include "mlp.cuh"
 
 namespace gfcc {
 
@@ -556,15 +558,54 @@ int solve_impl(gfcc_ctx *c, int n_omega, const double *d_om, double eta, int n_o
   return rc;
 }
 
+// Kept-solution store of one sector: [omega][orbital][n] complex FP32, done flags cleared.
+int prepare_kept(gfcc_ctx *c, int sector, long long n, int n_omega, int n_orb, const double *d_om, const int *d_orb,
+                 double eta) {
+  KeptSolutions &kp = c->kept;
+  const size_t bytes = sizeof(float2) * (size_t)n_omega * n_orb * (size_t)n;
+  if (kp.bytes < bytes) {
+    if (kp.X) dfree(kp.X);
+    kp.X = nullptr;
+    kp.bytes = 0;
+    if (dmalloc(reinterpret_cast<void **>(&kp.X), bytes) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cannot allocate %.3f GB for the kept solutions of the initial guesses", bytes / 1e9);
+      return GFCC_ERR_OOM;
+    }
+    kp.bytes = bytes;
+  }
+  kp.sector = sector;
+  kp.n = n;
+  kp.nw = n_omega;
+  kp.norb = n_orb;
+  kp.eta = eta;
+  kp.omega.resize(n_omega);
+  kp.orb.resize(n_orb);
+  kp.done.assign((size_t)n_omega * n_orb, 0);
+  GFCC_CUDA(cudaMemcpyAsync(kp.omega.data(), d_om, sizeof(double) * n_omega, cudaMemcpyDeviceToHost, c->stream));
+  GFCC_CUDA(cudaMemcpyAsync(kp.orb.data(), d_orb, sizeof(int) * n_orb, cudaMemcpyDeviceToHost, c->stream));
+  GFCC_CUDA(cudaStreamSynchronize(c->stream));
+  return GFCC_OK;
+}
+
 int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, int n_orb, const int *d_orb,
                      const int *h_orb, double tol, double *d_G) {
   cudaStream_t st = c->stream;
   const int sectors[2] = {GFCC_SECTOR_IP, GFCC_SECTOR_EA};
   const long long ntasks = (long long)n_omega * n_orb;
   const int nsec = (c->sectors & GFCC_SECTOR_IP ? 1 : 0) + (c->sectors & GFCC_SECTOR_EA ? 1 : 0);
+  const int guess = c->guess;
+  if (guess == GFCC_GUESS_LEARNED && c->mlp == nullptr) {
+    set_error("gfcc_solve: GFCC_GUESS_LEARNED needs a model (gfcc_set_guess_model)");
+    return GFCC_ERR_STATE;
+  }
+  const bool keep = guess != GFCC_GUESS_ZERO || c->keep_solutions;
   c->st_iters.assign(ntasks * nsec, 0);
   c->st_status.assign(ntasks * nsec, GFCC_STATUS_NOT_CONVERGED);
   c->st_relres.assign(ntasks * nsec, 0.0);
+  c->st_guess.assign(ntasks * nsec, GFCC_GUESS_ZERO);
+  c->st_guess_pred.assign(ntasks * nsec, 1.0);
+  c->st_relres0.assign(ntasks * nsec, 1.0);
   GFCC_CUDA(cudaMemsetAsync(d_G, 0, sizeof(double) * 2 * n_omega * n_orb * n_orb, st));
   int sec_slot = 0;
   bool all_ok = true;
@@ -575,11 +616,17 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
     const long long n = ip ? c->dim_ip : c->dim_ea;
     // mixed precision covers the IP sector; EA systems of a mixed context are solved in FP64
     const bool mixed = ip && c->precision == GFCC_PREC_MIXED_BF16;
+    if (keep) GFCC_TRY(prepare_kept(c, sector, n, n_omega, n_orb, d_om, d_orb, eta));
     const int nsys = choose_batch(c, sector, n, ntasks);
     const int m = c->restart;
     const long long nsplit = (n + 8191) / 8192;
     const long long gw = gmres_work_doubles(c, sector, n, nsys, m, mixed);
-    const long long work = gw + (long long)n_orb * n + nsplit * 2LL * nsys * n_orb + 4LL * nsys + 64;
+    // guess workspace: Gram, features, model outputs, coefficients, predictions, deltas, p/n,
+    // Gram partials; then the ints (neighbour slots, counts, kinds, store slots)
+    const long long gq = keep ? 2LL * nsys * GUESS_G + (long long)nsys * (GUESS_NF + 2 * GUESS_NO + 1 + GUESS_K + 1) +
+                                    guess_gram_work_doubles(nsys, n) + (long long)nsys * (GUESS_K + 3) / 2 + 64
+                              : 0;
+    const long long work = gw + (long long)n_orb * n + nsplit * 2LL * nsys * n_orb + 4LL * nsys + 64 + gq;
     GFCC_TRY(grow_scratch(c, sizeof(double) * work));
     double *base = static_cast<double *>(c->scratch);
     Gmres gm;
@@ -589,6 +636,18 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
     int *d_tw = reinterpret_cast<int *>(part + nsplit * 2LL * nsys * n_orb);
     int *d_ta = d_tw + nsys;
     int *d_porb = d_ta + nsys;
+    double *g_Gm = part + nsplit * 2LL * nsys * n_orb + 4LL * nsys + 64;
+    double *g_feat = g_Gm + 2LL * nsys * GUESS_G;
+    double *g_y = g_feat + (long long)nsys * GUESS_NF;
+    double *g_coef = g_y + (long long)nsys * GUESS_NO;
+    double *g_pred = g_coef + (long long)nsys * GUESS_NO;
+    double *g_delta = g_pred + nsys;
+    double *g_pf = g_delta + (long long)nsys * GUESS_K;
+    double *g_work = g_pf + nsys;
+    int *g_nbr = reinterpret_cast<int *>(g_work + (keep ? guess_gram_work_doubles(nsys, n) : 0));
+    int *g_navail = g_nbr + (long long)nsys * GUESS_K;
+    int *g_kind = g_navail + nsys;
+    int *g_slot = g_kind + nsys;
     gm.eta = eta;
     gm.use_precond = c->precond == GFCC_PRECOND_DIAG;
     // left vectors for all orbitals of the list
@@ -612,14 +671,20 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
       }
     }
     }
-    std::vector<int> h_tw(nsys), h_ta(nsys), h_state(nsys), h_it(nsys);
-    std::vector<double> h_rel(nsys);
+    // task order: frequency-major; with initial guesses the frequencies go in the order of
+    // guess_frequency_order so that later ones have converged neighbours on both sides
+    std::vector<int> word(n_omega);
+    for (int w = 0; w < n_omega; w++) word[w] = w;
+    if (guess != GFCC_GUESS_ZERO) word = guess_frequency_order(c->kept.omega);
+    std::vector<int> h_tw(nsys), h_ta(nsys), h_state(nsys), h_it(nsys), h_kind(nsys), h_nbr((size_t)nsys * GUESS_K),
+        h_navail(nsys), h_slot(nsys);
+    std::vector<double> h_rel(nsys), h_rel0(nsys), h_pred(nsys), h_delta((size_t)nsys * GUESS_K), h_pf(nsys);
     for (long long t0 = 0; t0 < ntasks; t0 += nsys) {
       const int nb = (int)std::min<long long>(nsys, ntasks - t0);
       // pad a short last batch by repeating its last task (results of the padding are dropped)
       for (int s = 0; s < nsys; s++) {
         const long long t = t0 + std::min(s, nb - 1);
-        h_tw[s] = (int)(t / n_orb);
+        h_tw[s] = word[t / n_orb];
         h_ta[s] = (int)(t % n_orb);
       }
       GFCC_CUDA(cudaMemcpyAsync(d_tw, h_tw.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
@@ -630,19 +695,40 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
       GFCC_LAUNCH_CHECK();
       {
       PhaseTimer trhs(c, PH_OVERLAP);
-      if (ip) {
-        rhs_ip_kernel<<<grid1d(n * nsys), 256, 0, st>>>(gm.B, n, nsys, d_porb, c->o, c->v, c->t1, c->t2);
-      } else {
-        rhs_ea_kernel<<<grid1d(n * nsys), 256, 0, st>>>(gm.B, n, nsys, d_porb, c->o, c->v, c->Pv, c->t1, c->t2);
+      GFCC_TRY(build_rhs(c, sector, nsys, d_porb, gm.B, st));
       }
-      GFCC_LAUNCH_CHECK();
+      bool use_x0 = false;
+      if (guess != GFCC_GUESS_ZERO) {
+        // neighbours among the converged solutions of earlier batches (same orbital)
+        PhaseTimer tg(c, PH_GUESS);
+        const KeptSolutions &kp = c->kept;
+        for (int s = 0; s < nsys; s++) {
+          int idx[GUESS_K];
+          const int a = h_ta[s], w = h_tw[s];
+          const int k = guess_neighbours(kp.omega, kp.done.data() + a, n_orb, w, GUESS_K, idx);
+          h_navail[s] = k;
+          for (int q = 0; q < GUESS_K; q++) {
+            h_nbr[s * GUESS_K + q] = q < k ? idx[q] * n_orb + a : -1;
+            h_delta[s * GUESS_K + q] = q < k ? kp.omega[w] - kp.omega[idx[q]] : 0.0;
+          }
+          h_pf[s] = (double)kp.orb[a] / (double)c->n;
+        }
+        GFCC_CUDA(cudaMemcpyAsync(g_nbr, h_nbr.data(), sizeof(int) * nsys * GUESS_K, cudaMemcpyHostToDevice, st));
+        GFCC_CUDA(cudaMemcpyAsync(g_navail, h_navail.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+        GFCC_CUDA(cudaMemcpyAsync(g_delta, h_delta.data(), sizeof(double) * nsys * GUESS_K, cudaMemcpyHostToDevice, st));
+        GFCC_CUDA(cudaMemcpyAsync(g_pf, h_pf.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, st));
+        GFCC_TRY(guess_gram(st, nsys, n, gm.B, n, kp.X, g_nbr, g_delta, gm.omega, eta, g_pf, g_Gm, g_feat, g_work));
+        if (guess == GFCC_GUESS_LEARNED) GFCC_TRY(mlp_infer(c->mlp, st, nsys, g_feat, g_y));
+        GFCC_TRY(guess_choose(st, nsys, guess, g_Gm, g_y, g_navail, g_coef, g_pred, g_kind));
+        GFCC_TRY(guess_combine(st, nsys, n, kp.X, g_nbr, g_coef, g_kind, mixed ? gm.X : gm.U, n));
+        use_x0 = true;
       }
       if (mixed) {
         GFCC_TRY(umma_error_reset(st));
-        GFCC_TRY(gm.solve_refined(tol, c->inner_tol, c->max_iters, h_state.data(), h_it.data()));
+        GFCC_TRY(gm.solve_refined(tol, c->inner_tol, c->max_iters, h_state.data(), h_it.data(), use_x0));
         GFCC_TRY(umma_error_check(st));
       } else {
-        GFCC_TRY(gm.solve(tol, c->max_iters, h_state.data()));
+        GFCC_TRY(gm.solve(tol, c->max_iters, h_state.data(), 0, use_x0));
       }
       // overlaps: part[z][(s,t)][q] = sum_{mu in chunk z} x_s[mu] C[q][mu]
       {
@@ -658,15 +744,33 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
                                                                              ip ? 1 : 0, d_G);
       GFCC_LAUNCH_CHECK();
       }
+      if (keep) {
+        for (int s = 0; s < nsys; s++) h_slot[s] = s < nb ? h_tw[s] * n_orb + h_ta[s] : -1;
+        GFCC_CUDA(cudaMemcpyAsync(g_slot, h_slot.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+        GFCC_TRY(guess_store_put(st, nsys, n, gm.U, n, g_slot, c->kept.X));
+      }
       GFCC_CUDA(cudaMemcpyAsync(h_it.data(), gm.iters, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
       GFCC_CUDA(cudaMemcpyAsync(h_rel.data(), gm.relres, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
+      GFCC_CUDA(cudaMemcpyAsync(h_rel0.data(), gm.relres0, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
       GFCC_CUDA(cudaMemcpyAsync(h_state.data(), gm.state, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
+      if (guess != GFCC_GUESS_ZERO) {
+        GFCC_CUDA(cudaMemcpyAsync(h_kind.data(), g_kind, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
+        GFCC_CUDA(cudaMemcpyAsync(h_pred.data(), g_pred, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
+      }
       GFCC_CUDA(cudaStreamSynchronize(st));
       for (int s = 0; s < nb; s++) {
-        const long long idx = sec_slot * ntasks + t0 + s;
+        // statistics in (omega, orbital) order of the request
+        const long long idx = sec_slot * ntasks + (long long)h_tw[s] * n_orb + h_ta[s];
         c->st_iters[idx] = h_it[s];
         c->st_relres[idx] = h_rel[s];
+        c->st_relres0[idx] = h_rel0[s];
         c->st_status[idx] = h_state[s] == 3 ? GFCC_STATUS_CONVERGED : GFCC_STATUS_NOT_CONVERGED;
+        if (guess != GFCC_GUESS_ZERO) {
+          c->st_guess[idx] = h_kind[s];
+          c->st_guess_pred[idx] = h_pred[s];
+        }
+        // only converged solutions serve as neighbours (the Gram identity assumes A X_k = b)
+        if (keep && h_state[s] == 3) c->kept.done[(size_t)h_tw[s] * n_orb + h_ta[s]] = 1;
         all_ok &= h_state[s] == 3;
       }
     }
@@ -688,6 +792,19 @@ int check_solve_args(gfcc_ctx *c, int n_omega, double eta, int n_orb, double tol
 }
 
 }  // namespace
+
+int build_rhs(gfcc_ctx *c, int sector, int nsys, const int *d_porb, double *B, cudaStream_t st) {
+  if (nsys <= 0) return GFCC_OK;
+  if (sector == GFCC_SECTOR_IP) {
+    rhs_ip_kernel<<<grid1d(c->dim_ip * nsys), 256, 0, st>>>(B, c->dim_ip, nsys, d_porb, c->o, c->v, c->t1, c->t2);
+  } else {
+    rhs_ea_kernel<<<grid1d(c->dim_ea * nsys), 256, 0, st>>>(B, c->dim_ea, nsys, d_porb, c->o, c->v, c->Pv, c->t1,
+                                                            c->t2);
+  }
+  GFCC_LAUNCH_CHECK();
+  return GFCC_OK;
+}
+
 }  // namespace gfcc
 
 using namespace gfcc;
@@ -753,6 +870,14 @@ int gfcc_set_option(gfcc_ctx *c, int key, double value) {
     case GFCC_OPT_INNER_TOL:
       if (!(value > 0.0 && value < 1.0)) break;
       c->inner_tol = value;
+      return GFCC_OK;
+    case GFCC_OPT_GUESS:
+      if (iv != GFCC_GUESS_ZERO && iv != GFCC_GUESS_LEARNED && iv != GFCC_GUESS_MINRES) break;
+      c->guess = iv;
+      return GFCC_OK;
+    case GFCC_OPT_KEEP_SOLUTIONS:
+      if (iv != 0 && iv != 1) break;
+      c->keep_solutions = iv;
       return GFCC_OK;
     default:
       set_error("gfcc_set_option: unknown key %d", key);
@@ -854,6 +979,31 @@ int gfcc_last_stats(gfcc_ctx *c, int *count, int *iters, double *relres, int *st
   return GFCC_OK;
 }
 
+int gfcc_guess_stats(gfcc_ctx *c, int *count, int *kind, double *pred, double *relres0) {
+  if (c == nullptr || count == nullptr) {
+    set_error("gfcc_guess_stats: NULL argument");
+    return GFCC_ERR_ARG;
+  }
+  const int total = (int)c->st_guess.size();
+  const int nout = std::min(*count, total);
+  for (int i = 0; i < nout; i++) {
+    if (kind) kind[i] = c->st_guess[i];
+    if (pred) pred[i] = c->st_guess_pred[i];
+    if (relres0) relres0[i] = c->st_relres0[i];
+  }
+  *count = total;
+  return GFCC_OK;
+}
+
+int gfcc_set_guess_model(gfcc_ctx *c, gfcc_mlp *m) {
+  if (c == nullptr) {
+    set_error("gfcc_set_guess_model: ctx is NULL");
+    return GFCC_ERR_ARG;
+  }
+  c->mlp = m;
+  return GFCC_OK;
+}
+
 int gfcc_sigma(gfcc_ctx *c, int sector, int n_vec, const double *x, double *y) {
   return gfcc_sigma_ex(c, sector, GFCC_PREC_FP64, n_vec, x, y);
 }
@@ -915,6 +1065,7 @@ void gfcc_destroy(gfcc_ctx *c) {
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (void *p : c->allocs) dfree(p);
   if (c->scratch) dfree(c->scratch);
+  if (c->kept.X) dfree(c->kept.X);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
 }

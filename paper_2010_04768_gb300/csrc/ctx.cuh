@@ -20,7 +20,24 @@ enum GfccPhase {
   PH_RING_BF16 = 8,   // the ring contraction on the BF16 tensor cores (mixed precision)
   PH_RING_EMU = 9,    // the FP64-accurate ring contraction of the refinement residual (digit planes)
   PH_UNPACK = 10,     // expansion of packed vectors into the contraction layouts (BF16 / digits)
-  PH_COUNT = 11
+  PH_GUESS = 11,      // initial guesses: neighbour Gram matrices, model, coefficients, combination
+  PH_COUNT = 12
+};
+
+struct gfcc_mlp;
+
+// Converged solutions kept after a solve (FP32 complex, [omega][orbital][dim]): the neighbours
+// of the initial guesses, and training data for the guess model.
+struct KeptSolutions {
+  float2 *X = nullptr;
+  size_t bytes = 0;
+  int sector = 0;
+  long long n = 0;
+  int nw = 0, norb = 0;
+  double eta = 0.0;
+  std::vector<double> omega;
+  std::vector<int> orb;
+  std::vector<char> done;   // [omega][orbital]: slot holds a converged solution
 };
 
 struct gfcc_ctx {
@@ -84,9 +101,15 @@ struct gfcc_ctx {
 
   std::vector<void *> allocs;
 
+  // initial guesses (Algorithm 1: "compute initial guess")
+  int guess = 0;                 // GFCC_GUESS_*
+  int keep_solutions = 0;        // keep the converged solutions of the last sector solved
+  gfcc_mlp *mlp = nullptr;       // model of GFCC_GUESS_LEARNED (not owned)
+  KeptSolutions kept;
+
   // statistics of the last solve
-  std::vector<int> st_iters, st_status;
-  std::vector<double> st_relres;
+  std::vector<int> st_iters, st_status, st_guess;
+  std::vector<double> st_relres, st_guess_pred, st_relres0;
 
   // profiling (CUDA events on the context's stream)
   bool prof = false;

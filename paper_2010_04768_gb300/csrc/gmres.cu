@@ -465,6 +465,19 @@ __global__ void unprecondition_kernel(double *U, long long n, int nsys, const do
   }
 }
 
+// u_s = D_s x_s (an initial iterate into the preconditioned coordinates)
+__global__ void precondition_kernel(double *U, long long n, int nsys, const double *omega, double eta, double zsign,
+                                    const double *diag, double dsign) {
+  const long long tot = n * nsys;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(t / n);
+    const long long mu = t - (long long)s * n;
+    const double dr = omega[s] + dsign * diag[mu], di = zsign * eta;
+    const double2 x = ld2(U, t);
+    st2(U, t, make_double2(x.x * dr - x.y * di, x.x * di + x.y * dr));
+  }
+}
+
 __global__ void norm_from_partial_kernel(int nsys, const double *nrm2, int NV, double *out) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s < nsys) out[s] = sqrt(fmax(nrm2[2 * (long long)s * NV], 0.0));
@@ -486,7 +499,7 @@ long long gmres_work_doubles(const gfcc_ctx *c, int sector, long long n, int nsy
   w += 2LL * nsys * NV * 5;                 // h, h2, y, nrm (two slots)
   w += 2LL * nsys * (m + 1) * m;            // H
   w += 2LL * nsys * (2 * m + (m + 1));      // cs, sn, g
-  w += 7LL * nsys + 512;                    // bnorm, relres, est, omega, int state/kcyc/iters, alignment
+  w += 8LL * nsys + 512;                    // bnorm, relres, relres0, est, omega, int state/kcyc/iters, alignment
   w += sigma_work_doubles(c, sector, nsys);
   if (mixed) {
     w += 3 * 2LL * nsys * n + nsys + 64;     // X, R, B0, ||b0||
@@ -526,6 +539,7 @@ int Gmres::init(gfcc_ctx *ctx, int sec, long long dim, int ns, int mm, double *w
   take(g, 2LL * nsys * (m + 1));
   take(bnorm, nsys);
   take(relres, nsys);
+  take(relres0, nsys);
   take(est, nsys);
   take(omega, nsys);
   double *ip;
@@ -668,11 +682,18 @@ int Gmres::cgs2(const double *Vb, long long vs, int nv, double *w, cudaStream_t 
   return GFCC_OK;
 }
 
-int Gmres::solve(double tol, int max_iters, int *h_state, int max_cycles) {
+int Gmres::solve(double tol, int max_iters, int *h_state, int max_cycles, bool use_x0) {
   cudaStream_t st = c->stream;
   const long long vs = (long long)(m + 1) * n;   // basis stride per system (complex elements)
   const int T = 256;
-  GFCC_CUDA(cudaMemsetAsync(U, 0, sizeof(double) * 2 * nsys * n, st));
+  if (!use_x0) {
+    GFCC_CUDA(cudaMemsetAsync(U, 0, sizeof(double) * 2 * nsys * n, st));
+  } else if (use_precond) {
+    precondition_kernel<<<grid1d(n * nsys), T, 0, st>>>(
+        U, n, nsys, omega, eta, sector == GFCC_SECTOR_IP ? -1.0 : 1.0,
+        sector == GFCC_SECTOR_IP ? c->diag_ip : c->diag_ea, sector == GFCC_SECTOR_IP ? 1.0 : -1.0);
+    GFCC_LAUNCH_CHECK();
+  }
   GFCC_CUDA(cudaMemsetAsync(V, 0, sizeof(double) * 2 * nsys * (m + 1) * n, st));
   GFCC_CUDA(cudaMemsetAsync(iters, 0, sizeof(int) * nsys, st));
   GFCC_CUDA(cudaMemsetAsync(state, 0, sizeof(int) * nsys, st));   // ST_PENDING
@@ -680,7 +701,7 @@ int Gmres::solve(double tol, int max_iters, int *h_state, int max_cycles) {
   GFCC_TRY(mdot(B, n, 0, 1, B, n, nrm, ST_PENDING, 0));
   norm_from_partial_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, nrm, NV, bnorm);
   GFCC_LAUNCH_CHECK();
-  bool first = true;
+  bool first = !use_x0;
   for (int cycle = 0;; cycle++) {
     if (max_cycles > 0 && cycle >= max_cycles) {
       // cycle budget spent: the systems still pending keep their iterate (state 4)
@@ -702,6 +723,7 @@ int Gmres::solve(double tol, int max_iters, int *h_state, int max_cycles) {
     GFCC_LAUNCH_CHECK();
     vscale_kernel<<<grid1d(n * nsys), T, 0, st>>>(V, vs, n, nsys, nrm, NV, 0, state, ST_IN_CYCLE);
     GFCC_LAUNCH_CHECK();
+    if (cycle == 0) GFCC_CUDA(cudaMemcpyAsync(relres0, relres, sizeof(double) * nsys, cudaMemcpyDeviceToDevice, st));
     first = false;
     GFCC_CUDA(cudaMemcpyAsync(h_state, state, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
     GFCC_CUDA(cudaStreamSynchronize(st));
@@ -779,14 +801,14 @@ __global__ void zero_done_kernel(double *R, long long n, int nsys, const int *do
 }
 }  // namespace
 
-int Gmres::solve_refined(double tol, double inner_tol, int max_iters, int *h_state, int *h_iters) {
+int Gmres::solve_refined(double tol, double inner_tol, int max_iters, int *h_state, int *h_iters, bool use_x0) {
   cudaStream_t st = c->stream;
   const long long tot = 2LL * nsys * n;
   const int T = 256;
   std::vector<int> h_done(nsys, 0), it(nsys, 0);
   for (int s = 0; s < nsys; s++) h_iters[s] = 0;
   GFCC_CUDA(cudaMemcpyAsync(B0, B, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
-  GFCC_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * tot, st));
+  if (!use_x0) GFCC_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * tot, st));
   // ||b0|| into est (a free per-system slot during refinement)
   GFCC_TRY(mdot(B0, n, 0, 1, B0, n, nrm, -1, 0));
   int *done = kcyc;   // reused: per-system done flags between inner solves
@@ -795,7 +817,7 @@ int Gmres::solve_refined(double tol, double inner_tol, int max_iters, int *h_sta
   const int max_outer = 400;
   bool all_done = false;
   for (int outer = 0; outer <= max_outer; outer++) {
-    if (outer == 0) {
+    if (outer == 0 && !use_x0) {
       GFCC_CUDA(cudaMemcpyAsync(R, B0, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
     } else {
       GFCC_TRY(op_fp64(X, n, W, n));
@@ -805,6 +827,7 @@ int Gmres::solve_refined(double tol, double inner_tol, int max_iters, int *h_sta
     GFCC_TRY(mdot(R, n, 0, 1, R, n, nrm, -1, 0));
     refine_check_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, nrm, NV, b0norm, tol, done, relres);
     GFCC_LAUNCH_CHECK();
+    if (outer == 0) GFCC_CUDA(cudaMemcpyAsync(relres0, relres, sizeof(double) * nsys, cudaMemcpyDeviceToDevice, st));
     GFCC_CUDA(cudaMemcpyAsync(h_done.data(), done, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
     GFCC_CUDA(cudaStreamSynchronize(st));
     all_done = true;

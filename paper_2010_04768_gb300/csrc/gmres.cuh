@@ -25,6 +25,7 @@ struct Gmres {
   double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr;
   double *bnorm = nullptr, *relres = nullptr, *est = nullptr, *omega = nullptr;
   int *state = nullptr, *kcyc = nullptr, *iters = nullptr, *rflag = nullptr;
+  double *relres0 = nullptr;   // relative residual of the initial iterate (first true residual)
   double *sigma_work = nullptr;
 
   int init(gfcc_ctx *ctx, int sector, long long n, int nsys, int m, double *work, bool mixed = false);
@@ -32,14 +33,16 @@ struct Gmres {
   int op_fp64(const double *x, long long ldx, double *y, long long ldy);     // FP64, no preconditioner
   int mdot(const double *Vb, long long vs, long long vi, int nv, const double *w, long long ws, double *out, int want,
            int accumulate);
-  // max_cycles > 0 bounds the number of restart cycles (systems left pending end in state 4)
-  int solve(double tol, int max_iters, int *h_state, int max_cycles = 0);
+  // max_cycles > 0 bounds the number of restart cycles (systems left pending end in state 4).
+  // use_x0: U holds an initial iterate (unpreconditioned coordinates) instead of zero.
+  int solve(double tol, int max_iters, int *h_state, int max_cycles = 0, bool use_x0 = false);
   // one CGS2 orthogonalisation of w against basis vectors [0, nv) of every system in cycle
   int cgs2(const double *Vb, long long vs, int nv, double *w, cudaStream_t st);
   // iterative refinement: FP64 residual r = b - A x, inner GMRES on the mixed operator to
   // inner_tol, x += d, until ||r|| <= tol ||b||.  Leaves x in U, the FP64 relative residual in
   // relres, the summed inner iterations in h_iters and the final state (3 / 4) in h_state.
-  int solve_refined(double tol, double inner_tol, int max_iters, int *h_state, int *h_iters);
+  // use_x0: X holds an initial iterate instead of zero.
+  int solve_refined(double tol, double inner_tol, int max_iters, int *h_state, int *h_iters, bool use_x0 = false);
 };
 
 }  // namespace gfcc

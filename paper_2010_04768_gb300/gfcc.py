@@ -23,6 +23,10 @@ PREC_FP64, PREC_MIXED_BF16, PREC_FP64_EMULATED = 0, 1, 2
 PRECOND_NONE, PRECOND_DIAG = 0, 1
 OPT_SECTOR, OPT_PRECISION, OPT_RESTART, OPT_MAX_ITERS, OPT_PRECOND, OPT_BATCH, OPT_INNER_TOL = 1, 2, 3, 4, 5, 6, 7
 OPT_RESIDUAL, OPT_INNER_CYCLES, OPT_EMU_LEVEL = 8, 9, 10
+OPT_GUESS, OPT_KEEP_SOLUTIONS = 11, 12
+GUESS_ZERO, GUESS_LEARNED, GUESS_MINRES = 0, 1, 2
+MLP_FP32, MLP_FP64 = 0, 1
+MLP_FEATURES, MLP_OUTPUTS = 27, 16
 
 _SECTORS = {"IP": SECTOR_IP, "EA": SECTOR_EA, "IP+EA": SECTOR_BOTH, "BOTH": SECTOR_BOTH}
 _PRECS = {"fp64": PREC_FP64, "mixed": PREC_MIXED_BF16, "bf16": PREC_MIXED_BF16, "fp64emu": PREC_FP64_EMULATED}
@@ -74,10 +78,32 @@ def load():
     lib.gfcc_selftest_gemm_f64emu.restype = ctypes.c_int
     lib.gfcc_destroy.argtypes = [P]
     lib.gfcc_destroy.restype = None
+    lib.gfcc_guess_stats.argtypes = [P, ip, ip, dp, dp]
+    lib.gfcc_set_guess_model.argtypes = [P, P]
+    ull = ctypes.c_ulonglong
+    lib.gfcc_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.POINTER(P)]
+    lib.gfcc_mlp_destroy.argtypes = [P]
+    lib.gfcc_mlp_destroy.restype = None
+    lib.gfcc_mlp_num_params.argtypes = [P]
+    lib.gfcc_mlp_num_params.restype = ctypes.c_longlong
+    lib.gfcc_mlp_num_samples.argtypes = [P]
+    lib.gfcc_mlp_num_samples.restype = ctypes.c_longlong
+    lib.gfcc_mlp_get_params.argtypes = [P, dp]
+    lib.gfcc_mlp_set_params.argtypes = [P, dp]
+    lib.gfcc_mlp_forward.argtypes = [P, ctypes.c_int, dp, dp]
+    lib.gfcc_mlp_loss_grad.argtypes = [P, ctypes.c_int, dp, dp, dp, dp]
+    lib.gfcc_mlp_train_batch.argtypes = [P, ctypes.c_int, dp, dp, ctypes.c_double, dp]
+    lib.gfcc_mlp_collect.argtypes = [P, P, ctypes.c_int, ull, ctypes.POINTER(ctypes.c_longlong)]
+    lib.gfcc_mlp_train.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ull, dp]
+    lib.gfcc_mlp_eval.argtypes = [P, dp]
+    lib.gfcc_mlp_get_samples.argtypes = [P, ctypes.c_longlong, ctypes.c_int, dp, dp]
     lib.gfcc_last_error.restype = ctypes.c_char_p
     for name in ("gfcc_create", "gfcc_create_ex", "gfcc_set_option", "gfcc_set_stream", "gfcc_solve",
                  "gfcc_solve_device", "gfcc_last_stats", "gfcc_sigma", "gfcc_dims", "gfcc_profile",
-                 "gfcc_profile_read"):
+                 "gfcc_profile_read", "gfcc_guess_stats", "gfcc_set_guess_model", "gfcc_mlp_create",
+                 "gfcc_mlp_get_params", "gfcc_mlp_set_params", "gfcc_mlp_forward", "gfcc_mlp_loss_grad",
+                 "gfcc_mlp_train_batch", "gfcc_mlp_collect", "gfcc_mlp_train", "gfcc_mlp_eval",
+                 "gfcc_mlp_get_samples"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -203,8 +229,26 @@ class GFCC:
         _check(load().gfcc_sigma_noalloc(self._h, _SECTORS[sector], n_vec, ctypes.c_void_p(x_ptr),
                                          ctypes.c_void_p(y_ptr)))
 
+    def guess_stats(self):
+        """(kind, predicted ||r0||^2/||b||^2, measured ||r0||/||b||) per statistics entry of the last solve."""
+        lib = load()
+        cnt = ctypes.c_int(0)
+        _check(lib.gfcc_guess_stats(self._h, ctypes.byref(cnt), None, None, None))
+        n = cnt.value
+        kind = np.zeros(n, dtype=np.int32)
+        pred = np.zeros(n, dtype=np.float64)
+        rel0 = np.zeros(n, dtype=np.float64)
+        cnt = ctypes.c_int(n)
+        _check(lib.gfcc_guess_stats(self._h, ctypes.byref(cnt), kind.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                    _dp(pred), _dp(rel0)))
+        return kind, pred, rel0
+
+    def set_guess_model(self, model: "MLP | None"):
+        self._model = model   # keeps the model alive while attached
+        _check(load().gfcc_set_guess_model(self._h, None if model is None else model.handle))
+
     PHASES = ("setup", "ring", "vvvv", "sigma", "arnoldi", "lsq", "overlap", "solve", "ring_bf16", "ring_emu",
-              "unpack")
+              "unpack", "guess")
 
     def profile(self, enable: bool = True):
         _check(load().gfcc_profile(self._h, 1 if enable else 0))
@@ -226,3 +270,101 @@ class GFCC:
                                     X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                     Y.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return Y
+
+
+class MLP:
+    """One gfcc_mlp: the learned initial-guess model (3-layer perceptron, trained with Adam on the
+    Gram-matrix loss of the kept solutions)."""
+
+    def __init__(self, init_params: np.ndarray, hidden: int = 256, precision: int = MLP_FP32):
+        lib = load()
+        p = _f64(init_params).reshape(-1)
+        h = ctypes.c_void_p()
+        _check(lib.gfcc_mlp_create(int(hidden), int(precision), _dp(p), ctypes.byref(h)))
+        self._h = h
+        self.hidden = hidden
+        self.precision = precision
+
+    @staticmethod
+    def num_params_for(hidden: int) -> int:
+        return hidden * MLP_FEATURES + hidden + hidden * hidden + hidden + MLP_OUTPUTS * hidden + MLP_OUTPUTS + \
+            2 * MLP_FEATURES
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().gfcc_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def num_params(self) -> int:
+        return int(load().gfcc_mlp_num_params(self._h))
+
+    def num_samples(self) -> int:
+        return int(load().gfcc_mlp_num_samples(self._h))
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.num_params())
+        _check(load().gfcc_mlp_get_params(self._h, _dp(p)))
+        return p
+
+    def set_params(self, p: np.ndarray):
+        p = _f64(p).reshape(-1)
+        assert p.size == self.num_params()
+        _check(load().gfcc_mlp_set_params(self._h, _dp(p)))
+
+    def forward(self, features: np.ndarray) -> np.ndarray:
+        F = _f64(np.atleast_2d(features))
+        y = np.zeros((F.shape[0], MLP_OUTPUTS))
+        _check(load().gfcc_mlp_forward(self._h, F.shape[0], _dp(F), _dp(y)))
+        return y
+
+    def loss_grad(self, features: np.ndarray, gram: np.ndarray):
+        F = _f64(np.atleast_2d(features))
+        Gm = np.ascontiguousarray(gram, dtype=np.complex128).reshape(F.shape[0], 9, 9)
+        loss = ctypes.c_double()
+        g = np.zeros(self.num_params())
+        _check(load().gfcc_mlp_loss_grad(self._h, F.shape[0], _dp(F), Gm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         ctypes.byref(loss), _dp(g)))
+        return loss.value, g
+
+    def train_batch(self, features: np.ndarray, gram: np.ndarray, lr: float) -> float:
+        F = _f64(np.atleast_2d(features))
+        Gm = np.ascontiguousarray(gram, dtype=np.complex128).reshape(F.shape[0], 9, 9)
+        loss = ctypes.c_double()
+        _check(load().gfcc_mlp_train_batch(self._h, F.shape[0], _dp(F),
+                                           Gm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(lr),
+                                           ctypes.byref(loss)))
+        return loss.value
+
+    def collect(self, ctx: GFCC, samples_per_system: int = 2, seed: int = 0) -> int:
+        added = ctypes.c_longlong()
+        _check(load().gfcc_mlp_collect(self._h, ctx.handle, int(samples_per_system), int(seed), ctypes.byref(added)))
+        return added.value
+
+    def samples(self, start: int = 0, count: int | None = None):
+        """(features [count][27], Gram matrices [count][9][9] complex) of collected samples."""
+        count = self.num_samples() - start if count is None else count
+        F = np.zeros((count, MLP_FEATURES))
+        Gm = np.zeros((count, 9, 9), dtype=np.complex128)
+        _check(load().gfcc_mlp_get_samples(self._h, int(start), int(count), _dp(F),
+                                           Gm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return F, Gm
+
+    def train(self, steps: int, minibatch: int = 256, lr: float = 1e-3, seed: int = 0) -> float:
+        loss = ctypes.c_double()
+        _check(load().gfcc_mlp_train(self._h, int(steps), int(minibatch), float(lr), int(seed), ctypes.byref(loss)))
+        return loss.value
+
+    def eval(self) -> dict:
+        out = np.zeros(4)
+        _check(load().gfcc_mlp_eval(self._h, _dp(out)))
+        return {"loss": out[0], "loss_fallback": out[1], "loss_minres": out[2], "frac_better_than_zero": out[3]}

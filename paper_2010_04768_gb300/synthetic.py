@@ -43,6 +43,9 @@ STREAM_T2 = 5
 STREAM_LAMBDA1 = 6
 STREAM_LAMBDA2 = 7
 STREAM_VECTOR = 8
+STREAM_MLP_W1 = 101
+STREAM_MLP_W2 = 102
+STREAM_MLP_W3 = 103
 
 _CHUNK = 1 << 22
 
@@ -207,6 +210,18 @@ def random_vector(seed: int, count: int, stream_offset: int = 0) -> np.ndarray:
 # --------------------------------------------------------------------------------------------
 # Workload recipes
 # --------------------------------------------------------------------------------------------
+
+
+def mlp_init_params(hidden: int, seed: int, nin: int = 27, nout: int = 16) -> np.ndarray:
+    """Initial parameters of the guess model in its flat layout W1 b1 W2 b2 W3 b3 mu sd: He-scaled
+    normal weights (std sqrt(2 / fan_in); the output layer 0.1 sqrt(1 / hidden)), zero biases,
+    mu = 0, sd = 1."""
+    W1 = normal(seed, STREAM_MLP_W1, hidden * nin, math.sqrt(2.0 / nin))
+    W2 = normal(seed, STREAM_MLP_W2, hidden * hidden, math.sqrt(2.0 / hidden))
+    W3 = normal(seed, STREAM_MLP_W3, nout * hidden, 0.1 * math.sqrt(1.0 / hidden))
+    return np.concatenate([W1, np.zeros(hidden), W2, np.zeros(hidden), W3, np.zeros(nout), np.zeros(nin),
+                           np.ones(nin)])
+
 
 @dataclasses.dataclass
 class Workload:

@@ -48,3 +48,16 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert b"o >= 1" in typed.gfcc_last_error()
     assert typed.gfcc_set_option(None, 1, 1.0) == gfcc.ERR_ARG
     typed.gfcc_destroy(None)
+
+
+def test_guess_model_arguments_are_rejected_without_a_gpu(lib):
+    typed = gfcc.load()
+    h = ctypes.c_void_p()
+    assert typed.gfcc_mlp_create(256, gfcc.MLP_FP32, None, ctypes.byref(h)) == gfcc.ERR_ARG
+    assert typed.gfcc_mlp_create(0, gfcc.MLP_FP32, None, ctypes.byref(h)) == gfcc.ERR_ARG
+    loss = ctypes.c_double()
+    assert typed.gfcc_mlp_train(None, 10, 32, 1e-3, 0, ctypes.byref(loss)) == gfcc.ERR_ARG
+    assert typed.gfcc_mlp_collect(None, None, 1, 0, None) == gfcc.ERR_ARG
+    assert typed.gfcc_set_guess_model(None, None) == gfcc.ERR_ARG
+    assert typed.gfcc_mlp_num_params(None) == 0
+    typed.gfcc_mlp_destroy(None)
