@@ -295,7 +295,8 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         e2e_dt, e2e_cols = float(tmax[0]), int(t[1])
 
-    # roofline of the dominant kernel: the FP64 (DFMA) or the BF16 (tcgen05) ring contraction,
+    # roofline of the dominant kernel: the FP64 (DFMA) or BF16 (tcgen05) ring contraction or the
+    # Arnoldi orthogonalisation,
     # whichever took more device time inside the timed region
     peaks = measured_peaks()
     rf = {}
@@ -315,6 +316,16 @@ def main():
                                    "bf16_tflops_sustained of measured (kernel timed inside a long step); the "
                                    "achieved figure counts the tensor-core work of the launches (all digit "
                                    "pairs for the residual)"}
+    # Arnoldi orthogonalisation (HBM): algorithmic bytes of one classical Gram-Schmidt pass per step
+    ms, n_l, nbytes = prof["arnoldi"]
+    if ms > 0:
+        ach = nbytes / (ms / 1e3) / 1e9
+        hbm = peaks.get("hbm_gbs", 6761.6)
+        rf["arnoldi"] = {"bound": "hbm", "kernel": "cgs_dots_kernel + cgs_update_norm_kernel (+ vscale) of the "
+                         "Arnoldi step", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                         "traffic": None, "launches": n_l, "ms_total": ms,
+                         "peak_note": "hbm_gbs of measured; algorithmic bytes = (2(k+1) + 5) vectors x n x "
+                                      "bytes per complex element per system in cycle at Arnoldi step k"}
     dominant = max(rf, key=lambda k: rf[k]["ms_total"]) if rf else None
     # sigma TFLOP/s: algorithmic flops of every complex sigma product (inner BF16, FP64 and the
     # FP64-accurate residuals) at F_IP / F_EA each, over the device time of the sigma products

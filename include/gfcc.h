@@ -74,6 +74,9 @@ extern "C" {
 #define GFCC_OPT_GUESS      11    /* GFCC_GUESS_*: initial iterate of each GMRES solve; default ZERO     */
 #define GFCC_OPT_KEEP_SOLUTIONS 12 /* 1: keep the converged solutions of the last sector solved after
                                      gfcc_solve (for gfcc_mlp_collect); default 0                        */
+#define GFCC_OPT_INNER_KRYLOV 13  /* mixed precision: precision of the Krylov vectors of the inner GMRES
+                                     solves, 32 (default) or 64 bits; the refinement residual and the
+                                     solution stay FP64                                                  */
 
 /* Initial guesses (Algorithm 1, "compute initial guess").  With a guess other than ZERO, gfcc_solve
  * keeps every converged solution X_p(omega) (FP32 complex, n_omega * n_orb * dim * 8 bytes of device
@@ -196,7 +199,8 @@ int gfcc_dims(gfcc_ctx *ctx, long long *dim_ip, long long *dim_ea);
  * Profiling.  gfcc_profile(ctx, 1) resets the counters and times every later solve phase with CUDA
  * events on the context's stream (gfcc_profile(ctx, 0) stops).  gfcc_profile_read returns, for one
  * phase, the summed device time in milliseconds, the number of timed regions and the algorithmic
- * floating-point operations they performed (counted from the problem sizes, not measured).
+ * floating-point operations they performed (counted from the problem sizes, not measured; for
+ * phase 4 the count is algorithmic bytes of one classical Gram-Schmidt pass instead).
  * Phases: 0 setup (gfcc_create), 1 ring contraction of the sigma product, 2 EA vvvv contraction,
  * 3 whole sigma products (contains 1 and 2), 4 Arnoldi orthogonalisation, 5 Givens / least squares,
  * 6 right-hand sides, left vectors and overlaps, 7 whole gfcc_solve calls, 8 ring contraction on the

@@ -516,7 +516,7 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
 
 int choose_batch(gfcc_ctx *c, int sector, long long n, long long ntasks) {
   if (c->batch > 0) return (int)std::min<long long>(c->batch, ntasks);
-  const bool mixed = sector == GFCC_SECTOR_IP && c->precision == GFCC_PREC_MIXED_BF16;
+  const bool mixed = c->precision == GFCC_PREC_MIXED_BF16 && (sector == GFCC_SECTOR_IP ? c->Wr_bf : c->Wre_bf) != nullptr;
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
     cudaGetLastError();
@@ -614,8 +614,9 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
     if (!(c->sectors & sector)) continue;
     const bool ip = sector == GFCC_SECTOR_IP;
     const long long n = ip ? c->dim_ip : c->dim_ea;
-    // mixed precision covers the IP sector; EA systems of a mixed context are solved in FP64
-    const bool mixed = ip && c->precision == GFCC_PREC_MIXED_BF16;
+    // mixed precision: BF16 operator inside FP64-accurate refinement, in every sector whose BF16
+    // operands were built
+    const bool mixed = c->precision == GFCC_PREC_MIXED_BF16 && (ip ? c->Wr_bf : c->Wre_bf) != nullptr;
     if (keep) GFCC_TRY(prepare_kept(c, sector, n, n_omega, n_orb, d_om, d_orb, eta));
     const int nsys = choose_batch(c, sector, n, ntasks);
     const int m = c->restart;
@@ -695,7 +696,7 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
       GFCC_LAUNCH_CHECK();
       {
       PhaseTimer trhs(c, PH_OVERLAP);
-      GFCC_TRY(build_rhs(c, sector, nsys, d_porb, gm.B, st));
+      GFCC_TRY(build_rhs(c, sector, nsys, d_porb, gm.rhs(), st));
       }
       bool use_x0 = false;
       if (guess != GFCC_GUESS_ZERO) {
@@ -717,10 +718,10 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
         GFCC_CUDA(cudaMemcpyAsync(g_navail, h_navail.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
         GFCC_CUDA(cudaMemcpyAsync(g_delta, h_delta.data(), sizeof(double) * nsys * GUESS_K, cudaMemcpyHostToDevice, st));
         GFCC_CUDA(cudaMemcpyAsync(g_pf, h_pf.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, st));
-        GFCC_TRY(guess_gram(st, nsys, n, gm.B, n, kp.X, g_nbr, g_delta, gm.omega, eta, g_pf, g_Gm, g_feat, g_work));
+        GFCC_TRY(guess_gram(st, nsys, n, gm.rhs(), n, kp.X, g_nbr, g_delta, gm.omega, eta, g_pf, g_Gm, g_feat, g_work));
         if (guess == GFCC_GUESS_LEARNED) GFCC_TRY(mlp_infer(c->mlp, st, nsys, g_feat, g_y));
         GFCC_TRY(guess_choose(st, nsys, guess, g_Gm, g_y, g_navail, g_coef, g_pred, g_kind));
-        GFCC_TRY(guess_combine(st, nsys, n, kp.X, g_nbr, g_coef, g_kind, mixed ? gm.X : gm.U, n));
+        GFCC_TRY(guess_combine(st, nsys, n, kp.X, g_nbr, g_coef, g_kind, gm.solution(), n));
         use_x0 = true;
       }
       if (mixed) {
@@ -734,7 +735,7 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
       {
       PhaseTimer tov(c, PH_OVERLAP);
       Contract k;
-      k.A = gm.U; k.am = imap2(2, 1, 2 * n); k.ak = imap1(2);
+      k.A = gm.solution(); k.am = imap2(2, 1, 2 * n); k.ak = imap1(2);
       k.B = Cl; k.bk = imap1(1); k.bn = imap1(n);
       k.C = part; k.cm = imap1(n_orb); k.cn = imap1(1);
       k.M = 2LL * nsys; k.N = n_orb; k.K = n;
@@ -747,7 +748,7 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
       if (keep) {
         for (int s = 0; s < nsys; s++) h_slot[s] = s < nb ? h_tw[s] * n_orb + h_ta[s] : -1;
         GFCC_CUDA(cudaMemcpyAsync(g_slot, h_slot.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
-        GFCC_TRY(guess_store_put(st, nsys, n, gm.U, n, g_slot, c->kept.X));
+        GFCC_TRY(guess_store_put(st, nsys, n, gm.solution(), n, g_slot, c->kept.X));
       }
       GFCC_CUDA(cudaMemcpyAsync(h_it.data(), gm.iters, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
       GFCC_CUDA(cudaMemcpyAsync(h_rel.data(), gm.relres, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
@@ -874,6 +875,10 @@ int gfcc_set_option(gfcc_ctx *c, int key, double value) {
     case GFCC_OPT_GUESS:
       if (iv != GFCC_GUESS_ZERO && iv != GFCC_GUESS_LEARNED && iv != GFCC_GUESS_MINRES) break;
       c->guess = iv;
+      return GFCC_OK;
+    case GFCC_OPT_INNER_KRYLOV:
+      if (iv != 32 && iv != 64) break;
+      c->inner_fp64 = iv == 64 ? 1 : 0;
       return GFCC_OK;
     case GFCC_OPT_KEEP_SOLUTIONS:
       if (iv != 0 && iv != 1) break;
@@ -1016,10 +1021,10 @@ int gfcc_sigma_ex(gfcc_ctx *c, int sector, int precision, int n_vec, const doubl
   }
   const bool mixed = precision == GFCC_PREC_MIXED_BF16;
   const bool emu = precision == GFCC_PREC_FP64_EMULATED;
+  const bool ip = sector == GFCC_SECTOR_IP;
   if ((precision != GFCC_PREC_FP64 && !mixed && !emu) ||
-      ((mixed || emu) && (sector != GFCC_SECTOR_IP || c->Wr_bf == nullptr))) {
-    set_error("gfcc_sigma_ex: mixed / emulated precision needs the IP sector of a context created with "
-              "GFCC_PREC_MIXED_BF16");
+      ((mixed || emu) && (ip ? c->Wr_bf : c->Wre_bf) == nullptr)) {
+    set_error("gfcc_sigma_ex: mixed / emulated precision needs a context created with GFCC_PREC_MIXED_BF16");
     return GFCC_ERR_ARG;
   }
   if (n_vec == 0) return GFCC_OK;
@@ -1038,7 +1043,10 @@ int gfcc_sigma_ex(gfcc_ctx *c, int sector, int precision, int n_vec, const doubl
   b.y = dy; b.ldy = n;
   if (mixed || emu) {
     GFCC_TRY(umma_error_reset(c->stream));
-    GFCC_TRY(mixed ? apply_ip_mixed(c, b, w) : apply_ip_emu(c, b, w, ew));
+    if (ip)
+      GFCC_TRY(mixed ? apply_ip_mixed(c, b, w) : apply_ip_emu(c, b, w, ew));
+    else
+      GFCC_TRY(mixed ? apply_ea_mixed(c, b, w) : apply_ea_emu(c, b, w, ew));
     GFCC_TRY(umma_error_check(c->stream));
   } else {
     GFCC_TRY(sector == GFCC_SECTOR_IP ? apply_ip(c, b, w) : apply_ea(c, b, w));

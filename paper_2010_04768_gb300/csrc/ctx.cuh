@@ -54,6 +54,7 @@ struct gfcc_ctx {
   int batch = 0;
   double inner_tol = 1e-3;
   int inner_cycles = 1;      // GMRES restart cycles per refinement step (each ends with an FP64-accurate residual)
+  int inner_fp64 = 0;        // 1: FP64 Krylov vectors in the inner solves (default FP32)
 
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;
@@ -98,6 +99,18 @@ struct gfcc_ctx {
   double *T3e = nullptr;     // [(i,b,a)][m]    -t2[m,i,a,b]
   double *U1e = nullptr;     // [a][(m,x,y)]    Fov / Wvovv couplings of the 1p row
   double *diag_ea = nullptr;
+
+  // mixed-precision EA operands (BF16, K-major, strides padded to multiples of 8; the Fock-like
+  // diagonal diag_ea is left out and applied in FP64)
+  __nv_bfloat16 *Wre_bf = nullptr;  // [(i,b)][(m,e)]   ring core + off-diagonal Fbar folding, ld_ov
+  __nv_bfloat16 *Wp_bf = nullptr;   // [(a<b)][(e<f)]   Wvvvv, ld_pv
+  __nv_bfloat16 *W3_bf = nullptr;   // [(i,b,a)][e]     Wvvvo, ld_v
+  __nv_bfloat16 *V3e_bf = nullptr;  // [m][(n,f,e)]     1/2 <mn||ef>', ld_ov2
+  __nv_bfloat16 *T3e_bf = nullptr;  // [(i,b,a)][m]     -t2[m,i,a,b], ld_o
+  __nv_bfloat16 *U1e_bf = nullptr;  // [a][(m,x,y) | e] U1e and the off-diagonal Fbar_vv of the 1p row, ld_k1e
+  long long ld_pv = 0, ld_ov2 = 0, ld_k1e = 0;
+  // digit planes of the FP64 EA operands (full Fock folding) for the FP64-accurate residual
+  gfcc::EmuOperand eWre, eWp, eW3, eV3e, eT3e, eU1e;
 
   std::vector<void *> allocs;
 

@@ -31,6 +31,37 @@ constexpr int DOT_THREADS = 256, DOT_PER_THREAD = 8, DOT_CHUNK = DOT_THREADS * D
 __device__ __forceinline__ double2 ld2(const double *p, long long i) { return reinterpret_cast<const double2 *>(p)[i]; }
 __device__ __forceinline__ void st2(double *p, long long i, double2 v) { reinterpret_cast<double2 *>(p)[i] = v; }
 
+// Krylov vectors are complex interleaved arrays of T = double (FP64 solves) or T = float (the inner
+// solves of mixed-precision refinement).  Arithmetic on vector elements runs in T; sums across
+// elements are reduced in double.
+template <typename T>
+struct Cplx;
+template <>
+struct Cplx<double> {
+  using type = double2;
+};
+template <>
+struct Cplx<float> {
+  using type = float2;
+};
+template <typename T>
+using CT = typename Cplx<T>::type;
+template <typename T>
+__device__ __forceinline__ CT<T> ldc(const T *p, long long i) {
+  return reinterpret_cast<const CT<T> *>(p)[i];
+}
+template <typename T>
+__device__ __forceinline__ void stc(T *p, long long i, CT<T> v) {
+  reinterpret_cast<CT<T> *>(p)[i] = v;
+}
+template <typename T>
+__device__ __forceinline__ CT<T> mkc(double x, double y) {
+  CT<T> r;
+  r.x = (T)x;
+  r.y = (T)y;
+  return r;
+}
+
 // Block-wide sum of a complex value; result valid in thread 0.
 __device__ __forceinline__ double2 block_sum(double2 v, double2 *sh) {
   for (int off = 16; off > 0; off >>= 1) {
@@ -52,8 +83,9 @@ __device__ __forceinline__ double2 block_sum(double2 v, double2 *sh) {
 }
 
 // partial[(s*NV + i)*nch + chunk] = sum_{mu in chunk} conj(Vs_i[mu]) w_s[mu]   (systems with state == want)
-__global__ __launch_bounds__(DOT_THREADS) void mdot_partial_kernel(const double *V, long long vs_stride,
-                                                                   long long vi_stride, int nv, const double *w,
+template <typename T>
+__global__ __launch_bounds__(DOT_THREADS) void mdot_partial_kernel(const T *V, long long vs_stride,
+                                                                   long long vi_stride, int nv, const T *w,
                                                                    long long ws_stride, long long n, int nch,
                                                                    const int *state, int want, double *partial,
                                                                    int NV) {
@@ -61,25 +93,26 @@ __global__ __launch_bounds__(DOT_THREADS) void mdot_partial_kernel(const double 
   const int s = blockIdx.y, chunk = blockIdx.x;
   if (state != nullptr && state[s] != want) return;
   const long long base = (long long)chunk * DOT_CHUNK;
-  double2 wv[DOT_PER_THREAD];
-  const double *ws = w + 2 * s * ws_stride;
+  CT<T> wv[DOT_PER_THREAD];
+  const T *ws = w + 2 * s * ws_stride;
 #pragma unroll
   for (int r = 0; r < DOT_PER_THREAD; r++) {
     const long long mu = base + threadIdx.x + (long long)r * DOT_THREADS;
-    wv[r] = mu < n ? ld2(ws, mu) : make_double2(0.0, 0.0);
+    wv[r] = mu < n ? ldc(ws, mu) : mkc<T>(0.0, 0.0);
   }
   for (int i = 0; i < nv; i++) {
-    const double *vi = V + 2 * (s * vs_stride + i * vi_stride);
-    double2 acc = make_double2(0.0, 0.0);
+    const T *vi = V + 2 * (s * vs_stride + i * vi_stride);
+    CT<T> a2 = mkc<T>(0.0, 0.0);
 #pragma unroll
     for (int r = 0; r < DOT_PER_THREAD; r++) {
       const long long mu = base + threadIdx.x + (long long)r * DOT_THREADS;
       if (mu < n) {
-        const double2 a = ld2(vi, mu);
-        acc.x += a.x * wv[r].x + a.y * wv[r].y;
-        acc.y += a.x * wv[r].y - a.y * wv[r].x;
+        const CT<T> a = ldc(vi, mu);
+        a2.x += a.x * wv[r].x + a.y * wv[r].y;
+        a2.y += a.x * wv[r].y - a.y * wv[r].x;
       }
     }
+    double2 acc = make_double2((double)a2.x, (double)a2.y);
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) reinterpret_cast<double2 *>(partial)[((long long)s * NV + i) * nch + chunk] = acc;
   }
@@ -115,32 +148,34 @@ __global__ void mdot_final_kernel(const double *partial, int nsys, int nv, int N
 
 // w_s[mu] += sign * sum_{i<nv_s} coef[s*NV + i] Vs_i[mu]   (systems with state == want;
 // nv_s = nvs[s] when nvs != nullptr, else nv)
-__global__ void vupdate_kernel(const double *V, long long vs_stride, long long vi_stride, int nv, const int *nvs,
-                               const double *coef, int NV, double sign, double *w, long long ws_stride, long long n,
+template <typename T>
+__global__ void vupdate_kernel(const T *V, long long vs_stride, long long vi_stride, int nv, const int *nvs,
+                               const double *coef, int NV, double sign, T *w, long long ws_stride, long long n,
                                int nsys, const int *state, int want) {
   const long long tot = n * nsys;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     const int s = (int)(t / n);
     const long long mu = t - (long long)s * n;
     if (state != nullptr && state[s] != want) continue;
-    double2 acc = make_double2(0.0, 0.0);
+    CT<T> acc = mkc<T>(0.0, 0.0);
     const double2 *cf = reinterpret_cast<const double2 *>(coef) + (long long)s * NV;
     const int nvv = nvs != nullptr ? nvs[s] : nv;
     for (int i = 0; i < nvv; i++) {
-      const double2 a = ld2(V + 2 * (s * vs_stride + i * vi_stride), mu);
-      const double2 c = cf[i];
-      acc.x += c.x * a.x - c.y * a.y;
-      acc.y += c.x * a.y + c.y * a.x;
+      const CT<T> a = ldc(V + 2 * (s * vs_stride + i * vi_stride), mu);
+      const T cx = (T)cf[i].x, cy = (T)cf[i].y;
+      acc.x += cx * a.x - cy * a.y;
+      acc.y += cx * a.y + cy * a.x;
     }
-    double2 x = ld2(w + 2 * s * ws_stride, mu);
-    x.x += sign * acc.x;
-    x.y += sign * acc.y;
-    st2(w + 2 * s * ws_stride, mu, x);
+    CT<T> x = ldc(w + 2 * s * ws_stride, mu);
+    x.x += (T)sign * acc.x;
+    x.y += (T)sign * acc.y;
+    stc(w + 2 * s * ws_stride, mu, x);
   }
 }
 
 // w_s *= 1 / scale[s] (real scale stored as the real part of a complex entry scale[s*NV + idx])
-__global__ void vscale_kernel(double *w, long long ws_stride, long long n, int nsys, const double *nrm2, int NV,
+template <typename T>
+__global__ void vscale_kernel(T *w, long long ws_stride, long long n, int nsys, const double *nrm2, int NV,
                               int idx, const int *state, int want) {
   const long long tot = n * nsys;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
@@ -149,24 +184,25 @@ __global__ void vscale_kernel(double *w, long long ws_stride, long long n, int n
     if (state != nullptr && state[s] != want) continue;
     const double nn = nrm2[2 * ((long long)s * NV + idx)];
     if (!(nn > 0.0)) continue;
-    const double inv = 1.0 / sqrt(nn);
-    double2 x = ld2(w + 2 * s * ws_stride, mu);
+    const T inv = (T)(1.0 / sqrt(nn));
+    CT<T> x = ldc(w + 2 * s * ws_stride, mu);
     x.x *= inv;
     x.y *= inv;
-    st2(w + 2 * s * ws_stride, mu, x);
+    stc(w + 2 * s * ws_stride, mu, x);
   }
 }
 
 // r_s = b_s - w_s for systems that are not finished
-__global__ void resid_form_kernel(const double *B, const double *W, double *R, long long r_stride, long long n,
-                                  int nsys, const int *state) {
+template <typename T>
+__global__ void resid_form_kernel(const T *B, const T *W, T *R, long long r_stride, long long n, int nsys,
+                                  const int *state) {
   const long long tot = n * nsys;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     const int s = (int)(t / n);
     const long long mu = t - (long long)s * n;
     if (state[s] != ST_PENDING) continue;
-    const double2 b = ld2(B, t), w = ld2(W, t);
-    st2(R + 2 * s * r_stride, mu, make_double2(b.x - w.x, b.y - w.y));
+    const CT<T> b = ldc(B, t), w = ldc(W, t);
+    stc(R + 2 * s * r_stride, mu, mkc<T>(b.x - w.x, b.y - w.y));
   }
 }
 
@@ -312,108 +348,73 @@ __device__ __forceinline__ void block_reduce_store(double2 (&acc)[NVT], int nv, 
 }
 
 // pass 1: partial dots conj(V_i) . w (i < nv) and, in slot nv, the squared norm of w
-template <int NVT>
-__global__ __launch_bounds__(FUSED_THREADS) void cgs_dots_kernel(const double *V, long long vs, long long vi, int nv,
-                                                                 const double *w, long long n, int nch,
-                                                                 const int *state, int want, double *partial, int NV) {
+template <int NVT, typename T>
+__global__ __launch_bounds__(FUSED_THREADS) void cgs_dots_kernel(const T *V, long long vs, long long vi, int nv,
+                                                                 const T *w, long long n, int nch, const int *state,
+                                                                 int want, double *partial, int NV) {
   __shared__ double2 sh[(FUSED_THREADS / 32) * NVT];
   const int s = blockIdx.y, chunk = blockIdx.x;
   if (state[s] != want) return;
-  double2 acc[NVT];
+  CT<T> a2[NVT];
 #pragma unroll
-  for (int i = 0; i < NVT; i++) acc[i] = make_double2(0.0, 0.0);
-  const double *ws = w + 2 * s * vs;
-  const double *Vs = V + 2 * s * vs;
+  for (int i = 0; i < NVT; i++) a2[i] = mkc<T>(0.0, 0.0);
+  const T *ws = w + 2 * s * vs;
+  const T *Vs = V + 2 * s * vs;
   for (int r = 0; r < FUSED_PER; r++) {
     const long long mu = (long long)chunk * FUSED_CHUNK + threadIdx.x + (long long)r * FUSED_THREADS;
     if (mu >= n) break;
-    const double2 x = ld2(ws, mu);
+    const CT<T> x = ldc(ws, mu);
 #pragma unroll
     for (int i = 0; i < NVT; i++) {
       if (i >= nv) break;
-      const double2 a = ld2(Vs + 2 * i * vi, mu);
-      acc[i].x += a.x * x.x + a.y * x.y;
-      acc[i].y += a.x * x.y - a.y * x.x;
+      const CT<T> a = ldc(Vs + 2 * i * vi, mu);
+      a2[i].x += a.x * x.x + a.y * x.y;
+      a2[i].y += a.x * x.y - a.y * x.x;
     }
 #pragma unroll
     for (int i = 0; i < NVT; i++)
-      if (i == nv) acc[i].x += x.x * x.x + x.y * x.y;
+      if (i == nv) a2[i].x += x.x * x.x + x.y * x.y;
   }
+  double2 acc[NVT];
+#pragma unroll
+  for (int i = 0; i < NVT; i++) acc[i] = make_double2((double)a2[i].x, (double)a2[i].y);
   block_reduce_store<NVT>(acc, nv + 1, sh, partial, s, NV, nch, chunk);
 }
 
-// pass 2: w -= V h1 (in place), then partial dots conj(V_i) . w  (each basis value read once)
-template <int NVT>
-__global__ __launch_bounds__(FUSED_THREADS) void cgs_update_dots_kernel(const double *V, long long vs, long long vi,
-                                                                        int nv, double *w, long long n, int nch,
-                                                                        const int *state, int want, const double *h1,
-                                                                        double *partial, int NV) {
-  __shared__ double2 sh[(FUSED_THREADS / 32) * NVT];
-  __shared__ double2 hh[NVT];
-  const int s = blockIdx.y, chunk = blockIdx.x;
-  if (state[s] != want) return;
-  if (threadIdx.x < nv) hh[threadIdx.x] = reinterpret_cast<const double2 *>(h1)[(long long)s * NV + threadIdx.x];
-  __syncthreads();
-  double2 acc[NVT];
-#pragma unroll
-  for (int i = 0; i < NVT; i++) acc[i] = make_double2(0.0, 0.0);
-  double *ws = w + 2 * s * vs;
-  const double *Vs = V + 2 * s * vs;
-  for (int r = 0; r < FUSED_PER; r++) {
-    const long long mu = (long long)chunk * FUSED_CHUNK + threadIdx.x + (long long)r * FUSED_THREADS;
-    if (mu >= n) break;
-    double2 x = ld2(ws, mu);
-#pragma unroll
-    for (int i = 0; i < NVT; i++) {
-      if (i >= nv) break;
-      const double2 a = ld2(Vs + 2 * i * vi, mu);
-      const double2 c = hh[i];
-      x.x -= c.x * a.x - c.y * a.y;
-      x.y -= c.x * a.y + c.y * a.x;
-    }
-    st2(ws, mu, x);
-    // second sweep over the same basis elements: served from L1
-#pragma unroll
-    for (int i = 0; i < NVT; i++) {
-      if (i >= nv) break;
-      const double2 a = ld2(Vs + 2 * i * vi, mu);
-      acc[i].x += a.x * x.x + a.y * x.y;
-      acc[i].y += a.x * x.y - a.y * x.x;
-    }
-  }
-  block_reduce_store<NVT>(acc, nv, sh, partial, s, NV, nch, chunk);
-}
-
 // pass 3: w -= V h2 (in place), then the partial squared norm of w
-template <int NVT>
-__global__ __launch_bounds__(FUSED_THREADS) void cgs_update_norm_kernel(const double *V, long long vs, long long vi,
-                                                                        int nv, double *w, long long n, int nch,
+template <int NVT, typename T>
+__global__ __launch_bounds__(FUSED_THREADS) void cgs_update_norm_kernel(const T *V, long long vs, long long vi,
+                                                                        int nv, T *w, long long n, int nch,
                                                                         const int *state, int want, const double *h2,
                                                                         double *partial, int NV) {
   __shared__ double2 sh[(FUSED_THREADS / 32) * 1];
-  __shared__ double2 hh[NVT];
+  __shared__ CT<T> hh[NVT];
   const int s = blockIdx.y, chunk = blockIdx.x;
   if (state[s] != want) return;
-  if (threadIdx.x < nv) hh[threadIdx.x] = reinterpret_cast<const double2 *>(h2)[(long long)s * NV + threadIdx.x];
+  if (threadIdx.x < nv) {
+    const double2 c = reinterpret_cast<const double2 *>(h2)[(long long)s * NV + threadIdx.x];
+    hh[threadIdx.x] = mkc<T>(c.x, c.y);
+  }
   __syncthreads();
-  double2 acc[1] = {make_double2(0.0, 0.0)};
-  double *ws = w + 2 * s * vs;
-  const double *Vs = V + 2 * s * vs;
+  T nn = T(0);
+  T *ws = w + 2 * s * vs;
+  const T *Vs = V + 2 * s * vs;
   for (int r = 0; r < FUSED_PER; r++) {
     const long long mu = (long long)chunk * FUSED_CHUNK + threadIdx.x + (long long)r * FUSED_THREADS;
     if (mu >= n) break;
-    double2 x = ld2(ws, mu);
+    CT<T> x = ldc(ws, mu);
 #pragma unroll
     for (int i = 0; i < NVT; i++) {
       if (i >= nv) break;
-      const double2 a = ld2(Vs + 2 * i * vi, mu);
-      const double2 c = hh[i];
+      const CT<T> a = ldc(Vs + 2 * i * vi, mu);
+      const CT<T> c = hh[i];
       x.x -= c.x * a.x - c.y * a.y;
       x.y -= c.x * a.y + c.y * a.x;
     }
-    st2(ws, mu, x);
-    acc[0].x += x.x * x.x + x.y * x.y;
+    stc(ws, mu, x);
+    nn += x.x * x.x + x.y * x.y;
   }
+  double2 acc[1] = {make_double2((double)nn, 0.0)};
   block_reduce_store<1>(acc, 1, sh, partial, s, NV, nch, chunk);
 }
 
@@ -452,7 +453,8 @@ __global__ void set_state_kernel(int nsys, int *state, int from, int to) {
 }
 
 // x_s = u_s / D_s (final solution from the preconditioned iterate)
-__global__ void unprecondition_kernel(double *U, long long n, int nsys, const double *omega, double eta, double zsign,
+template <typename T>
+__global__ void unprecondition_kernel(T *U, long long n, int nsys, const double *omega, double eta, double zsign,
                                       const double *diag, double dsign) {
   const long long tot = n * nsys;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
@@ -460,21 +462,24 @@ __global__ void unprecondition_kernel(double *U, long long n, int nsys, const do
     const long long mu = t - (long long)s * n;
     const double dr = omega[s] + dsign * diag[mu], di = zsign * eta;
     const double d2 = dr * dr + di * di;
-    const double2 u = ld2(U, t);
-    st2(U, t, make_double2((u.x * dr + u.y * di) / d2, (u.y * dr - u.x * di) / d2));
+    const CT<T> u = ldc(U, t);
+    const double ux = u.x, uy = u.y;
+    stc(U, t, mkc<T>((ux * dr + uy * di) / d2, (uy * dr - ux * di) / d2));
   }
 }
 
 // u_s = D_s x_s (an initial iterate into the preconditioned coordinates)
-__global__ void precondition_kernel(double *U, long long n, int nsys, const double *omega, double eta, double zsign,
+template <typename T>
+__global__ void precondition_kernel(T *U, long long n, int nsys, const double *omega, double eta, double zsign,
                                     const double *diag, double dsign) {
   const long long tot = n * nsys;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     const int s = (int)(t / n);
     const long long mu = t - (long long)s * n;
     const double dr = omega[s] + dsign * diag[mu], di = zsign * eta;
-    const double2 x = ld2(U, t);
-    st2(U, t, make_double2(x.x * dr - x.y * di, x.x * di + x.y * dr));
+    const CT<T> x = ldc(U, t);
+    const double xx = x.x, xy = x.y;
+    stc(U, t, mkc<T>(xx * dr - xy * di, xx * di + xy * dr));
   }
 }
 
@@ -489,12 +494,22 @@ __global__ void norm_from_partial_kernel(int nsys, const double *nrm2, int NV, d
 // host side
 // ------------------------------------------------------------------------------------------
 
+namespace {
+// doubles occupied by `count` elements of type T
+template <typename T>
+long long dbl_of(long long count) {
+  return (count * (long long)sizeof(T) + 7) / 8;
+}
+}  // namespace
+
 long long gmres_work_doubles(const gfcc_ctx *c, int sector, long long n, int nsys, int m, bool mixed) {
   const long long NV = m + 2;
   const long long nch = (n + FUSED_CHUNK - 1) / FUSED_CHUNK;   // the finer of the two chunkings
+  const bool f32 = mixed && c->inner_fp64 == 0;
   long long w = 0;
-  w += 2LL * nsys * (m + 1) * n;            // V
-  w += 3 * 2LL * nsys * n;                  // U, B, W
+  const long long vb = 2LL * nsys * (m + 1) * n, vv = 2LL * nsys * n;
+  w += f32 ? dbl_of<float>(vb) : vb;            // V
+  w += 3 * (f32 ? dbl_of<float>(vv) : vv);      // U, B, W
   w += 2LL * nsys * NV * nch;               // dot partials
   w += 2LL * nsys * NV * 5;                 // h, h2, y, nrm (two slots)
   w += 2LL * nsys * (m + 1) * m;            // H
@@ -504,7 +519,7 @@ long long gmres_work_doubles(const gfcc_ctx *c, int sector, long long n, int nsy
   if (mixed) {
     w += 3 * 2LL * nsys * n + nsys + 64;     // X, R, B0, ||b0||
     w += sigma_mixed_work_doubles(c, nsys);
-    if (c->eWr.dig != nullptr) w += sigma_emu_work_doubles(c, std::min(nsys, 16));
+    if (c->eWr.dig != nullptr || c->eWre.dig != nullptr) w += sigma_emu_work_doubles(c, std::min(nsys, 16));
   }
   return w;
 }
@@ -512,6 +527,7 @@ long long gmres_work_doubles(const gfcc_ctx *c, int sector, long long n, int nsy
 int Gmres::init(gfcc_ctx *ctx, int sec, long long dim, int ns, int mm, double *work, bool mx) {
   c = ctx;
   mixed = mx;
+  f32 = mixed && c->inner_fp64 == 0;
   sector = sec;
   n = dim;
   nsys = ns;
@@ -524,10 +540,11 @@ int Gmres::init(gfcc_ctx *ctx, int sec, long long dim, int ns, int mm, double *w
     dst = p;
     p += (cnt + 7) & ~7LL;
   };
-  take(V, 2LL * nsys * (m + 1) * n);
-  take(U, 2LL * nsys * n);
-  take(B, 2LL * nsys * n);
-  take(W, 2LL * nsys * n);
+  const long long vb = 2LL * nsys * (m + 1) * n, vv = 2LL * nsys * n;
+  take(V, f32 ? dbl_of<float>(vb) : vb);
+  take(U, f32 ? dbl_of<float>(vv) : vv);
+  take(B, f32 ? dbl_of<float>(vv) : vv);
+  take(W, f32 ? dbl_of<float>(vv) : vv);
   take(partial, 2LL * nsys * NV * nch_alloc);
   take(h, 2LL * nsys * NV);
   take(h2, 2LL * nsys * NV);
@@ -565,7 +582,8 @@ int Gmres::init(gfcc_ctx *ctx, int sec, long long dim, int ns, int mm, double *w
 }
 
 int Gmres::op_fp64(const double *x, long long ldx, double *yout, long long ldy) {
-  if (mixed && sector == GFCC_SECTOR_IP && c->residual_emulated && c->eWr.dig != nullptr) {
+  const bool ip = sector == GFCC_SECTOR_IP;
+  if (mixed && c->residual_emulated && (ip ? c->eWr.dig : c->eWre.dig) != nullptr) {
     SysBatch b;
     b.nsys = nsys;
     b.x = x;
@@ -575,7 +593,8 @@ int Gmres::op_fp64(const double *x, long long ldx, double *yout, long long ldy) 
     b.omega = omega;
     b.eta = eta;
     double *ew = sigma_work + sigma_work_doubles(c, sector, nsys) + sigma_mixed_work_doubles(c, nsys);
-    return apply_ip_emu(c, b, ew, sigma_emu_work_doubles(c, std::min(nsys, 16)));
+    const long long ewd = sigma_emu_work_doubles(c, std::min(nsys, 16));
+    return ip ? apply_ip_emu(c, b, ew, ewd) : apply_ea_emu(c, b, ew, ewd);
   }
   SysBatch b;
   b.nsys = nsys;
@@ -591,32 +610,44 @@ int Gmres::op_fp64(const double *x, long long ldx, double *yout, long long ldy) 
   return sector == GFCC_SECTOR_IP ? apply_ip(c, b, sigma_work) : apply_ea(c, b, sigma_work);
 }
 
-int Gmres::op(const double *x, long long ldx, double *yout, long long ldy) {
+template <typename T>
+int Gmres::op_t(const T *x, long long ldx, T *yout, long long ldy) {
   SysBatch b;
   b.nsys = nsys;
-  b.x = x;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    b.xf = x;
+    b.yf = yout;
+  } else {
+    b.x = x;
+    b.y = yout;
+  }
   b.ldx = ldx;
-  b.y = yout;
   b.ldy = ldy;
   b.omega = omega;
   b.eta = eta;
   b.diag = use_precond ? (sector == GFCC_SECTOR_IP ? c->diag_ip : c->diag_ea) : nullptr;
   b.dsign = sector == GFCC_SECTOR_IP ? 1.0 : -1.0;
   b.zsign = sector == GFCC_SECTOR_IP ? -1.0 : 1.0;
-  if (mixed && sector == GFCC_SECTOR_IP) {
+  if (mixed) {
     double *mw = sigma_work + sigma_work_doubles(c, sector, nsys);
-    return apply_ip_mixed(c, b, mw);
+    return sector == GFCC_SECTOR_IP ? apply_ip_mixed(c, b, mw) : apply_ea_mixed(c, b, mw);
   }
-  return sector == GFCC_SECTOR_IP ? apply_ip(c, b, sigma_work) : apply_ea(c, b, sigma_work);
+  if constexpr (sizeof(T) == sizeof(float)) {
+    set_error("internal: FP32 Krylov vectors need the mixed-precision IP operator");
+    return GFCC_ERR_STATE;
+  } else {
+    return sector == GFCC_SECTOR_IP ? apply_ip(c, b, sigma_work) : apply_ea(c, b, sigma_work);
+  }
 }
 
 // dots of vectors [0, nv) of each system's basis (V + s*vs + i*vi) with w (w + s*ws) -> out
-int Gmres::mdot(const double *Vb, long long vs, long long vi, int nv, const double *w, long long ws, double *out,
-                int want, int accumulate) {
+template <typename T>
+int Gmres::mdot_t(const T *Vb, long long vs, long long vi, int nv, const T *w, long long ws, double *out, int want,
+                  int accumulate) {
   cudaStream_t st = c->stream;
   dim3 grid(nch, nsys);
   const int *filt = want < 0 ? nullptr : state;   // want < 0: every system
-  mdot_partial_kernel<<<grid, DOT_THREADS, 0, st>>>(Vb, vs, vi, nv, w, ws, n, nch, filt, want, partial, NV);
+  mdot_partial_kernel<T><<<grid, DOT_THREADS, 0, st>>>(Vb, vs, vi, nv, w, ws, n, nch, filt, want, partial, NV);
   GFCC_LAUNCH_CHECK();
   const int warps = nsys * nv;
   mdot_final_kernel<<<cdiv(warps * 32LL, 256), 256, 0, st>>>(partial, nsys, nv, NV, nch, filt, want, out, accumulate);
@@ -624,33 +655,38 @@ int Gmres::mdot(const double *Vb, long long vs, long long vi, int nv, const doub
   return GFCC_OK;
 }
 
+int Gmres::mdot(const double *Vb, long long vs, long long vi, int nv, const double *w, long long ws, double *out,
+                int want, int accumulate) {
+  return mdot_t<double>(Vb, vs, vi, nv, w, ws, out, want, accumulate);
+}
+
 namespace {
-template <int NVT>
-void launch_cgs(int pass, dim3 grid, cudaStream_t st, const double *V, long long vs, int nv, double *w, long long n,
-                int nch, const int *filt, const double *coef, double *partial, int NV, int want) {
+template <int NVT, typename T>
+void launch_cgs(int pass, dim3 grid, cudaStream_t st, const T *V, long long vs, int nv, T *w, long long n, int nch,
+                const int *filt, const double *coef, double *partial, int NV, int want) {
   if (pass == 0)
-    cgs_dots_kernel<NVT><<<grid, FUSED_THREADS, 0, st>>>(V, vs, n, nv, w, n, nch, filt, want, partial, NV);
-  else if (pass == 1)
-    cgs_update_dots_kernel<NVT><<<grid, FUSED_THREADS, 0, st>>>(V, vs, n, nv, w, n, nch, filt, want, coef, partial, NV);
+    cgs_dots_kernel<NVT, T><<<grid, FUSED_THREADS, 0, st>>>(V, vs, n, nv, w, n, nch, filt, want, partial, NV);
   else
-    cgs_update_norm_kernel<NVT><<<grid, FUSED_THREADS, 0, st>>>(V, vs, n, nv, w, n, nch, filt, want, coef, partial, NV);
+    cgs_update_norm_kernel<NVT, T><<<grid, FUSED_THREADS, 0, st>>>(V, vs, n, nv, w, n, nch, filt, want, coef, partial,
+                                                                  NV);
 }
 }  // namespace
 
-int Gmres::cgs2(const double *Vb, long long vs, int nv, double *w, cudaStream_t st) {
+template <typename T>
+int Gmres::cgs2_t(const T *Vb, long long vs, int nv, T *w, cudaStream_t st) {
   const int nchf = (int)((n + FUSED_CHUNK - 1) / FUSED_CHUNK);   // partial is sized for this chunking
   dim3 grid(nchf, nsys);
-  const int T = 256;
-  // pass p over the systems whose filter array equals `want`
+  const int TH = 256;
+  // pass p (0: dots and norm, 2: update and norm) over the systems whose filter array equals `want`
   auto pass = [&](int p, int nvt, const double *coef, const int *filt, int want) -> int {
     if (nvt <= 8)
-      launch_cgs<8>(p, grid, st, Vb, vs, nv, w, n, nchf, filt, coef, partial, NV, want);
+      launch_cgs<8, T>(p, grid, st, Vb, vs, nv, w, n, nchf, filt, coef, partial, NV, want);
     else if (nvt <= 16)
-      launch_cgs<16>(p, grid, st, Vb, vs, nv, w, n, nchf, filt, coef, partial, NV, want);
+      launch_cgs<16, T>(p, grid, st, Vb, vs, nv, w, n, nchf, filt, coef, partial, NV, want);
     else if (nvt <= 33)
-      launch_cgs<33>(p, grid, st, Vb, vs, nv, w, n, nchf, filt, coef, partial, NV, want);
+      launch_cgs<33, T>(p, grid, st, Vb, vs, nv, w, n, nchf, filt, coef, partial, NV, want);
     else
-      launch_cgs<66>(p, grid, st, Vb, vs, nv, w, n, nchf, filt, coef, partial, NV, want);
+      launch_cgs<66, T>(p, grid, st, Vb, vs, nv, w, n, nchf, filt, coef, partial, NV, want);
     GFCC_LAUNCH_CHECK();
     return GFCC_OK;
   };
@@ -668,60 +704,68 @@ int Gmres::cgs2(const double *Vb, long long vs, int nv, double *w, cudaStream_t 
   GFCC_TRY(pass(2, nv, h, state, ST_IN_CYCLE));
   GFCC_TRY(final(1, nrm, state, ST_IN_CYCLE));
   // passes 3-4 only where the first pass cancelled most of w
-  reorth_flag_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, state, ST_IN_CYCLE, h, nrm, NV, nv, flag);
+  reorth_flag_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, state, ST_IN_CYCLE, h, nrm, NV, nv, flag);
   GFCC_LAUNCH_CHECK();
   GFCC_TRY(pass(0, nv + 1, nullptr, flag, 1));
   GFCC_TRY(final(nv, h2, flag, 1));
   GFCC_TRY(pass(2, nv, h2, flag, 1));
   GFCC_TRY(final(1, nrm + 2 * NV * (long long)nsys, flag, 1));
-  reorth_merge_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, nv, h, h2, nrm, nrm + 2 * NV * (long long)nsys, NV, state,
-                                                   ST_IN_CYCLE, flag);
+  reorth_merge_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, nv, h, h2, nrm, nrm + 2 * NV * (long long)nsys, NV, state,
+                                                     ST_IN_CYCLE, flag);
   GFCC_LAUNCH_CHECK();
-  vscale_kernel<<<grid1d(n * nsys), T, 0, st>>>(w, vs, n, nsys, h, NV, nv, state, ST_IN_CYCLE);
+  vscale_kernel<T><<<grid1d(n * nsys), TH, 0, st>>>(w, vs, n, nsys, h, NV, nv, state, ST_IN_CYCLE);
   GFCC_LAUNCH_CHECK();
   return GFCC_OK;
 }
 
 int Gmres::solve(double tol, int max_iters, int *h_state, int max_cycles, bool use_x0) {
+  return f32 ? solve_t<float>(tol, max_iters, h_state, max_cycles, use_x0)
+             : solve_t<double>(tol, max_iters, h_state, max_cycles, use_x0);
+}
+
+template <typename T>
+int Gmres::solve_t(double tol, int max_iters, int *h_state, int max_cycles, bool use_x0) {
   cudaStream_t st = c->stream;
   const long long vs = (long long)(m + 1) * n;   // basis stride per system (complex elements)
-  const int T = 256;
+  const int TH = 256;
+  T *Vt = reinterpret_cast<T *>(V), *Ut = reinterpret_cast<T *>(U), *Bt = reinterpret_cast<T *>(B);
+  T *Wt = reinterpret_cast<T *>(W);
+  const double dsg = sector == GFCC_SECTOR_IP ? 1.0 : -1.0, zsg = sector == GFCC_SECTOR_IP ? -1.0 : 1.0;
+  const double *dg = sector == GFCC_SECTOR_IP ? c->diag_ip : c->diag_ea;
   if (!use_x0) {
-    GFCC_CUDA(cudaMemsetAsync(U, 0, sizeof(double) * 2 * nsys * n, st));
+    GFCC_CUDA(cudaMemsetAsync(Ut, 0, sizeof(T) * 2 * nsys * n, st));
   } else if (use_precond) {
-    precondition_kernel<<<grid1d(n * nsys), T, 0, st>>>(
-        U, n, nsys, omega, eta, sector == GFCC_SECTOR_IP ? -1.0 : 1.0,
-        sector == GFCC_SECTOR_IP ? c->diag_ip : c->diag_ea, sector == GFCC_SECTOR_IP ? 1.0 : -1.0);
+    precondition_kernel<T><<<grid1d(n * nsys), TH, 0, st>>>(Ut, n, nsys, omega, eta, zsg, dg, dsg);
     GFCC_LAUNCH_CHECK();
   }
-  GFCC_CUDA(cudaMemsetAsync(V, 0, sizeof(double) * 2 * nsys * (m + 1) * n, st));
+  GFCC_CUDA(cudaMemsetAsync(Vt, 0, sizeof(T) * 2 * nsys * (m + 1) * n, st));
   GFCC_CUDA(cudaMemsetAsync(iters, 0, sizeof(int) * nsys, st));
   GFCC_CUDA(cudaMemsetAsync(state, 0, sizeof(int) * nsys, st));   // ST_PENDING
   // ||b||
-  GFCC_TRY(mdot(B, n, 0, 1, B, n, nrm, ST_PENDING, 0));
-  norm_from_partial_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, nrm, NV, bnorm);
+  GFCC_TRY(mdot_t<T>(Bt, n, 0, 1, Bt, n, nrm, ST_PENDING, 0));
+  norm_from_partial_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, nrm, NV, bnorm);
   GFCC_LAUNCH_CHECK();
   bool first = !use_x0;
   for (int cycle = 0;; cycle++) {
     if (max_cycles > 0 && cycle >= max_cycles) {
       // cycle budget spent: the systems still pending keep their iterate (state 4)
-      set_state_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, state, ST_PENDING, ST_FAILED);
+      set_state_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, state, ST_PENDING, ST_FAILED);
       GFCC_LAUNCH_CHECK();
       break;
     }
     // true residual r = b - A x into V_0 (x = 0 on the first cycle)
     if (first) {
-      GFCC_CUDA(cudaMemsetAsync(W, 0, sizeof(double) * 2 * nsys * n, st));
+      GFCC_CUDA(cudaMemsetAsync(Wt, 0, sizeof(T) * 2 * nsys * n, st));
     } else {
-      GFCC_TRY(op(U, n, W, n));
+      GFCC_TRY(op_t<T>(Ut, n, Wt, n));
     }
-    resid_form_kernel<<<grid1d(n * nsys), T, 0, st>>>(B, W, V, vs, n, nsys, state);
+    resid_form_kernel<T><<<grid1d(n * nsys), TH, 0, st>>>(Bt, Wt, Vt, vs, n, nsys, state);
     GFCC_LAUNCH_CHECK();
-    GFCC_TRY(mdot(V, vs, 0, 1, V, vs, nrm, ST_PENDING, 0));
-    cycle_start_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, nrm, NV, bnorm, tol, max_iters, m + 1, state, iters, relres,
-                                                    g, H);
+    GFCC_TRY(mdot_t<T>(Vt, vs, 0, 1, Vt, vs, nrm, ST_PENDING, 0));
+    cycle_start_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, nrm, NV, bnorm, tol, max_iters, m + 1, state, iters,
+                                                      relres, g, H);
     GFCC_LAUNCH_CHECK();
-    vscale_kernel<<<grid1d(n * nsys), T, 0, st>>>(V, vs, n, nsys, nrm, NV, 0, state, ST_IN_CYCLE);
+    vscale_kernel<T><<<grid1d(n * nsys), TH, 0, st>>>(Vt, vs, n, nsys, nrm, NV, 0, state, ST_IN_CYCLE);
     GFCC_LAUNCH_CHECK();
     if (cycle == 0) GFCC_CUDA(cudaMemcpyAsync(relres0, relres, sizeof(double) * nsys, cudaMemcpyDeviceToDevice, st));
     first = false;
@@ -731,56 +775,65 @@ int Gmres::solve(double tol, int max_iters, int *h_state, int max_cycles, bool u
     for (int s = 0; s < nsys; s++) any |= h_state[s] == ST_IN_CYCLE;
     if (!any) break;
     // Arnoldi steps
+    int active = 0;
+    for (int s = 0; s < nsys; s++) active += h_state[s] == ST_IN_CYCLE;
     for (int k = 0; k < m; k++) {
-      double *vk = V + 2 * (long long)k * n;
-      double *w = V + 2 * (long long)(k + 1) * n;
-      GFCC_TRY(op(vk, vs, w, vs));
+      T *vk = Vt + 2 * (long long)k * n;
+      T *w = Vt + 2 * (long long)(k + 1) * n;
+      GFCC_TRY(op_t<T>(vk, vs, w, vs));
       // Gram-Schmidt against the basis: one classical pass (dots with ||w||^2, then update with
-      // ||w'||^2), a second pass only where needed, then w /= ||w||
+      // ||w'||^2), a second pass only where needed, then w /= ||w||.  Algorithmic bytes of one
+      // classical pass per system: dots read k+1 basis vectors and w, the update reads k+1 basis
+      // vectors and reads / writes w, the scaling reads / writes w.
       {
-        PhaseTimer ta(c, PH_ARNOLDI);
-        GFCC_TRY(cgs2(V, vs, k + 1, w, st));
+        const double bytes = (double)active * (2.0 * (k + 1) + 5.0) * (double)n * 2.0 * sizeof(T);
+        PhaseTimer ta(c, PH_ARNOLDI, bytes);
+        GFCC_TRY(cgs2_t<T>(Vt, vs, k + 1, w, st));
       }
       {
         PhaseTimer tl(c, PH_LSQ);
-        givens_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, k, m, h, NV, H, cs, sn, g, bnorm, tol, state, kcyc, iters,
-                                                   est);
+        givens_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, k, m, h, NV, H, cs, sn, g, bnorm, tol, state, kcyc, iters,
+                                                     est);
         GFCC_LAUNCH_CHECK();
       }
       GFCC_CUDA(cudaMemcpyAsync(h_state, state, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
       GFCC_CUDA(cudaStreamSynchronize(st));
-      bool in_cycle = false;
-      for (int s = 0; s < nsys; s++) in_cycle |= h_state[s] == ST_IN_CYCLE;
-      if (!in_cycle) break;
+      active = 0;
+      for (int s = 0; s < nsys; s++) active += h_state[s] == ST_IN_CYCLE;
+      if (active == 0) break;
     }
     // x += V y
-    backsolve_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, m, H, g, state, kcyc, y, NV);
+    backsolve_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, m, H, g, state, kcyc, y, NV);
     GFCC_LAUNCH_CHECK();
-    vupdate_kernel<<<grid1d(n * nsys), T, 0, st>>>(V, vs, n, m, kcyc, y, NV, 1.0, U, n, n, nsys, state,
-                                                    ST_CYCLE_DONE);
+    vupdate_kernel<T><<<grid1d(n * nsys), TH, 0, st>>>(Vt, vs, n, m, kcyc, y, NV, 1.0, Ut, n, n, nsys, state,
+                                                       ST_CYCLE_DONE);
     GFCC_LAUNCH_CHECK();
-    set_state_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, state, ST_CYCLE_DONE, ST_PENDING);
+    set_state_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, state, ST_CYCLE_DONE, ST_PENDING);
     GFCC_LAUNCH_CHECK();
   }
   if (use_precond) {
-    unprecondition_kernel<<<grid1d(n * nsys), T, 0, st>>>(
-        U, n, nsys, omega, eta, sector == GFCC_SECTOR_IP ? -1.0 : 1.0,
-        sector == GFCC_SECTOR_IP ? c->diag_ip : c->diag_ea, sector == GFCC_SECTOR_IP ? 1.0 : -1.0);
+    unprecondition_kernel<T><<<grid1d(n * nsys), TH, 0, st>>>(Ut, n, nsys, omega, eta, zsg, dg, dsg);
     GFCC_LAUNCH_CHECK();
   }
   return GFCC_OK;
 }
 
 namespace {
-// y = a - b (all systems, contiguous [s][n] complex)
-__global__ void sub_kernel(const double *a, const double *b, double *y, long long tot) {
+// y = a - y (all systems, contiguous [s][n] complex)
+__global__ void rsub_kernel(const double *a, double *y, long long tot) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
-    y[t] = a[t] - b[t];
+    y[t] = a[t] - y[t];
 }
 // x += d (all systems)
-__global__ void add_kernel(double *x, const double *d, long long tot) {
+template <typename T>
+__global__ void add_kernel(double *x, const T *d, long long tot) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
-    x[t] += d[t];
+    x[t] += (double)d[t];
+}
+// y = x rounded to FP32
+__global__ void to_f32_kernel(const double *x, float *y, long long tot) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
+    y[t] = (float)x[t];
 }
 // per system: relres = ||r|| / ||b0||; done systems get r = 0 so that the inner solve leaves them alone
 __global__ void refine_check_kernel(int nsys, const double *nrm2, int NV, const double *b0norm, double tol, int *done,
@@ -804,28 +857,28 @@ __global__ void zero_done_kernel(double *R, long long n, int nsys, const int *do
 int Gmres::solve_refined(double tol, double inner_tol, int max_iters, int *h_state, int *h_iters, bool use_x0) {
   cudaStream_t st = c->stream;
   const long long tot = 2LL * nsys * n;
-  const int T = 256;
+  const int TH = 256;
   std::vector<int> h_done(nsys, 0), it(nsys, 0);
   for (int s = 0; s < nsys; s++) h_iters[s] = 0;
-  GFCC_CUDA(cudaMemcpyAsync(B0, B, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
+  // B0 holds the right-hand sides (FP64), X the initial iterate when use_x0
   if (!use_x0) GFCC_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * tot, st));
-  // ||b0|| into est (a free per-system slot during refinement)
   GFCC_TRY(mdot(B0, n, 0, 1, B0, n, nrm, -1, 0));
   int *done = kcyc;   // reused: per-system done flags between inner solves
-  norm_from_partial_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, nrm, NV, b0norm);
+  norm_from_partial_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, nrm, NV, b0norm);
   GFCC_LAUNCH_CHECK();
   const int max_outer = 400;
   bool all_done = false;
   for (int outer = 0; outer <= max_outer; outer++) {
+    // FP64-accurate residual r = b - A x
     if (outer == 0 && !use_x0) {
       GFCC_CUDA(cudaMemcpyAsync(R, B0, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
     } else {
-      GFCC_TRY(op_fp64(X, n, W, n));
-      sub_kernel<<<grid1d(tot), T, 0, st>>>(B0, W, R, tot);
+      GFCC_TRY(op_fp64(X, n, R, n));
+      rsub_kernel<<<grid1d(tot), TH, 0, st>>>(B0, R, tot);
       GFCC_LAUNCH_CHECK();
     }
     GFCC_TRY(mdot(R, n, 0, 1, R, n, nrm, -1, 0));
-    refine_check_kernel<<<cdiv(nsys, T), T, 0, st>>>(nsys, nrm, NV, b0norm, tol, done, relres);
+    refine_check_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, nrm, NV, b0norm, tol, done, relres);
     GFCC_LAUNCH_CHECK();
     if (outer == 0) GFCC_CUDA(cudaMemcpyAsync(relres0, relres, sizeof(double) * nsys, cudaMemcpyDeviceToDevice, st));
     GFCC_CUDA(cudaMemcpyAsync(h_done.data(), done, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
@@ -840,20 +893,28 @@ int Gmres::solve_refined(double tol, double inner_tol, int max_iters, int *h_sta
     }
     if (all_done || !any_active || outer == max_outer) break;
     GFCC_CUDA(cudaMemcpyAsync(done, h_done.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
-    zero_done_kernel<<<grid1d(n * nsys), T, 0, st>>>(R, n, nsys, done);
+    zero_done_kernel<<<grid1d(n * nsys), TH, 0, st>>>(R, n, nsys, done);
     GFCC_LAUNCH_CHECK();
-    GFCC_CUDA(cudaMemcpyAsync(B, R, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
+    // inner correction A d = r on the BF16 operator (FP32 or FP64 Krylov vectors), x += d
+    if (f32) {
+      to_f32_kernel<<<grid1d(tot), TH, 0, st>>>(R, reinterpret_cast<float *>(B), tot);
+      GFCC_LAUNCH_CHECK();
+    } else {
+      GFCC_CUDA(cudaMemcpyAsync(B, R, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
+    }
     GFCC_TRY(solve(inner_tol, max_iters, h_state, c->inner_cycles));
     GFCC_CUDA(cudaMemcpyAsync(it.data(), iters, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
     GFCC_CUDA(cudaStreamSynchronize(st));
     for (int s = 0; s < nsys; s++) h_iters[s] += it[s];
-    add_kernel<<<grid1d(tot), T, 0, st>>>(X, U, tot);
+    if (f32)
+      add_kernel<float><<<grid1d(tot), TH, 0, st>>>(X, reinterpret_cast<const float *>(U), tot);
+    else
+      add_kernel<double><<<grid1d(tot), TH, 0, st>>>(X, U, tot);
     GFCC_LAUNCH_CHECK();
   }
-  // final state: converged where the FP64 residual met tol
+  // final state: converged where the FP64 residual met tol; the solution stays in X
   for (int s = 0; s < nsys; s++) h_state[s] = h_done[s] == 1 ? 3 : 4;
   GFCC_CUDA(cudaMemcpyAsync(state, h_state, sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
-  GFCC_CUDA(cudaMemcpyAsync(U, X, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
   GFCC_CUDA(cudaMemcpyAsync(iters, h_iters, sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
   return GFCC_OK;
 }

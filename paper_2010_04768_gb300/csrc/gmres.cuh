@@ -7,8 +7,8 @@ namespace gfcc {
 long long gmres_work_doubles(const gfcc_ctx *c, int sector, long long n, int nsys, int m, bool mixed = false);
 
 // One batch of nsys systems of packed dimension n in one sector.  The caller fills B
-// (right-hand sides, complex interleaved, [s][n]) and omega, then calls solve(); the
-// solution is left in U ([s][n], complex).  Per-system results: iters, relres, state
+// (right-hand sides, complex interleaved, [s][n]; rhs()) and omega, then calls solve() or
+// solve_refined(); the solution is left in solution() ([s][n], complex FP64).  Per-system results: iters, relres, state
 // (3 = converged, 4 = not converged).
 struct Gmres {
   gfcc_ctx *c = nullptr;
@@ -18,6 +18,7 @@ struct Gmres {
   double eta = 0.0;
   bool use_precond = false;
   bool mixed = false;      // inner operator on the BF16 tensor cores (IP), FP64 residuals outside
+  bool f32 = false;        // Krylov vectors V, U, B, W in FP32 (inner solves of the refinement)
   double *X = nullptr, *R = nullptr, *B0 = nullptr;   // refinement: solution, residual, original rhs
   double *b0norm = nullptr;
   double *V = nullptr, *U = nullptr, *B = nullptr, *W = nullptr;
@@ -29,20 +30,31 @@ struct Gmres {
   double *sigma_work = nullptr;
 
   int init(gfcc_ctx *ctx, int sector, long long n, int nsys, int m, double *work, bool mixed = false);
-  int op(const double *x, long long ldx, double *y, long long ldy);          // the inner operator
+  // where the caller puts the FP64 right-hand sides ([s][n] complex) and finds the solutions
+  double *rhs() const { return mixed ? B0 : B; }
+  double *solution() const { return mixed ? X : U; }
   int op_fp64(const double *x, long long ldx, double *y, long long ldy);     // FP64, no preconditioner
   int mdot(const double *Vb, long long vs, long long vi, int nv, const double *w, long long ws, double *out, int want,
            int accumulate);
   // max_cycles > 0 bounds the number of restart cycles (systems left pending end in state 4).
   // use_x0: U holds an initial iterate (unpreconditioned coordinates) instead of zero.
   int solve(double tol, int max_iters, int *h_state, int max_cycles = 0, bool use_x0 = false);
-  // one CGS2 orthogonalisation of w against basis vectors [0, nv) of every system in cycle
-  int cgs2(const double *Vb, long long vs, int nv, double *w, cudaStream_t st);
   // iterative refinement: FP64 residual r = b - A x, inner GMRES on the mixed operator to
   // inner_tol, x += d, until ||r|| <= tol ||b||.  Leaves x in U, the FP64 relative residual in
   // relres, the summed inner iterations in h_iters and the final state (3 / 4) in h_state.
   // use_x0: X holds an initial iterate instead of zero.
   int solve_refined(double tol, double inner_tol, int max_iters, int *h_state, int *h_iters, bool use_x0 = false);
+
+ private:
+  template <typename T>
+  int op_t(const T *x, long long ldx, T *y, long long ldy);
+  template <typename T>
+  int mdot_t(const T *Vb, long long vs, long long vi, int nv, const T *w, long long ws, double *out, int want,
+             int accumulate);
+  template <typename T>
+  int cgs2_t(const T *Vb, long long vs, int nv, T *w, cudaStream_t st);
+  template <typename T>
+  int solve_t(double tol, int max_iters, int *h_state, int max_cycles, bool use_x0);
 };
 
 }  // namespace gfcc

@@ -156,6 +156,12 @@ __global__ void ring_undiag_kernel(double *Wr, int o, int v, const double *Foo, 
   Wr[row * ov + row] -= cvv * Fvv[(long long)a * v + a] + coo * Foo[(long long)i * o + i];
 }
 
+// p[k * stride] = 0 for k < count (zeroes a diagonal)
+__global__ void diag_zero_kernel(double *p, int count, long long stride) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < count) p[(long long)k * stride] = 0.0;
+}
+
 // U1x[i][o2v + m] = -Foo[m][i] for m != i (the off-diagonal part of the 1h row)
 __global__ void u1_foo_kernel(double *U1x, int o, long long o2v, long long ld, const double *Foo) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -612,6 +618,69 @@ int build_hbar(gfcc_ctx *c, const double *d_fock, const double *d_chol) {
       GFCC_TRY(permute4(st, d2, c->Foo, is2, t2x + o2v, os2, -1.0, 0.0));
     }
     GFCC_TRY(slice(t2x, o, o2v + o, o2v + o, c->eU1));
+  }
+  if (want_ea && c->precision == GFCC_PREC_MIXED_BF16) {
+    // BF16 EA operands (the Fock-like diagonal stays in FP64) and their FP64 digit planes
+    const long long Pv = c->Pv;
+    c->ld_ov = round8(ov);
+    c->ld_o = round8(o);
+    c->ld_v = round8(v);
+    c->ld_pv = round8(std::max<long long>(Pv, 1));
+    c->ld_ov2 = round8(ov2);
+    c->ld_k1e = round8(ov2 + v);
+    const int S = c->emu_S;
+    auto slice = [&](const double *A, long long rows, long long K, long long lda, EmuOperand &e) -> int {
+      double *mem;
+      GFCC_TRY(dev_alloc(c, &mem, emu_operand_bytes(rows, K, S) / 8 + 1));
+      return emu_slice(st, A, rows, K, lda, S, mem, e);
+    };
+    double *t;
+    GFCC_TRY(tmp.get(&t, std::max(ov * ov, v * (ov2 + v))));
+    // ring: Wr_ea without the diagonal entries Fbar_vv[b][b] - 1/2 Fbar_oo[i][i]
+    GFCC_CUDA(cudaMemcpyAsync(t, c->Wr_ea, sizeof(double) * ov * ov, cudaMemcpyDeviceToDevice, st));
+    ring_undiag_kernel<<<cdiv(ov, 128), 128, 0, st>>>(t, o, v, c->Foo, c->Fvv, 1.0, -0.5);
+    GFCC_LAUNCH_CHECK();
+    GFCC_TRY(alloc_bf16(c, &c->Wre_bf, ov * c->ld_ov));
+    GFCC_TRY(to_bf16(st, t, ov, ov, ov, 1.0, c->Wre_bf, c->ld_ov));
+    GFCC_TRY(slice(c->Wr_ea, ov, ov, ov, c->eWre));
+    if (Pv > 0) {
+      GFCC_TRY(alloc_bf16(c, &c->Wp_bf, Pv * c->ld_pv));
+      GFCC_TRY(to_bf16(st, c->Wp, Pv, Pv, Pv, 1.0, c->Wp_bf, c->ld_pv));
+      GFCC_TRY(slice(c->Wp, Pv, Pv, Pv, c->eWp));
+    }
+    GFCC_TRY(alloc_bf16(c, &c->W3_bf, ov2 * c->ld_v));
+    GFCC_TRY(to_bf16(st, c->W3, ov2, v, v, 1.0, c->W3_bf, c->ld_v));
+    GFCC_TRY(slice(c->W3, ov2, v, v, c->eW3));
+    GFCC_TRY(alloc_bf16(c, &c->V3e_bf, o * c->ld_ov2));
+    GFCC_TRY(to_bf16(st, c->V3e, o, ov2, ov2, 1.0, c->V3e_bf, c->ld_ov2));
+    GFCC_TRY(alloc_bf16(c, &c->T3e_bf, ov2 * c->ld_o));
+    GFCC_TRY(to_bf16(st, c->T3e, ov2, o, o, 1.0, c->T3e_bf, c->ld_o));
+    GFCC_TRY(slice(c->T3e, ov2, o, o, c->eT3e));
+    // [V3e | 0]: padded to the K of the 1p row
+    {
+      const long long d[4] = {1, 1, o, ov2};
+      const long long is[4] = {0, 0, ov2, 1};
+      const long long os[4] = {0, 0, ov2 + v, 1};
+      GFCC_TRY(fill_f64(st, t, o * (ov2 + v), 0.0));
+      GFCC_TRY(permute4(st, d, c->V3e, is, t, os, 1.0, 0.0));
+    }
+    GFCC_TRY(slice(t, o, ov2 + v, ov2 + v, c->eV3e));
+    // 1p row: [U1e | Fbar_vv] (full, for the digit planes) and [U1e | Fbar_vv off-diagonal] (BF16)
+    {
+      const long long d[4] = {1, 1, v, ov2};
+      const long long is[4] = {0, 0, ov2, 1};
+      const long long os[4] = {0, 0, ov2 + v, 1};
+      GFCC_TRY(permute4(st, d, c->U1e, is, t, os, 1.0, 0.0));
+      const long long d2[4] = {1, 1, v, v};             // t[a][ov2 + e] = Fvv[a][e]
+      const long long is2[4] = {0, 0, v, 1};
+      const long long os2[4] = {0, 0, ov2 + v, 1};
+      GFCC_TRY(permute4(st, d2, c->Fvv, is2, t + ov2, os2, 1.0, 0.0));
+    }
+    GFCC_TRY(slice(t, v, ov2 + v, ov2 + v, c->eU1e));
+    diag_zero_kernel<<<cdiv(v, 128), 128, 0, st>>>(t + ov2, v, ov2 + v + 1);
+    GFCC_LAUNCH_CHECK();
+    GFCC_TRY(alloc_bf16(c, &c->U1e_bf, v * c->ld_k1e));
+    GFCC_TRY(to_bf16(st, t, v, ov2 + v, ov2 + v, 1.0, c->U1e_bf, c->ld_k1e));
   }
   GFCC_CUDA(cudaStreamSynchronize(st));
   return GFCC_OK;

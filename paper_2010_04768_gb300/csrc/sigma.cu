@@ -208,6 +208,15 @@ int launch_epilogue_ip(gfcc_ctx *c, const SysBatch &b, const double *S1, const d
   return GFCC_OK;
 }
 
+int launch_epilogue_ea(gfcc_ctx *c, const SysBatch &b, const double *S1, const double *T, const double *Qp,
+                       const double *U) {
+  const long long C2 = 2LL * b.nsys;
+  epilogue_ea_kernel<<<grid1d(c->dim_ea * b.nsys), 256, 0, c->stream>>>(b, c->o, c->v, c->Pv, C2, c->dim_ea, S1, T,
+                                                                         Qp, U);
+  GFCC_LAUNCH_CHECK();
+  return GFCC_OK;
+}
+
 double sigma_flops(const gfcc_ctx *c, int sector) {
   const double o = c->o, v = c->v;
   if (sector == GFCC_SECTOR_IP)

@@ -15,6 +15,8 @@ struct SysBatch {
   long long ldx = 0;
   double *y = nullptr;
   long long ldy = 0;
+  const float *xf = nullptr;       // FP32 vectors instead of x / y (mixed-precision operator only)
+  float *yf = nullptr;
   const double *omega = nullptr;   // device [nsys]
   double eta = 0.0;
   const double *diag = nullptr;    // device [dim] or nullptr
@@ -37,5 +39,12 @@ int launch_epilogue_ip(gfcc_ctx *c, const SysBatch &b, const double *S1, const d
 long long sigma_emu_work_doubles(const gfcc_ctx *c, int nsub);
 int apply_ip_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_doubles);
 int apply_ea(gfcc_ctx *c, const SysBatch &b, double *work);
+// mixed precision (EA): BF16 tensor-core couplings + FP64 diagonal and shift (sigma_mixed.cu)
+int apply_ea_mixed(gfcc_ctx *c, const SysBatch &b, double *work);
+// FP64-accurate EA operator from digit planes (sigma_emu.cu)
+int apply_ea_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_doubles);
+// the FP64 epilogue of the EA operator on given S1 / T / Qp / U (FP64, layouts of sigma.cu)
+int launch_epilogue_ea(gfcc_ctx *c, const SysBatch &b, const double *S1, const double *T, const double *Qp,
+                       const double *U);
 
 }  // namespace gfcc

@@ -147,6 +147,128 @@ __global__ void transpose_kernel(const double *Z, long long rows, long long cols
   }
 }
 
+// ---------------------------------------------------------------------------------------- EA
+__device__ __forceinline__ double packed_y2(const double *x, long long ldx, int v, long long Pv, int c, int m, int a,
+                                            int e) {
+  if (a == e) return 0.0;
+  const long long lo = a < e ? a : e, hi = a < e ? e : a;
+  const long long mu = v + (long long)m * Pv + pair_index(lo, hi, v);
+  const double val = x[2 * ((long long)(c >> 1) * ldx + mu) + (c & 1)];
+  return a > e ? -val : val;
+}
+
+// digit planes of r2e[(a,c)][(m,e)] = y2[m,a,e]
+__global__ void digits_ea_ring_kernel(const double *x, long long ldx, int C2, int o, int v, long long Pv,
+                                      const int *ec, int S, long long ld, __nv_bfloat16 *dig, int *rexp) {
+  const long long K = (long long)o * v, rows = (long long)v * C2, plane = rows * ld;
+  const long long tot = rows * ld;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long row = t / ld, k = t - row * ld;
+    const int c = (int)(row % C2), a = (int)(row / C2);
+    const double val = k < K ? packed_y2(x, ldx, v, Pv, c, (int)(k / v), a, (int)(k % v)) : 0.0;
+    put_digits(val, ec[c], S, dig + t, plane);
+    if (k == 0) rexp[row] = ec[c];
+  }
+}
+
+// digit planes of r2p[(i,c)][(e<f)] = y2[i,e,f]
+__global__ void digits_ea_vvvv_kernel(const double *x, long long ldx, int C2, int o, int v, long long Pv,
+                                      const int *ec, int S, long long ld, __nv_bfloat16 *dig, int *rexp) {
+  const long long rows = (long long)o * C2, plane = rows * ld;
+  const long long tot = rows * ld;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long row = t / ld, k = t - row * ld;
+    const int c = (int)(row % C2), i = (int)(row / C2);
+    const double val = k < Pv ? x[2 * ((long long)(c >> 1) * ldx + v + (long long)i * Pv + k) + (c & 1)] : 0.0;
+    put_digits(val, ec[c], S, dig + t, plane);
+    if (k == 0) rexp[row] = ec[c];
+  }
+}
+
+// digit planes of rk[c][(m,x,y)] = y2[m,y,x], rk[c][o v v + e] = y1[e] (zero padding to ldk), and
+// r1[c][e] = y1[e] (zero padding to ld1); exponents of both operands
+__global__ void digits_ea_k_kernel(const double *x, long long ldx, int C2, int o, int v, long long Pv, const int *ec,
+                                   int S, long long ldk, __nv_bfloat16 *digk, int *rexpk, long long ld1,
+                                   __nv_bfloat16 *dig1, int *rexp1) {
+  const long long ov2 = (long long)o * v * v;
+  const long long planek = (long long)C2 * ldk, plane1 = (long long)C2 * ld1;
+  const long long span = ldk > ld1 ? ldk : ld1;
+  const long long tot = (long long)C2 * span;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(t / span);
+    const long long k = t % span;
+    if (k < ldk) {
+      double val = 0.0;
+      if (k < ov2) {
+        const int y = (int)(k % v);
+        const long long r = k / v;
+        val = packed_y2(x, ldx, v, Pv, c, (int)(r / v), y, (int)(r % v));
+      } else if (k < ov2 + v) {
+        val = x[2 * ((long long)(c >> 1) * ldx + (k - ov2)) + (c & 1)];
+      }
+      put_digits(val, ec[c], S, digk + (long long)c * ldk + k, planek);
+    }
+    if (k < ld1) {
+      const double val = k < v ? x[2 * ((long long)(c >> 1) * ldx + k) + (c & 1)] : 0.0;
+      put_digits(val, ec[c], S, dig1 + (long long)c * ld1 + k, plane1);
+    }
+    if (k == 0) {
+      rexpk[c] = ec[c];
+      rexp1[c] = ec[c];
+    }
+  }
+}
+
+struct EmuWorkEA {
+  EmuOperand r2e, r2p, rk, r1, Zo;
+  int *ec;
+  double *T, *Qp, *U, *S1, *Z, *Zt;
+  void *gw;
+  long long bytes;
+};
+
+EmuWorkEA emu_layout_ea(const gfcc_ctx *c, int nsub, void *base) {
+  const long long o = c->o, v = c->v, C2 = 2LL * nsub, S = c->emu_S, Pv = c->Pv;
+  const long long ov = o * v, ov2 = ov * v;
+  EmuWorkEA w;
+  unsigned char *p = static_cast<unsigned char *>(base);
+  auto take = [&](long long bytes) {
+    unsigned char *q = p;
+    p += (bytes + 255) / 256 * 256;
+    return q;
+  };
+  auto op = [&](EmuOperand &e, long long rows, long long K) {
+    e.rows = rows;
+    e.K = K;
+    e.ld = (K + 7) / 8 * 8;
+    e.S = (int)S;
+    e.dig = reinterpret_cast<__nv_bfloat16 *>(take(S * rows * e.ld * 2));
+    e.exp2 = reinterpret_cast<int *>(take(rows * 4));
+  };
+  op(w.r2e, v * C2, ov);
+  op(w.r2p, o * C2, std::max<long long>(Pv, 1));
+  op(w.rk, C2, ov2 + v);
+  op(w.r1, C2, v);
+  op(w.Zo, C2, o);
+  w.ec = reinterpret_cast<int *>(take(C2 * 4));
+  w.T = reinterpret_cast<double *>(take(ov * v * C2 * 8));
+  w.Qp = reinterpret_cast<double *>(take(std::max<long long>(Pv, 1) * o * C2 * 8));
+  w.U = reinterpret_cast<double *>(take(ov2 * C2 * 8));
+  w.S1 = reinterpret_cast<double *>(take(v * C2 * 8));
+  w.Z = reinterpret_cast<double *>(take(o * C2 * 8));
+  w.Zt = reinterpret_cast<double *>(take(o * C2 * 8));
+  long long g = 0;
+  g = std::max(g, emu_gemm_work_bytes(ov, v * C2, ov));
+  g = std::max(g, emu_gemm_work_bytes(std::max<long long>(Pv, 1), o * C2, std::max<long long>(Pv, 1)));
+  g = std::max(g, emu_gemm_work_bytes(ov2, C2, v));
+  g = std::max(g, emu_gemm_work_bytes(o, C2, ov2 + v));
+  g = std::max(g, emu_gemm_work_bytes(ov2, C2, o));
+  g = std::max(g, emu_gemm_work_bytes(v, C2, ov2 + v));
+  w.gw = take(g);
+  w.bytes = p - static_cast<unsigned char *>(base);
+  return w;
+}
+
 struct EmuWork {
   EmuOperand r2b, r2o, rk, r1b, Zo;
   int *ec;
@@ -199,7 +321,12 @@ EmuWork emu_layout(const gfcc_ctx *c, int nsub, void *base) {
 
 }  // namespace
 
-long long sigma_emu_work_doubles(const gfcc_ctx *c, int nsub) { return emu_layout(c, nsub, nullptr).bytes / 8 + 64; }
+long long sigma_emu_work_doubles(const gfcc_ctx *c, int nsub) {
+  long long b = 0;
+  if (c->eWr.dig != nullptr) b = std::max(b, emu_layout(c, nsub, nullptr).bytes);
+  if (c->eWre.dig != nullptr) b = std::max(b, emu_layout_ea(c, nsub, nullptr).bytes);
+  return b / 8 + 64;
+}
 
 int apply_ip_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_doubles) {
   if (c->eWr.dig == nullptr) {
@@ -263,6 +390,68 @@ int apply_ip_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_do
     bb.omega = b.omega ? b.omega + s0 : nullptr;
     bb.diag = nullptr;
     GFCC_TRY(launch_epilogue_ip(c, bb, w.S1, w.T, w.Q, w.U));
+  }
+  return GFCC_OK;
+}
+
+
+int apply_ea_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_doubles) {
+  if (c->eWre.dig == nullptr) {
+    set_error("FP64-emulated EA residual requested but its digit planes were not built");
+    return GFCC_ERR_STATE;
+  }
+  cudaStream_t st = c->stream;
+  const long long o = c->o, v = c->v, ov = o * v, ov2 = ov * v, Pv = c->Pv, n = c->dim_ea;
+  int nsub = b.nsys;
+  while (nsub > 1 && emu_layout_ea(c, nsub, nullptr).bytes / 8 + 64 > work_doubles) nsub = (nsub + 1) / 2;
+  if (emu_layout_ea(c, nsub, nullptr).bytes / 8 + 64 > work_doubles) {
+    set_error("apply_ea_emu: workspace too small for one system");
+    return GFCC_ERR_OOM;
+  }
+  const int S = c->emu_S, P = c->emu_P;
+  PhaseTimer tsig(c, PH_SIGMA, b.nsys * sigma_flops(c, GFCC_SECTOR_EA));
+  for (int s0 = 0; s0 < b.nsys; s0 += nsub) {
+    const int ns = std::min(nsub, b.nsys - s0);
+    const int C2 = 2 * ns;
+    EmuWorkEA w = emu_layout_ea(c, ns, work);
+    const double *x = b.x + 2 * (long long)s0 * b.ldx;
+    {
+      PhaseTimer tu(c, PH_UNPACK);
+      plane_exp_kernel<<<C2, 256, 0, st>>>(x, b.ldx, n, w.ec);
+      GFCC_LAUNCH_CHECK();
+      digits_ea_ring_kernel<<<grid1d(w.r2e.rows * w.r2e.ld), 256, 0, st>>>(x, b.ldx, C2, (int)o, (int)v, Pv, w.ec, S,
+                                                                            w.r2e.ld, w.r2e.dig, w.r2e.exp2);
+      GFCC_LAUNCH_CHECK();
+      digits_ea_vvvv_kernel<<<grid1d(w.r2p.rows * w.r2p.ld), 256, 0, st>>>(x, b.ldx, C2, (int)o, (int)v, Pv, w.ec, S,
+                                                                            w.r2p.ld, w.r2p.dig, w.r2p.exp2);
+      GFCC_LAUNCH_CHECK();
+      digits_ea_k_kernel<<<grid1d((long long)C2 * std::max(w.rk.ld, w.r1.ld)), 256, 0, st>>>(
+          x, b.ldx, C2, (int)o, (int)v, Pv, w.ec, S, w.rk.ld, w.rk.dig, w.rk.exp2, w.r1.ld, w.r1.dig, w.r1.exp2);
+      GFCC_LAUNCH_CHECK();
+    }
+    {
+      int pairs = 0;
+      for (int L = 2; L <= P; L++)
+        for (int i = 1; i <= S; i++)
+          if (L - i >= 1 && L - i <= S) pairs++;
+      PhaseTimer tr(c, PH_RING_EMU, pairs * 2.0 * (double)ov * (double)ov * (double)(v * C2));
+      GFCC_TRY(emu_gemm(st, c->eWre, w.r2e, P, 1.0, 0.0, w.T, imap1(v * C2), imap1(1), w.gw));
+    }
+    if (Pv > 0) GFCC_TRY(emu_gemm(st, c->eWp, w.r2p, P, 1.0, 0.0, w.Qp, imap1(o * C2), imap1(1), w.gw));
+    GFCC_TRY(emu_gemm(st, c->eW3, w.r1, P, 1.0, 0.0, w.U, imap1(C2), imap1(1), w.gw));
+    GFCC_TRY(emu_gemm(st, c->eV3e, w.rk, P, 1.0, 0.0, w.Z, imap1(C2), imap1(1), w.gw));
+    transpose_kernel<<<grid1d(o * C2), 256, 0, st>>>(w.Z, o, C2, w.Zt);
+    GFCC_LAUNCH_CHECK();
+    GFCC_TRY(emu_slice(st, w.Zt, C2, o, o, S, w.Zo.dig, w.Zo));
+    GFCC_TRY(emu_gemm(st, c->eT3e, w.Zo, P, 1.0, 1.0, w.U, imap1(C2), imap1(1), w.gw));
+    GFCC_TRY(emu_gemm(st, c->eU1e, w.rk, P, 1.0, 0.0, w.S1, imap1(C2), imap1(1), w.gw));
+    SysBatch bb = b;
+    bb.nsys = ns;
+    bb.x = x;
+    bb.y = b.y + 2 * (long long)s0 * b.ldy;
+    bb.omega = b.omega ? b.omega + s0 : nullptr;
+    bb.diag = nullptr;
+    GFCC_TRY(launch_epilogue_ea(c, bb, w.S1, w.T, w.Qp, w.U));
   }
   return GFCC_OK;
 }

