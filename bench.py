@@ -37,6 +37,8 @@ WORKLOADS = {
     # o=40 v=200 L=800, 40 orbitals nearest the gap, 64 frequencies in [-1.2, 0.5], eta 0.005, tol 1e-8
     "medium-ip-fp64": dict(base="medium", sector="IP", precision="fp64", per_step=1),
     "medium-ip-mixed": dict(base="medium", sector="IP", precision="mixed", per_step=1),
+    "medium-ipea-mixed": dict(base="medium", sector="IP+EA", precision="mixed", per_step=1),
+    "medium-ipea-fp64": dict(base="medium", sector="IP+EA", precision="fp64", per_step=1),
     # C60-shaped: o=90 v=450 L=1800, the 30 highest occupied orbitals, 128 frequencies in [-1.0, -0.3]
     "c60-ip-mixed": dict(base="c60", sector="IP", precision="mixed", per_step=1),
     "c60-ip-fp64": dict(base="c60", sector="IP", precision="fp64", per_step=1),
@@ -125,36 +127,42 @@ def dist_setup():
     return world, rank, local
 
 
+def sectors_of(spec):
+    return ("IP", "EA") if spec["sector"] in ("IP+EA", "BOTH") else (spec["sector"],)
+
+
 def cpu_baseline(wl, spec, problem, max_columns=1):
-    """The CPU oracle as it stands, on a bounded sample: `max_columns` (omega, p) columns of the same
-    workload solved by its GMRES with the same tolerance, restart and preconditioner."""
+    """The CPU oracle as it stands, on a bounded sample: `max_columns` (omega, p) columns per sector of
+    the same workload solved by its GMRES with the same tolerance, restart and preconditioner."""
     from oracle.gfcc_ref import GFCCOracle, gmres
+    secs = sectors_of(spec)
     t0 = time.perf_counter()
-    orc = GFCCOracle(problem.fock, problem.chol, problem.t1, problem.t2, o=wl.o, sectors=(spec["sector"],))
+    orc = GFCCOracle(problem.fock, problem.chol, problem.t1, problem.t2, o=wl.o, sectors=secs)
     t_setup = time.perf_counter() - t0
     cols = 0
     its_total = 0
     t0 = time.perf_counter()
-    for c in range(max_columns):
-        # the frequencies of the timed steps 1, 2, ... (step 0 sits deep in the 2h1p continuum and would
-        # take the CPU several minutes per column), first orbital of the list
-        om = wl.omegas[((c + 1) * FREQ_STRIDE) % wl.omegas.size]
-        p = int(wl.orbitals[0])
-        if spec["sector"] == "IP":
-            D = (om - 1j * wl.eta) + orc.ip_diag()
-            x, its, rel, ok = gmres(orc.ip_apply(om, wl.eta), orc.ip_rhs(p), wl.tol, wl.restart, 50, diag=D)
-            G = np.stack([orc.ip_left(int(q)) for q in wl.orbitals]) @ x
-        else:
-            D = (om + 1j * wl.eta) - orc.ea_diag()
-            x, its, rel, ok = gmres(orc.ea_apply(om, wl.eta), orc.ea_rhs(p), wl.tol, wl.restart, 50, diag=D)
-            G = np.stack([orc.ea_left(int(q)) for q in wl.orbitals]) @ x
-        cols += 1 if ok else 0
-        its_total += its
+    for sec in secs:
+        for c in range(max_columns):
+            # the frequencies of the timed steps 1, 2, ... (step 0 sits deep in the 2h1p continuum and
+            # would take the CPU several minutes per column), first orbital of the list
+            om = wl.omegas[((c + 1) * FREQ_STRIDE) % wl.omegas.size]
+            p = int(wl.orbitals[0])
+            if sec == "IP":
+                D = (om - 1j * wl.eta) + orc.ip_diag()
+                x, its, rel, ok = gmres(orc.ip_apply(om, wl.eta), orc.ip_rhs(p), wl.tol, wl.restart, 50, diag=D)
+                G = np.stack([orc.ip_left(int(q)) for q in wl.orbitals]) @ x
+            else:
+                D = (om + 1j * wl.eta) - orc.ea_diag()
+                x, its, rel, ok = gmres(orc.ea_apply(om, wl.eta), orc.ea_rhs(p), wl.tol, wl.restart, 50, diag=D)
+                G = np.stack([orc.ea_left(int(q)) for q in wl.orbitals]) @ x
+            cols += 1 if ok else 0
+            its_total += its
     dt = time.perf_counter() - t0
     return {"value": cols / dt, "unit": "columns/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{max_columns} (omega, p) column(s) of the same workload (omega of timed step 1, first "
-                      f"orbital; {its_total} GMRES iterations), numpy FP64 GMRES with the same tol/restart/"
-                      f"preconditioner; oracle setup {t_setup:.1f} s excluded like gfcc_create",
+            "sample": f"{max_columns} (omega, p) column(s) per sector {'+'.join(secs)} of the same workload (omega "
+                      f"of timed step 1, first orbital; {its_total} GMRES iterations), numpy FP64 GMRES with the "
+                      f"same tol/restart/preconditioner; oracle setup {t_setup:.1f} s excluded like gfcc_create",
             "seconds": dt}
 
 
@@ -183,7 +191,7 @@ def config_of(spec, wl, world):
                         f"{spec['per_step']} frequency x {wl.orbitals.size} orbitals per step per GPU",
             "o": wl.o, "v": wl.v, "L": wl.L, "sector": spec["sector"], "precision": spec["precision"],
             "eta": wl.eta, "tol": wl.tol, "restart": wl.restart, "preconditioner": "diag",
-            "columns_per_step": spec["per_step"] * int(wl.orbitals.size) * world,
+            "columns_per_step": spec["per_step"] * int(wl.orbitals.size) * len(sectors_of(spec)) * world,
             "parallelism": f"{world} independent GPU(s), frequencies sharded", "l2": "inputs larger than L2 "
             "(ring matrix and Krylov basis are each > 129 MB)"}
 

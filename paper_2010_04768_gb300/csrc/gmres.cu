@@ -317,105 +317,134 @@ __global__ void coef_add_kernel(int nsys, int nv, double *h, const double *h2, i
 }
 
 
-// ---------------------------------------------------------------- fused CGS2 passes
-// Each block handles one chunk of FUSED_CHUNK elements of one system; NVT >= nv is a compile-time
-// bound so that the per-thread basis values and dot accumulators stay in registers.
-constexpr int FUSED_THREADS = 256, FUSED_PER = 4, FUSED_CHUNK = FUSED_THREADS * FUSED_PER;
+// ---------------------------------------------------------------- fused Gram-Schmidt passes
+// Both passes stream the Krylov basis of a system once per chunk of CGS_CHUNK elements.  They are
+// HBM-bound, so what matters is the number of independent loads each thread has in flight:
+// * dots: each warp of a block owns whole basis vectors (i = warp, warp + 8, ...; i = nv is w
+//   itself, for ||w||^2) and sweeps the chunk with CGS_UNROLL independent loads per lane; w is
+//   re-read by every warp from L1.  No block-level reduction: one warp shuffle per vector.
+// * update: every thread owns two elements and accumulates sum_i c_i V_i over batches of
+//   CGS_BATCH vectors whose loads are predicated (not branched), so they issue together.
+constexpr int CGS_THREADS = 256, CGS_CHUNK = 4096, CGS_UNROLL = 8, CGS_BATCH = 8;
 
-template <int NVT>
-__device__ __forceinline__ void block_reduce_store(double2 (&acc)[NVT], int nv, double2 *sh, double *partial, int s,
-                                                   int NV, int nch, int chunk) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NVT; i++) {
-    if (i >= nv) break;
-    double2 v = acc[i];
-    for (int off = 16; off > 0; off >>= 1) {
-      v.x += __shfl_down_sync(0xffffffffu, v.x, off);
-      v.y += __shfl_down_sync(0xffffffffu, v.y, off);
-    }
-    if (lane == 0) sh[warp * NVT + i] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < nv) {
-    double2 t = make_double2(0.0, 0.0);
-    for (int w = 0; w < FUSED_THREADS / 32; w++) {
-      t.x += sh[w * NVT + threadIdx.x].x;
-      t.y += sh[w * NVT + threadIdx.x].y;
-    }
-    reinterpret_cast<double2 *>(partial)[((long long)s * NV + threadIdx.x) * nch + chunk] = t;
-  }
-}
-
-// pass 1: partial dots conj(V_i) . w (i < nv) and, in slot nv, the squared norm of w
-template <int NVT, typename T>
-__global__ __launch_bounds__(FUSED_THREADS) void cgs_dots_kernel(const T *V, long long vs, long long vi, int nv,
-                                                                 const T *w, long long n, int nch, const int *state,
-                                                                 int want, double *partial, int NV) {
-  __shared__ double2 sh[(FUSED_THREADS / 32) * NVT];
+template <typename T>
+__global__ __launch_bounds__(CGS_THREADS) void cgs_dots_kernel(const T *V, long long vs, long long vi, int nv,
+                                                               const T *w, long long n, int nch, const int *state,
+                                                               int want, double *partial, int NV) {
   const int s = blockIdx.y, chunk = blockIdx.x;
   if (state[s] != want) return;
-  CT<T> a2[NVT];
-#pragma unroll
-  for (int i = 0; i < NVT; i++) a2[i] = mkc<T>(0.0, 0.0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long e0 = (long long)chunk * CGS_CHUNK;
+  const long long e1 = e0 + CGS_CHUNK < n ? e0 + CGS_CHUNK : n;
   const T *ws = w + 2 * s * vs;
   const T *Vs = V + 2 * s * vs;
-  for (int r = 0; r < FUSED_PER; r++) {
-    const long long mu = (long long)chunk * FUSED_CHUNK + threadIdx.x + (long long)r * FUSED_THREADS;
-    if (mu >= n) break;
-    const CT<T> x = ldc(ws, mu);
+  for (int i = warp; i <= nv; i += CGS_THREADS / 32) {
+    const T *vp = i < nv ? Vs + 2 * i * vi : ws;   // slot nv: ||w||^2
+    T ar = T(0), ai = T(0);
+    long long e = e0 + lane;
+    // full rounds: CGS_UNROLL unconditional loads of the basis vector and of w in flight per lane
+    for (; e + 32 * (CGS_UNROLL - 1) < e1; e += 32 * CGS_UNROLL) {
+      CT<T> a[CGS_UNROLL], x[CGS_UNROLL];
 #pragma unroll
-    for (int i = 0; i < NVT; i++) {
-      if (i >= nv) break;
-      const CT<T> a = ldc(Vs + 2 * i * vi, mu);
-      a2[i].x += a.x * x.x + a.y * x.y;
-      a2[i].y += a.x * x.y - a.y * x.x;
+      for (int u = 0; u < CGS_UNROLL; u++) {
+        a[u] = ldc(vp, e + 32 * u);
+        x[u] = ldc(ws, e + 32 * u);
+      }
+#pragma unroll
+      for (int u = 0; u < CGS_UNROLL; u++) {
+        ar += a[u].x * x[u].x + a[u].y * x[u].y;
+        ai += a[u].x * x[u].y - a[u].y * x[u].x;
+      }
     }
-#pragma unroll
-    for (int i = 0; i < NVT; i++)
-      if (i == nv) a2[i].x += x.x * x.x + x.y * x.y;
+    for (; e < e1; e += 32) {
+      const CT<T> a = ldc(vp, e), x = ldc(ws, e);
+      ar += a.x * x.x + a.y * x.y;
+      ai += a.x * x.y - a.y * x.x;
+    }
+    double2 acc = make_double2((double)ar, (double)ai);
+    for (int off = 16; off > 0; off >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    if (lane == 0) reinterpret_cast<double2 *>(partial)[((long long)s * NV + i) * nch + chunk] = acc;
   }
-  double2 acc[NVT];
-#pragma unroll
-  for (int i = 0; i < NVT; i++) acc[i] = make_double2((double)a2[i].x, (double)a2[i].y);
-  block_reduce_store<NVT>(acc, nv + 1, sh, partial, s, NV, nch, chunk);
 }
 
-// pass 3: w -= V h2 (in place), then the partial squared norm of w
-template <int NVT, typename T>
-__global__ __launch_bounds__(FUSED_THREADS) void cgs_update_norm_kernel(const T *V, long long vs, long long vi,
-                                                                        int nv, T *w, long long n, int nch,
-                                                                        const int *state, int want, const double *h2,
-                                                                        double *partial, int NV) {
-  __shared__ double2 sh[(FUSED_THREADS / 32) * 1];
-  __shared__ CT<T> hh[NVT];
+// w -= V h2 (in place), then the partial squared norm of w (slot 0)
+template <typename T>
+__global__ __launch_bounds__(CGS_THREADS) void cgs_update_norm_kernel(const T *V, long long vs, long long vi, int nv,
+                                                                      T *w, long long n, int nch, const int *state,
+                                                                      int want, const double *h2, double *partial,
+                                                                      int NV) {
+  __shared__ CT<T> hh[72];
+  __shared__ double sh[CGS_THREADS / 32];
   const int s = blockIdx.y, chunk = blockIdx.x;
   if (state[s] != want) return;
-  if (threadIdx.x < nv) {
-    const double2 c = reinterpret_cast<const double2 *>(h2)[(long long)s * NV + threadIdx.x];
-    hh[threadIdx.x] = mkc<T>(c.x, c.y);
+  for (int i = threadIdx.x; i < nv; i += CGS_THREADS) {
+    const double2 c = reinterpret_cast<const double2 *>(h2)[(long long)s * NV + i];
+    hh[i] = mkc<T>(c.x, c.y);
   }
   __syncthreads();
-  T nn = T(0);
+  const long long e0 = (long long)chunk * CGS_CHUNK;
+  const long long e1 = e0 + CGS_CHUNK < n ? e0 + CGS_CHUNK : n;
   T *ws = w + 2 * s * vs;
   const T *Vs = V + 2 * s * vs;
-  for (int r = 0; r < FUSED_PER; r++) {
-    const long long mu = (long long)chunk * FUSED_CHUNK + threadIdx.x + (long long)r * FUSED_THREADS;
-    if (mu >= n) break;
-    CT<T> x = ldc(ws, mu);
+  T nn = T(0);
+  for (long long e = e0 + threadIdx.x; e < e1; e += 2 * CGS_THREADS) {
+    const long long f = e + CGS_THREADS;
+    const bool inf = f < e1;
+    CT<T> acc0 = mkc<T>(0.0, 0.0), acc1 = mkc<T>(0.0, 0.0);
+    // element f: the second element of the thread, or (past the chunk) a repeat of e whose result is
+    // not stored, so that every load below is unconditional
+    const long long fl = inf ? f : e;
+    int i0 = 0;
+    for (; i0 + CGS_BATCH <= nv; i0 += CGS_BATCH) {
+      CT<T> a0[CGS_BATCH], a1[CGS_BATCH];
 #pragma unroll
-    for (int i = 0; i < NVT; i++) {
-      if (i >= nv) break;
-      const CT<T> a = ldc(Vs + 2 * i * vi, mu);
-      const CT<T> c = hh[i];
-      x.x -= c.x * a.x - c.y * a.y;
-      x.y -= c.x * a.y + c.y * a.x;
+      for (int j = 0; j < CGS_BATCH; j++) {
+        const T *vp = Vs + 2 * (long long)(i0 + j) * vi;
+        a0[j] = ldc(vp, e);
+        a1[j] = ldc(vp, fl);
+      }
+#pragma unroll
+      for (int j = 0; j < CGS_BATCH; j++) {
+        const CT<T> c = hh[i0 + j];
+        acc0.x += c.x * a0[j].x - c.y * a0[j].y;
+        acc0.y += c.x * a0[j].y + c.y * a0[j].x;
+        acc1.x += c.x * a1[j].x - c.y * a1[j].y;
+        acc1.y += c.x * a1[j].y + c.y * a1[j].x;
+      }
     }
-    stc(ws, mu, x);
-    nn += x.x * x.x + x.y * x.y;
+    for (; i0 < nv; i0++) {
+      const T *vp = Vs + 2 * (long long)i0 * vi;
+      const CT<T> a0 = ldc(vp, e), a1 = ldc(vp, fl), c = hh[i0];
+      acc0.x += c.x * a0.x - c.y * a0.y;
+      acc0.y += c.x * a0.y + c.y * a0.x;
+      acc1.x += c.x * a1.x - c.y * a1.y;
+      acc1.y += c.x * a1.y + c.y * a1.x;
+    }
+    CT<T> x0 = ldc(ws, e);
+    x0.x -= acc0.x;
+    x0.y -= acc0.y;
+    stc(ws, e, x0);
+    nn += x0.x * x0.x + x0.y * x0.y;
+    if (inf) {
+      CT<T> x1 = ldc(ws, f);
+      x1.x -= acc1.x;
+      x1.y -= acc1.y;
+      stc(ws, f, x1);
+      nn += x1.x * x1.x + x1.y * x1.y;
+    }
   }
-  double2 acc[1] = {make_double2((double)nn, 0.0)};
-  block_reduce_store<1>(acc, 1, sh, partial, s, NV, nch, chunk);
+  double t = (double)nn;
+  for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int k = 0; k < CGS_THREADS / 32; k++) tot += sh[k];
+    reinterpret_cast<double2 *>(partial)[((long long)s * NV) * nch + chunk] = make_double2(tot, 0.0);
+  }
 }
 
 // Selective reorthogonalisation (Daniel, Gragg, Kaufman & Stewart 1976): a second Gram-Schmidt
@@ -504,7 +533,7 @@ long long dbl_of(long long count) {
 
 long long gmres_work_doubles(const gfcc_ctx *c, int sector, long long n, int nsys, int m, bool mixed) {
   const long long NV = m + 2;
-  const long long nch = (n + FUSED_CHUNK - 1) / FUSED_CHUNK;   // the finer of the two chunkings
+  const long long nch = (n + DOT_CHUNK - 1) / DOT_CHUNK;   // the finer of the two chunkings
   const bool f32 = mixed && c->inner_fp64 == 0;
   long long w = 0;
   const long long vb = 2LL * nsys * (m + 1) * n, vv = 2LL * nsys * n;
@@ -534,7 +563,7 @@ int Gmres::init(gfcc_ctx *ctx, int sec, long long dim, int ns, int mm, double *w
   m = mm;
   NV = m + 2;
   nch = (int)((n + DOT_CHUNK - 1) / DOT_CHUNK);
-  const long long nch_alloc = (n + FUSED_CHUNK - 1) / FUSED_CHUNK;
+  const long long nch_alloc = (n + DOT_CHUNK - 1) / DOT_CHUNK;
   double *p = work;
   auto take = [&](double *&dst, long long cnt) {
     dst = p;
@@ -660,55 +689,40 @@ int Gmres::mdot(const double *Vb, long long vs, long long vi, int nv, const doub
   return mdot_t<double>(Vb, vs, vi, nv, w, ws, out, want, accumulate);
 }
 
-namespace {
-template <int NVT, typename T>
-void launch_cgs(int pass, dim3 grid, cudaStream_t st, const T *V, long long vs, int nv, T *w, long long n, int nch,
-                const int *filt, const double *coef, double *partial, int NV, int want) {
-  if (pass == 0)
-    cgs_dots_kernel<NVT, T><<<grid, FUSED_THREADS, 0, st>>>(V, vs, n, nv, w, n, nch, filt, want, partial, NV);
-  else
-    cgs_update_norm_kernel<NVT, T><<<grid, FUSED_THREADS, 0, st>>>(V, vs, n, nv, w, n, nch, filt, want, coef, partial,
-                                                                  NV);
-}
-}  // namespace
-
 template <typename T>
 int Gmres::cgs2_t(const T *Vb, long long vs, int nv, T *w, cudaStream_t st) {
-  const int nchf = (int)((n + FUSED_CHUNK - 1) / FUSED_CHUNK);   // partial is sized for this chunking
-  dim3 grid(nchf, nsys);
+  const int nchc = (int)((n + CGS_CHUNK - 1) / CGS_CHUNK);   // partial holds nch_alloc >= nchc chunks
+  dim3 grid(nchc, nsys);
   const int TH = 256;
   // pass p (0: dots and norm, 2: update and norm) over the systems whose filter array equals `want`
-  auto pass = [&](int p, int nvt, const double *coef, const int *filt, int want) -> int {
-    if (nvt <= 8)
-      launch_cgs<8, T>(p, grid, st, Vb, vs, nv, w, n, nchf, filt, coef, partial, NV, want);
-    else if (nvt <= 16)
-      launch_cgs<16, T>(p, grid, st, Vb, vs, nv, w, n, nchf, filt, coef, partial, NV, want);
-    else if (nvt <= 33)
-      launch_cgs<33, T>(p, grid, st, Vb, vs, nv, w, n, nchf, filt, coef, partial, NV, want);
+  auto pass = [&](int p, const double *coef, const int *filt, int want) -> int {
+    if (p == 0)
+      cgs_dots_kernel<T><<<grid, CGS_THREADS, 0, st>>>(Vb, vs, n, nv, w, n, nchc, filt, want, partial, NV);
     else
-      launch_cgs<66, T>(p, grid, st, Vb, vs, nv, w, n, nchf, filt, coef, partial, NV, want);
+      cgs_update_norm_kernel<T><<<grid, CGS_THREADS, 0, st>>>(Vb, vs, n, nv, w, n, nchc, filt, want, coef, partial,
+                                                             NV);
     GFCC_LAUNCH_CHECK();
     return GFCC_OK;
   };
   auto final = [&](int nvv, double *out, const int *filt, int want) -> int {
-    mdot_final_kernel<<<cdiv(nsys * (long long)nvv * 32, 256), 256, 0, st>>>(partial, nsys, nvv, NV, nchf, filt, want,
+    mdot_final_kernel<<<cdiv(nsys * (long long)nvv * 32, 256), 256, 0, st>>>(partial, nsys, nvv, NV, nchc, filt, want,
                                                                              out, 0);
     GFCC_LAUNCH_CHECK();
     return GFCC_OK;
   };
   int *flag = rflag;
   // pass 1: h = V^H w and ||w||^2 (slot nv)
-  GFCC_TRY(pass(0, nv + 1, nullptr, state, ST_IN_CYCLE));
+  GFCC_TRY(pass(0, nullptr, state, ST_IN_CYCLE));
   GFCC_TRY(final(nv + 1, h, state, ST_IN_CYCLE));
   // pass 2: w -= V h, ||w'||^2
-  GFCC_TRY(pass(2, nv, h, state, ST_IN_CYCLE));
+  GFCC_TRY(pass(2, h, state, ST_IN_CYCLE));
   GFCC_TRY(final(1, nrm, state, ST_IN_CYCLE));
   // passes 3-4 only where the first pass cancelled most of w
   reorth_flag_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, state, ST_IN_CYCLE, h, nrm, NV, nv, flag);
   GFCC_LAUNCH_CHECK();
-  GFCC_TRY(pass(0, nv + 1, nullptr, flag, 1));
+  GFCC_TRY(pass(0, nullptr, flag, 1));
   GFCC_TRY(final(nv, h2, flag, 1));
-  GFCC_TRY(pass(2, nv, h2, flag, 1));
+  GFCC_TRY(pass(2, h2, flag, 1));
   GFCC_TRY(final(1, nrm + 2 * NV * (long long)nsys, flag, 1));
   reorth_merge_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, nv, h, h2, nrm, nrm + 2 * NV * (long long)nsys, NV, state,
                                                      ST_IN_CYCLE, flag);

@@ -635,7 +635,7 @@ int build_hbar(gfcc_ctx *c, const double *d_fock, const double *d_chol) {
       return emu_slice(st, A, rows, K, lda, S, mem, e);
     };
     double *t;
-    GFCC_TRY(tmp.get(&t, std::max(ov * ov, v * (ov2 + v))));
+    GFCC_TRY(tmp.get(&t, std::max(ov * ov, std::max<long long>(o, v) * (ov2 + v))));
     // ring: Wr_ea without the diagonal entries Fbar_vv[b][b] - 1/2 Fbar_oo[i][i]
     GFCC_CUDA(cudaMemcpyAsync(t, c->Wr_ea, sizeof(double) * ov * ov, cudaMemcpyDeviceToDevice, st));
     ring_undiag_kernel<<<cdiv(ov, 128), 128, 0, st>>>(t, o, v, c->Foo, c->Fvv, 1.0, -0.5);
