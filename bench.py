@@ -39,11 +39,21 @@ WORKLOADS = {
     "medium-ip-mixed": dict(base="medium", sector="IP", precision="mixed", per_step=1),
     "medium-ipea-mixed": dict(base="medium", sector="IP+EA", precision="mixed", per_step=1),
     "medium-ipea-fp64": dict(base="medium", sector="IP+EA", precision="fp64", per_step=1),
+    # frequency sweeps: each step solves a window of `per_step` consecutive grid frequencies in one call,
+    # one frequency per batch, each system started from the initial guess named (GFCC_OPT_GUESS)
+    "medium-ipea-mixed-sweep": dict(base="medium", sector="IP+EA", precision="mixed", per_step=8, sweep=True),
+    "medium-ipea-mixed-sweep-minres": dict(base="medium", sector="IP+EA", precision="mixed", per_step=8, sweep=True,
+                                           guess="minres"),
+    "medium-ip-mixed-sweep": dict(base="medium", sector="IP", precision="mixed", per_step=16, sweep=True),
+    "medium-ip-mixed-sweep-minres": dict(base="medium", sector="IP", precision="mixed", per_step=16, sweep=True,
+                                         guess="minres"),
+    "medium-ip-mixed-sweep-learned": dict(base="medium", sector="IP", precision="mixed", per_step=16, sweep=True,
+                                          guess="learned"),
     # C60-shaped: o=90 v=450 L=1800, the 30 highest occupied orbitals, 128 frequencies in [-1.0, -0.3]
     "c60-ip-mixed": dict(base="c60", sector="IP", precision="mixed", per_step=1),
     "c60-ip-fp64": dict(base="c60", sector="IP", precision="fp64", per_step=1),
 }
-DEFAULT_WORKLOAD = "medium-ip-mixed"
+DEFAULT_WORKLOAD = "medium-ipea-mixed"
 FREQ_STRIDE = 17   # timed step k takes grid frequency (k * 17) mod n_omega (coprime with 64: covers the grid)
 
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 flops x max clock
@@ -132,38 +142,72 @@ def sectors_of(spec):
 
 
 def cpu_baseline(wl, spec, problem, max_columns=1):
-    """The CPU oracle as it stands, on a bounded sample: `max_columns` (omega, p) columns per sector of
-    the same workload solved by its GMRES with the same tolerance, restart and preconditioner."""
+    """The CPU oracle as it stands, on a bounded sample of the same workload: `max_columns` IP columns
+    solved by its GMRES (same tolerance, restart and preconditioner); for the EA sector, whose oracle
+    sigma product alone takes tens of seconds, one sigma product is timed and an EA column is
+    estimated as that time x the GMRES iterations of the sampled IP column(s) (40 without IP)."""
     from oracle.gfcc_ref import GFCCOracle, gmres
     secs = sectors_of(spec)
     t0 = time.perf_counter()
     orc = GFCCOracle(problem.fock, problem.chol, problem.t1, problem.t2, o=wl.o, sectors=secs)
     t_setup = time.perf_counter() - t0
-    cols = 0
-    its_total = 0
-    t0 = time.perf_counter()
-    for sec in secs:
-        for c in range(max_columns):
-            # the frequencies of the timed steps 1, 2, ... (step 0 sits deep in the 2h1p continuum and
-            # would take the CPU several minutes per column), first orbital of the list
-            om = wl.omegas[((c + 1) * FREQ_STRIDE) % wl.omegas.size]
-            p = int(wl.orbitals[0])
-            if sec == "IP":
-                D = (om - 1j * wl.eta) + orc.ip_diag()
-                x, its, rel, ok = gmres(orc.ip_apply(om, wl.eta), orc.ip_rhs(p), wl.tol, wl.restart, 50, diag=D)
-                G = np.stack([orc.ip_left(int(q)) for q in wl.orbitals]) @ x
-            else:
-                D = (om + 1j * wl.eta) - orc.ea_diag()
-                x, its, rel, ok = gmres(orc.ea_apply(om, wl.eta), orc.ea_rhs(p), wl.tol, wl.restart, 50, diag=D)
-                G = np.stack([orc.ea_left(int(q)) for q in wl.orbitals]) @ x
+    cols, its_ip, t_ip, t_ea_est, t_sig_ea = 0, 0, 0.0, 0.0, None
+    for c in range(max_columns):
+        # the frequencies of the timed steps 1, 2, ... (step 0 sits deep in the 2h1p continuum and
+        # would take the CPU several minutes per column), first orbital of the list
+        om = wl.omegas[((c + 1) * FREQ_STRIDE) % wl.omegas.size]
+        p = int(wl.orbitals[0])
+        if "IP" in secs:
+            t0 = time.perf_counter()
+            D = (om - 1j * wl.eta) + orc.ip_diag()
+            x, its, rel, ok = gmres(orc.ip_apply(om, wl.eta), orc.ip_rhs(p), wl.tol, wl.restart, 50, diag=D)
+            G = np.stack([orc.ip_left(int(q)) for q in wl.orbitals]) @ x
+            t_ip += time.perf_counter() - t0
             cols += 1 if ok else 0
-            its_total += its
-    dt = time.perf_counter() - t0
-    return {"value": cols / dt, "unit": "columns/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{max_columns} (omega, p) column(s) per sector {'+'.join(secs)} of the same workload (omega "
-                      f"of timed step 1, first orbital; {its_total} GMRES iterations), numpy FP64 GMRES with the "
-                      f"same tol/restart/preconditioner; oracle setup {t_setup:.1f} s excluded like gfcc_create",
+            its_ip += its
+        if "EA" in secs:
+            if t_sig_ea is None:
+                y = orc.ea_rhs(p).astype(complex)
+                t0 = time.perf_counter()
+                orc.ea_apply(om, wl.eta)(y)
+                t_sig_ea = time.perf_counter() - t0
+            n_it = its_ip / max(1, c + 1) if "IP" in secs else 40
+            t_ea_est += t_sig_ea * n_it
+            cols += 1
+    dt = t_ip + t_ea_est
+    sample = (f"{max_columns} (omega, p) column(s) per sector {'+'.join(secs)} of the same workload (omega of timed "
+              f"step 1, first orbital), numpy FP64 with the same tol/restart/preconditioner; oracle setup "
+              f"{t_setup:.1f} s excluded like gfcc_create")
+    if "IP" in secs:
+        sample += f"; IP: full GMRES ({its_ip} iterations, {t_ip:.1f} s)"
+    if "EA" in secs:
+        sample += (f"; EA: one sigma product timed ({t_sig_ea:.1f} s) x the IP iteration count per column "
+                   f"(estimated, {t_ea_est:.1f} s)")
+    return {"value": cols / dt, "unit": "columns/s", "cores": os.cpu_count(), "kind": "oracle", "sample": sample,
             "seconds": dt}
+
+
+def train_guess_model(gfcc, spec, wl, seed=1, n_freq=24):
+    """Train the learned-guess model on the method's own converged solutions of another problem of
+    the same shape (seed `seed`): a zero-guess sweep over n_freq spread frequencies with the solutions
+    kept, 3 samples per system, 1500 Adam steps.  Excluded from the timed region like gfcc_create."""
+    from paper_2010_04768_gb300.synthetic import make_problem, mlp_init_params
+    t0 = time.perf_counter()
+    pr = make_problem(wl.o, wl.v, wl.L, seed=seed)
+    g = gfcc.GFCC(pr, sectors=spec["sector"], precision=spec["precision"])
+    g.set_option(gfcc.OPT_RESTART, wl.restart)
+    g.set_option(gfcc.OPT_KEEP_SOLUTIONS, 1)
+    om = wl.omegas[np.linspace(0, wl.omegas.size - 1, n_freq).round().astype(int)]
+    g.solve(om, wl.eta, wl.orbitals, wl.tol)
+    model = gfcc.MLP(mlp_init_params(256, seed), 256, gfcc.MLP_FP32)
+    added = model.collect(g, samples_per_system=3, seed=seed)
+    g.close()
+    loss = model.train(steps=1500, minibatch=256, lr=1e-3, seed=seed)
+    ev = model.eval()
+    info = {"train_problem_seed": seed, "train_frequencies": int(n_freq), "samples": int(added),
+            "final_loss": loss, "eval": {k: float(v) for k, v in ev.items()},
+            "seconds": time.perf_counter() - t0}
+    return model, info
 
 
 def run_reference(args, world, rank):
@@ -237,19 +281,37 @@ def main():
     per = spec["per_step"]
     orb_dev = torch.tensor(wl.orbitals, dtype=torch.int32, device="cuda")
     G_dev = torch.zeros((per, no, no, 2), dtype=torch.float64, device="cuda")
+    guess_train = None
+    if spec.get("sweep"):
+        ctx.set_option(gfcc.OPT_BATCH, no)
+    if spec.get("guess") == "minres":
+        ctx.set_option(gfcc.OPT_GUESS, gfcc.GUESS_MINRES)
+    elif spec.get("guess") == "learned":
+        model, guess_train = train_guess_model(gfcc, spec, wl)
+        ctx.set_guess_model(model)
+        ctx.set_option(gfcc.OPT_GUESS, gfcc.GUESS_LEARNED)
 
     def freqs(step):
-        # rank r, timed step k: grid frequencies ((k * world + r) * per + j) * FREQ_STRIDE mod n_omega;
-        # warm-up steps (negative k) take the top end of the grid
+        # sweeps: rank r, timed step k takes the window of `per` consecutive grid frequencies starting at
+        # ((k * world + r) * per) mod n_omega; single-frequency steps take grid frequency
+        # ((k * world + r) * per + j) * FREQ_STRIDE mod n_omega.  Warm-up steps (negative k) take the top
+        # end of the grid.
         if step < 0:
             return np.array([wl.omegas[(nw + step * per + j) % nw] for j in range(per)])
         base = (step * world + rank) * per
+        if spec.get("sweep"):
+            return np.array([wl.omegas[(base + j) % nw] for j in range(per)])
         return np.array([wl.omegas[((base + j) * FREQ_STRIDE) % nw] for j in range(per)])
+
+    iter_log = []
 
     def device_step(k):
         om = torch.tensor(freqs(k), dtype=torch.float64, device="cuda")
         code = ctx.solve_device(om.data_ptr(), per, wl.eta, orb_dev.data_ptr(), no, wl.tol, G_dev.data_ptr())
         it, rr, st = ctx.stats()
+        if k >= 0:
+            kind, _, rel0 = ctx.guess_stats()
+            iter_log.append((int(it.sum()), it.size, int(np.sum(kind != 0)), float(np.mean(rel0))))
         return int(np.sum(st == 0)), code
 
     for k in range(args.warmup):
@@ -355,6 +417,11 @@ def main():
         "sigma_tflops": sigma_tflops,
         "phases_ms": {k: round(v[0], 3) for k, v in prof.items()},
         "setup_s": setup_s,
+        "iterations_per_column": sum(x[0] for x in iter_log) / max(1, sum(x[1] for x in iter_log)),
+        "guess": {"kind": spec.get("guess", "zero"),
+                  "guessed_fraction": sum(x[2] for x in iter_log) / max(1, sum(x[1] for x in iter_log)),
+                  "mean_initial_relres": float(np.mean([x[3] for x in iter_log])) if iter_log else None,
+                  "training": guess_train},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
