@@ -311,7 +311,8 @@ def main():
         it, rr, st = ctx.stats()
         if k >= 0:
             kind, _, rel0 = ctx.guess_stats()
-            iter_log.append((int(it.sum()), it.size, int(np.sum(kind != 0)), float(np.mean(rel0))))
+            outer = ctx.refine_stats()
+            iter_log.append((int(it.sum()), it.size, int(np.sum(kind != 0)), float(np.mean(rel0)), int(outer.sum())))
         return int(np.sum(st == 0)), code
 
     for k in range(args.warmup):
@@ -418,6 +419,7 @@ def main():
         "phases_ms": {k: round(v[0], 3) for k, v in prof.items()},
         "setup_s": setup_s,
         "iterations_per_column": sum(x[0] for x in iter_log) / max(1, sum(x[1] for x in iter_log)),
+        "fp64_residuals_per_column": sum(x[4] for x in iter_log) / max(1, sum(x[1] for x in iter_log)),
         "guess": {"kind": spec.get("guess", "zero"),
                   "guessed_fraction": sum(x[2] for x in iter_log) / max(1, sum(x[1] for x in iter_log)),
                   "mean_initial_relres": float(np.mean([x[3] for x in iter_log])) if iter_log else None,

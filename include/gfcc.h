@@ -239,6 +239,11 @@ int gfcc_selftest_gemm_f64emu(int M, int N, int K, const double *A, const double
  */
 int gfcc_guess_stats(gfcc_ctx *ctx, int *count, int *kind, double *pred, double *relres0);
 
+/* gfcc_refine_stats - mixed precision: per statistics entry of the last gfcc_solve, the number of
+ * FP64-accurate residuals evaluated for the system (refinement steps + 1; 0 for FP64 sectors).
+ * `count` as in gfcc_last_stats. */
+int gfcc_refine_stats(gfcc_ctx *ctx, int *count, int *outer);
+
 /*
  * The learned-guess model: a 3-layer perceptron with ReLU activations,
  *     x^ = (x - mu) / sd,  h1 = relu(W1 x^ + b1),  h2 = relu(W2 h1 + b2),  y = W3 h2 + b3,

@@ -606,6 +606,7 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
   c->st_guess.assign(ntasks * nsec, GFCC_GUESS_ZERO);
   c->st_guess_pred.assign(ntasks * nsec, 1.0);
   c->st_relres0.assign(ntasks * nsec, 1.0);
+  c->st_outer.assign(ntasks * nsec, 0);
   GFCC_CUDA(cudaMemsetAsync(d_G, 0, sizeof(double) * 2 * n_omega * n_orb * n_orb, st));
   int sec_slot = 0;
   bool all_ok = true;
@@ -678,7 +679,7 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
     for (int w = 0; w < n_omega; w++) word[w] = w;
     if (guess != GFCC_GUESS_ZERO) word = guess_frequency_order(c->kept.omega);
     std::vector<int> h_tw(nsys), h_ta(nsys), h_state(nsys), h_it(nsys), h_kind(nsys), h_nbr((size_t)nsys * GUESS_K),
-        h_navail(nsys), h_slot(nsys);
+        h_navail(nsys), h_slot(nsys), h_outer(nsys, 0);
     std::vector<double> h_rel(nsys), h_rel0(nsys), h_pred(nsys), h_delta((size_t)nsys * GUESS_K), h_pf(nsys);
     for (long long t0 = 0; t0 < ntasks; t0 += nsys) {
       const int nb = (int)std::min<long long>(nsys, ntasks - t0);
@@ -726,7 +727,8 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
       }
       if (mixed) {
         GFCC_TRY(umma_error_reset(st));
-        GFCC_TRY(gm.solve_refined(tol, c->inner_tol, c->max_iters, h_state.data(), h_it.data(), use_x0));
+        GFCC_TRY(gm.solve_refined(tol, c->inner_tol, c->max_iters, h_state.data(), h_it.data(), use_x0,
+                                  h_outer.data()));
         GFCC_TRY(umma_error_check(st));
       } else {
         GFCC_TRY(gm.solve(tol, c->max_iters, h_state.data(), 0, use_x0));
@@ -765,6 +767,7 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
         c->st_iters[idx] = h_it[s];
         c->st_relres[idx] = h_rel[s];
         c->st_relres0[idx] = h_rel0[s];
+        c->st_outer[idx] = mixed ? h_outer[s] : 0;
         c->st_status[idx] = h_state[s] == 3 ? GFCC_STATUS_CONVERGED : GFCC_STATUS_NOT_CONVERGED;
         if (guess != GFCC_GUESS_ZERO) {
           c->st_guess[idx] = h_kind[s];
@@ -996,6 +999,18 @@ int gfcc_guess_stats(gfcc_ctx *c, int *count, int *kind, double *pred, double *r
     if (pred) pred[i] = c->st_guess_pred[i];
     if (relres0) relres0[i] = c->st_relres0[i];
   }
+  *count = total;
+  return GFCC_OK;
+}
+
+int gfcc_refine_stats(gfcc_ctx *c, int *count, int *outer) {
+  if (c == nullptr || count == nullptr) {
+    set_error("gfcc_refine_stats: NULL argument");
+    return GFCC_ERR_ARG;
+  }
+  const int total = (int)c->st_outer.size();
+  const int nout = std::min(*count, total);
+  for (int i = 0; i < nout && outer; i++) outer[i] = c->st_outer[i];
   *count = total;
   return GFCC_OK;
 }

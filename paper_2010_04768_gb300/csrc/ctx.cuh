@@ -121,7 +121,7 @@ struct gfcc_ctx {
   KeptSolutions kept;
 
   // statistics of the last solve
-  std::vector<int> st_iters, st_status, st_guess;
+  std::vector<int> st_iters, st_status, st_guess, st_outer;
   std::vector<double> st_relres, st_guess_pred, st_relres0;
 
   // profiling (CUDA events on the context's stream)

@@ -868,12 +868,15 @@ __global__ void zero_done_kernel(double *R, long long n, int nsys, const int *do
 }
 }  // namespace
 
-int Gmres::solve_refined(double tol, double inner_tol, int max_iters, int *h_state, int *h_iters, bool use_x0) {
+int Gmres::solve_refined(double tol, double inner_tol, int max_iters, int *h_state, int *h_iters, bool use_x0,
+                         int *h_outer) {
   cudaStream_t st = c->stream;
   const long long tot = 2LL * nsys * n;
   const int TH = 256;
   std::vector<int> h_done(nsys, 0), it(nsys, 0);
   for (int s = 0; s < nsys; s++) h_iters[s] = 0;
+  if (h_outer)
+    for (int s = 0; s < nsys; s++) h_outer[s] = 0;
   // B0 holds the right-hand sides (FP64), X the initial iterate when use_x0
   if (!use_x0) GFCC_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * tot, st));
   GFCC_TRY(mdot(B0, n, 0, 1, B0, n, nrm, -1, 0));
@@ -900,6 +903,7 @@ int Gmres::solve_refined(double tol, double inner_tol, int max_iters, int *h_sta
     all_done = true;
     bool any_active = false;
     for (int s = 0; s < nsys; s++) {
+      if (h_outer && h_outer[s] == outer) h_outer[s] = outer + 1;   // still active before this check
       all_done &= h_done[s] != 0;
       // a system over its iteration budget stops here (not converged); the others go on
       if (!h_done[s] && h_iters[s] >= max_iters) h_done[s] = 2;

@@ -43,7 +43,9 @@ struct Gmres {
   // inner_tol, x += d, until ||r|| <= tol ||b||.  Leaves x in U, the FP64 relative residual in
   // relres, the summed inner iterations in h_iters and the final state (3 / 4) in h_state.
   // use_x0: X holds an initial iterate instead of zero.
-  int solve_refined(double tol, double inner_tol, int max_iters, int *h_state, int *h_iters, bool use_x0 = false);
+  // h_outer (optional): per system, the FP64-accurate residuals evaluated (refinement steps + 1)
+  int solve_refined(double tol, double inner_tol, int max_iters, int *h_state, int *h_iters, bool use_x0 = false,
+                    int *h_outer = nullptr);
 
  private:
   template <typename T>

@@ -22,6 +22,7 @@
 #include "ctx.cuh"
 #include "kernels.cuh"
 #include "sigma.cuh"
+#include "epilogue.cuh"
 
 namespace gfcc {
 
@@ -79,40 +80,6 @@ __global__ void unpack_ip_kernel(SysBatch b, int o, int v, long long C2, double 
   }
 }
 
-__global__ void epilogue_ip_kernel(SysBatch b, int o, int v, long long C2, long long dim, const double *S1,
-                                   const double *T, const double *Q, const double *U) {
-  const int ns = b.nsys;
-  const long long tot = dim * ns;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const long long mu = t % dim;
-    const int s = (int)(t / dim);
-    Cplx sg;
-    if (mu < o) {
-      sg = {S1[mu * C2 + 2 * s], S1[mu * C2 + 2 * s + 1]};
-    } else {
-      const long long r = mu - o;
-      const long long a = r % v;
-      long long i, j;
-      pair_decode(r / v, o, i, j);
-      const long long tij = ((i * v + a) * o + j) * C2 + 2 * s;
-      const long long tji = ((j * v + a) * o + i) * C2 + 2 * s;
-      const long long qij = ((i * o + j) * v + a) * C2 + 2 * s;
-      sg.r = T[tij] - T[tji] + Q[qij] + U[tij];
-      sg.i = T[tij + 1] - T[tji + 1] + Q[qij + 1] + U[tij + 1];
-    }
-    Cplx y = sg;
-    if (b.omega != nullptr) {
-      const Cplx u = precond_in(b.x, s * b.ldx + mu, b, s, mu);
-      const Cplx z{b.omega[s], -b.eta};
-      const Cplx zu = cmul(z, u);
-      y.r += zu.r;
-      y.i += zu.i;
-    }
-    b.y[2 * (s * b.ldy + mu)] = y.r;
-    b.y[2 * (s * b.ldy + mu) + 1] = y.i;
-  }
-}
-
 // ---------------------------------------------------------------- EA
 __global__ void unpack_ea_kernel(SysBatch b, int o, int v, long long Pv, long long C2, double *y1u, double *y2u,
                                  double *y2p) {
@@ -162,59 +129,20 @@ __global__ void unpack_ea_kernel(SysBatch b, int o, int v, long long Pv, long lo
   }
 }
 
-__global__ void epilogue_ea_kernel(SysBatch b, int o, int v, long long Pv, long long C2, long long dim,
-                                   const double *S1, const double *T, const double *Qp, const double *U) {
-  const int ns = b.nsys;
-  const long long tot = dim * ns;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const long long mu = t % dim;
-    const int s = (int)(t / dim);
-    Cplx sg;
-    if (mu < v) {
-      sg = {S1[mu * C2 + 2 * s], S1[mu * C2 + 2 * s + 1]};
-    } else {
-      const long long r = mu - v;
-      const long long i = r / Pv, ab = r % Pv;
-      long long a, bb;
-      pair_decode(ab, v, a, bb);
-      const long long tiba = ((i * v + bb) * v + a) * C2 + 2 * s;   // T[(i,b)][(a)]
-      const long long tiab = ((i * v + a) * v + bb) * C2 + 2 * s;   // T[(i,a)][(b)]
-      const long long qq = (ab * o + i) * C2 + 2 * s;
-      sg.r = T[tiba] - T[tiab] + Qp[qq] + U[tiba];
-      sg.i = T[tiba + 1] - T[tiab + 1] + Qp[qq + 1] + U[tiba + 1];
-    }
-    Cplx y{-sg.r, -sg.i};
-    if (b.omega == nullptr) {
-      y = sg;   // pure sigma
-    } else {
-      const Cplx u = precond_in(b.x, s * b.ldx + mu, b, s, mu);
-      const Cplx z{b.omega[s], b.eta};
-      const Cplx zu = cmul(z, u);
-      y.r += zu.r;
-      y.i += zu.i;
-    }
-    b.y[2 * (s * b.ldy + mu)] = y.r;
-    b.y[2 * (s * b.ldy + mu) + 1] = y.i;
-  }
-}
-
 }  // namespace
 
 int launch_epilogue_ip(gfcc_ctx *c, const SysBatch &b, const double *S1, const double *T, const double *Q,
                        const double *U) {
   const long long C2 = 2LL * b.nsys;
-  epilogue_ip_kernel<<<grid1d(c->dim_ip * b.nsys), 256, 0, c->stream>>>(b, c->o, c->v, C2, c->dim_ip, S1, T, Q, U);
-  GFCC_LAUNCH_CHECK();
-  return GFCC_OK;
+  (void)C2;
+  return epi::launch_ip<double, epi::MODE_FULL>(c->stream, b, c->o, c->v, S1, T, Q, U, nullptr);
 }
 
 int launch_epilogue_ea(gfcc_ctx *c, const SysBatch &b, const double *S1, const double *T, const double *Qp,
                        const double *U) {
   const long long C2 = 2LL * b.nsys;
-  epilogue_ea_kernel<<<grid1d(c->dim_ea * b.nsys), 256, 0, c->stream>>>(b, c->o, c->v, c->Pv, C2, c->dim_ea, S1, T,
-                                                                         Qp, U);
-  GFCC_LAUNCH_CHECK();
-  return GFCC_OK;
+  (void)C2;
+  return epi::launch_ea<double, epi::MODE_FULL>(c->stream, b, c->o, c->v, c->Pv, S1, T, Qp, U, nullptr);
 }
 
 double sigma_flops(const gfcc_ctx *c, int sector) {
@@ -266,8 +194,7 @@ int apply_ip(gfcc_ctx *c, const SysBatch &b, double *work) {
                     imap1(1)));
   GFCC_TRY(gemm_f64(st, o, C2, o * v * o, 1.0, c->U1, imap1(o * v * o), imap1(1), r2u, imap1(C2), imap1(1), 1.0, S1,
                     imap1(C2), imap1(1)));
-  epilogue_ip_kernel<<<grid1d(c->dim_ip * b.nsys), 256, 0, st>>>(b, (int)o, (int)v, C2, c->dim_ip, S1, T, Q, U);
-  GFCC_LAUNCH_CHECK();
+  GFCC_TRY((epi::launch_ip<double, epi::MODE_FULL>(st, b, (int)o, (int)v, S1, T, Q, U, nullptr)));
   return GFCC_OK;
 }
 
@@ -310,8 +237,7 @@ int apply_ea(gfcc_ctx *c, const SysBatch &b, double *work) {
                     imap1(1)));
   GFCC_TRY(gemm_f64(st, v, C2, o * v * v, 1.0, c->U1e, imap1(o * v * v), imap1(1), y2u, imap1(C2), imap1(1), 1.0, S1,
                     imap1(C2), imap1(1)));
-  epilogue_ea_kernel<<<grid1d(c->dim_ea * b.nsys), 256, 0, st>>>(b, (int)o, (int)v, Pv, C2, c->dim_ea, S1, T, Qp, U);
-  GFCC_LAUNCH_CHECK();
+  GFCC_TRY((epi::launch_ea<double, epi::MODE_FULL>(st, b, (int)o, (int)v, Pv, S1, T, Qp, U, nullptr)));
   return GFCC_OK;
 }
 

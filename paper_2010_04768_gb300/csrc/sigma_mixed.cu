@@ -23,6 +23,7 @@
 #include "kernels.cuh"
 #include "sigma.cuh"
 #include "umma.cuh"
+#include "epilogue.cuh"
 
 namespace gfcc {
 
@@ -157,57 +158,6 @@ __global__ void reduce_splits_kernel(float *part, int nsplit, long long rows, lo
   }
 }
 
-__global__ void epilogue_ip_mixed_kernel(SysBatch b, int o, int v, long long C2, long long dim, const double *diag,
-                                         const float *S1, const float *T, const float *Q, const float *U) {
-  const int ns = b.nsys;
-  const long long tot = dim * ns;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const long long mu = t % dim;
-    const int s = (int)(t / dim);
-    double sr, si;
-    if (mu < o) {
-      sr = S1[mu * C2 + 2 * s];
-      si = S1[mu * C2 + 2 * s + 1];
-    } else {
-      const long long r = mu - o;
-      const long long a = r % v;
-      long long i, j;
-      pair_decode(r / v, o, i, j);
-      const long long tij = ((i * v + a) * o + j) * C2 + 2 * s;
-      const long long tji = ((j * v + a) * o + i) * C2 + 2 * s;
-      const long long qij = ((i * o + j) * v + a) * C2 + 2 * s;
-      sr = (double)T[tij] - (double)T[tji] + (double)Q[qij] + (double)U[tij];
-      si = (double)T[tij + 1] - (double)T[tji + 1] + (double)Q[qij + 1] + (double)U[tij + 1];
-    }
-    double xr, xi;
-    if (b.xf != nullptr) {
-      xr = b.xf[2 * (s * b.ldx + mu)];
-      xi = b.xf[2 * (s * b.ldx + mu) + 1];
-    } else {
-      xr = b.x[2 * (s * b.ldx + mu)];
-      xi = b.x[2 * (s * b.ldx + mu) + 1];
-    }
-    double yr, yi;
-    if (b.omega == nullptr) {            // sigma(x) = d x + sigma_off(x)
-      yr = diag[mu] * xr + sr;
-      yi = diag[mu] * xi + si;
-    } else if (b.diag != nullptr) {      // right-preconditioned: D u = x
-      yr = xr + sr;
-      yi = xi + si;
-    } else {                             // (omega - i eta + d) x + sigma_off(x)
-      const double dr = b.omega[s] + diag[mu], di = -b.eta;
-      yr = dr * xr - di * xi + sr;
-      yi = dr * xi + di * xr + si;
-    }
-    if (b.yf != nullptr) {
-      reinterpret_cast<float2 *>(b.yf)[s * b.ldy + mu] = make_float2((float)yr, (float)yi);
-    } else {
-      b.y[2 * (s * b.ldy + mu)] = yr;
-      b.y[2 * (s * b.ldy + mu) + 1] = yi;
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------------------- EA
 // y2[m, a, e] of system s (antisymmetric in a, e; zero for a == e) from the packed EA vector
 // (1p a, then i-major 2p1h with pairs a < b)
@@ -269,60 +219,6 @@ __global__ void unpack_ea_k_kernel(SysBatch b, int o, int v, long long Pv, long 
     const __nv_bfloat16 h = __float2bfloat16((c & 1) ? u.i : u.r);
     rk[(long long)c * ldk + k] = h;
     if (k >= ov2) r1[(long long)c * ld1 + (k - ov2)] = h;
-  }
-}
-
-// y = x - sigma_off(u) (right-preconditioned), (omega + i eta - d) x - sigma_off(x), or, without
-// omega, sigma(x) = d x + sigma_off(x); sigma_off from the FP32 partial products
-__global__ void epilogue_ea_mixed_kernel(SysBatch b, int o, int v, long long Pv, long long C2, long long dim,
-                                         const double *diag, const float *S1, const float *T, const float *Qp,
-                                         const float *U) {
-  const int ns = b.nsys;
-  const long long tot = dim * ns;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const long long mu = t % dim;
-    const int s = (int)(t / dim);
-    double sr, si;
-    if (mu < v) {
-      sr = S1[mu * C2 + 2 * s];
-      si = S1[mu * C2 + 2 * s + 1];
-    } else {
-      const long long r = mu - v;
-      const long long i = r / Pv, ab = r % Pv;
-      long long a, bb;
-      pair_decode(ab, v, a, bb);
-      const long long tiba = ((i * v + bb) * v + a) * C2 + 2 * s;   // T[(i,b)][(a)]
-      const long long tiab = ((i * v + a) * v + bb) * C2 + 2 * s;   // T[(i,a)][(b)]
-      const long long qq = (ab * o + i) * C2 + 2 * s;
-      sr = (double)T[tiba] - (double)T[tiab] + (double)Qp[qq] + (double)U[tiba];
-      si = (double)T[tiba + 1] - (double)T[tiab + 1] + (double)Qp[qq + 1] + (double)U[tiba + 1];
-    }
-    double xr, xi;
-    if (b.xf != nullptr) {
-      xr = b.xf[2 * (s * b.ldx + mu)];
-      xi = b.xf[2 * (s * b.ldx + mu) + 1];
-    } else {
-      xr = b.x[2 * (s * b.ldx + mu)];
-      xi = b.x[2 * (s * b.ldx + mu) + 1];
-    }
-    double yr, yi;
-    if (b.omega == nullptr) {
-      yr = diag[mu] * xr + sr;
-      yi = diag[mu] * xi + si;
-    } else if (b.diag != nullptr) {
-      yr = xr - sr;
-      yi = xi - si;
-    } else {
-      const double dr = b.omega[s] - diag[mu], di = b.eta;
-      yr = dr * xr - di * xi - sr;
-      yi = dr * xi + di * xr - si;
-    }
-    if (b.yf != nullptr) {
-      reinterpret_cast<float2 *>(b.yf)[s * b.ldy + mu] = make_float2((float)yr, (float)yi);
-    } else {
-      b.y[2 * (s * b.ldy + mu)] = yr;
-      b.y[2 * (s * b.ldy + mu) + 1] = yi;
-    }
   }
 }
 
@@ -438,9 +334,7 @@ int apply_ip_mixed(gfcc_ctx *c, const SysBatch &b, double *work) {
                         ss, o * C2));
   reduce_splits_kernel<<<grid1d(o * C2), 256, 0, st>>>(w.S1p, ss, o, C2, o * C2, nullptr, 0);
   GFCC_LAUNCH_CHECK();
-  epilogue_ip_mixed_kernel<<<grid1d(c->dim_ip * b.nsys), 256, 0, st>>>(b, (int)o, (int)v, C2, c->dim_ip, c->diag_ip,
-                                                                       w.S1p, w.T, w.Q, w.U);
-  GFCC_LAUNCH_CHECK();
+  GFCC_TRY((epi::launch_ip<float, epi::MODE_OFFDIAG>(st, b, (int)o, (int)v, w.S1p, w.T, w.Q, w.U, c->diag_ip)));
   return GFCC_OK;
 }
 
@@ -491,9 +385,8 @@ int apply_ea_mixed(gfcc_ctx *c, const SysBatch &b, double *work) {
                         0.0f, ss, v * C2));
   reduce_splits_kernel<<<grid1d(v * C2), 256, 0, st>>>(w.S1p, ss, v, C2, v * C2, nullptr, 0);
   GFCC_LAUNCH_CHECK();
-  epilogue_ea_mixed_kernel<<<grid1d(c->dim_ea * b.nsys), 256, 0, st>>>(b, (int)o, (int)v, Pv, C2, c->dim_ea,
-                                                                       c->diag_ea, w.S1p, w.T, w.Qp, w.U);
-  GFCC_LAUNCH_CHECK();
+  GFCC_TRY((epi::launch_ea<float, epi::MODE_OFFDIAG>(st, b, (int)o, (int)v, Pv, w.S1p, w.T, w.Qp, w.U,
+                                                     c->diag_ea)));
   return GFCC_OK;
 }
 

@@ -80,6 +80,7 @@ def load():
     lib.gfcc_destroy.restype = None
     lib.gfcc_guess_stats.argtypes = [P, ip, ip, dp, dp]
     lib.gfcc_set_guess_model.argtypes = [P, P]
+    lib.gfcc_refine_stats.argtypes = [P, ip, ip]
     ull = ctypes.c_ulonglong
     lib.gfcc_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.POINTER(P)]
     lib.gfcc_mlp_destroy.argtypes = [P]
@@ -100,7 +101,7 @@ def load():
     lib.gfcc_last_error.restype = ctypes.c_char_p
     for name in ("gfcc_create", "gfcc_create_ex", "gfcc_set_option", "gfcc_set_stream", "gfcc_solve",
                  "gfcc_solve_device", "gfcc_last_stats", "gfcc_sigma", "gfcc_dims", "gfcc_profile",
-                 "gfcc_profile_read", "gfcc_guess_stats", "gfcc_set_guess_model", "gfcc_mlp_create",
+                 "gfcc_profile_read", "gfcc_guess_stats", "gfcc_set_guess_model", "gfcc_refine_stats", "gfcc_mlp_create",
                  "gfcc_mlp_get_params", "gfcc_mlp_set_params", "gfcc_mlp_forward", "gfcc_mlp_loss_grad",
                  "gfcc_mlp_train_batch", "gfcc_mlp_collect", "gfcc_mlp_train", "gfcc_mlp_eval",
                  "gfcc_mlp_get_samples"):
@@ -242,6 +243,16 @@ class GFCC:
         _check(lib.gfcc_guess_stats(self._h, ctypes.byref(cnt), kind.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                     _dp(pred), _dp(rel0)))
         return kind, pred, rel0
+
+    def refine_stats(self) -> np.ndarray:
+        """FP64-accurate residuals evaluated per statistics entry of the last solve (mixed precision)."""
+        lib = load()
+        cnt = ctypes.c_int(0)
+        _check(lib.gfcc_refine_stats(self._h, ctypes.byref(cnt), None))
+        out = np.zeros(cnt.value, dtype=np.int32)
+        cnt = ctypes.c_int(out.size)
+        _check(lib.gfcc_refine_stats(self._h, ctypes.byref(cnt), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return out
 
     def set_guess_model(self, model: "MLP | None"):
         self._model = model   # keeps the model alive while attached
