@@ -169,10 +169,11 @@ __global__ void symmetry_kernel(const double *x, long long d0, long long d1, lon
 // ---------------------------------------------------------------- right-hand sides
 // IP b_p: p occupied: unit 1h vector; p = o + b virtual: r1 = t1[:, b], r2[i<j, a] = t2[i][j][b][a]
 __global__ void rhs_ip_kernel(double *B, long long n, int nsys, const int *porb, int o, int v, const double *t1,
-                              const double *t2) {
+                              const double *t2, const int *mask) {
   const long long tot = n * nsys;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     const int s = (int)(t / n);
+    if (mask != nullptr && !mask[s]) continue;
     const long long mu = t - (long long)s * n;
     const int p = porb[s];
     double val = 0.0;
@@ -192,10 +193,11 @@ __global__ void rhs_ip_kernel(double *B, long long n, int nsys, const int *porb,
 
 // EA b_q: q virtual: unit 1p vector; q = m occupied: y1 = -t1[m, :], y2[i, a<b] = -t2[m][i][a][b]
 __global__ void rhs_ea_kernel(double *B, long long n, int nsys, const int *qorb, int o, int v, long long Pv,
-                              const double *t1, const double *t2) {
+                              const double *t1, const double *t2, const int *mask) {
   const long long tot = n * nsys;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     const int s = (int)(t / n);
+    if (mask != nullptr && !mask[s]) continue;
     const long long mu = t - (long long)s * n;
     const int q = qorb[s];
     double val = 0.0;
@@ -342,11 +344,13 @@ __global__ void left_ea_1p_kernel(double *C, long long n, int np, const int *por
 
 // ---------------------------------------------------------------- overlaps
 // part[z][(s,t)][q] summed over z -> G: IP row (w_s, a_s) gets columns q; EA column (w_s, a_s) gets rows q
-__global__ void overlap_scatter_kernel(const double *part, int nsplit, int nsys, int nq, const int *tw, const int *ta,
-                                       int is_ip, double *G) {
-  const long long tot = (long long)nsys * nq;
+// G rows of systems s < count with tw[s] >= 0 from the split-K partial overlaps (batch of nsys systems)
+__global__ void overlap_scatter_kernel(const double *part, int nsplit, int nsys, int count, int nq, const int *tw,
+                                       const int *ta, int is_ip, double *G) {
+  const long long tot = (long long)count * nq;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     const int s = (int)(t / nq), q = (int)(t % nq);
+    if (tw[s] < 0) continue;
     double re = 0.0, im = 0.0;
     const long long zs = 2LL * nsys * nq;
     for (int z = 0; z < nsplit; z++) {
@@ -673,6 +677,133 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
       }
     }
     }
+    if (mixed && guess == GFCC_GUESS_ZERO) {
+      // continuous batching: a slot whose system has converged (or spent its budget) after a
+      // refinement step is finalised (G row, statistics, kept solution) and refilled with the next
+      // task, so the batched contractions keep running on live systems
+      std::vector<long long> task(nsys, -1);
+      std::vector<int> h_tw(nsys, 0), h_ta(nsys, 0), h_done(nsys, 0), h_state(nsys), sl_it(nsys, 0), sl_outer(nsys, 0);
+      std::vector<int> h_twf(nsys, -1), h_mask(nsys, 0), h_slot(nsys, -1);
+      std::vector<double> h_rel(nsys, 0.0);
+      int *d_twf = d_porb + nsys;   // within the 4 nsys doubles reserved after the partials
+      int *d_mask = d_twf + nsys;
+      long long next = 0;
+      gm.tol_outer = tol;
+      auto load_slots = [&](bool all) -> int {
+        // tasks of the (re)filled slots: omega, orbital, right-hand side, X = 0, R = B0
+        for (int s = 0; s < nsys; s++) {
+          const long long t = task[s] >= 0 ? task[s] : 0;
+          h_tw[s] = (int)(t / n_orb);
+          h_ta[s] = (int)(t % n_orb);
+          h_mask[s] = all || h_mask[s] ? 1 : 0;
+        }
+        GFCC_CUDA(cudaMemcpyAsync(d_tw, h_tw.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+        GFCC_CUDA(cudaMemcpyAsync(d_ta, h_ta.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+        gather_omega_kernel<<<cdiv(nsys, 128), 128, 0, st>>>(d_om, d_tw, nsys, gm.omega);
+        GFCC_LAUNCH_CHECK();
+        gather_orb_kernel<<<cdiv(nsys, 128), 128, 0, st>>>(d_orb, d_ta, nsys, d_porb);
+        GFCC_LAUNCH_CHECK();
+        GFCC_CUDA(cudaMemcpyAsync(d_mask, h_mask.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+        {
+          PhaseTimer trhs(c, PH_OVERLAP);
+          GFCC_TRY(build_rhs_masked(c, sector, nsys, d_porb, d_mask, gm.rhs(), st));
+        }
+        for (int s = 0; s < nsys; s++)
+          if (h_mask[s] && task[s] < 0) {
+            // an empty slot: zero right-hand side (inert: ||b|| = 0 counts as converged)
+            GFCC_CUDA(cudaMemsetAsync(gm.rhs() + 2LL * s * n, 0, sizeof(double) * 2 * n, st));
+          }
+        GFCC_TRY(gm.reset_slots(d_mask));
+        GFCC_TRY(gm.refine_norms());
+        return GFCC_OK;
+      };
+      for (int s = 0; s < nsys; s++) task[s] = next < ntasks ? next++ : -1;
+      GFCC_TRY(load_slots(true));
+      GFCC_TRY(umma_error_reset(st));
+      bool first = true;
+      for (int step = 0;; step++) {
+        if (first) {
+          // X = 0: R = B0 already; only the norms and the checks
+          GFCC_TRY(gm.refine_residual_free(h_done.data(), h_rel.data()));
+          first = false;
+        } else {
+          GFCC_TRY(gm.refine_residual(h_done.data(), h_rel.data()));
+        }
+        bool any_fin = false, any_active = false;
+        for (int s = 0; s < nsys; s++) {
+          h_twf[s] = -1;
+          h_mask[s] = 0;
+          if (task[s] < 0) continue;
+          sl_outer[s]++;
+          const bool conv = h_done[s] == 1;
+          const bool fail = !conv && (sl_it[s] >= c->max_iters || sl_outer[s] > 400);
+          if (!conv && !fail) {
+            any_active = true;
+            continue;
+          }
+          // finalise the slot
+          const long long t = task[s];
+          const long long idx = sec_slot * ntasks + t;
+          c->st_iters[idx] = sl_it[s];
+          c->st_relres[idx] = h_rel[s];
+          c->st_relres0[idx] = 1.0;
+          c->st_outer[idx] = sl_outer[s];
+          c->st_status[idx] = conv ? GFCC_STATUS_CONVERGED : GFCC_STATUS_NOT_CONVERGED;
+          all_ok &= conv;
+          h_twf[s] = h_tw[s];
+          any_fin = true;
+        }
+        if (any_fin) {
+          GFCC_CUDA(cudaMemcpyAsync(d_twf, h_twf.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+          {
+            PhaseTimer tov(c, PH_OVERLAP);
+            Contract k;
+            k.A = gm.solution(); k.am = imap2(2, 1, 2 * n); k.ak = imap1(2);
+            k.B = Cl; k.bk = imap1(1); k.bn = imap1(n);
+            k.C = part; k.cm = imap1(n_orb); k.cn = imap1(1);
+            k.M = 2LL * nsys; k.N = n_orb; k.K = n;
+            k.nsplit = nsplit; k.kchunk = 8192; k.scz = 2LL * nsys * n_orb;
+            GFCC_TRY(contract_f64(k, st));
+            overlap_scatter_kernel<<<grid1d((long long)nsys * n_orb), 256, 0, st>>>(
+                part, (int)nsplit, nsys, nsys, n_orb, d_twf, d_ta, ip ? 1 : 0, d_G);
+            GFCC_LAUNCH_CHECK();
+          }
+          if (keep) {
+            for (int s = 0; s < nsys; s++) h_slot[s] = h_twf[s] >= 0 ? h_tw[s] * n_orb + h_ta[s] : -1;
+            GFCC_CUDA(cudaMemcpyAsync(g_slot, h_slot.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+            GFCC_TRY(guess_store_put(st, nsys, n, gm.solution(), n, g_slot, c->kept.X));
+            for (int s = 0; s < nsys; s++)
+              if (h_twf[s] >= 0 && h_done[s] == 1) c->kept.done[(size_t)h_tw[s] * n_orb + h_ta[s]] = 1;
+          }
+          // refill the finished slots
+          bool refill = false;
+          for (int s = 0; s < nsys; s++) {
+            if (h_twf[s] < 0) continue;
+            task[s] = next < ntasks ? next++ : -1;
+            sl_it[s] = 0;
+            sl_outer[s] = 0;
+            h_mask[s] = 1;
+            refill = true;
+            if (task[s] >= 0) any_active = true;
+          }
+          if (refill) {
+            GFCC_TRY(load_slots(false));
+            // the refilled slots start from X = 0: residual R = B0 (set by reset_slots), checked below
+            GFCC_TRY(gm.refine_residual_free(h_done.data(), h_rel.data()));
+            for (int s = 0; s < nsys; s++)
+              if (h_mask[s] && task[s] >= 0) sl_outer[s] = 1;
+          }
+        }
+        if (!any_active) break;
+        // inner correction for the live slots (done and empty slots have R = 0)
+        for (int s = 0; s < nsys; s++)
+          if (task[s] < 0) h_done[s] = 1;
+        GFCC_TRY(gm.refine_correct(h_done.data(), h_state.data(), sl_it.data()));
+      }
+      GFCC_TRY(umma_error_check(st));
+      sec_slot++;
+      continue;
+    }
     // task order: frequency-major; with initial guesses the frequencies go in the order of
     // guess_frequency_order so that later ones have converged neighbours on both sides
     std::vector<int> word(n_omega);
@@ -743,8 +874,8 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
       k.M = 2LL * nsys; k.N = n_orb; k.K = n;
       k.nsplit = nsplit; k.kchunk = 8192; k.scz = 2LL * nsys * n_orb;
       GFCC_TRY(contract_f64(k, st));
-      overlap_scatter_kernel<<<grid1d((long long)nb * n_orb), 256, 0, st>>>(part, (int)nsplit, nb, n_orb, d_tw, d_ta,
-                                                                             ip ? 1 : 0, d_G);
+      overlap_scatter_kernel<<<grid1d((long long)nb * n_orb), 256, 0, st>>>(part, (int)nsplit, nsys, nb, n_orb, d_tw,
+                                                                             d_ta, ip ? 1 : 0, d_G);
       GFCC_LAUNCH_CHECK();
       }
       if (keep) {
@@ -797,16 +928,22 @@ int check_solve_args(gfcc_ctx *c, int n_omega, double eta, int n_orb, double tol
 
 }  // namespace
 
-int build_rhs(gfcc_ctx *c, int sector, int nsys, const int *d_porb, double *B, cudaStream_t st) {
+int build_rhs_masked(gfcc_ctx *c, int sector, int nsys, const int *d_porb, const int *d_mask, double *B,
+                     cudaStream_t st) {
   if (nsys <= 0) return GFCC_OK;
   if (sector == GFCC_SECTOR_IP) {
-    rhs_ip_kernel<<<grid1d(c->dim_ip * nsys), 256, 0, st>>>(B, c->dim_ip, nsys, d_porb, c->o, c->v, c->t1, c->t2);
+    rhs_ip_kernel<<<grid1d(c->dim_ip * nsys), 256, 0, st>>>(B, c->dim_ip, nsys, d_porb, c->o, c->v, c->t1, c->t2,
+                                                            d_mask);
   } else {
     rhs_ea_kernel<<<grid1d(c->dim_ea * nsys), 256, 0, st>>>(B, c->dim_ea, nsys, d_porb, c->o, c->v, c->Pv, c->t1,
-                                                            c->t2);
+                                                            c->t2, d_mask);
   }
   GFCC_LAUNCH_CHECK();
   return GFCC_OK;
+}
+
+int build_rhs(gfcc_ctx *c, int sector, int nsys, const int *d_porb, double *B, cudaStream_t st) {
+  return build_rhs_masked(c, sector, nsys, d_porb, nullptr, B, st);
 }
 
 }  // namespace gfcc
@@ -882,6 +1019,10 @@ int gfcc_set_option(gfcc_ctx *c, int key, double value) {
     case GFCC_OPT_INNER_KRYLOV:
       if (iv != 32 && iv != 64) break;
       c->inner_fp64 = iv == 64 ? 1 : 0;
+      return GFCC_OK;
+    case GFCC_OPT_AUTOTUNE:
+      if (iv != 0 && iv != 1) break;
+      umma_set_autotune(iv == 1);
       return GFCC_OK;
     case GFCC_OPT_KEEP_SOLUTIONS:
       if (iv != 0 && iv != 1) break;

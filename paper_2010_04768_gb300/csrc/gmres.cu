@@ -621,6 +621,8 @@ int Gmres::op_fp64(const double *x, long long ldx, double *yout, long long ldy) 
     b.ldy = ldy;
     b.omega = omega;
     b.eta = eta;
+    b.dsign = ip ? 1.0 : -1.0;
+    b.zsign = ip ? -1.0 : 1.0;
     double *ew = sigma_work + sigma_work_doubles(c, sector, nsys) + sigma_mixed_work_doubles(c, nsys);
     const long long ewd = sigma_emu_work_doubles(c, std::min(nsys, 16));
     return ip ? apply_ip_emu(c, b, ew, ewd) : apply_ea_emu(c, b, ew, ewd);
@@ -867,6 +869,76 @@ __global__ void zero_done_kernel(double *R, long long n, int nsys, const int *do
     }
 }
 }  // namespace
+
+namespace {
+__global__ void reset_slots_kernel(double *X, double *R, const double *B0, long long n, int nsys, const int *mask) {
+  const long long tot = n * nsys;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    if (!mask[t / n]) continue;
+    reinterpret_cast<double2 *>(X)[t] = make_double2(0.0, 0.0);
+    reinterpret_cast<double2 *>(R)[t] = reinterpret_cast<const double2 *>(B0)[t];
+  }
+}
+}  // namespace
+
+int Gmres::refine_norms() {
+  GFCC_TRY(mdot(B0, n, 0, 1, B0, n, nrm, -1, 0));
+  norm_from_partial_kernel<<<cdiv(nsys, 256), 256, 0, c->stream>>>(nsys, nrm, NV, b0norm);
+  GFCC_LAUNCH_CHECK();
+  return GFCC_OK;
+}
+
+int Gmres::reset_slots(const int *d_mask) {
+  reset_slots_kernel<<<grid1d(n * nsys), 256, 0, c->stream>>>(X, R, B0, n, nsys, d_mask);
+  GFCC_LAUNCH_CHECK();
+  return GFCC_OK;
+}
+
+int Gmres::refine_residual(int *h_done, double *h_relres) {
+  cudaStream_t st = c->stream;
+  const long long tot = 2LL * nsys * n;
+  GFCC_TRY(op_fp64(X, n, R, n));
+  rsub_kernel<<<grid1d(tot), 256, 0, st>>>(B0, R, tot);
+  GFCC_LAUNCH_CHECK();
+  return refine_residual_free(h_done, h_relres);
+}
+
+int Gmres::refine_residual_free(int *h_done, double *h_relres) {
+  cudaStream_t st = c->stream;
+  GFCC_TRY(mdot(R, n, 0, 1, R, n, nrm, -1, 0));
+  refine_check_kernel<<<cdiv(nsys, 256), 256, 0, st>>>(nsys, nrm, NV, b0norm, tol_outer, kcyc, relres);
+  GFCC_LAUNCH_CHECK();
+  GFCC_CUDA(cudaMemcpyAsync(h_done, kcyc, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
+  GFCC_CUDA(cudaMemcpyAsync(h_relres, relres, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
+  GFCC_CUDA(cudaStreamSynchronize(st));
+  return GFCC_OK;
+}
+
+int Gmres::refine_correct(const int *h_done, int *h_state, int *h_iters) {
+  cudaStream_t st = c->stream;
+  const long long tot = 2LL * nsys * n;
+  int *done = kcyc;
+  GFCC_CUDA(cudaMemcpyAsync(done, h_done, sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+  zero_done_kernel<<<grid1d(n * nsys), 256, 0, st>>>(R, n, nsys, done);
+  GFCC_LAUNCH_CHECK();
+  if (f32) {
+    to_f32_kernel<<<grid1d(tot), 256, 0, st>>>(R, reinterpret_cast<float *>(B), tot);
+    GFCC_LAUNCH_CHECK();
+  } else {
+    GFCC_CUDA(cudaMemcpyAsync(B, R, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
+  }
+  GFCC_TRY(solve(c->inner_tol, c->max_iters, h_state, c->inner_cycles));
+  std::vector<int> it(nsys);
+  GFCC_CUDA(cudaMemcpyAsync(it.data(), iters, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
+  if (f32)
+    add_kernel<float><<<grid1d(tot), 256, 0, st>>>(X, reinterpret_cast<const float *>(U), tot);
+  else
+    add_kernel<double><<<grid1d(tot), 256, 0, st>>>(X, U, tot);
+  GFCC_LAUNCH_CHECK();
+  GFCC_CUDA(cudaStreamSynchronize(st));
+  for (int s = 0; s < nsys; s++) h_iters[s] += it[s];
+  return GFCC_OK;
+}
 
 int Gmres::solve_refined(double tol, double inner_tol, int max_iters, int *h_state, int *h_iters, bool use_x0,
                          int *h_outer) {

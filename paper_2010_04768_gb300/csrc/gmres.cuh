@@ -16,6 +16,7 @@ struct Gmres {
   long long n = 0;
   int nsys = 0, m = 30, NV = 32, nch = 1;
   double eta = 0.0;
+  double tol_outer = 0.0;  // continuous refinement: the outer (FP64) tolerance
   bool use_precond = false;
   bool mixed = false;      // inner operator on the BF16 tensor cores (IP), FP64 residuals outside
   bool f32 = false;        // Krylov vectors V, U, B, W in FP32 (inner solves of the refinement)
@@ -46,6 +47,18 @@ struct Gmres {
   // h_outer (optional): per system, the FP64-accurate residuals evaluated (refinement steps + 1)
   int solve_refined(double tol, double inner_tol, int max_iters, int *h_state, int *h_iters, bool use_x0 = false,
                     int *h_outer = nullptr);
+
+  // Pieces of solve_refined for continuous batching (slots refilled with new systems as others
+  // finish).  refine_norms: ||b0|| of every slot.  refine_residual: R = B0 - A X (FP64-accurate),
+  // relres = ||R|| / ||b0||, per-slot done flags (device kcyc: 1 = converged) copied to h_done.
+  // refine_correct: for the slots with h_done[s] == 0, one inner solve A d = R (BF16 operator)
+  // and X += d; the inner iterations of each slot are added to h_iters.
+  int refine_norms();
+  int refine_residual(int *h_done, double *h_relres);
+  int refine_residual_free(int *h_done, double *h_relres);   // the checks on R as it is (no operator)
+  int refine_correct(const int *h_done, int *h_state, int *h_iters);
+  // X[s] = 0 and R[s] = B0[s] for the slots with mask[s] != 0 (device mask)
+  int reset_slots(const int *d_mask);
 
  private:
   template <typename T>

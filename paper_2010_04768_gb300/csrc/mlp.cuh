@@ -28,4 +28,7 @@ namespace gfcc {
 int mlp_infer(gfcc_mlp *m, cudaStream_t st, int nb, const double *feat, double *y);
 // Right-hand sides of orbitals porb[s] (device) of one sector into B ([s][n] complex).
 int build_rhs(gfcc_ctx *c, int sector, int nsys, const int *d_porb, double *B, cudaStream_t st);
+// the same for the systems with d_mask[s] != 0 only
+int build_rhs_masked(gfcc_ctx *c, int sector, int nsys, const int *d_porb, const int *d_mask, double *B,
+                     cudaStream_t st);
 }  // namespace gfcc

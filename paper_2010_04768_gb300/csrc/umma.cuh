@@ -15,6 +15,10 @@ int gemm_bf16_tn(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const _
                  long long split_stride = 0);
 // number of partial sums gemm_bf16_tn writes for a requested split of K
 int umma_splits(int K, int nsplit);
+// Tile autotuning (on by default): the first call of each GEMM shape with beta == 0 times the
+// 64 / 128 / 256-column tiles and every later call of the shape uses the fastest.
+void umma_set_autotune(bool on);
+int umma_tuned_tile(int M, int N, int K, int nsplit);   // 0 if the shape was not tuned yet
 int umma_error_reset(cudaStream_t st);
 int umma_error_check(cudaStream_t st);   // GFCC_ERR_TIMEOUT if a bounded wait gave up
 

@@ -20,6 +20,10 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "common.cuh"
 #include "umma.cuh"
 
@@ -326,6 +330,11 @@ int umma_error_check(cudaStream_t st) {
 }
 
 namespace {
+// tile autotuner state: (device, M, N, K, split) -> tile width
+bool g_autotune = true;
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, int> g_tune;
+
 template <int BN>
 int launch_umma(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const __nv_bfloat16 *B, long long ldb,
                 float *D, long long ldd, int M, int N, int K, float alpha, float beta, int nsplit, int kbs,
@@ -374,10 +383,65 @@ int gemm_bf16_tn(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const _
   GFCC_TRY(check_extent_bytes(B, (long long)(N - 1) * ldb * 2 + (long long)K * 2, "bf16 GEMM operand B"));
   GFCC_TRY(check_extent_bytes(D, ((long long)(M - 1) * ldd + N + (long long)(nsplit - 1) * split_stride) * 4,
                               "bf16 GEMM output D"));
-  // narrowest tile that covers N (wide N keeps the 256-column tile)
-  if (N <= 64) return launch_umma<64>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
-  if (N <= 128) return launch_umma<128>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
-  return launch_umma<256>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
+  auto run = [&](int bn) -> int {
+    if (bn == 64) return launch_umma<64>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
+    if (bn == 128) return launch_umma<128>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
+    return launch_umma<256>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
+  };
+  // default: the narrowest tile that covers N (wide N keeps the 256-column tile)
+  int bn = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
+  if (g_autotune && beta == 0.0f) {
+    int dev = 0;
+    GFCC_CUDA(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(dev, M, N, K, nsplit);
+    int best = 0;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) best = it->second;
+    }
+    if (best == 0) {
+      // first call of this shape: time every tile width (second of two launches each, CUDA events on
+      // the stream; beta == 0, so the repeated launches leave the same D) and keep the fastest
+      cudaEvent_t e0, e1;
+      GFCC_CUDA(cudaEventCreate(&e0));
+      GFCC_CUDA(cudaEventCreate(&e1));
+      float best_ms = 0.0f;
+      for (int cand : {64, 128, 256}) {
+        if (cand > 64 && cand / 2 >= N) continue;   // wider than twice the columns: never better
+        GFCC_TRY(run(cand));
+        GFCC_CUDA(cudaEventRecord(e0, st));
+        GFCC_TRY(run(cand));
+        GFCC_CUDA(cudaEventRecord(e1, st));
+        GFCC_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        GFCC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (best == 0 || ms < best_ms) {
+          best = cand;
+          best_ms = ms;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune[key] = best;
+    }
+    bn = best;
+  }
+  return run(bn);
+}
+
+void umma_set_autotune(bool on) { g_autotune = on; }
+
+int umma_tuned_tile(int M, int N, int K, int nsplit) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(std::make_tuple(dev, M, N, K, nsplit));
+  return it == g_tune.end() ? 0 : it->second;
 }
 
 }  // namespace gfcc

@@ -165,3 +165,41 @@ def test_inner_krylov_precision_does_not_change_the_result(krylov):
     gm.close()
     assert code == gfcc.OK and np.all(st == 0) and np.all(rr <= 1e-10)
     assert rel_err(Gm, G64) <= 1e-7
+
+
+@pytest.mark.parametrize("batch", [3, 5, 7])
+def test_continuous_batching_refills_slots(batch):
+    # mixed precision refills a slot as soon as its system converges; task counts that are not a
+    # multiple of the batch leave empty slots at the end
+    wl = workload("tiny")
+    pr = wl.problem()
+    orbs = wl.orbitals[:5]
+    g = gfcc.GFCC(pr, sectors="IP", precision="mixed")
+    g.set_option(gfcc.OPT_BATCH, batch)
+    G, code = g.solve(wl.omegas, wl.eta, orbs, 1e-10)
+    it, rr, st = g.stats()
+    outer = g.refine_stats()
+    g.close()
+    assert code == gfcc.OK and np.all(st == 0) and np.all(rr <= 1e-10) and np.all(outer >= 2)
+    ref = GFCCOracle(pr.fock, pr.chol, pr.t1, pr.t2, o=wl.o, sectors=("IP",)).green_dense(
+        wl.omegas, wl.eta, list(orbs), sectors=("IP",))
+    assert rel_err(G, ref) <= 1e-6
+
+
+def test_fp64_batches_with_a_short_last_batch():
+    # n_IP = 9114 > 8192, so the G overlaps are summed over two K-split partials; 2 frequencies x 5
+    # orbitals = 10 tasks in batches of 4 leave a last batch of 2 systems.  The same G must come out
+    # of a single batch of 10.
+    o, v, L = 14, 100, 120
+    pr = make_problem(o, v, L, seed=12)
+    om = np.array([-0.9, -0.5])
+    orbs = np.array([o - 3, o - 2, o - 1, o, o + 1], dtype=np.int32)
+    out = []
+    for batch in (4, 10):
+        g = gfcc.GFCC(pr, sectors="IP")
+        g.set_option(gfcc.OPT_BATCH, batch)
+        G, code = g.solve(om, 0.01, orbs, 1e-10)
+        g.close()
+        assert code == gfcc.OK
+        out.append(G)
+    assert rel_err(out[0], out[1]) <= 1e-9

@@ -57,3 +57,24 @@ def test_f64_emulation_accuracy(M, N, K):
     assert (np.abs(C - ref) / scale).max() <= 1e-13
     C6 = gfcc.selftest_gemm_f64emu(A, B, S=6, P=7)
     assert (np.abs(C6 - ref) / scale).max() <= 3e-10
+
+
+def test_tile_autotuner_gives_the_same_products():
+    # the first call of a shape times the 64 / 128 / 256-column tiles; the tile width does not change
+    # the order of the K accumulation, so every choice gives the same FP32 result
+    from paper_2010_04768_gb300.synthetic import workload
+    g = gfcc.GFCC(workload("tiny").problem(), sectors="IP")
+    rng = np.random.default_rng(8)
+    out = {}
+    for tune in (0, 1):
+        g.set_option(gfcc.OPT_AUTOTUNE, tune)
+        for (M, N, K) in ((384, 80, 200), (256, 300, 640), (128, 40, 1000)):
+            A = rng.normal(size=(M, K)).astype(np.float32) if tune == 0 else out[(M, N, K)][1]
+            B = rng.normal(size=(N, K)).astype(np.float32) if tune == 0 else out[(M, N, K)][2]
+            D = gfcc.selftest_gemm_bf16(A, B)
+            if tune == 0:
+                out[(M, N, K)] = (D, A, B)
+            else:
+                assert np.max(np.abs(D - out[(M, N, K)][0])) <= 1e-5 * np.max(np.abs(D))
+    g.set_option(gfcc.OPT_AUTOTUNE, 1)
+    g.close()
