@@ -38,6 +38,8 @@ WORKLOADS = {
     "medium-ip-fp64": dict(base="medium", sector="IP", precision="fp64", per_step=1),
     "medium-ip-mixed": dict(base="medium", sector="IP", precision="mixed", per_step=1),
     "medium-ipea-mixed": dict(base="medium", sector="IP+EA", precision="mixed", per_step=1),
+    "medium-ip-mixed-4f": dict(base="medium", sector="IP", precision="mixed", per_step=4),
+    "medium-ipea-mixed-4f": dict(base="medium", sector="IP+EA", precision="mixed", per_step=4),
     "medium-ipea-fp64": dict(base="medium", sector="IP+EA", precision="fp64", per_step=1),
     # frequency sweeps: each step solves a window of `per_step` consecutive grid frequencies in one call,
     # one frequency per batch, each system started from the initial guess named (GFCC_OPT_GUESS)

@@ -52,7 +52,7 @@ struct gfcc_ctx {
   int max_iters = 1500;
   int precond = GFCC_PRECOND_DIAG;
   int batch = 0;
-  double inner_tol = 1e-3;
+  double inner_tol = 1e-4;
   int inner_cycles = 1;      // GMRES restart cycles per refinement step (each ends with an FP64-accurate residual)
   int inner_fp64 = 0;        // 1: FP64 Krylov vectors in the inner solves (default FP32)
 
