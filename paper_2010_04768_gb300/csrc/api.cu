@@ -680,35 +680,41 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
     if (mixed && guess == GFCC_GUESS_ZERO) {
       // continuous batching: a slot whose system has converged (or spent its budget) after a
       // refinement step is finalised (G row, statistics, kept solution) and refilled with the next
-      // task, so the batched contractions keep running on live systems
+      // task, so the batched contractions keep running on live systems; once the task list is
+      // exhausted the live slots are compacted to the front and the batch shrinks with them
+      int ns = nsys;   // slots in use (a prefix of the nsys slots)
       std::vector<long long> task(nsys, -1);
       std::vector<int> h_tw(nsys, 0), h_ta(nsys, 0), h_done(nsys, 0), h_state(nsys), sl_it(nsys, 0), sl_outer(nsys, 0);
-      std::vector<int> h_twf(nsys, -1), h_mask(nsys, 0), h_slot(nsys, -1);
+      std::vector<int> h_twf(nsys, -1), h_mask(nsys, 0), h_slot(nsys, -1), perm;
       std::vector<double> h_rel(nsys, 0.0);
       int *d_twf = d_porb + nsys;   // within the 4 nsys doubles reserved after the partials
       int *d_mask = d_twf + nsys;
       long long next = 0;
       gm.tol_outer = tol;
-      auto load_slots = [&](bool all) -> int {
-        // tasks of the (re)filled slots: omega, orbital, right-hand side, X = 0, R = B0
-        for (int s = 0; s < nsys; s++) {
+      auto upload_tasks = [&]() -> int {
+        for (int s = 0; s < ns; s++) {
           const long long t = task[s] >= 0 ? task[s] : 0;
           h_tw[s] = (int)(t / n_orb);
           h_ta[s] = (int)(t % n_orb);
-          h_mask[s] = all || h_mask[s] ? 1 : 0;
         }
-        GFCC_CUDA(cudaMemcpyAsync(d_tw, h_tw.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
-        GFCC_CUDA(cudaMemcpyAsync(d_ta, h_ta.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
-        gather_omega_kernel<<<cdiv(nsys, 128), 128, 0, st>>>(d_om, d_tw, nsys, gm.omega);
+        GFCC_CUDA(cudaMemcpyAsync(d_tw, h_tw.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
+        GFCC_CUDA(cudaMemcpyAsync(d_ta, h_ta.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
+        gather_omega_kernel<<<cdiv(ns, 128), 128, 0, st>>>(d_om, d_tw, ns, gm.omega);
         GFCC_LAUNCH_CHECK();
-        gather_orb_kernel<<<cdiv(nsys, 128), 128, 0, st>>>(d_orb, d_ta, nsys, d_porb);
+        gather_orb_kernel<<<cdiv(ns, 128), 128, 0, st>>>(d_orb, d_ta, ns, d_porb);
         GFCC_LAUNCH_CHECK();
-        GFCC_CUDA(cudaMemcpyAsync(d_mask, h_mask.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+        return GFCC_OK;
+      };
+      auto load_slots = [&](bool all) -> int {
+        // tasks of the (re)filled slots: omega, orbital, right-hand side, X = 0, R = B0
+        for (int s = 0; s < ns; s++) h_mask[s] = all || h_mask[s] ? 1 : 0;
+        GFCC_TRY(upload_tasks());
+        GFCC_CUDA(cudaMemcpyAsync(d_mask, h_mask.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
         {
           PhaseTimer trhs(c, PH_OVERLAP);
-          GFCC_TRY(build_rhs_masked(c, sector, nsys, d_porb, d_mask, gm.rhs(), st));
+          GFCC_TRY(build_rhs_masked(c, sector, ns, d_porb, d_mask, gm.rhs(), st));
         }
-        for (int s = 0; s < nsys; s++)
+        for (int s = 0; s < ns; s++)
           if (h_mask[s] && task[s] < 0) {
             // an empty slot: zero right-hand side (inert: ||b|| = 0 counts as converged)
             GFCC_CUDA(cudaMemsetAsync(gm.rhs() + 2LL * s * n, 0, sizeof(double) * 2 * n, st));
@@ -730,7 +736,7 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
           GFCC_TRY(gm.refine_residual(h_done.data(), h_rel.data()));
         }
         bool any_fin = false, any_active = false;
-        for (int s = 0; s < nsys; s++) {
+        for (int s = 0; s < ns; s++) {
           h_twf[s] = -1;
           h_mask[s] = 0;
           if (task[s] < 0) continue;
@@ -754,30 +760,30 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
           any_fin = true;
         }
         if (any_fin) {
-          GFCC_CUDA(cudaMemcpyAsync(d_twf, h_twf.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+          GFCC_CUDA(cudaMemcpyAsync(d_twf, h_twf.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
           {
             PhaseTimer tov(c, PH_OVERLAP);
             Contract k;
             k.A = gm.solution(); k.am = imap2(2, 1, 2 * n); k.ak = imap1(2);
             k.B = Cl; k.bk = imap1(1); k.bn = imap1(n);
             k.C = part; k.cm = imap1(n_orb); k.cn = imap1(1);
-            k.M = 2LL * nsys; k.N = n_orb; k.K = n;
-            k.nsplit = nsplit; k.kchunk = 8192; k.scz = 2LL * nsys * n_orb;
+            k.M = 2LL * ns; k.N = n_orb; k.K = n;
+            k.nsplit = nsplit; k.kchunk = 8192; k.scz = 2LL * ns * n_orb;
             GFCC_TRY(contract_f64(k, st));
-            overlap_scatter_kernel<<<grid1d((long long)nsys * n_orb), 256, 0, st>>>(
-                part, (int)nsplit, nsys, nsys, n_orb, d_twf, d_ta, ip ? 1 : 0, d_G);
+            overlap_scatter_kernel<<<grid1d((long long)ns * n_orb), 256, 0, st>>>(part, (int)nsplit, ns, ns, n_orb,
+                                                                                   d_twf, d_ta, ip ? 1 : 0, d_G);
             GFCC_LAUNCH_CHECK();
           }
           if (keep) {
-            for (int s = 0; s < nsys; s++) h_slot[s] = h_twf[s] >= 0 ? h_tw[s] * n_orb + h_ta[s] : -1;
-            GFCC_CUDA(cudaMemcpyAsync(g_slot, h_slot.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
-            GFCC_TRY(guess_store_put(st, nsys, n, gm.solution(), n, g_slot, c->kept.X));
-            for (int s = 0; s < nsys; s++)
+            for (int s = 0; s < ns; s++) h_slot[s] = h_twf[s] >= 0 ? h_tw[s] * n_orb + h_ta[s] : -1;
+            GFCC_CUDA(cudaMemcpyAsync(g_slot, h_slot.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
+            GFCC_TRY(guess_store_put(st, ns, n, gm.solution(), n, g_slot, c->kept.X));
+            for (int s = 0; s < ns; s++)
               if (h_twf[s] >= 0 && h_done[s] == 1) c->kept.done[(size_t)h_tw[s] * n_orb + h_ta[s]] = 1;
           }
-          // refill the finished slots
+          // refill the finished slots while tasks remain
           bool refill = false;
-          for (int s = 0; s < nsys; s++) {
+          for (int s = 0; s < ns; s++) {
             if (h_twf[s] < 0) continue;
             task[s] = next < ntasks ? next++ : -1;
             sl_it[s] = 0;
@@ -790,17 +796,38 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
             GFCC_TRY(load_slots(false));
             // the refilled slots start from X = 0: residual R = B0 (set by reset_slots), checked below
             GFCC_TRY(gm.refine_residual_free(h_done.data(), h_rel.data()));
-            for (int s = 0; s < nsys; s++)
+            for (int s = 0; s < ns; s++)
               if (h_mask[s] && task[s] >= 0) sl_outer[s] = 1;
           }
         }
         if (!any_active) break;
         // inner correction for the live slots (done and empty slots have R = 0)
-        for (int s = 0; s < nsys; s++)
+        for (int s = 0; s < ns; s++)
           if (task[s] < 0) h_done[s] = 1;
         GFCC_TRY(gm.refine_correct(h_done.data(), h_state.data(), sl_it.data()));
+        // drain: no task left to refill with, so move the live slots to the front and shrink the batch
+        if (next >= ntasks) {
+          perm.clear();
+          for (int s = 0; s < ns; s++)
+            if (task[s] >= 0) perm.push_back(s);
+          const int na = (int)perm.size();
+          if (na > 0 && na < ns) {
+            GFCC_CUDA(cudaMemcpyAsync(d_mask, perm.data(), sizeof(int) * na, cudaMemcpyHostToDevice, st));
+            GFCC_TRY(gm.compact_slots(d_mask, na));
+            for (int q = 0; q < na; q++) {
+              const int s = perm[q];
+              task[q] = task[s];
+              sl_it[q] = sl_it[s];
+              sl_outer[q] = sl_outer[s];
+            }
+            ns = na;
+            GFCC_TRY(upload_tasks());
+            GFCC_TRY(gm.refine_norms());
+          }
+        }
       }
       GFCC_TRY(umma_error_check(st));
+      gm.nsys = nsys;
       sec_slot++;
       continue;
     }

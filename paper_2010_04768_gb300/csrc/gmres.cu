@@ -881,6 +881,35 @@ __global__ void reset_slots_kernel(double *X, double *R, const double *B0, long 
 }
 }  // namespace
 
+namespace {
+// dst[q] = src[perm[q]] for q < na (rows of n complex)
+__global__ void gather_rows_kernel(const double *src, double *dst, long long n, int na, const int *perm) {
+  const long long tot = n * na;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(t / n);
+    const long long i = t - (long long)q * n;
+    reinterpret_cast<double2 *>(dst)[t] = reinterpret_cast<const double2 *>(src)[(long long)perm[q] * n + i];
+  }
+}
+}  // namespace
+
+int Gmres::compact_slots(const int *d_perm, int na) {
+  cudaStream_t st = c->stream;
+  if (na <= 0 || na > nsys) {
+    set_error("internal: compact_slots(%d) with %d slots", na, nsys);
+    return GFCC_ERR_ARG;
+  }
+  // R (free between refinement steps) is the staging buffer
+  gather_rows_kernel<<<grid1d(n * na), 256, 0, st>>>(X, R, n, na, d_perm);
+  GFCC_LAUNCH_CHECK();
+  GFCC_CUDA(cudaMemcpyAsync(X, R, sizeof(double) * 2 * na * n, cudaMemcpyDeviceToDevice, st));
+  gather_rows_kernel<<<grid1d(n * na), 256, 0, st>>>(B0, R, n, na, d_perm);
+  GFCC_LAUNCH_CHECK();
+  GFCC_CUDA(cudaMemcpyAsync(B0, R, sizeof(double) * 2 * na * n, cudaMemcpyDeviceToDevice, st));
+  nsys = na;
+  return GFCC_OK;
+}
+
 int Gmres::refine_norms() {
   GFCC_TRY(mdot(B0, n, 0, 1, B0, n, nrm, -1, 0));
   norm_from_partial_kernel<<<cdiv(nsys, 256), 256, 0, c->stream>>>(nsys, nrm, NV, b0norm);

@@ -59,6 +59,9 @@ struct Gmres {
   int refine_correct(const int *h_done, int *h_state, int *h_iters);
   // X[s] = 0 and R[s] = B0[s] for the slots with mask[s] != 0 (device mask)
   int reset_slots(const int *d_mask);
+  // keep slots perm[0..na) (device, increasing) as slots 0..na-1 (X and B0 move; R is clobbered and
+  // must be recomputed) and continue with nsys = na
+  int compact_slots(const int *d_perm, int na);
 
  private:
   template <typename T>

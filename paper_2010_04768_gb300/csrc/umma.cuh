@@ -8,8 +8,8 @@ namespace gfcc {
 
 // D[m][n] = alpha * sum_k A[m][k] B[n][k] + beta * D[m][n]; A: M x K, B: N x K (BF16, K-major,
 // row strides lda / ldb multiples of 8 elements, 16-byte aligned), D: FP32 row-major.
-// nsplit > 1 splits K: partial sum z goes to D + z * split_stride (beta must be 0); the caller
-// reduces the partials.  The split count actually used is returned through *nsplit_used if given.
+// nsplit > 1 splits K: partial sum z goes to D + z * split_stride (with beta != 0 each partial
+// accumulates onto its own previous contents); the caller reduces the partials.  The split count actually used is returned through *nsplit_used if given.
 int gemm_bf16_tn(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const __nv_bfloat16 *B, long long ldb,
                  float *D, long long ldd, int M, int N, int K, float alpha, float beta, int nsplit = 1,
                  long long split_stride = 0);

@@ -248,6 +248,14 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int i = 0; i < 32; i += 4)
             *reinterpret_cast<float4 *>(dst + i) = make_float4(alpha * v[i], alpha * v[i + 1], alpha * v[i + 2],
                                                                alpha * v[i + 3]);
+        } else if (ncols == 32 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+#pragma unroll
+          for (int i = 0; i < 32; i += 4) {
+            const float4 d = *reinterpret_cast<const float4 *>(dst + i);
+            *reinterpret_cast<float4 *>(dst + i) =
+                make_float4(alpha * v[i] + beta * d.x, alpha * v[i + 1] + beta * d.y, alpha * v[i + 2] + beta * d.z,
+                            alpha * v[i + 3] + beta * d.w);
+          }
         } else {
           for (int i = 0; i < ncols; i++) dst[i] = alpha * v[i] + (beta != 0.0f ? beta * dst[i] : 0.0f);
         }
@@ -369,8 +377,8 @@ int gemm_bf16_tn(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const _
   if (nsplit > nk) nsplit = nk;
   const int kbs = (nk + nsplit - 1) / nsplit;
   nsplit = (nk + kbs - 1) / kbs;   // every split gets at least one K block
-  if (nsplit > 1 && (beta != 0.0f || split_stride < (long long)(M - 1) * ldd + N)) {
-    set_error("gemm_bf16_tn: split-K writes separate partial sums (beta must be 0, stride >= one output)");
+  if (nsplit > 1 && split_stride < (long long)(M - 1) * ldd + N) {
+    set_error("gemm_bf16_tn: split-K writes separate partial sums (stride >= one output)");
     return GFCC_ERR_ARG;
   }
   if (K <= 0 || (lda % 8) || (ldb % 8) || lda < K || ldb < K || ldd < N ||
@@ -390,7 +398,11 @@ int gemm_bf16_tn(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const _
   };
   // default: the narrowest tile that covers N (wide N keeps the 256-column tile)
   int bn = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
-  if (g_autotune && beta == 0.0f) {
+  if (g_autotune && beta != 0.0f) {
+    // accumulating calls are not timed (they would change D); they reuse a tuned choice if any
+    const int t = umma_tuned_tile(M, N, K, nsplit);
+    if (t) bn = t;
+  } else if (g_autotune) {
     int dev = 0;
     GFCC_CUDA(cudaGetDevice(&dev));
     const auto key = std::make_tuple(dev, M, N, K, nsplit);
