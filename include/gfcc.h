@@ -154,6 +154,28 @@ int gfcc_solve(gfcc_ctx *ctx, int n_omega, const double *omegas, double eta,
 int gfcc_solve_device(gfcc_ctx *ctx, int n_omega, const double *omegas_dev, double eta,
                       int n_orb, const int *orbitals_dev, double tol, double *G_dev);
 
+/* One request of gfcc_solve_batch: the arguments of gfcc_solve (host arrays). */
+typedef struct gfcc_request {
+  int n_omega;
+  const double *omegas;
+  double eta;
+  int n_orb;
+  const int *orbitals;
+  double tol;
+  double *G;        /* out: as gfcc_solve */
+} gfcc_request;
+
+/*
+ * gfcc_solve_batch - gfcc_solve on several contexts (molecules of different sizes) at once: each
+ * context solves its request on its own stream from one of up to 8 host threads, so small problems
+ * share the GPU (Algorithm 1's task list over molecules; the paper runs them on separate process
+ * groups).  Contexts must be distinct and on the device current at the call; while they run, each
+ * plans its batch for its share of the free device memory.  codes (optional, n_ctx entries) gets
+ * every context's return code; the call returns GFCC_OK, GFCC_WARN_NOT_CONVERGED, or the first
+ * error (gfcc_last_error names the context).
+ */
+int gfcc_solve_batch(gfcc_ctx *const *ctxs, int n_ctx, const gfcc_request *reqs, int *codes);
+
 /*
  * gfcc_last_stats - statistics of the last gfcc_solve, one entry per (sector, omega, orbital)
  * in the order IP then EA, omega-major: `iters` sigma products, `relres` final true relative

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "ctx.cuh"
@@ -528,7 +529,7 @@ int choose_batch(gfcc_ctx *c, int sector, long long n, long long ntasks) {
   }
   const double per = 8.0 * (double)(gmres_work_doubles(c, sector, n, 2, c->restart, mixed) -
                                    gmres_work_doubles(c, sector, n, 1, c->restart, mixed));
-  long long b = (long long)(0.6 * (double)fr / std::max(per, 1.0));
+  long long b = (long long)(0.6 * c->mem_share * (double)fr / std::max(per, 1.0));
   b = std::max<long long>(1, std::min<long long>(b, 256));
   return (int)std::min<long long>(b, ntasks);
 }
@@ -1153,6 +1154,61 @@ int gfcc_last_stats(gfcc_ctx *c, int *count, int *iters, double *relres, int *st
   }
   *count = total;
   return GFCC_OK;
+}
+
+int gfcc_solve_batch(gfcc_ctx *const *ctxs, int n_ctx, const gfcc_request *reqs, int *codes) {
+  if (n_ctx < 0 || (n_ctx > 0 && (ctxs == nullptr || reqs == nullptr))) {
+    set_error("gfcc_solve_batch: bad arguments");
+    return GFCC_ERR_ARG;
+  }
+  for (int i = 0; i < n_ctx; i++) {
+    if (ctxs[i] == nullptr) {
+      set_error("gfcc_solve_batch: context %d is NULL", i);
+      return GFCC_ERR_ARG;
+    }
+    for (int j = 0; j < i; j++)
+      if (ctxs[j] == ctxs[i]) {
+        set_error("gfcc_solve_batch: context %d appears twice (contexts are not thread-safe)", i);
+        return GFCC_ERR_ARG;
+      }
+  }
+  if (n_ctx == 0) return GFCC_OK;
+  int dev = 0;
+  GFCC_CUDA(cudaGetDevice(&dev));
+  const int nthreads = std::min(n_ctx, 8);
+  std::vector<int> rc(n_ctx, GFCC_OK);
+  std::vector<std::string> msg(n_ctx);
+  std::vector<double> share(n_ctx);
+  for (int i = 0; i < n_ctx; i++) {
+    share[i] = ctxs[i]->mem_share;
+    ctxs[i]->mem_share = share[i] / nthreads;   // concurrent solves split the free memory
+  }
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    if (cudaSetDevice(dev) != cudaSuccess) {
+      cudaGetLastError();
+    }
+    for (int i = next++; i < n_ctx; i = next++) {
+      const gfcc_request &r = reqs[i];
+      rc[i] = gfcc_solve(ctxs[i], r.n_omega, r.omegas, r.eta, r.n_orb, r.orbitals, r.tol, r.G);
+      if (rc[i] < 0) msg[i] = gfcc_last_error();
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 0; t < nthreads; t++) th.emplace_back(worker);
+  for (auto &t : th) t.join();
+  for (int i = 0; i < n_ctx; i++) ctxs[i]->mem_share = share[i];
+  int out = GFCC_OK;
+  for (int i = 0; i < n_ctx; i++) {
+    if (codes) codes[i] = rc[i];
+    if (rc[i] < 0 && out >= 0) {
+      set_error("gfcc_solve_batch: context %d: %s", i, msg[i].c_str());
+      out = rc[i];
+    } else if (rc[i] == GFCC_WARN_NOT_CONVERGED && out == GFCC_OK) {
+      out = GFCC_WARN_NOT_CONVERGED;
+    }
+  }
+  return out;
 }
 
 int gfcc_guess_stats(gfcc_ctx *c, int *count, int *kind, double *pred, double *relres0) {

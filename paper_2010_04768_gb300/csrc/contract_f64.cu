@@ -8,6 +8,9 @@
 // DFMA per SM and clock), so this kernel is bound by the DFMA pipe: a 64x64 tile
 // per 256-thread block with 4x4 outputs per thread keeps the pipe fed while the
 // tile loads stay in L1/L2.
+#include <map>
+#include <mutex>
+
 #include "common.cuh"
 #include <algorithm>
 
@@ -131,8 +134,14 @@ __global__ void splitk_reduce_kernel(const double *part, int nsplit, long long M
   }
 }
 
-double *g_splitk_buf = nullptr;
-long long g_splitk_cap = 0;
+// split-K partial sums, one buffer per stream (work on a stream is ordered, so a buffer is never
+// shared by concurrent contractions)
+struct SplitBuf {
+  double *p = nullptr;
+  long long cap = 0;
+};
+std::mutex g_splitk_mu;
+std::map<cudaStream_t, SplitBuf> g_splitk;
 }  // namespace
 
 thread_local bool g_emulate_big = false;
@@ -158,19 +167,25 @@ int gemm_f64(cudaStream_t st, long long M, long long N, long long K, double alph
     nsplit = std::min<long long>(nsplit, 512);
     if (nsplit >= 2) {
       const long long need = nsplit * M * N;
-      if (need > g_splitk_cap) {
-        if (g_splitk_buf) dfree(g_splitk_buf);
-        g_splitk_buf = nullptr;
-        g_splitk_cap = 0;
-        if (dmalloc((void **)&g_splitk_buf, sizeof(double) * need) != cudaSuccess) {
-          cudaGetLastError();
-          set_error("gemm_f64: cannot allocate %lld doubles of split-K workspace", need);
-          return GFCC_ERR_OOM;
+      double *buf = nullptr;
+      {
+        std::lock_guard<std::mutex> lk(g_splitk_mu);
+        SplitBuf &sb = g_splitk[st];
+        if (need > sb.cap) {
+          if (sb.p) dfree(sb.p);   // cudaFree synchronises: earlier work on the buffer is done
+          sb.p = nullptr;
+          sb.cap = 0;
+          if (dmalloc((void **)&sb.p, sizeof(double) * need) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("gemm_f64: cannot allocate %lld doubles of split-K workspace", need);
+            return GFCC_ERR_OOM;
+          }
+          sb.cap = need;
         }
-        g_splitk_cap = need;
+        buf = sb.p;
       }
       Contract p = c;
-      p.C = g_splitk_buf;
+      p.C = buf;
       p.cm = imap1(N);
       p.cn = imap1(1);
       p.alpha = 1.0;
@@ -179,7 +194,7 @@ int gemm_f64(cudaStream_t st, long long M, long long N, long long K, double alph
       p.kchunk = (K + nsplit - 1) / nsplit;
       p.scz = M * N;
       GFCC_TRY(contract_f64(p, st));
-      splitk_reduce_kernel<<<grid1d(M * N), 256, 0, st>>>(g_splitk_buf, (int)nsplit, M, N, alpha, beta, C, cm, cn);
+      splitk_reduce_kernel<<<grid1d(M * N), 256, 0, st>>>(buf, (int)nsplit, M, N, alpha, beta, C, cm, cn);
       GFCC_LAUNCH_CHECK();
       return GFCC_OK;
     }

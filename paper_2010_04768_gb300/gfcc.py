@@ -34,6 +34,12 @@ _PRECS = {"fp64": PREC_FP64, "mixed": PREC_MIXED_BF16, "bf16": PREC_MIXED_BF16, 
 _lib = None
 
 
+class _Request(ctypes.Structure):
+    _fields_ = [("n_omega", ctypes.c_int), ("omegas", ctypes.POINTER(ctypes.c_double)), ("eta", ctypes.c_double),
+                ("n_orb", ctypes.c_int), ("orbitals", ctypes.POINTER(ctypes.c_int)), ("tol", ctypes.c_double),
+                ("G", ctypes.POINTER(ctypes.c_double))]
+
+
 class GFCCError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"libgfcc error {code}: {msg}")
@@ -81,6 +87,7 @@ def load():
     lib.gfcc_guess_stats.argtypes = [P, ip, ip, dp, dp]
     lib.gfcc_set_guess_model.argtypes = [P, P]
     lib.gfcc_refine_stats.argtypes = [P, ip, ip]
+    lib.gfcc_solve_batch.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(_Request), ip]
     ull = ctypes.c_ulonglong
     lib.gfcc_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.POINTER(P)]
     lib.gfcc_mlp_destroy.argtypes = [P]
@@ -101,7 +108,7 @@ def load():
     lib.gfcc_last_error.restype = ctypes.c_char_p
     for name in ("gfcc_create", "gfcc_create_ex", "gfcc_set_option", "gfcc_set_stream", "gfcc_solve",
                  "gfcc_solve_device", "gfcc_last_stats", "gfcc_sigma", "gfcc_dims", "gfcc_profile",
-                 "gfcc_profile_read", "gfcc_guess_stats", "gfcc_set_guess_model", "gfcc_refine_stats", "gfcc_mlp_create",
+                 "gfcc_profile_read", "gfcc_guess_stats", "gfcc_set_guess_model", "gfcc_refine_stats", "gfcc_solve_batch", "gfcc_mlp_create",
                  "gfcc_mlp_get_params", "gfcc_mlp_set_params", "gfcc_mlp_forward", "gfcc_mlp_loss_grad",
                  "gfcc_mlp_train_batch", "gfcc_mlp_collect", "gfcc_mlp_train", "gfcc_mlp_eval",
                  "gfcc_mlp_get_samples"):
@@ -281,6 +288,27 @@ class GFCC:
                                     X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                     Y.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return Y
+
+
+def solve_batch(ctxs, requests):
+    """gfcc_solve_batch: requests[i] = (omegas, eta, orbitals, tol) for context ctxs[i]; returns the G
+    arrays and the per-context return codes."""
+    n = len(ctxs)
+    keep = []
+    reqs = (_Request * n)()
+    Gs = []
+    for i, (om, eta, orb, tol) in enumerate(requests):
+        om = _f64(om).reshape(-1)
+        orb = np.ascontiguousarray(orb, dtype=np.int32).reshape(-1)
+        G = np.zeros((om.size, orb.size, orb.size), dtype=np.complex128)
+        keep += [om, orb]
+        Gs.append(G)
+        reqs[i] = _Request(om.size, _dp(om), float(eta), orb.size, orb.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                           float(tol), G.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    hs = (ctypes.c_void_p * n)(*[c.handle.value for c in ctxs])
+    codes = np.zeros(n, dtype=np.int32)
+    _check(load().gfcc_solve_batch(hs, n, reqs, codes.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+    return Gs, codes
 
 
 class MLP:

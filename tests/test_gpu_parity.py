@@ -162,3 +162,24 @@ def test_not_converged_is_reported():
     it, rr, st = g.stats()
     assert np.all(st == 1) and np.all(it <= 4) and np.isfinite(G).all()
     g.close()
+
+
+def test_solve_batch_matches_individual_solves():
+    # molecules of uneven sizes solved concurrently (one stream and host thread per context)
+    shapes = [(3, 9, 20), (5, 15, 30), (4, 12, 48), (6, 20, 40)]
+    ctxs, reqs, refs = [], [], []
+    for k, (o, v, L) in enumerate(shapes):
+        pr = make_problem(o, v, L, seed=20 + k)
+        om = np.linspace(-1.0, 0.4, 3 + k)
+        orbs = np.arange(max(0, o - 2), min(o + v, o + 2), dtype=np.int32)
+        g = gfcc.GFCC(pr, sectors="IP+EA", precision="fp64" if k % 2 == 0 else "mixed")
+        ref, code = g.solve(om, 0.01, orbs, 1e-10)
+        ctxs.append(g)
+        reqs.append((om, 0.01, orbs, 1e-10))
+        refs.append(ref)
+    Gs, codes = gfcc.solve_batch(ctxs, reqs)
+    assert np.all(codes >= 0)
+    for G, ref in zip(Gs, refs):
+        assert rel_err(G, ref) <= 1e-8
+    for g in ctxs:
+        g.close()
