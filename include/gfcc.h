@@ -74,6 +74,9 @@ extern "C" {
 #define GFCC_OPT_GUESS      11    /* GFCC_GUESS_*: initial iterate of each GMRES solve; default ZERO     */
 #define GFCC_OPT_KEEP_SOLUTIONS 12 /* 1: keep the converged solutions of the last sector solved after
                                      gfcc_solve (for gfcc_mlp_collect); default 0                        */
+#define GFCC_OPT_GRAPHS     15    /* 1 (default): the Arnoldi steps of the inner solves of the mixed
+                                     refinement are captured once per batch size into CUDA graphs and
+                                     replayed (not while profiling, not on the legacy default stream)    */
 #define GFCC_OPT_AUTOTUNE   14    /* 1 (default): the first tensor-core contraction of each shape times
                                      the 64 / 128 / 256-column tiles and later ones use the fastest;
                                      0: the narrowest tile covering N.  Process-wide.                    */

@@ -82,6 +82,8 @@ void dfree(void *p) {
 
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(); }
 
 static cudaEvent_t take_event(gfcc_ctx *c) {
   if (!c->ev_pool.empty()) {
@@ -1051,6 +1053,10 @@ int gfcc_set_option(gfcc_ctx *c, int key, double value) {
     case GFCC_OPT_AUTOTUNE:
       if (iv != 0 && iv != 1) break;
       umma_set_autotune(iv == 1);
+      return GFCC_OK;
+    case GFCC_OPT_GRAPHS:
+      if (iv != 0 && iv != 1) break;
+      c->use_graphs = iv;
       return GFCC_OK;
     case GFCC_OPT_KEEP_SOLUTIONS:
       if (iv != 0 && iv != 1) break;

@@ -42,6 +42,8 @@ void dfree(void *p);                           // unreg_alloc + cudaFree
 
 // Check the last kernel launch (and count it: gfcc_launch_count reports the total).
 void count_launch();
+void count_launches(long long n);   // kernels replayed from a CUDA graph
+long long launch_count();
 #define GFCC_LAUNCH_CHECK()   \
   do {                        \
     ::gfcc::count_launch();   \

@@ -56,6 +56,7 @@ struct gfcc_ctx {
   double inner_tol = 1e-4;
   int inner_cycles = 1;      // GMRES restart cycles per refinement step (each ends with an FP64-accurate residual)
   int inner_fp64 = 0;        // 1: FP64 Krylov vectors in the inner solves (default FP32)
+  int use_graphs = 1;        // replay the Arnoldi steps of the inner solves from CUDA graphs
 
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;

@@ -734,6 +734,16 @@ int Gmres::cgs2_t(const T *Vb, long long vs, int nv, T *w, cudaStream_t st) {
   return GFCC_OK;
 }
 
+Gmres::~Gmres() { drop_graphs(); }
+
+void Gmres::drop_graphs() {
+  for (cudaGraphExec_t &g : gexec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
 int Gmres::solve(double tol, int max_iters, int *h_state, int max_cycles, bool use_x0) {
   return f32 ? solve_t<float>(tol, max_iters, h_state, max_cycles, use_x0)
              : solve_t<double>(tol, max_iters, h_state, max_cycles, use_x0);
@@ -748,6 +758,20 @@ int Gmres::solve_t(double tol, int max_iters, int *h_state, int max_cycles, bool
   T *Wt = reinterpret_cast<T *>(W);
   const double dsg = sector == GFCC_SECTOR_IP ? 1.0 : -1.0, zsg = sector == GFCC_SECTOR_IP ? -1.0 : 1.0;
   const double *dg = sector == GFCC_SECTOR_IP ? c->diag_ip : c->diag_ea;
+  // CUDA graphs for the inner solves of the refinement (FP32 Krylov vectors) on a created stream,
+  // not while profiling (the phase timers are stream events); the contraction shapes of the current
+  // number of systems must have been seen (and tuned) before a capture
+  const bool use_graphs = sizeof(T) == sizeof(float) && mixed && c->use_graphs && !c->prof && st != nullptr;
+  if (use_graphs) {
+    if (gnsys != nsys) {
+      drop_graphs();
+      gexec.assign(m, nullptr);
+      glaunch.assign(m, 0);
+      gnsys = nsys;
+      gseen = 0;
+    }
+    gseen++;
+  }
   if (!use_x0) {
     GFCC_CUDA(cudaMemsetAsync(Ut, 0, sizeof(T) * 2 * nsys * n, st));
   } else if (use_precond) {
@@ -796,22 +820,58 @@ int Gmres::solve_t(double tol, int max_iters, int *h_state, int max_cycles, bool
     for (int k = 0; k < m; k++) {
       T *vk = Vt + 2 * (long long)k * n;
       T *w = Vt + 2 * (long long)(k + 1) * n;
-      GFCC_TRY(op_t<T>(vk, vs, w, vs));
-      // Gram-Schmidt against the basis: one classical pass (dots with ||w||^2, then update with
-      // ||w'||^2), a second pass only where needed, then w /= ||w||.  Algorithmic bytes of one
-      // classical pass per system: dots read k+1 basis vectors and w, the update reads k+1 basis
-      // vectors and reads / writes w, the scaling reads / writes w.
-      {
-        const double bytes = (double)active * (2.0 * (k + 1) + 5.0) * (double)n * 2.0 * sizeof(T);
-        PhaseTimer ta(c, PH_ARNOLDI, bytes);
-        GFCC_TRY(cgs2_t<T>(Vt, vs, k + 1, w, st));
+      auto step = [&]() -> int {
+        GFCC_TRY(op_t<T>(vk, vs, w, vs));
+        // Gram-Schmidt against the basis: one classical pass (dots with ||w||^2, then update with
+        // ||w'||^2), a second pass only where needed, then w /= ||w||.  Algorithmic bytes of one
+        // classical pass per system: dots read k+1 basis vectors and w, the update reads k+1 basis
+        // vectors and reads / writes w, the scaling reads / writes w.
+        {
+          const double bytes = (double)active * (2.0 * (k + 1) + 5.0) * (double)n * 2.0 * sizeof(T);
+          PhaseTimer ta(c, PH_ARNOLDI, bytes);
+          GFCC_TRY(cgs2_t<T>(Vt, vs, k + 1, w, st));
+        }
+        {
+          PhaseTimer tl(c, PH_LSQ);
+          givens_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, k, m, h, NV, H, cs, sn, g, bnorm, tol, state, kcyc,
+                                                       iters, est);
+          GFCC_LAUNCH_CHECK();
+        }
+        return GFCC_OK;
+      };
+      bool done_step = false;
+      if (use_graphs && gseen > 1 && !gbroken) {
+        if (!gexec[k]) {
+          // capture the step once (its launches are counted as they are recorded; the launch right
+          // after the capture runs them), replay it afterwards.  A capture that fails leaves the
+          // graphs off for this solver and the step runs directly.
+          const long long l0 = launch_count();
+          cudaGraph_t gr = nullptr;
+          cudaError_t ec = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+          int rc = GFCC_ERR_CUDA;
+          if (ec == cudaSuccess) {
+            rc = step();
+            ec = cudaStreamEndCapture(st, &gr);
+          }
+          if (rc == GFCC_OK && ec == cudaSuccess && gr != nullptr &&
+              cudaGraphInstantiate(&gexec[k], gr, 0) == cudaSuccess) {
+            glaunch[k] = launch_count() - l0;
+            GFCC_CUDA(cudaGraphLaunch(gexec[k], st));
+            done_step = true;
+          } else {
+            cudaGetLastError();
+            gexec[k] = nullptr;
+            gbroken = true;
+            count_launches(l0 - launch_count());   // nothing of the failed capture ran
+          }
+          if (gr) cudaGraphDestroy(gr);
+        } else {
+          GFCC_CUDA(cudaGraphLaunch(gexec[k], st));
+          count_launches(glaunch[k]);
+          done_step = true;
+        }
       }
-      {
-        PhaseTimer tl(c, PH_LSQ);
-        givens_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, k, m, h, NV, H, cs, sn, g, bnorm, tol, state, kcyc, iters,
-                                                     est);
-        GFCC_LAUNCH_CHECK();
-      }
+      if (!done_step) GFCC_TRY(step());
       GFCC_CUDA(cudaMemcpyAsync(h_state, state, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
       GFCC_CUDA(cudaStreamSynchronize(st));
       active = 0;

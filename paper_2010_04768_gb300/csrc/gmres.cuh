@@ -1,5 +1,7 @@
 // Batched restarted GMRES over the shifted operator of eq. xplin.
 #pragma once
+#include <vector>
+
 #include "ctx.cuh"
 
 namespace gfcc {
@@ -11,6 +13,10 @@ long long gmres_work_doubles(const gfcc_ctx *c, int sector, long long n, int nsy
 // solve_refined(); the solution is left in solution() ([s][n], complex FP64).  Per-system results: iters, relres, state
 // (3 = converged, 4 = not converged).
 struct Gmres {
+  Gmres() = default;
+  Gmres(const Gmres &) = delete;
+  Gmres &operator=(const Gmres &) = delete;
+  ~Gmres();
   gfcc_ctx *c = nullptr;
   int sector = GFCC_SECTOR_IP;
   long long n = 0;
@@ -64,6 +70,13 @@ struct Gmres {
   int compact_slots(const int *d_perm, int na);
 
  private:
+  // CUDA graphs of the Arnoldi steps of the inner (FP32) solves: one per step k, captured for the
+  // current number of systems once its contraction shapes have been seen (tuned) in an earlier call
+  std::vector<cudaGraphExec_t> gexec;
+  std::vector<long long> glaunch;
+  int gnsys = -1, gseen = 0;
+  bool gbroken = false;
+  void drop_graphs();
   template <typename T>
   int op_t(const T *x, long long ldx, T *y, long long ldy);
   template <typename T>

@@ -127,20 +127,14 @@ int emu_slice(cudaStream_t st, const double *A, long long rows, long long K, lon
   return GFCC_OK;
 }
 
-// The digit pairs of one level L = i + j share a weight, so their products are accumulated in the
-// same FP32 partial sums (beta = 1) as long as the sum stays an exact integer: a partial covers at
-// most 2^14 digit products of magnitude <= 2^10 over all the pairs of the level, so a level of p
-// pairs splits K into chunks of KCHUNK_BLOCKS / p blocks.  One integer combine per level.
-constexpr int MAX_LEVEL_PAIRS = 8;
-
-int level_splits(long long nk, int pairs) {
-  const long long kb = std::max<long long>(1, KCHUNK_BLOCKS / std::max(1, pairs));
-  return (int)((nk + kb - 1) / kb);
-}
-
+// The digit pairs of one level L = i + j share a weight, so several of them can accumulate in the
+// same FP32 partial sums (beta = 1) while the sums stay exact integers: a partial over kbs K blocks
+// of 64 holds up to KCHUNK_BLOCKS / kbs pairs (2^14 digit products of magnitude <= 2^10).  The K
+// split is the one of a single pair; pairs are grouped within that bound, one integer combine per
+// group.
 long long emu_gemm_work_bytes(long long M, long long N, long long K) {
   const long long nk = (K + 63) / 64;
-  const long long nz = level_splits(nk, MAX_LEVEL_PAIRS);
+  const long long nz = (nk + KCHUNK_BLOCKS - 1) / KCHUNK_BLOCKS;
   return nz * M * N * 4 + M * N * 16 + 512;
 }
 
@@ -153,7 +147,9 @@ int emu_gemm(cudaStream_t st, const EmuOperand &A, const EmuOperand &B, int P, d
     return GFCC_ERR_ARG;
   }
   const long long nk = (K + 63) / 64;
-  const int nz = level_splits(nk, MAX_LEVEL_PAIRS);   // the most splits any level uses
+  const int nz = (int)((nk + KCHUNK_BLOCKS - 1) / KCHUNK_BLOCKS);
+  const long long kbs = (nk + nz - 1) / nz;
+  const int group = (int)std::max<long long>(1, KCHUNK_BLOCKS / kbs);   // pairs per exact partial
   float *part = static_cast<float *>(work);
   long long *acc =
       reinterpret_cast<long long *>(static_cast<unsigned char *>(work) + ((nz * M * N * 4 + 255) / 256) * 256);
@@ -161,7 +157,8 @@ int emu_gemm(cudaStream_t st, const EmuOperand &A, const EmuOperand &B, int P, d
   GFCC_TRY(check_extent(C, 0, imap_max(cm, M) + imap_max(cn, n0 + N), "digit GEMM output"));
   const long long plA = A.rows * A.ld, plB = B.rows * B.ld;
   // two exact int64 accumulators: levels 2..Lhi (weights 64^(Lhi-L)) and Lhi+1..P (64^(P-L));
-  // a level sum is below nz 2^24 < 2^33, so 4 levels of 6-bit shifts stay below 2^63
+  // a group sum is below nz 2^24 < 2^33 (and a level holds at most S groups), so 4 levels of 6-bit
+  // shifts stay below 2^63
   const int Lhi = std::min(P, 5);
   if (P - Lhi > 4 || nz > (1 << 16)) {
     set_error("emu_gemm: level %d or K %lld beyond the exact integer accumulation", P, K);
@@ -169,29 +166,27 @@ int emu_gemm(cudaStream_t st, const EmuOperand &A, const EmuOperand &B, int P, d
   }
   bool first = true;
   for (int L = P; L >= 2; L--) {
-    int pairs = 0;
-    for (int i = 1; i <= A.S; i++)
-      if (L - i >= 1 && L - i <= B.S) pairs++;
-    if (pairs == 0) continue;
-    if (pairs > MAX_LEVEL_PAIRS) {
-      set_error("emu_gemm: %d digit pairs in one level (at most %d)", pairs, MAX_LEVEL_PAIRS);
-      return GFCC_ERR_ARG;
-    }
-    const int nzl = level_splits(nk, pairs);
-    bool first_pair = true;
+    const int which = L <= Lhi ? 0 : 1;
+    const int shift = which == 0 ? 6 * (Lhi - L) : 6 * (P - L);
+    int in_group = 0;
     for (int i = 1; i <= A.S; i++) {
       const int j = L - i;
       if (j < 1 || j > B.S) continue;
       GFCC_TRY(gemm_bf16_tn(st, A.dig + (long long)(i - 1) * plA, A.ld, B.dig + (long long)(j - 1) * plB, B.ld, part,
-                            N, (int)M, (int)N, (int)K, 1.0f, first_pair ? 0.0f : 1.0f, nzl, M * N));
-      first_pair = false;
+                            N, (int)M, (int)N, (int)K, 1.0f, in_group == 0 ? 0.0f : 1.0f, nz, M * N));
+      in_group++;
+      // last pair of the level or a full group: fold the partials into the integer accumulators
+      bool last = true;
+      for (int i2 = i + 1; i2 <= A.S; i2++)
+        if (L - i2 >= 1 && L - i2 <= B.S) last = false;
+      if (in_group == group || last) {
+        combine_int_kernel<<<grid1d(M * N), 256, 0, st>>>(part, umma_splits((int)K, nz), M * N, shift, which, acc,
+                                                           first ? 1 : 0);
+        GFCC_LAUNCH_CHECK();
+        first = false;
+        in_group = 0;
+      }
     }
-    const int which = L <= Lhi ? 0 : 1;
-    const int shift = which == 0 ? 6 * (Lhi - L) : 6 * (P - L);
-    combine_int_kernel<<<grid1d(M * N), 256, 0, st>>>(part, umma_splits((int)K, nzl), M * N, shift, which, acc,
-                                                       first ? 1 : 0);
-    GFCC_LAUNCH_CHECK();
-    first = false;
   }
   if (first) GFCC_CUDA(cudaMemsetAsync(acc, 0, sizeof(long long) * 2 * M * N, st));
   finalize_kernel<<<grid1d(M * N), 256, 0, st>>>(acc, M, N, A.exp2, B.exp2, Lhi, P, alpha, beta, C, cm, cn, n0);

@@ -203,3 +203,24 @@ def test_fp64_batches_with_a_short_last_batch():
         assert code == gfcc.OK
         out.append(G)
     assert rel_err(out[0], out[1]) <= 1e-9
+
+
+def test_cuda_graph_replay_gives_the_same_result():
+    # the Arnoldi steps of the inner solves replayed from CUDA graphs run the same kernels
+    o, v, L = 10, 50, 100
+    pr = make_problem(o, v, L, seed=6)
+    om = np.array([-0.9, -0.45, -0.3])
+    orbs = np.array([o - 2, o - 1, o, o + 1], dtype=np.int32)
+    out = []
+    for graphs in (0, 1):
+        g = gfcc.GFCC(pr, sectors="IP", precision="mixed")
+        g.set_option(gfcc.OPT_GRAPHS, graphs)
+        g.set_option(gfcc.OPT_BATCH, 4)
+        l0 = gfcc.launch_count()
+        G, code = g.solve(om, 0.005, orbs, 1e-10)
+        out.append((G, gfcc.launch_count() - l0))
+        g.close()
+        assert code == gfcc.OK
+    assert rel_err(out[1][0], out[0][0]) <= 1e-12
+    # every replayed kernel is counted
+    assert abs(out[1][1] - out[0][1]) <= 0.02 * out[0][1]
