@@ -15,6 +15,14 @@ int gemm_bf16_tn(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const _
                  long long split_stride = 0);
 // number of partial sums gemm_bf16_tn writes for a requested split of K
 int umma_splits(int K, int nsplit);
+// FP64-accurate product from digit planes with all digit pairs of a tile in one kernel (levels in
+// TMEM): C(m, n0 + n) = alpha 2^(eA[m] + eB[n]) sum_{i+j<=P} 64^-(i+j) A_i B_j^T + beta C(m, n0 + n).
+// A planes: Adig + i * plA (M x K, row stride ld), B planes: Bdig + j * plB (N x K).  With K longer
+// than 2048 the product is split over K and `work` holds emu_fused_work_bytes of FP64 partials.
+int emu_gemm_fused(cudaStream_t st, const __nv_bfloat16 *Adig, long long plA, int SA, const int *eA,
+                   const __nv_bfloat16 *Bdig, long long plB, int SB, const int *eB, long long ld, int M, int N, int K,
+                   int P, double alpha, double beta, double *C, IMap cm, IMap cn, long long n0, double *work);
+long long emu_fused_work_bytes(long long M, long long N, long long K);
 // Tile autotuning (on by default): the first call of each GEMM shape with beta == 0 times the
 // 64 / 128 / 256-column tiles and every later call of the shape uses the fastest.
 void umma_set_autotune(bool on);

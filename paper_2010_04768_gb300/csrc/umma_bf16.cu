@@ -34,9 +34,11 @@ namespace {
 constexpr int BM = 128, BK = 64, THREADS = 128;
 // BN (the N extent of a tile and of the TMEM accumulator) is a template parameter: 256 for wide
 // operands, 128 / 64 when the contraction has few columns (a tile wider than N wastes MMA work).
-template <int BN>
+// ST: pipeline stages (0: the default for BN).  Contractions with only a K block or two per CTA use
+// 2 stages, so that several CTAs fit an SM and the per-CTA set-up overlaps.
+template <int BN, int ST = 0>
 struct Tile {
-  static constexpr int STAGES = BN == 256 ? 4 : 6;
+  static constexpr int STAGES = ST > 0 ? ST : (BN == 256 ? 4 : 6);
   static constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
 };
@@ -146,12 +148,13 @@ __device__ __forceinline__ void tmem_ld_32(unsigned taddr, float (&v)[32]) {
   for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
 }
 
-template <int BN>
+template <int BN, int ST>
 __global__ void __launch_bounds__(THREADS, 1)
     umma_bf16_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, float *D,
                           long long ldd, int M, int N, int K, float alpha, float beta, int kb_per_split,
                           long long split_stride) {
-  constexpr int STAGES = Tile<BN>::STAGES, A_BYTES = Tile<BN>::A_BYTES, STAGE_BYTES = Tile<BN>::STAGE_BYTES;
+  constexpr int STAGES = Tile<BN, ST>::STAGES, A_BYTES = Tile<BN, ST>::A_BYTES,
+                STAGE_BYTES = Tile<BN, ST>::STAGE_BYTES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + STAGES * STAGE_BYTES);
@@ -275,6 +278,183 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// FP64-accurate product from digit planes with every digit pair of a tile in one CTA:
+//   C = alpha 2^(eA[m] + eB[n]) sum_L 2^(-6L) sum_{i+j=L, L<=P} A_i B_j^T + beta C.
+// The accumulator of each level L = i + j lives in its own 64-column block of TMEM (8 levels fill
+// the 512 columns).  A stage holds the tile of one A plane i and the tiles of the B planes
+// j = 1 .. min(SB, P - i), so every level of pair (i, j) is fed from the same stage.  A level
+// accumulates at most 8 pairs x 32 K blocks x 64 = 2^14 products of magnitude <= 2^10, so its FP32
+// sums are exact integers; the epilogue adds the levels in FP64 (smallest weight first) and writes
+// the FP64 result (or, with a K split, an FP64 partial per split).
+constexpr int EMU_BN = 64, EMU_STAGES = 2, EMU_MAXS = 8;
+constexpr int EMU_A_BYTES = BM * BK * 2, EMU_B_BYTES = EMU_BN * BK * 2;
+constexpr int EMU_STAGE_BYTES = EMU_A_BYTES + EMU_MAXS * EMU_B_BYTES;
+constexpr int EMU_SMEM_BYTES = EMU_STAGES * EMU_STAGE_BYTES + 1024 + 256;
+
+struct EmuMaps {
+  CUtensorMap a[EMU_MAXS];
+  CUtensorMap b[EMU_MAXS];
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+    umma_emu_kernel(const __grid_constant__ EmuMaps maps, int SA, int SB, int P, int M, int N, int K,
+                    int kb_per_split, const int *eA, const int *eB, double alpha, double beta, double *C, IMap cm,
+                    IMap cn, long long n0g, double *part) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + EMU_STAGES * EMU_STAGE_BYTES);
+  unsigned long long *full = bars, *empty = bars + EMU_STAGES, *done = bars + 2 * EMU_STAGES;
+  unsigned *tmem_slot = reinterpret_cast<unsigned *>(bars + 2 * EMU_STAGES + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  volatile int *issued = reinterpret_cast<volatile int *>(tmem_slot + 2);
+  volatile int *consumed = reinterpret_cast<volatile int *>(tmem_slot + 3);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * EMU_BN;
+  const int nk_all = (K + BK - 1) / BK;
+  const int kb0 = blockIdx.z * kb_per_split;
+  const int kb1 = min(nk_all, kb0 + kb_per_split);
+  const int nk = kb1 - kb0;
+  const int SAe = min(SA, P - 1);            // A planes with at least one partner
+  const int iters = nk * SAe;                // stages: (K block, A plane)
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < EMU_STAGES; s++) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(done), 1);
+    *abort_flag = 0;
+    *issued = 0;
+    *consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {   // TMEM: 8 level accumulators of 64 FP32 columns x 128 lanes
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer: stage t = (K block t / SAe, A plane t % SAe + 1)
+    for (int t = 0; t < iters; t++) {
+      const int s = t % EMU_STAGES;
+      const unsigned ph = (t / EMU_STAGES) & 1;
+      if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag)) break;
+      const int kb = kb0 + t / SAe, i = t % SAe + 1;
+      const int nb = min(SB, P - i);
+      unsigned char *sa = smem + s * EMU_STAGE_BYTES;
+      mbar_expect_tx(smem_u32(&full[s]), EMU_A_BYTES + nb * EMU_B_BYTES);
+      tma_load_2d(smem_u32(sa), &maps.a[i - 1], smem_u32(&full[s]), kb * BK, m0);
+      for (int j = 1; j <= nb; j++)
+        tma_load_2d(smem_u32(sa + EMU_A_BYTES + (j - 1) * EMU_B_BYTES), &maps.b[j - 1], smem_u32(&full[s]), kb * BK,
+                    n0);
+      *issued = t + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    const unsigned idesc = idesc_bf16(BM, EMU_BN);
+    unsigned started = 0;   // bit L: level L has received its first product
+    bool ok = true;
+    for (int t = 0; t < iters && ok; t++) {
+      const int s = t % EMU_STAGES;
+      const unsigned ph = (t / EMU_STAGES) & 1;
+      if (!mbar_wait(smem_u32(&full[s]), ph, abort_flag)) {
+        ok = false;
+        break;
+      }
+      *consumed = t + 1;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int i = t % SAe + 1;
+      const int nb = min(SB, P - i);
+      const unsigned sa = smem_u32(smem + s * EMU_STAGE_BYTES);
+      for (int j = 1; j <= nb; j++) {
+        const int L = i + j;
+        const unsigned acc_col = tmem + (unsigned)((L - 2) * EMU_BN);
+        const unsigned sb = sa + EMU_A_BYTES + (j - 1) * EMU_B_BYTES;
+#pragma unroll
+        for (int k = 0; k < BK / 16; k++) {
+          const unsigned acc = ((started >> L) & 1u) || k > 0 ? 1u : 0u;
+          umma_bf16(acc_col, smem_desc(sa + 32 * k), smem_desc(sb + 32 * k), idesc, acc);
+        }
+        started |= 1u << L;
+      }
+      umma_commit(smem_u32(&empty[s]));
+    }
+    umma_commit(smem_u32(done));
+  }
+  __syncwarp();
+
+  // ---------------- epilogue: all 4 warps, one row per thread
+  const bool ready = mbar_wait(smem_u32(done), 0, abort_flag);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (__all_sync(0xffffffffu, ready && !*abort_flag) && nk > 0) {
+    const int row = m0 + warp * 32 + lane;
+    const int ea = row < M ? eA[row] : 0;
+#pragma unroll 1
+    for (int c0 = 0; c0 < EMU_BN; c0 += 32) {
+      double acc[32];
+#pragma unroll
+      for (int q = 0; q < 32; q++) acc[q] = 0.0;
+#pragma unroll 1
+      for (int L = P; L >= 2; L--) {
+        // a level receives products when some pair i + j = L exists
+        const int ilo = max(1, L - SB), ihi = min(SAe, L - 1);
+        if (ilo > ihi) continue;
+        float v[32];
+        tmem_ld_32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)((L - 2) * EMU_BN + c0), v);
+        const double w = ldexp(1.0, -6 * L);
+#pragma unroll
+        for (int q = 0; q < 32; q++) acc[q] += (double)v[q] * w;
+      }
+      if (row < M) {
+        const int ncols = min(32, N - (n0 + c0));
+        if (part != nullptr) {
+          double *dst = part + ((long long)blockIdx.z * M + row) * N + n0 + c0;
+          for (int q = 0; q < ncols; q++) dst[q] = acc[q];
+        } else {
+          const long long ro = imap_apply(cm, row);
+          for (int q = 0; q < ncols; q++) {
+            const int col = n0 + c0 + q;
+            const long long off = ro + imap_apply(cn, n0g + col);
+            const double val = alpha * ldexp(acc[q], ea + eB[col]);
+            C[off] = beta != 0.0 ? val + beta * C[off] : val;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) {
+    volatile int never = 0;
+    for (int t = *consumed; t < *issued; t++) mbar_wait(smem_u32(&full[t % EMU_STAGES]), (t / EMU_STAGES) & 1, &never);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+// C = alpha 2^(eA + eB) sum_z part[z] + beta C (the K splits of umma_emu_kernel)
+__global__ void emu_split_reduce_kernel(const double *part, int nz, int M, int N, const int *eA, const int *eB,
+                                        double alpha, double beta, double *C, IMap cm, IMap cn, long long n0g) {
+  const long long tot = (long long)M * N;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(t / N), n = (int)(t - (long long)m * N);
+    double s = 0.0;
+    for (int z = 0; z < nz; z++) s += part[(long long)z * tot + t];
+    const long long off = imap_apply(cm, m) + imap_apply(cn, n0g + n);
+    const double val = alpha * ldexp(s, eA[m] + eB[n]);
+    C[off] = beta != 0.0 ? val + beta * C[off] : val;
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (fn == nullptr) {
@@ -343,28 +523,40 @@ bool g_autotune = true;
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, int> g_tune;
 
-template <int BN>
-int launch_umma(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const __nv_bfloat16 *B, long long ldb,
-                float *D, long long ldd, int M, int N, int K, float alpha, float beta, int nsplit, int kbs,
-                long long split_stride) {
+template <int BN, int ST>
+int launch_umma_st(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const __nv_bfloat16 *B, long long ldb,
+                   float *D, long long ldd, int M, int N, int K, float alpha, float beta, int nsplit, int kbs,
+                   long long split_stride) {
   CUtensorMap ma, mb;
   GFCC_TRY(make_map(&ma, A, M, K, lda, BM));
   GFCC_TRY(make_map(&mb, B, N, K, ldb, BN));
-  static bool attr = false;
-  if (!attr) {
-    GFCC_CUDA(cudaFuncSetAttribute(umma_bf16_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   Tile<BN>::SMEM_BYTES));
-    attr = true;
+  static bool attr[64] = {false};
+  int dev = 0;
+  GFCC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64 || !attr[dev]) {
+    GFCC_CUDA(cudaFuncSetAttribute(umma_bf16_gemm_kernel<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   Tile<BN, ST>::SMEM_BYTES));
+    if (dev >= 0 && dev < 64) attr[dev] = true;
   }
   if ((N + BN - 1) / BN > 65535 || nsplit > 65535) {
     set_error("gemm_bf16_tn: grid too large (N=%d, nsplit=%d)", N, nsplit);
     return GFCC_ERR_ARG;
   }
   dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, nsplit);
-  umma_bf16_gemm_kernel<BN><<<grid, THREADS, Tile<BN>::SMEM_BYTES, st>>>(ma, mb, D, ldd, M, N, K, alpha, beta, kbs,
+  umma_bf16_gemm_kernel<BN, ST><<<grid, THREADS, Tile<BN, ST>::SMEM_BYTES, st>>>(ma, mb, D, ldd, M, N, K, alpha, beta, kbs,
                                                                          split_stride);
   GFCC_LAUNCH_CHECK();
   return GFCC_OK;
+}
+
+// few K blocks per CTA: two stages
+template <int BN>
+int launch_umma(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const __nv_bfloat16 *B, long long ldb,
+                float *D, long long ldd, int M, int N, int K, float alpha, float beta, int nsplit, int kbs,
+                long long split_stride) {
+  if (kbs <= 2)
+    return launch_umma_st<BN, 2>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
+  return launch_umma_st<BN, 0>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
 }
 }  // namespace
 
@@ -441,6 +633,58 @@ int gemm_bf16_tn(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const _
     bn = best;
   }
   return run(bn);
+}
+
+int emu_fused_splits(long long K) {
+  const int nk = (int)((K + BK - 1) / BK);
+  return (nk + 31) / 32;
+}
+
+long long emu_fused_work_bytes(long long M, long long N, long long K) {
+  const int nz = emu_fused_splits(K);
+  return nz > 1 ? (long long)nz * M * N * 8 + 256 : 0;
+}
+
+int emu_gemm_fused(cudaStream_t st, const __nv_bfloat16 *Adig, long long plA, int SA, const int *eA,
+                   const __nv_bfloat16 *Bdig, long long plB, int SB, const int *eB, long long ld, int M, int N, int K,
+                   int P, double alpha, double beta, double *C, IMap cm, IMap cn, long long n0, double *work) {
+  if (M <= 0 || N <= 0) return GFCC_OK;
+  if (SA < 1 || SB < 1 || SA > EMU_MAXS || SB > EMU_MAXS || P < 2 || P > 9 || K <= 0 || (ld % 8) ||
+      (reinterpret_cast<uintptr_t>(Adig) & 15) || (reinterpret_cast<uintptr_t>(Bdig) & 15) || (plA % 8) ||
+      (plB % 8)) {
+    set_error("emu_gemm_fused: unsupported digits (SA=%d SB=%d P=%d) or alignment", SA, SB, P);
+    return GFCC_ERR_ARG;
+  }
+  EmuMaps maps;
+  for (int i = 0; i < SA; i++) GFCC_TRY(make_map(&maps.a[i], Adig + (long long)i * plA, M, K, ld, BM));
+  for (int j = 0; j < SB; j++) GFCC_TRY(make_map(&maps.b[j], Bdig + (long long)j * plB, N, K, ld, EMU_BN));
+  for (int i = SA; i < EMU_MAXS; i++) maps.a[i] = maps.a[0];
+  for (int j = SB; j < EMU_MAXS; j++) maps.b[j] = maps.b[0];
+  static bool attr[64] = {false};
+  int dev = 0;
+  GFCC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64 || !attr[dev]) {
+    GFCC_CUDA(cudaFuncSetAttribute(umma_emu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, EMU_SMEM_BYTES));
+    if (dev >= 0 && dev < 64) attr[dev] = true;
+  }
+  const int nz = emu_fused_splits(K);
+  double *part = nz > 1 ? work : nullptr;
+  if (nz > 1) GFCC_TRY(check_extent_bytes(work, emu_fused_work_bytes(M, N, K), "fused digit GEMM partials"));
+  GFCC_TRY(check_extent(C, 0, imap_max(cm, M) + imap_max(cn, n0 + N), "fused digit GEMM output"));
+  dim3 grid((M + BM - 1) / BM, (N + EMU_BN - 1) / EMU_BN, nz);
+  if (grid.y > 65535 || grid.z > 65535) {
+    set_error("emu_gemm_fused: grid too large");
+    return GFCC_ERR_ARG;
+  }
+  umma_emu_kernel<<<grid, THREADS, EMU_SMEM_BYTES, st>>>(maps, SA, SB, P, M, N, K, 32, eA, eB, alpha, beta, C, cm, cn,
+                                                          n0, part);
+  GFCC_LAUNCH_CHECK();
+  if (nz > 1) {
+    emu_split_reduce_kernel<<<grid1d((long long)M * N), 256, 0, st>>>(part, nz, M, N, eA, eB, alpha, beta, C, cm, cn,
+                                                                       n0);
+    GFCC_LAUNCH_CHECK();
+  }
+  return GFCC_OK;
 }
 
 void umma_set_autotune(bool on) { g_autotune = on; }

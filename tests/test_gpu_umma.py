@@ -46,7 +46,10 @@ def test_umma_integer_products_are_exact():
     assert np.array_equal(D.astype(np.int64), ref)
 
 
-@pytest.mark.parametrize("M,N,K", [(200, 300, 700), (128, 256, 20000), (1, 5, 8)])
+# N <= 512: all digit pairs of a tile in one kernel (with a K split for K > 2048); wider: one GEMM
+# per digit pair
+@pytest.mark.parametrize("M,N,K", [(200, 300, 700), (128, 256, 20000), (1, 5, 8), (300, 80, 40), (100, 700, 300),
+                                   (130, 600, 5000)])
 def test_f64_emulation_accuracy(M, N, K):
     rng = np.random.default_rng(M + N + K)
     A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-3, 3, size=(M, 1)))
