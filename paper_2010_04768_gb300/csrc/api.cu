@@ -807,6 +807,8 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
         // inner correction for the live slots (done and empty slots have R = 0)
         for (int s = 0; s < ns; s++)
           if (task[s] < 0) h_done[s] = 1;
+        // the batch size only stays put while tasks remain (the drain compacts it)
+        gm.graphs_ok = next < ntasks;
         GFCC_TRY(gm.refine_correct(h_done.data(), h_state.data(), sl_it.data()));
         // drain: no task left to refill with, so move the live slots to the front and shrink the batch
         if (next >= ntasks) {

@@ -761,7 +761,8 @@ int Gmres::solve_t(double tol, int max_iters, int *h_state, int max_cycles, bool
   // CUDA graphs for the inner solves of the refinement (FP32 Krylov vectors) on a created stream,
   // not while profiling (the phase timers are stream events); the contraction shapes of the current
   // number of systems must have been seen (and tuned) before a capture
-  const bool use_graphs = sizeof(T) == sizeof(float) && mixed && c->use_graphs && !c->prof && st != nullptr;
+  const bool use_graphs =
+      sizeof(T) == sizeof(float) && mixed && c->use_graphs && graphs_ok && !c->prof && st != nullptr;
   if (use_graphs) {
     if (gnsys != nsys) {
       drop_graphs();

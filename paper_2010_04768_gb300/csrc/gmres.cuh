@@ -23,6 +23,7 @@ struct Gmres {
   int nsys = 0, m = 30, NV = 32, nch = 1;
   double eta = 0.0;
   double tol_outer = 0.0;  // continuous refinement: the outer (FP64) tolerance
+  bool graphs_ok = true;   // the caller expects the batch size to stay (captured graphs pay off)
   bool use_precond = false;
   bool mixed = false;      // inner operator on the BF16 tensor cores (IP), FP64 residuals outside
   bool f32 = false;        // Krylov vectors V, U, B, W in FP32 (inner solves of the refinement)
