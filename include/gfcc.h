@@ -74,6 +74,9 @@ extern "C" {
 #define GFCC_OPT_GUESS      11    /* GFCC_GUESS_*: initial iterate of each GMRES solve; default ZERO     */
 #define GFCC_OPT_KEEP_SOLUTIONS 12 /* 1: keep the converged solutions of the last sector solved after
                                      gfcc_solve (for gfcc_mlp_collect); default 0                        */
+#define GFCC_OPT_EMU_FUSED_N 16   /* FP64-accurate products with at most this many columns run all digit
+                                     pairs of a tile in one kernel (levels in TMEM); wider ones one GEMM
+                                     per digit pair.  Process-wide; default 512                          */
 #define GFCC_OPT_GRAPHS     15    /* 1 (default): the Arnoldi steps of the inner solves of the mixed
                                      refinement are captured once per batch size into CUDA graphs and
                                      replayed (not while profiling, not on the legacy default stream)    */

@@ -1056,6 +1056,10 @@ int gfcc_set_option(gfcc_ctx *c, int key, double value) {
       if (iv != 0 && iv != 1) break;
       umma_set_autotune(iv == 1);
       return GFCC_OK;
+    case GFCC_OPT_EMU_FUSED_N:
+      if (iv < 0) break;
+      emu_set_fused_max_n(iv);
+      return GFCC_OK;
     case GFCC_OPT_GRAPHS:
       if (iv != 0 && iv != 1) break;
       c->use_graphs = iv;

@@ -24,6 +24,10 @@
 
 namespace gfcc {
 
+// products with at most this many columns take the fused kernel (all digit pairs of a tile in one
+// CTA, levels in TMEM); wider ones keep one GEMM per digit pair (256-column tiles)
+long long g_fused_max_n = 512;
+
 namespace {
 
 constexpr int KCHUNK_BLOCKS = (1 << 14) / 64;   // K blocks (of 64) per exact partial sum
@@ -138,9 +142,7 @@ long long emu_gemm_work_bytes(long long M, long long N, long long K) {
   return std::max(nz * M * N * 4 + M * N * 16 + 512, emu_fused_work_bytes(M, N, K));
 }
 
-// products with at most this many columns take the fused kernel (all digit pairs of a tile in one
-// CTA, levels in TMEM); wider ones are compute-bound and keep one GEMM per digit pair
-constexpr long long FUSED_MAX_N = 512;
+void emu_set_fused_max_n(long long n) { g_fused_max_n = n; }
 
 int emu_gemm(cudaStream_t st, const EmuOperand &A, const EmuOperand &B, int P, double alpha, double beta, double *C,
              IMap cm, IMap cn, void *work, long long n0) {
@@ -150,7 +152,7 @@ int emu_gemm(cudaStream_t st, const EmuOperand &A, const EmuOperand &B, int P, d
     set_error("emu_gemm: operands disagree in K (%lld vs %lld)", A.K, B.K);
     return GFCC_ERR_ARG;
   }
-  if (N <= FUSED_MAX_N && A.S <= 8 && B.S <= 8 && P <= 9 && M <= (1LL << 31) - 1)
+  if (N <= g_fused_max_n && A.S <= 8 && B.S <= 8 && P <= 9 && M <= (1LL << 31) - 1)
     return emu_gemm_fused(st, A.dig, A.rows * A.ld, A.S, A.exp2, B.dig, B.rows * B.ld, B.S, B.exp2, A.ld, (int)M,
                           (int)N, (int)K, P, alpha, beta, C, cm, cn, n0, static_cast<double *>(work));
   const long long nk = (K + 63) / 64;

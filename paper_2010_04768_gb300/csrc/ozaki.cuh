@@ -19,6 +19,7 @@ long long emu_operand_bytes(long long rows, long long K, int S);
 int emu_slice(cudaStream_t st, const double *A, long long rows, long long K, long long lda, int S, void *mem,
               EmuOperand &out);
 long long emu_gemm_work_bytes(long long M, long long N, long long K);
+void emu_set_fused_max_n(long long n);   // widest product (columns) for the fused digit kernel
 // C(m, n) = alpha * sum_k A[m][k] B[n][k] + beta * C(m, n) with digit pairs i + j <= P
 // (the output column index of B's row n is n0 + n)
 int emu_gemm(cudaStream_t st, const EmuOperand &A, const EmuOperand &B, int P, double alpha, double beta, double *C,

@@ -32,6 +32,7 @@ namespace gfcc {
 namespace {
 
 constexpr int BM = 128, BK = 64, THREADS = 128;
+constexpr int RASTER_GM = 16;   // row tiles per rasterisation group
 // BN (the N extent of a tile and of the TMEM accumulator) is a template parameter: 256 for wide
 // operands, 128 / 64 when the contraction has few columns (a tile wider than N wastes MMA work).
 // ST: pipeline stages (0: the default for BN).  Contractions with only a K block or two per CTA use
@@ -165,7 +166,19 @@ __global__ void __launch_bounds__(THREADS, 1)
   volatile int *consumed = reinterpret_cast<volatile int *>(tmem_slot + 3);   // stages the MMA warp waited for
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  // tile order: groups of RASTER_GM row tiles sweep all column tiles, row tile fastest, so the CTAs
+  // in flight share a few A row panels and B column panels (L2 reuse on long-K products)
+  int m_tile, n_tile;
+  {
+    const int nM = gridDim.x, nN = gridDim.y;
+    const int id = blockIdx.y * nM + blockIdx.x;
+    const int first_m = (id / (RASTER_GM * nN)) * RASTER_GM;
+    const int gm = min(nM - first_m, RASTER_GM);
+    const int r = id - first_m * nN;
+    m_tile = first_m + r % gm;
+    n_tile = r / gm;
+  }
+  const int m0 = m_tile * BM, n0 = n_tile * BN;
   // split-K: this CTA covers K blocks [kb0, kb1) and writes its partial sum to D + z * split_stride
   const int nk_all = (K + BK - 1) / BK;
   const int kb0 = blockIdx.z * kb_per_split;

@@ -23,7 +23,7 @@ PREC_FP64, PREC_MIXED_BF16, PREC_FP64_EMULATED = 0, 1, 2
 PRECOND_NONE, PRECOND_DIAG = 0, 1
 OPT_SECTOR, OPT_PRECISION, OPT_RESTART, OPT_MAX_ITERS, OPT_PRECOND, OPT_BATCH, OPT_INNER_TOL = 1, 2, 3, 4, 5, 6, 7
 OPT_RESIDUAL, OPT_INNER_CYCLES, OPT_EMU_LEVEL = 8, 9, 10
-OPT_GUESS, OPT_KEEP_SOLUTIONS, OPT_INNER_KRYLOV, OPT_AUTOTUNE, OPT_GRAPHS = 11, 12, 13, 14, 15
+OPT_GUESS, OPT_KEEP_SOLUTIONS, OPT_INNER_KRYLOV, OPT_AUTOTUNE, OPT_GRAPHS, OPT_EMU_FUSED_N = 11, 12, 13, 14, 15, 16
 GUESS_ZERO, GUESS_LEARNED, GUESS_MINRES = 0, 1, 2
 MLP_FP32, MLP_FP64 = 0, 1
 MLP_FEATURES, MLP_OUTPUTS = 27, 16
