@@ -449,9 +449,8 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         e2e_dt, e2e_cols = float(tmax[0]), int(t[1])
 
-    # roofline of the dominant kernel: the FP64 (DFMA) or BF16 (tcgen05) ring contraction or the
-    # Arnoldi orthogonalisation,
-    # whichever took more device time inside the timed region
+    # roofline of the dominant kernel: the FP64 (DFMA) or BF16 (tcgen05) ring or EA vvvv contraction,
+    # or the Arnoldi orthogonalisation, whichever took the most device time inside the timed region
     peaks = measured_peaks()
     rf = {}
     for ph, bound, peak, unit, kernel in (
@@ -459,14 +458,18 @@ def main():
             ("ring_bf16", "tensor", peaks.get("bf16_tflops_sustained", 1727.1), "TFLOP/s",
              "umma_bf16_gemm_kernel (BF16 ring contraction)"),
             ("ring_emu", "tensor", peaks.get("bf16_tflops_sustained", 1727.1), "TFLOP/s",
-             "umma_bf16_gemm_kernel (digit-pair products of the FP64-accurate residual ring contraction)")):
+             "umma_bf16_gemm_kernel (digit-pair products of the FP64-accurate residual ring contraction)"),
+            ("vvvv",) + (("alu", FP64_PEAK_TFLOPS, "TFLOP/s", "contract_f64_kernel (FP64 EA vvvv contraction)")
+                         if spec["precision"] == "fp64" else
+                         ("tensor", peaks.get("bf16_tflops_sustained", 1727.1), "TFLOP/s",
+                          "umma_bf16_gemm_kernel (BF16 EA vvvv contraction)"))):
         ms, n_l, fl = prof[ph]
         if ms > 0:
             ach = fl / (ms / 1e3) / 1e12
             rf[ph] = {"bound": bound, "kernel": kernel, "achieved": ach, "peak": peak, "unit": unit,
                       "frac": ach / peak, "traffic": None, "launches": n_l, "ms_total": ms,
                       "peak_note": ("FP64 FMA units: 152 SMs x 2 DFMA/clk x 2070 MHz (derived); cuBLAS DGEMM "
-                                    "measured 1.10 TFLOP/s on this pool") if ph == "ring" else
+                                    "measured 1.10 TFLOP/s on this pool") if bound == "alu" else
                                    "bf16_tflops_sustained of measured (kernel timed inside a long step); the "
                                    "achieved figure counts the tensor-core work of the launches (all digit "
                                    "pairs for the residual)"}

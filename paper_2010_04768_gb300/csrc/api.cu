@@ -1280,7 +1280,7 @@ int gfcc_sigma_ex(gfcc_ctx *c, int sector, int precision, int n_vec, const doubl
   }
   if (n_vec == 0) return GFCC_OK;
   const long long n = sector == GFCC_SECTOR_IP ? c->dim_ip : c->dim_ea;
-  const long long ew = emu ? sigma_emu_work_doubles(c, std::min(n_vec, 16)) : 0;
+  const long long ew = emu ? sigma_emu_work_doubles(c, std::min(n_vec, EMU_SUB_MAX)) : 0;
   const long long work = sigma_work_doubles(c, sector, n_vec) + 4LL * n_vec * n +
                          (mixed ? sigma_mixed_work_doubles(c, n_vec) : 0) + ew;
   GFCC_TRY(grow_scratch(c, sizeof(double) * work));

@@ -548,7 +548,8 @@ long long gmres_work_doubles(const gfcc_ctx *c, int sector, long long n, int nsy
   if (mixed) {
     w += 3 * 2LL * nsys * n + nsys + 64;     // X, R, B0, ||b0||
     w += sigma_mixed_work_doubles(c, nsys);
-    if (c->eWr.dig != nullptr || c->eWre.dig != nullptr) w += sigma_emu_work_doubles(c, std::min(nsys, 16));
+    if (c->eWr.dig != nullptr || c->eWre.dig != nullptr)
+      w += sigma_emu_work_doubles(c, std::min(nsys, EMU_SUB_MAX));
   }
   return w;
 }
@@ -624,7 +625,7 @@ int Gmres::op_fp64(const double *x, long long ldx, double *yout, long long ldy) 
     b.dsign = ip ? 1.0 : -1.0;
     b.zsign = ip ? -1.0 : 1.0;
     double *ew = sigma_work + sigma_work_doubles(c, sector, nsys) + sigma_mixed_work_doubles(c, nsys);
-    const long long ewd = sigma_emu_work_doubles(c, std::min(nsys, 16));
+    const long long ewd = sigma_emu_work_doubles(c, std::min(nsys, EMU_SUB_MAX));
     return ip ? apply_ip_emu(c, b, ew, ewd) : apply_ea_emu(c, b, ew, ewd);
   }
   SysBatch b;

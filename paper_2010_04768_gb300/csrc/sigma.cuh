@@ -35,7 +35,10 @@ int apply_ip(gfcc_ctx *c, const SysBatch &b, double *work);
 int launch_epilogue_ip(gfcc_ctx *c, const SysBatch &b, const double *S1, const double *T, const double *Q,
                        const double *U);
 // FP64-accurate IP operator from digit planes on the BF16 tensor cores (sigma_emu.cu); processes
-// the systems in sub-batches that fit its workspace
+// the systems in sub-batches that fit its workspace.  The solvers size that workspace for up to
+// EMU_SUB_MAX systems: each sub-batch re-reads the operator's digit planes, so fewer and wider
+// sub-batches cost less (about 0.3 GB per system at o=40 v=200 EA, 0.9 GB at o=90 v=450 IP)
+constexpr int EMU_SUB_MAX = 64;
 long long sigma_emu_work_doubles(const gfcc_ctx *c, int nsub);
 int apply_ip_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_doubles);
 int apply_ea(gfcc_ctx *c, const SysBatch &b, double *work);
