@@ -86,6 +86,11 @@ extern "C" {
 #define GFCC_OPT_INNER_KRYLOV 13  /* mixed precision: precision of the Krylov vectors of the inner GMRES
                                      solves, 32 (default) or 64 bits; the refinement residual and the
                                      solution stay FP64                                                  */
+#define GFCC_OPT_INCREMENTAL 17   /* mixed precision, FP64-accurate residuals: 1 (default) after the first
+                                     refinement step the residual is updated as r -= A d with the step's
+                                     correction d, its product taking only the digit levels that the
+                                     ratio max|d| / max|x| leaves significant (at most the error of the
+                                     full product A x); 0: every residual is b - A x at the full level */
 
 /* Initial guesses (Algorithm 1, "compute initial guess").  With a guess other than ZERO, gfcc_solve
  * keeps every converged solution X_p(omega) (FP32 complex, n_omega * n_orb * dim * 8 bytes of device
@@ -274,6 +279,12 @@ int gfcc_guess_stats(gfcc_ctx *ctx, int *count, int *kind, double *pred, double 
  * FP64-accurate residuals evaluated for the system (refinement steps + 1; 0 for FP64 sectors).
  * `count` as in gfcc_last_stats. */
 int gfcc_refine_stats(gfcc_ctx *ctx, int *count, int *outer);
+
+/* gfcc_residual_stats - mixed precision: FP64-accurate residual products of the last gfcc_solve (one
+ * per batch evaluation): `full` of b - A x at the context's digit level, `incremental` of r -= A d,
+ * and the mean digit level of the incremental ones (0 when there were none).  Any pointer may be
+ * NULL.  Errors: GFCC_ERR_ARG for a NULL ctx. */
+int gfcc_residual_stats(gfcc_ctx *ctx, long long *full, long long *incremental, double *mean_level);
 
 /*
  * The learned-guess model: a 3-layer perceptron with ReLU activations,

@@ -614,6 +614,7 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
   c->st_guess_pred.assign(ntasks * nsec, 1.0);
   c->st_relres0.assign(ntasks * nsec, 1.0);
   c->st_outer.assign(ntasks * nsec, 0);
+  c->res_full = c->res_inc = c->res_inc_levels = 0;
   GFCC_CUDA(cudaMemsetAsync(d_G, 0, sizeof(double) * 2 * n_omega * n_orb * n_orb, st));
   int sec_slot = 0;
   bool all_ok = true;
@@ -1056,6 +1057,10 @@ int gfcc_set_option(gfcc_ctx *c, int key, double value) {
       if (iv != 0 && iv != 1) break;
       umma_set_autotune(iv == 1);
       return GFCC_OK;
+    case GFCC_OPT_INCREMENTAL:
+      if (iv != 0 && iv != 1) break;
+      c->incremental = iv;
+      return GFCC_OK;
     case GFCC_OPT_EMU_FUSED_N:
       if (iv < 0) break;
       emu_set_fused_max_n(iv);
@@ -1248,6 +1253,17 @@ int gfcc_refine_stats(gfcc_ctx *c, int *count, int *outer) {
   const int nout = std::min(*count, total);
   for (int i = 0; i < nout && outer; i++) outer[i] = c->st_outer[i];
   *count = total;
+  return GFCC_OK;
+}
+
+int gfcc_residual_stats(gfcc_ctx *c, long long *full, long long *incremental, double *mean_level) {
+  if (c == nullptr) {
+    set_error("gfcc_residual_stats: ctx is NULL");
+    return GFCC_ERR_ARG;
+  }
+  if (full) *full = c->res_full;
+  if (incremental) *incremental = c->res_inc;
+  if (mean_level) *mean_level = c->res_inc > 0 ? (double)c->res_inc_levels / (double)c->res_inc : 0.0;
   return GFCC_OK;
 }
 

@@ -92,6 +92,8 @@ struct gfcc_ctx {
   gfcc::EmuOperand eWr, eWq, eW1, eV3, eT3, eU1;
   int emu_S = 8, emu_P = 9;
   int residual_emulated = 1;   // 0: refinement residuals with the FP64 (DFMA) sigma
+  int incremental = 1;         // 1: r -= A d at the digit level the correction needs (after the first step)
+  long long res_full = 0, res_inc = 0, res_inc_levels = 0;   // residual products of the last solve
 
   // EA sigma operands
   double *Wr_ea = nullptr;   // [(i,b)][(m,e)]  Wovvo[m,b,e,i] + d_mi Fvv[b,e] - 1/2 d_be Foo[m,i]

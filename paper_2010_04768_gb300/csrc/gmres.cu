@@ -14,6 +14,8 @@
 // reaches tol ||b|| (or on breakdown), and every cycle ends with the true
 // residual b - A x recomputed by the operator.
 #include <algorithm>
+#include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "ctx.cuh"
@@ -173,23 +175,34 @@ __global__ void vupdate_kernel(const T *V, long long vs_stride, long long vi_str
   }
 }
 
-// w_s *= 1 / scale[s] (real scale stored as the real part of a complex entry scale[s*NV + idx])
+// w_s *= 1 / scale[s] (real scale stored as the real part of a complex entry scale[s*NV + idx]).
+// Grid (cdiv(2n, VSCALE_PER_BLOCK), nsys): the factor is formed once per thread; each thread scales
+// VSCALE_UNROLL reals with independent loads.
+constexpr int VSCALE_UNROLL = 4, VSCALE_PER_BLOCK = 256 * VSCALE_UNROLL;
 template <typename T>
-__global__ void vscale_kernel(T *w, long long ws_stride, long long n, int nsys, const double *nrm2, int NV,
-                              int idx, const int *state, int want) {
-  const long long tot = n * nsys;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(t / n);
-    const long long mu = t - (long long)s * n;
-    if (state != nullptr && state[s] != want) continue;
-    const double nn = nrm2[2 * ((long long)s * NV + idx)];
-    if (!(nn > 0.0)) continue;
-    const T inv = (T)(1.0 / sqrt(nn));
-    CT<T> x = ldc(w + 2 * s * ws_stride, mu);
-    x.x *= inv;
-    x.y *= inv;
-    stc(w + 2 * s * ws_stride, mu, x);
+__global__ void vscale_kernel(T *w, long long ws_stride, long long n, const double *nrm2, int NV, int idx,
+                              const int *state, int want) {
+  const int s = blockIdx.y;
+  if (state != nullptr && state[s] != want) return;
+  const double nn = nrm2[2 * ((long long)s * NV + idx)];
+  if (!(nn > 0.0)) return;
+  const T inv = (T)(1.0 / sqrt(nn));
+  T *ws = w + 2 * s * ws_stride;
+  const long long n2 = 2 * n, t0 = (long long)blockIdx.x * VSCALE_PER_BLOCK + threadIdx.x;
+  T x[VSCALE_UNROLL];
+#pragma unroll
+  for (int u = 0; u < VSCALE_UNROLL; u++) {
+    const long long t = t0 + (long long)u * blockDim.x;
+    x[u] = t < n2 ? ws[t] : (T)0;
   }
+#pragma unroll
+  for (int u = 0; u < VSCALE_UNROLL; u++) {
+    const long long t = t0 + (long long)u * blockDim.x;
+    if (t < n2) ws[t] = x[u] * inv;
+  }
+}
+static inline dim3 vscale_grid(long long n, int nsys) {
+  return dim3((unsigned)std::max<long long>(1, (2 * n + VSCALE_PER_BLOCK - 1) / VSCALE_PER_BLOCK), (unsigned)nsys);
 }
 
 // r_s = b_s - w_s for systems that are not finished
@@ -546,7 +559,7 @@ long long gmres_work_doubles(const gfcc_ctx *c, int sector, long long n, int nsy
   w += 8LL * nsys + 512;                    // bnorm, relres, relres0, est, omega, int state/kcyc/iters, alignment
   w += sigma_work_doubles(c, sector, nsys);
   if (mixed) {
-    w += 3 * 2LL * nsys * n + nsys + 64;     // X, R, B0, ||b0||
+    w += 5 * 2LL * nsys * n + nsys + 64;     // X, R, B0, D, A D, ||b0||
     w += sigma_mixed_work_doubles(c, nsys);
     if (c->eWr.dig != nullptr || c->eWre.dig != nullptr)
       w += sigma_emu_work_doubles(c, std::min(nsys, EMU_SUB_MAX));
@@ -599,6 +612,8 @@ int Gmres::init(gfcc_ctx *ctx, int sec, long long dim, int ns, int mm, double *w
     take(X, 2LL * nsys * n);
     take(R, 2LL * nsys * n);
     take(B0, 2LL * nsys * n);
+    take(D, 2LL * nsys * n);
+    take(Yd, 2LL * nsys * n);
     take(b0norm, nsys);
   }
   sigma_work = p;
@@ -611,7 +626,7 @@ int Gmres::init(gfcc_ctx *ctx, int sec, long long dim, int ns, int mm, double *w
   return GFCC_OK;
 }
 
-int Gmres::op_fp64(const double *x, long long ldx, double *yout, long long ldy) {
+int Gmres::op_fp64(const double *x, long long ldx, double *yout, long long ldy, int level) {
   const bool ip = sector == GFCC_SECTOR_IP;
   if (mixed && c->residual_emulated && (ip ? c->eWr.dig : c->eWre.dig) != nullptr) {
     SysBatch b;
@@ -626,7 +641,7 @@ int Gmres::op_fp64(const double *x, long long ldx, double *yout, long long ldy) 
     b.zsign = ip ? -1.0 : 1.0;
     double *ew = sigma_work + sigma_work_doubles(c, sector, nsys) + sigma_mixed_work_doubles(c, nsys);
     const long long ewd = sigma_emu_work_doubles(c, std::min(nsys, EMU_SUB_MAX));
-    return ip ? apply_ip_emu(c, b, ew, ewd) : apply_ea_emu(c, b, ew, ewd);
+    return ip ? apply_ip_emu(c, b, ew, ewd, level) : apply_ea_emu(c, b, ew, ewd, level);
   }
   SysBatch b;
   b.nsys = nsys;
@@ -730,7 +745,7 @@ int Gmres::cgs2_t(const T *Vb, long long vs, int nv, T *w, cudaStream_t st) {
   reorth_merge_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, nv, h, h2, nrm, nrm + 2 * NV * (long long)nsys, NV, state,
                                                      ST_IN_CYCLE, flag);
   GFCC_LAUNCH_CHECK();
-  vscale_kernel<T><<<grid1d(n * nsys), TH, 0, st>>>(w, vs, n, nsys, h, NV, nv, state, ST_IN_CYCLE);
+  vscale_kernel<T><<<vscale_grid(n, nsys), 256, 0, st>>>(w, vs, n, h, NV, nv, state, ST_IN_CYCLE);
   GFCC_LAUNCH_CHECK();
   return GFCC_OK;
 }
@@ -807,7 +822,7 @@ int Gmres::solve_t(double tol, int max_iters, int *h_state, int max_cycles, bool
     cycle_start_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, nrm, NV, bnorm, tol, max_iters, m + 1, state, iters,
                                                       relres, g, H);
     GFCC_LAUNCH_CHECK();
-    vscale_kernel<T><<<grid1d(n * nsys), TH, 0, st>>>(Vt, vs, n, nsys, nrm, NV, 0, state, ST_IN_CYCLE);
+    vscale_kernel<T><<<vscale_grid(n, nsys), 256, 0, st>>>(Vt, vs, n, nrm, NV, 0, state, ST_IN_CYCLE);
     GFCC_LAUNCH_CHECK();
     if (cycle == 0) GFCC_CUDA(cudaMemcpyAsync(relres0, relres, sizeof(double) * nsys, cudaMemcpyDeviceToDevice, st));
     first = false;
@@ -913,6 +928,32 @@ __global__ void to_f32_kernel(const double *x, float *y, long long tot) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
     y[t] = (float)x[t];
 }
+// D = d (FP64 copy of the inner correction) and x += d (all systems)
+template <typename T>
+__global__ void add_keep_kernel(double *x, double *D, const T *d, long long tot) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const double v = (double)d[t];
+    D[t] = v;
+    x[t] += v;
+  }
+}
+// y -= a (all systems)
+__global__ void sub_kernel(double *y, const double *a, long long tot) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
+    y[t] -= a[t];
+}
+// amax[s] = max |v_s| over both planes of system s ([s][n] complex); grid (blocks, nsys), amax
+// zeroed by the caller.  Non-negative doubles order like their bit patterns, so the maximum is
+// an integer atomicMax.
+__global__ void absmax_kernel(const double *v, long long n, unsigned long long *amax) {
+  const int s = blockIdx.y;
+  const double *vs = v + 2 * (long long)s * n;
+  double m = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 2 * n; t += (long long)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(vs[t]));
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(&amax[s], (unsigned long long)__double_as_longlong(m));
+}
 // per system: relres = ||r|| / ||b0||; done systems get r = 0 so that the inner solve leaves them alone
 __global__ void refine_check_kernel(int nsys, const double *nrm2, int NV, const double *b0norm, double tol, int *done,
                                     double *relres) {
@@ -961,13 +1002,12 @@ int Gmres::compact_slots(const int *d_perm, int na) {
     set_error("internal: compact_slots(%d) with %d slots", na, nsys);
     return GFCC_ERR_ARG;
   }
-  // R (free between refinement steps) is the staging buffer
-  gather_rows_kernel<<<grid1d(n * na), 256, 0, st>>>(X, R, n, na, d_perm);
-  GFCC_LAUNCH_CHECK();
-  GFCC_CUDA(cudaMemcpyAsync(X, R, sizeof(double) * 2 * na * n, cudaMemcpyDeviceToDevice, st));
-  gather_rows_kernel<<<grid1d(n * na), 256, 0, st>>>(B0, R, n, na, d_perm);
-  GFCC_LAUNCH_CHECK();
-  GFCC_CUDA(cudaMemcpyAsync(B0, R, sizeof(double) * 2 * na * n, cudaMemcpyDeviceToDevice, st));
+  // Yd (free between refinement steps) is the staging buffer
+  for (double *a : {X, B0, R, D}) {
+    gather_rows_kernel<<<grid1d(n * na), 256, 0, st>>>(a, Yd, n, na, d_perm);
+    GFCC_LAUNCH_CHECK();
+    GFCC_CUDA(cudaMemcpyAsync(a, Yd, sizeof(double) * 2 * na * n, cudaMemcpyDeviceToDevice, st));
+  }
   nsys = na;
   return GFCC_OK;
 }
@@ -988,9 +1028,51 @@ int Gmres::reset_slots(const int *d_mask) {
 int Gmres::refine_residual(int *h_done, double *h_relres) {
   cudaStream_t st = c->stream;
   const long long tot = 2LL * nsys * n;
+  const bool emu = c->residual_emulated && (sector == GFCC_SECTOR_IP ? c->eWr.dig : c->eWre.dig) != nullptr;
+  if (c->incremental && have_d && emu) {
+    // R = B0 - A (X - D) already; R -= A D.  The digit-plane product of D at level P - k has the
+    // error bound of the level-P product of X when 2^(6k) <= max|X| / max|D| (the planes of a
+    // vector are sliced relative to its own largest entry), so k comes from the worst live slot.
+    have_d = false;
+    unsigned long long *am = reinterpret_cast<unsigned long long *>(partial);
+    GFCC_CUDA(cudaMemsetAsync(am, 0, sizeof(unsigned long long) * 2 * nsys, st));
+    const dim3 gr((unsigned)std::min<long long>(64, std::max<long long>(1, (2 * n + 2047) / 2048)), (unsigned)nsys);
+    absmax_kernel<<<gr, 256, 0, st>>>(X, n, am);
+    GFCC_LAUNCH_CHECK();
+    absmax_kernel<<<gr, 256, 0, st>>>(D, n, am + nsys);
+    GFCC_LAUNCH_CHECK();
+    std::vector<unsigned long long> h(2 * (size_t)nsys);
+    GFCC_CUDA(cudaMemcpyAsync(h.data(), am, sizeof(unsigned long long) * 2 * nsys, cudaMemcpyDeviceToHost, st));
+    GFCC_CUDA(cudaStreamSynchronize(st));
+    int drop = 1 << 20;
+    bool any = false;
+    for (int s = 0; s < nsys; s++) {
+      double dx, dd;
+      std::memcpy(&dx, &h[s], sizeof(double));
+      std::memcpy(&dd, &h[nsys + s], sizeof(double));
+      if (!(dd > 0.0)) continue;   // no correction in this slot (done or empty)
+      any = true;
+      int ex = 0, ed = 0;
+      std::frexp(dx, &ex);
+      std::frexp(dd, &ed);
+      const int gap = ex - ed - 1;   // log2(max|X| / max|D|) >= gap
+      drop = std::min(drop, gap > 0 ? gap / 6 : 0);
+    }
+    if (any) {
+      const int level = std::max(2, c->emu_P - drop);
+      GFCC_TRY(op_fp64(D, n, Yd, n, level));
+      sub_kernel<<<grid1d(tot), 256, 0, st>>>(R, Yd, tot);
+      GFCC_LAUNCH_CHECK();
+      c->res_inc++;
+      c->res_inc_levels += level;
+    }
+    return refine_residual_free(h_done, h_relres);
+  }
+  have_d = false;
   GFCC_TRY(op_fp64(X, n, R, n));
   rsub_kernel<<<grid1d(tot), 256, 0, st>>>(B0, R, tot);
   GFCC_LAUNCH_CHECK();
+  c->res_full++;
   return refine_residual_free(h_done, h_relres);
 }
 
@@ -1022,10 +1104,11 @@ int Gmres::refine_correct(const int *h_done, int *h_state, int *h_iters) {
   std::vector<int> it(nsys);
   GFCC_CUDA(cudaMemcpyAsync(it.data(), iters, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
   if (f32)
-    add_kernel<float><<<grid1d(tot), 256, 0, st>>>(X, reinterpret_cast<const float *>(U), tot);
+    add_keep_kernel<float><<<grid1d(tot), 256, 0, st>>>(X, D, reinterpret_cast<const float *>(U), tot);
   else
-    add_kernel<double><<<grid1d(tot), 256, 0, st>>>(X, U, tot);
+    add_keep_kernel<double><<<grid1d(tot), 256, 0, st>>>(X, D, U, tot);
   GFCC_LAUNCH_CHECK();
+  have_d = true;
   GFCC_CUDA(cudaStreamSynchronize(st));
   for (int s = 0; s < nsys; s++) h_iters[s] += it[s];
   return GFCC_OK;
@@ -1054,6 +1137,7 @@ int Gmres::solve_refined(double tol, double inner_tol, int max_iters, int *h_sta
       GFCC_CUDA(cudaMemcpyAsync(R, B0, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
     } else {
       GFCC_TRY(op_fp64(X, n, R, n));
+      c->res_full++;
       rsub_kernel<<<grid1d(tot), TH, 0, st>>>(B0, R, tot);
       GFCC_LAUNCH_CHECK();
     }

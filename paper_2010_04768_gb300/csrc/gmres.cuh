@@ -28,6 +28,8 @@ struct Gmres {
   bool mixed = false;      // inner operator on the BF16 tensor cores (IP), FP64 residuals outside
   bool f32 = false;        // Krylov vectors V, U, B, W in FP32 (inner solves of the refinement)
   double *X = nullptr, *R = nullptr, *B0 = nullptr;   // refinement: solution, residual, original rhs
+  double *D = nullptr, *Yd = nullptr;   // refinement: the last correction (FP64) and A D
+  bool have_d = false;                  // D holds the correction of the last refine_correct
   double *b0norm = nullptr;
   double *V = nullptr, *U = nullptr, *B = nullptr, *W = nullptr;
   double *partial = nullptr, *h = nullptr, *h2 = nullptr, *y = nullptr, *nrm = nullptr;
@@ -41,7 +43,8 @@ struct Gmres {
   // where the caller puts the FP64 right-hand sides ([s][n] complex) and finds the solutions
   double *rhs() const { return mixed ? B0 : B; }
   double *solution() const { return mixed ? X : U; }
-  int op_fp64(const double *x, long long ldx, double *y, long long ldy);     // FP64, no preconditioner
+  // FP64 or FP64-accurate (digit planes; level > 0 caps the digit level), no preconditioner
+  int op_fp64(const double *x, long long ldx, double *y, long long ldy, int level = 0);
   int mdot(const double *Vb, long long vs, long long vi, int nv, const double *w, long long ws, double *out, int want,
            int accumulate);
   // max_cycles > 0 bounds the number of restart cycles (systems left pending end in state 4).
@@ -57,17 +60,19 @@ struct Gmres {
 
   // Pieces of solve_refined for continuous batching (slots refilled with new systems as others
   // finish).  refine_norms: ||b0|| of every slot.  refine_residual: R = B0 - A X (FP64-accurate),
-  // relres = ||R|| / ||b0||, per-slot done flags (device kcyc: 1 = converged) copied to h_done.
-  // refine_correct: for the slots with h_done[s] == 0, one inner solve A d = R (BF16 operator)
-  // and X += d; the inner iterations of each slot are added to h_iters.
+  // or, after a correction with the incremental option, R -= A D with the digit level that
+  // max|D| / max|X| allows; relres = ||R|| / ||b0||, per-slot done flags (device kcyc: 1 =
+  // converged) copied to h_done.  refine_correct: for the slots with h_done[s] == 0, one inner
+  // solve A d = R (BF16 operator), D = d and X += d; the inner iterations of each slot are added
+  // to h_iters.
   int refine_norms();
   int refine_residual(int *h_done, double *h_relres);
   int refine_residual_free(int *h_done, double *h_relres);   // the checks on R as it is (no operator)
   int refine_correct(const int *h_done, int *h_state, int *h_iters);
   // X[s] = 0 and R[s] = B0[s] for the slots with mask[s] != 0 (device mask)
   int reset_slots(const int *d_mask);
-  // keep slots perm[0..na) (device, increasing) as slots 0..na-1 (X and B0 move; R is clobbered and
-  // must be recomputed) and continue with nsys = na
+  // keep slots perm[0..na) (device, increasing) as slots 0..na-1 (X, B0, R and D move) and continue
+  // with nsys = na
   int compact_slots(const int *d_perm, int na);
 
  private:

@@ -40,12 +40,13 @@ int launch_epilogue_ip(gfcc_ctx *c, const SysBatch &b, const double *S1, const d
 // sub-batches cost less (about 0.3 GB per system at o=40 v=200 EA, 0.9 GB at o=90 v=450 IP)
 constexpr int EMU_SUB_MAX = 64;
 long long sigma_emu_work_doubles(const gfcc_ctx *c, int nsub);
-int apply_ip_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_doubles);
+// level > 0: digit pairs i + j <= min(level, the context's level) only (products of small corrections)
+int apply_ip_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_doubles, int level = 0);
 int apply_ea(gfcc_ctx *c, const SysBatch &b, double *work);
 // mixed precision (EA): BF16 tensor-core couplings + FP64 diagonal and shift (sigma_mixed.cu)
 int apply_ea_mixed(gfcc_ctx *c, const SysBatch &b, double *work);
 // FP64-accurate EA operator from digit planes (sigma_emu.cu)
-int apply_ea_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_doubles);
+int apply_ea_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_doubles, int level = 0);
 // the FP64 epilogue of the EA operator on given S1 / T / Qp / U (FP64, layouts of sigma.cu)
 int launch_epilogue_ea(gfcc_ctx *c, const SysBatch &b, const double *S1, const double *T, const double *Qp,
                        const double *U);

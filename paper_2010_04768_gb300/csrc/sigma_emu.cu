@@ -328,7 +328,7 @@ long long sigma_emu_work_doubles(const gfcc_ctx *c, int nsub) {
   return b / 8 + 64;
 }
 
-int apply_ip_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_doubles) {
+int apply_ip_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_doubles, int level) {
   if (c->eWr.dig == nullptr) {
     set_error("FP64-emulated residual requested but its digit planes were not built");
     return GFCC_ERR_STATE;
@@ -342,7 +342,7 @@ int apply_ip_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_do
     set_error("apply_ip_emu: workspace too small for one system");
     return GFCC_ERR_OOM;
   }
-  const int S = c->emu_S, P = c->emu_P;
+  const int S = c->emu_S, P = level > 0 ? std::min(level, c->emu_P) : c->emu_P;
   PhaseTimer tsig(c, PH_SIGMA, b.nsys * sigma_flops(c, GFCC_SECTOR_IP));
   for (int s0 = 0; s0 < b.nsys; s0 += nsub) {
     const int ns = std::min(nsub, b.nsys - s0);
@@ -395,7 +395,7 @@ int apply_ip_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_do
 }
 
 
-int apply_ea_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_doubles) {
+int apply_ea_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_doubles, int level) {
   if (c->eWre.dig == nullptr) {
     set_error("FP64-emulated EA residual requested but its digit planes were not built");
     return GFCC_ERR_STATE;
@@ -408,7 +408,7 @@ int apply_ea_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_do
     set_error("apply_ea_emu: workspace too small for one system");
     return GFCC_ERR_OOM;
   }
-  const int S = c->emu_S, P = c->emu_P;
+  const int S = c->emu_S, P = level > 0 ? std::min(level, c->emu_P) : c->emu_P;
   PhaseTimer tsig(c, PH_SIGMA, b.nsys * sigma_flops(c, GFCC_SECTOR_EA));
   for (int s0 = 0; s0 < b.nsys; s0 += nsub) {
     const int ns = std::min(nsub, b.nsys - s0);

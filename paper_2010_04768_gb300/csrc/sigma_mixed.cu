@@ -129,6 +129,63 @@ __global__ void unpack_k_tiled_kernel(SysBatch b, int o, int v, long long ldk, _
   }
 }
 
+// All three 2h1p layouts in one pass.  One block per (e tile, m, system s): the tile r2[m, j, e]
+// of system s for every j (each packed element is read by the blocks of its two occupied indices;
+// the right preconditioner is applied once per read), then
+//   ring   r2b[(j, c)][(m, e)]  rows of the tile's e range,
+//   oooo   r2o[(e, c)][(m, j)]  rows of o consecutive columns,
+//   long K rk[c][(m, e, j)]     one contiguous run of (e range) x o columns,
+// for both planes c = 2 s + re/im.  Quotients by o come from a 32.32 fixed-point reciprocal
+// (exact while the dividend stays below 2^32 / o; here below 2 UNPACK_ET o).
+constexpr int UNPACK_ET = 32;   // e values per block (a power of two)
+constexpr int UNPACK_MAX_O = 180;   // tile o x (UNPACK_ET + 1) float2 within the default 48 KB
+
+__device__ __forceinline__ int quo(unsigned q, unsigned long long rcp) {
+  return (int)(((unsigned long long)q * rcp) >> 32);
+}
+
+__global__ __launch_bounds__(256) void unpack_ip_kernel(SysBatch b, int o, int v, unsigned long long rcp_o,
+                                                        long long ld_ov, long long ld_o2, long long ld_k1,
+                                                        __nv_bfloat16 *r2b, __nv_bfloat16 *r2o, __nv_bfloat16 *rk) {
+  extern __shared__ float2 tl[];   // [o][UNPACK_ET + 1]
+  constexpr int LD = UNPACK_ET + 1;
+  const int e0 = blockIdx.x * UNPACK_ET, m = blockIdx.y, s = blockIdx.z;
+  const int et = min(UNPACK_ET, v - e0);
+  const int C2 = 2 * b.nsys;
+  for (int t = threadIdx.x; t < o * UNPACK_ET; t += blockDim.x) {
+    const int j = t / UNPACK_ET, el = t % UNPACK_ET;
+    float2 val = make_float2(0.f, 0.f);
+    if (el < et) {
+      const Cz u = r2_at(b, o, v, s, m, j, e0 + el);
+      val = make_float2(u.r, u.i);
+    }
+    tl[j * LD + el] = val;
+  }
+  __syncthreads();
+  // ring: rows (j, 2 s + p), columns m v + e0 .. m v + e0 + et
+  for (int t = threadIdx.x; t < 2 * o * UNPACK_ET; t += blockDim.x) {
+    const int el = t % UNPACK_ET, jp = t / UNPACK_ET, p = jp & 1, j = jp >> 1;
+    if (el >= et) continue;
+    const float2 u = tl[j * LD + el];
+    r2b[((long long)j * C2 + 2 * s + p) * ld_ov + (long long)m * v + e0 + el] = __float2bfloat16(p ? u.y : u.x);
+  }
+  // oooo: rows (e, 2 s + p), columns m o + j
+  for (int t = threadIdx.x; t < 2 * et * o; t += blockDim.x) {
+    const int ep = quo((unsigned)t, rcp_o), j = t - ep * o, p = ep & 1, el = ep >> 1;
+    const float2 u = tl[j * LD + el];
+    r2o[((long long)(e0 + el) * C2 + 2 * s + p) * ld_o2 + (long long)m * o + j] = __float2bfloat16(p ? u.y : u.x);
+  }
+  // long K: row 2 s + p, columns (m v + e) o + j for the tile's e range
+  for (int p = 0; p < 2; p++) {
+    __nv_bfloat16 *dst = rk + (long long)(2 * s + p) * ld_k1 + ((long long)m * v + e0) * o;
+    for (int t = threadIdx.x; t < et * o; t += blockDim.x) {
+      const int el = quo((unsigned)t, rcp_o), j = t - el * o;
+      const float2 u = tl[j * LD + el];
+      dst[t] = __float2bfloat16(p ? u.y : u.x);
+    }
+  }
+}
+
 // rk[c][o2v + m] = r1[m] and r1b[c][m] = r1[m]
 __global__ void unpack_r1_kernel(SysBatch b, int o, int v, long long ldk, __nv_bfloat16 *rk, long long ld1,
                                  __nv_bfloat16 *r1b) {
@@ -302,14 +359,22 @@ int apply_ip_mixed(gfcc_ctx *c, const SysBatch &b, double *work) {
   PhaseTimer tsig(c, PH_SIGMA, b.nsys * sigma_flops(c, GFCC_SECTOR_IP));
   {
   PhaseTimer tu(c, PH_UNPACK);
-  unpack_ring_kernel<<<grid1d(o * C2 * ov), 256, 0, st>>>(b, (int)o, (int)v, c->ld_ov, w.r2b);
-  GFCC_LAUNCH_CHECK();
-  unpack_oooo_kernel<<<dim3(cdiv(oo, 32), cdiv(v, 32), C2), dim3(32, 8), 0, st>>>(b, (int)o, (int)v, c->ld_o2,
-                                                                                   w.r2o);
-  GFCC_LAUNCH_CHECK();
-  unpack_k_tiled_kernel<<<dim3(cdiv(o, 32), cdiv(v, 32), o * C2), dim3(32, 8), 0, st>>>(b, (int)o, (int)v, c->ld_k1,
-                                                                                        w.rk);
-  GFCC_LAUNCH_CHECK();
+  if (v > 0 && o <= UNPACK_MAX_O) {
+    const unsigned long long rcp_o = ((1ULL << 32) + (unsigned long long)o - 1) / (unsigned long long)o;
+    const size_t sm = (size_t)o * (UNPACK_ET + 1) * sizeof(float2);
+    unpack_ip_kernel<<<dim3(cdiv(v, UNPACK_ET), (unsigned)o, (unsigned)b.nsys), 256, sm, st>>>(
+        b, (int)o, (int)v, rcp_o, c->ld_ov, c->ld_o2, c->ld_k1, w.r2b, w.r2o, w.rk);
+    GFCC_LAUNCH_CHECK();
+  } else {
+    unpack_ring_kernel<<<grid1d(o * C2 * ov), 256, 0, st>>>(b, (int)o, (int)v, c->ld_ov, w.r2b);
+    GFCC_LAUNCH_CHECK();
+    unpack_oooo_kernel<<<dim3(cdiv(oo, 32), cdiv(v, 32), C2), dim3(32, 8), 0, st>>>(b, (int)o, (int)v, c->ld_o2,
+                                                                                     w.r2o);
+    GFCC_LAUNCH_CHECK();
+    unpack_k_tiled_kernel<<<dim3(cdiv(o, 32), cdiv(v, 32), o * C2), dim3(32, 8), 0, st>>>(b, (int)o, (int)v,
+                                                                                          c->ld_k1, w.rk);
+    GFCC_LAUNCH_CHECK();
+  }
   unpack_r1_kernel<<<cdiv(C2 * o, 128), 128, 0, st>>>(b, (int)o, (int)v, c->ld_k1, w.rk, c->ld_o, w.r1b);
   GFCC_LAUNCH_CHECK();
   }

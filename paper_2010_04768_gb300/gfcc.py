@@ -24,6 +24,7 @@ PRECOND_NONE, PRECOND_DIAG = 0, 1
 OPT_SECTOR, OPT_PRECISION, OPT_RESTART, OPT_MAX_ITERS, OPT_PRECOND, OPT_BATCH, OPT_INNER_TOL = 1, 2, 3, 4, 5, 6, 7
 OPT_RESIDUAL, OPT_INNER_CYCLES, OPT_EMU_LEVEL = 8, 9, 10
 OPT_GUESS, OPT_KEEP_SOLUTIONS, OPT_INNER_KRYLOV, OPT_AUTOTUNE, OPT_GRAPHS, OPT_EMU_FUSED_N = 11, 12, 13, 14, 15, 16
+OPT_INCREMENTAL = 17
 GUESS_ZERO, GUESS_LEARNED, GUESS_MINRES = 0, 1, 2
 MLP_FP32, MLP_FP64 = 0, 1
 MLP_FEATURES, MLP_OUTPUTS = 27, 16
@@ -87,6 +88,7 @@ def load():
     lib.gfcc_guess_stats.argtypes = [P, ip, ip, dp, dp]
     lib.gfcc_set_guess_model.argtypes = [P, P]
     lib.gfcc_refine_stats.argtypes = [P, ip, ip]
+    lib.gfcc_residual_stats.argtypes = [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), dp]
     lib.gfcc_solve_batch.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(_Request), ip]
     ull = ctypes.c_ulonglong
     lib.gfcc_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.POINTER(P)]
@@ -108,7 +110,8 @@ def load():
     lib.gfcc_last_error.restype = ctypes.c_char_p
     for name in ("gfcc_create", "gfcc_create_ex", "gfcc_set_option", "gfcc_set_stream", "gfcc_solve",
                  "gfcc_solve_device", "gfcc_last_stats", "gfcc_sigma", "gfcc_dims", "gfcc_profile",
-                 "gfcc_profile_read", "gfcc_guess_stats", "gfcc_set_guess_model", "gfcc_refine_stats", "gfcc_solve_batch", "gfcc_mlp_create",
+                 "gfcc_profile_read", "gfcc_guess_stats", "gfcc_set_guess_model", "gfcc_refine_stats",
+                 "gfcc_residual_stats", "gfcc_solve_batch", "gfcc_mlp_create",
                  "gfcc_mlp_get_params", "gfcc_mlp_set_params", "gfcc_mlp_forward", "gfcc_mlp_loss_grad",
                  "gfcc_mlp_train_batch", "gfcc_mlp_collect", "gfcc_mlp_train", "gfcc_mlp_eval",
                  "gfcc_mlp_get_samples"):
@@ -260,6 +263,13 @@ class GFCC:
         cnt = ctypes.c_int(out.size)
         _check(lib.gfcc_refine_stats(self._h, ctypes.byref(cnt), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
         return out
+
+    def residual_stats(self) -> tuple[int, int, float]:
+        """(full, incremental, mean digit level of the incremental) FP64-accurate residual products of
+        the last solve."""
+        full, inc, lvl = ctypes.c_longlong(0), ctypes.c_longlong(0), ctypes.c_double(0.0)
+        _check(load().gfcc_residual_stats(self._h, ctypes.byref(full), ctypes.byref(inc), ctypes.byref(lvl)))
+        return full.value, inc.value, lvl.value
 
     def set_guess_model(self, model: "MLP | None"):
         self._model = model   # keeps the model alive while attached

@@ -147,6 +147,37 @@ def test_mixed_matches_fp64_path_medium():
             assert np.linalg.norm(row - ref) <= 1e-6 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("sector", ["IP", "EA"])
+def test_incremental_residual_matches_full_residuals(sector):
+    # r -= A d at the digit level the correction needs gives the G of the FP64 path, like b - A x at
+    # the full level every step, and its products drop digit levels once the corrections shrink
+    o, v, L = 8, 40, 80
+    pr = make_problem(o, v, L, seed=7)
+    om = np.array([-0.9, -0.4, 0.3])
+    orbs = np.array([o - 2, o - 1, o, o + 1], dtype=np.int32)
+    g64 = gfcc.GFCC(pr, sectors=sector)
+    G64, c64 = g64.solve(om, 0.005, orbs, 1e-10)
+    g64.close()
+    g = gfcc.GFCC(pr, sectors=sector, precision="mixed")
+    g.set_option(gfcc.OPT_INCREMENTAL, 0)
+    Gf, cf = g.solve(om, 0.005, orbs, 1e-10)
+    full0, inc0, _ = g.residual_stats()
+    g.set_option(gfcc.OPT_INCREMENTAL, 1)
+    Gi, ci = g.solve(om, 0.005, orbs, 1e-10)
+    full1, inc1, level = g.residual_stats()
+    it, rr, st = g.stats()
+    g.close()
+    assert c64 == gfcc.OK and cf == gfcc.OK and ci == gfcc.OK
+    assert full0 > 0 and inc0 == 0
+    assert full1 == 0 and inc1 > 0 and 2 <= level < 9
+    assert np.all(st == 0) and np.all(rr <= 1e-10)
+    for w in range(om.size):
+        for a in range(orbs.size):
+            ref = np.linalg.norm(G64[w, a])
+            assert np.linalg.norm(Gi[w, a] - G64[w, a]) <= 1e-6 * ref
+            assert np.linalg.norm(Gf[w, a] - G64[w, a]) <= 1e-6 * ref
+
+
 @pytest.mark.parametrize("krylov", [32, 64])
 def test_inner_krylov_precision_does_not_change_the_result(krylov):
     # the inner GMRES of the refinement runs on FP32 (default) or FP64 Krylov vectors; the FP64
