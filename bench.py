@@ -61,6 +61,7 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "medium-ipea-mixed"
 FREQ_STRIDE = 17   # timed step k takes grid frequency (k * 17) mod n_omega (coprime with 64: covers the grid)
+INNER_RESTART = 60   # restart length of the inner GMRES of the mixed-precision refinement (library default)
 
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 flops x max clock
 
@@ -244,7 +245,8 @@ def config_of(spec, wl, world):
     return {"workload": f"{wl.name}: o={wl.o} v={wl.v} L={wl.L}, sector {spec['sector']}, "
                         f"{spec['per_step']} frequency x {wl.orbitals.size} orbitals per step per GPU",
             "o": wl.o, "v": wl.v, "L": wl.L, "sector": spec["sector"], "precision": spec["precision"],
-            "eta": wl.eta, "tol": wl.tol, "restart": wl.restart, "preconditioner": "diag",
+            "eta": wl.eta, "tol": wl.tol, "restart": wl.restart,
+            **({"inner_restart": INNER_RESTART} if spec["precision"] == "mixed" else {}), "preconditioner": "diag",
             "columns_per_step": spec["per_step"] * int(wl.orbitals.size) * len(sectors_of(spec)) * world,
             "parallelism": f"{world} independent GPU(s), frequencies sharded", "l2": "inputs larger than L2 "
             "(ring matrix and Krylov basis are each > 129 MB)"}
@@ -358,6 +360,7 @@ def main():
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream.cuda_stream)
     ctx.set_option(gfcc.OPT_RESTART, wl.restart)
+    ctx.set_option(gfcc.OPT_INNER_RESTART, INNER_RESTART)
     ctx.set_option(gfcc.OPT_PRECOND, gfcc.PRECOND_DIAG)
     nw = wl.omegas.size
     no = int(wl.orbitals.size)

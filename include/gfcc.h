@@ -86,6 +86,8 @@ extern "C" {
 #define GFCC_OPT_INNER_KRYLOV 13  /* mixed precision: precision of the Krylov vectors of the inner GMRES
                                      solves, 32 (default) or 64 bits; the refinement residual and the
                                      solution stay FP64                                                  */
+#define GFCC_OPT_INNER_RESTART 18 /* mixed precision: restart length of the inner GMRES solves (1..64);
+                                     default 60 (GFCC_OPT_RESTART is that of the FP64 GMRES)             */
 #define GFCC_OPT_INCREMENTAL 17   /* mixed precision, FP64-accurate residuals: 1 (default) after the first
                                      refinement step the residual is updated as r -= A d with the step's
                                      correction d, its product taking only the digit levels that the

@@ -529,8 +529,9 @@ int choose_batch(gfcc_ctx *c, int sector, long long n, long long ntasks) {
     cudaGetLastError();
     fr = 1ULL << 30;
   }
-  const double per = 8.0 * (double)(gmres_work_doubles(c, sector, n, 2, c->restart, mixed) -
-                                   gmres_work_doubles(c, sector, n, 1, c->restart, mixed));
+  const int m = mixed ? c->inner_restart : c->restart;
+  const double per = 8.0 * (double)(gmres_work_doubles(c, sector, n, 2, m, mixed) -
+                                   gmres_work_doubles(c, sector, n, 1, m, mixed));
   long long b = (long long)(0.6 * c->mem_share * (double)fr / std::max(per, 1.0));
   b = std::max<long long>(1, std::min<long long>(b, 256));
   return (int)std::min<long long>(b, ntasks);
@@ -628,7 +629,7 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
     const bool mixed = c->precision == GFCC_PREC_MIXED_BF16 && (ip ? c->Wr_bf : c->Wre_bf) != nullptr;
     if (keep) GFCC_TRY(prepare_kept(c, sector, n, n_omega, n_orb, d_om, d_orb, eta));
     const int nsys = choose_batch(c, sector, n, ntasks);
-    const int m = c->restart;
+    const int m = mixed ? c->inner_restart : c->restart;
     const long long nsplit = (n + 8191) / 8192;
     const long long gw = gmres_work_doubles(c, sector, n, nsys, m, mixed);
     // guess workspace: Gram, features, model outputs, coefficients, predictions, deltas, p/n,
@@ -1016,6 +1017,10 @@ int gfcc_set_option(gfcc_ctx *c, int key, double value) {
     case GFCC_OPT_RESTART:
       if (iv < 1 || iv > 64) break;
       c->restart = iv;
+      return GFCC_OK;
+    case GFCC_OPT_INNER_RESTART:
+      if (iv < 1 || iv > 64) break;
+      c->inner_restart = iv;
       return GFCC_OK;
     case GFCC_OPT_MAX_ITERS:
       if (iv < 1) break;

@@ -48,7 +48,8 @@ struct gfcc_ctx {
   int precision = GFCC_PREC_FP64;
 
   // options
-  int restart = 30;
+  int restart = 30;          // FP64 GMRES
+  int inner_restart = 60;    // inner GMRES of the mixed-precision refinement
   int max_iters = 1500;
   int precond = GFCC_PRECOND_DIAG;
   int batch = 0;
@@ -81,11 +82,10 @@ struct gfcc_ctx {
   // Fock-like diagonal d (diag_ip) is left out of them and applied in FP64 by the epilogue.
   __nv_bfloat16 *Wr_bf = nullptr;  // [(i,a)][(m,e)]   ring core + off-diagonal Fbar folding, ld_ov
   __nv_bfloat16 *Wq_bf = nullptr;  // [(i,j)][(m,n)]   1/2 Woooo[m,n,i,j], ld_o2
-  __nv_bfloat16 *W1_bf = nullptr;  // [(i,a,j)][m]     Wovoo[m,a,j,i], ld_o
+  __nv_bfloat16 *WT_bf = nullptr;  // [(i,a,j)][m | e] [Wovoo[m,a,j,i] | t2[i,j,a,e]] (ovoo and three-body), ld_ot
   __nv_bfloat16 *V3_bf = nullptr;  // [e][(m,f,n)]     1/2 <mn||ef>', ld_o2v
-  __nv_bfloat16 *T3_bf = nullptr;  // [(i,a,j)][e]     t2[i,j,a,e], ld_v
   __nv_bfloat16 *U1_bf = nullptr;  // [i][(m,e,n) | m] U1 and the off-diagonal -Fbar_oo of the 1h row, ld_k1
-  long long ld_ov = 0, ld_o2 = 0, ld_o = 0, ld_o2v = 0, ld_v = 0, ld_k1 = 0;
+  long long ld_ov = 0, ld_o2 = 0, ld_o = 0, ld_o2v = 0, ld_v = 0, ld_k1 = 0, ld_ot = 0;
 
   // digit planes of the FP64 IP operands for the FP64-accurate residual on the tensor cores
   // (full Fock folding, same GEMM roles as the BF16 operands; V3 padded to the K of U1x)
@@ -108,9 +108,8 @@ struct gfcc_ctx {
   // diagonal diag_ea is left out and applied in FP64)
   __nv_bfloat16 *Wre_bf = nullptr;  // [(i,b)][(m,e)]   ring core + off-diagonal Fbar folding, ld_ov
   __nv_bfloat16 *Wp_bf = nullptr;   // [(a<b)][(e<f)]   Wvvvv, ld_pv
-  __nv_bfloat16 *W3_bf = nullptr;   // [(i,b,a)][e]     Wvvvo, ld_v
+  __nv_bfloat16 *WTe_bf = nullptr;  // [(i,b,a)][e | m] [Wvvvo[a,b,e,i] | -t2[m,i,a,b]], ld_ot
   __nv_bfloat16 *V3e_bf = nullptr;  // [m][(n,f,e)]     1/2 <mn||ef>', ld_ov2
-  __nv_bfloat16 *T3e_bf = nullptr;  // [(i,b,a)][m]     -t2[m,i,a,b], ld_o
   __nv_bfloat16 *U1e_bf = nullptr;  // [a][(m,x,y) | e] U1e and the off-diagonal Fbar_vv of the 1p row, ld_k1e
   long long ld_pv = 0, ld_ov2 = 0, ld_k1e = 0;
   // digit planes of the FP64 EA operands (full Fock folding) for the FP64-accurate residual

@@ -70,31 +70,33 @@ __global__ void slice_kernel(const double *A, long long rows, long long K, long 
 // Exact integer accumulation of digit-pair products: the FP32 partial sums are integers of
 // magnitude <= 2^24, so they convert to int32 exactly; a pair of level L adds (sum_z part) shifted
 // by 6 (Lhi - L) into the high accumulator (levels <= Lsplit) or by 6 (P - L) into the low one.
-// acc[2t] = high, acc[2t + 1] = low (int64).  No FP64 arithmetic.
+// The two int64 accumulators are separate planes, acc[t] = high and acc[tot + t] = low, so that a
+// combine touches only its own; the first combine into a plane sets it.  No FP64 arithmetic.
 __global__ void combine_int_kernel(const float *part, int nz, long long tot, int shift, int which, long long *acc,
                                    int first) {
+  long long *a = acc + (which ? tot : 0);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     long long s = 0;
     for (int z = 0; z < nz; z++) s += (long long)__float2int_rn(part[(long long)z * tot + t]);
     s <<= shift;
-    if (first) {
-      acc[2 * t] = which == 0 ? s : 0;
-      acc[2 * t + 1] = which == 1 ? s : 0;
-    } else {
-      acc[2 * t + which] += s;
-    }
+    a[t] = first ? s : a[t] + s;
   }
 }
-
-// C(m, n0 + n) = alpha * 2^(eA[m] + eB[n]) (hi 64^-Lhi + lo 64^-P) + beta * C(m, n0 + n)
+// C = alpha * (high 2^(ex - 6 Lhi) + low 2^(ex - 6 P)) + beta C, ex = eA[m] + eB[n].  Grid
+// (cdiv(N, 256), rows): a block walks rows m = blockIdx.y, blockIdx.y + gridDim.y, ...
 __global__ void finalize_kernel(const long long *acc, long long M, long long N, const int *eA, const int *eB,
                                 int Lhi, int P, double alpha, double beta, double *C, IMap cm, IMap cn, long long n0) {
   const long long tot = M * N;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const long long m = t / N, n = t - m * N;
-    const long long off = imap_apply(cm, m) + imap_apply(cn, n0 + n);
-    const int ex = eA[m] + eB[n];
-    const double val = scalbn((double)acc[2 * t], ex - 6 * Lhi) + scalbn((double)acc[2 * t + 1], ex - 6 * P);
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int eb = eB[n];
+  const long long offn = imap_apply(cn, n0 + n);
+  for (long long m = blockIdx.y; m < M; m += gridDim.y) {
+    const long long t = m * N + n;
+    const int ex = eA[m] + eb;
+    double val = scalbn((double)acc[t], ex - 6 * Lhi);
+    if (P > Lhi) val += scalbn((double)acc[tot + t], ex - 6 * P);
+    const long long off = imap_apply(cm, m) + offn;
     const double v = alpha * val;
     C[off] = beta != 0.0 ? v + beta * C[off] : v;
   }
@@ -173,7 +175,7 @@ int emu_gemm(cudaStream_t st, const EmuOperand &A, const EmuOperand &B, int P, d
     set_error("emu_gemm: level %d or K %lld beyond the exact integer accumulation", P, K);
     return GFCC_ERR_ARG;
   }
-  bool first = true;
+  bool first = true, first_plane[2] = {true, true};
   for (int L = P; L >= 2; L--) {
     const int which = L <= Lhi ? 0 : 1;
     const int shift = which == 0 ? 6 * (Lhi - L) : 6 * (P - L);
@@ -190,15 +192,17 @@ int emu_gemm(cudaStream_t st, const EmuOperand &A, const EmuOperand &B, int P, d
         if (L - i2 >= 1 && L - i2 <= B.S) last = false;
       if (in_group == group || last) {
         combine_int_kernel<<<grid1d(M * N), 256, 0, st>>>(part, umma_splits((int)K, nz), M * N, shift, which, acc,
-                                                           first ? 1 : 0);
+                                                           first_plane[which] ? 1 : 0);
         GFCC_LAUNCH_CHECK();
         first = false;
+        first_plane[which] = false;
         in_group = 0;
       }
     }
   }
   if (first) GFCC_CUDA(cudaMemsetAsync(acc, 0, sizeof(long long) * 2 * M * N, st));
-  finalize_kernel<<<grid1d(M * N), 256, 0, st>>>(acc, M, N, A.exp2, B.exp2, Lhi, P, alpha, beta, C, cm, cn, n0);
+  finalize_kernel<<<dim3(cdiv(N, 256), (unsigned)std::min<long long>(M, 8192)), 256, 0, st>>>(
+      acc, M, N, A.exp2, B.exp2, Lhi, P, alpha, beta, C, cm, cn, n0);
   GFCC_LAUNCH_CHECK();
   return GFCC_OK;
 }

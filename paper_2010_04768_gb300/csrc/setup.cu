@@ -146,6 +146,17 @@ __global__ void to_bf16_kernel(const double *in, long long rows, long long cols,
   }
 }
 
+// out[r] = [bf16(in1[r][0..k1)) | bf16(in2[r][0..k2)) | 0 ...] (ld_out >= k1 + k2)
+__global__ void concat_bf16_kernel(const double *in1, long long k1, const double *in2, long long k2, long long rows,
+                                   __nv_bfloat16 *out, long long ld_out) {
+  const long long tot = rows * ld_out;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < tot; x += (long long)gridDim.x * blockDim.x) {
+    const long long r = x / ld_out, c = x - r * ld_out;
+    const double val = c < k1 ? in1[r * k1 + c] : c < k1 + k2 ? in2[r * k2 + (c - k1)] : 0.0;
+    out[x] = __double2bfloat16(val);
+  }
+}
+
 // remove the Fock-like diagonal element of the folded ring matrix: Wr[(i,a)][(i,a)] -= cvv Fvv[a][a] + coo Foo[i][i]
 __global__ void ring_undiag_kernel(double *Wr, int o, int v, const double *Foo, const double *Fvv, double cvv,
                                    double coo) {
@@ -560,12 +571,13 @@ int build_hbar(gfcc_ctx *c, const double *d_fock, const double *d_chol) {
     }
     GFCC_TRY(alloc_bf16(c, &c->Wq_bf, oo * c->ld_o2));
     GFCC_TRY(to_bf16(st, t, oo, oo, oo, 0.5, c->Wq_bf, c->ld_o2));
-    GFCC_TRY(alloc_bf16(c, &c->W1_bf, o2v * c->ld_o));
-    GFCC_TRY(to_bf16(st, c->W1, o2v, o, o, 1.0, c->W1_bf, c->ld_o));
+    // [W1 | T3]: the ovoo and three-body terms of U share one contraction over K = o + v
+    c->ld_ot = round8(o + v);
+    GFCC_TRY(alloc_bf16(c, &c->WT_bf, o2v * c->ld_ot));
+    concat_bf16_kernel<<<grid1d(o2v * c->ld_ot), 256, 0, st>>>(c->W1, o, c->T3, v, o2v, c->WT_bf, c->ld_ot);
+    GFCC_LAUNCH_CHECK();
     GFCC_TRY(alloc_bf16(c, &c->V3_bf, v * c->ld_o2v));
     GFCC_TRY(to_bf16(st, c->V3, v, o2v, o2v, 1.0, c->V3_bf, c->ld_o2v));
-    GFCC_TRY(alloc_bf16(c, &c->T3_bf, o2v * c->ld_v));
-    GFCC_TRY(to_bf16(st, c->T3, o2v, v, v, 1.0, c->T3_bf, c->ld_v));
     // U1x[i] = [U1[i][(m,e,n)] | -Foo_offdiag[m][i]]
     {
       const long long d[4] = {1, 1, o, o2v};
@@ -648,13 +660,14 @@ int build_hbar(gfcc_ctx *c, const double *d_fock, const double *d_chol) {
       GFCC_TRY(to_bf16(st, c->Wp, Pv, Pv, Pv, 1.0, c->Wp_bf, c->ld_pv));
       GFCC_TRY(slice(c->Wp, Pv, Pv, Pv, c->eWp));
     }
-    GFCC_TRY(alloc_bf16(c, &c->W3_bf, ov2 * c->ld_v));
-    GFCC_TRY(to_bf16(st, c->W3, ov2, v, v, 1.0, c->W3_bf, c->ld_v));
+    // [W3 | T3e]: one contraction over K = v + o for U
+    c->ld_ot = round8(o + v);
+    GFCC_TRY(alloc_bf16(c, &c->WTe_bf, ov2 * c->ld_ot));
+    concat_bf16_kernel<<<grid1d(ov2 * c->ld_ot), 256, 0, st>>>(c->W3, v, c->T3e, o, ov2, c->WTe_bf, c->ld_ot);
+    GFCC_LAUNCH_CHECK();
     GFCC_TRY(slice(c->W3, ov2, v, v, c->eW3));
     GFCC_TRY(alloc_bf16(c, &c->V3e_bf, o * c->ld_ov2));
     GFCC_TRY(to_bf16(st, c->V3e, o, ov2, ov2, 1.0, c->V3e_bf, c->ld_ov2));
-    GFCC_TRY(alloc_bf16(c, &c->T3e_bf, ov2 * c->ld_o));
-    GFCC_TRY(to_bf16(st, c->T3e, ov2, o, o, 1.0, c->T3e_bf, c->ld_o));
     GFCC_TRY(slice(c->T3e, ov2, o, o, c->eT3e));
     // [V3e | 0]: padded to the K of the 1p row
     {

@@ -13,9 +13,9 @@
 // Contractions (all D[m][n] = A[m][k] B[n][k], BF16 K-major, FP32 out):
 //   ring  T[(i,a)][(j,c)]  = Wr[(i,a)][(m,e)]   r2b[(j,c)][(m,e)],  r2b = r2[m,j,e]
 //   oooo  Q[(i,j)][(a,c)]  = Wq[(i,j)][(m,n)]   r2o[(a,c)][(m,n)],  r2o = r2[m,n,a]
-//   ovoo  U[(i,a,j)][c]    = W1[(i,a,j)][m]     r1b[c][m]
 //   3-body Z[e][c]         = V3[e][(m,f,n)]     rk[c][(m,f,n)]       (split K)
-//          U             += T3[(i,a,j)][e]     Zb[c][e]
+//   ovoo + 3-body
+//         U[(i,a,j)][c]    = [W1 | T3][(i,a,j)][m | e]  rz[c][m | e],  rz = [r1 | Z]
 //   1h    S1[i][c]         = U1x[i][(m,e,n)|m]  rk[c][(m,e,n)|m]     (split K)
 #include <cuda_bf16.h>
 
@@ -230,59 +230,77 @@ __device__ __forceinline__ Cz y2_at(const SysBatch &b, int v, long long Pv, int 
   return u;
 }
 
-// r2e[(a, c)][(m, e)] = y2[m, a, e] (reads along e: consecutive pairs of the packed vector)
-__global__ void unpack_ea_ring_kernel(SysBatch b, int o, int v, long long Pv, long long ld, __nv_bfloat16 *out) {
+// The ring and long-K layouts of the 2p1h block in one pass: block (e tile, a tile, (m, s)) holds the
+// 32 x 32 tile Y[a][e] = y2[m, a, e] of system s (antisymmetric: packed a < e, read along e above
+// the diagonal and along a below it, so that reads stay coalesced), then writes, for both planes,
+//   ring   r2e[(a, c)][(m, e)] =  Y[a][e]
+//   long K rk[c][(m, a, e)]     = -Y[a][e]  (= y2[m, e, a])
+// both along e.  grid (cdiv(v, 32), cdiv(v, 32), o * nsys), block (32, 8).
+__global__ void unpack_ea_tile_kernel(SysBatch b, int o, int v, long long Pv, long long ld_ov, long long ldk,
+                                      __nv_bfloat16 *r2e, __nv_bfloat16 *rk) {
+  __shared__ float2 tile[32][33];
+  const int e0 = blockIdx.x * 32, a0 = blockIdx.y * 32;
+  const int m = (int)(blockIdx.z % (unsigned)o), s = (int)(blockIdx.z / (unsigned)o);
   const int C2 = 2 * b.nsys;
-  const long long K = (long long)o * v;
-  const long long tot = (long long)v * C2 * K;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const long long k = t % K, row = t / K;
-    const int c = (int)(row % C2), a = (int)(row / C2);
-    const Cz u = y2_at(b, v, Pv, c >> 1, (int)(k / v), a, (int)(k % v));
-    out[row * ld + k] = __float2bfloat16((c & 1) ? u.i : u.r);
-  }
-}
-
-// r2p[(i, c)][(e<f)] = y2[i, e, f] (the packed 2p1h block of system s, row i)
-__global__ void unpack_ea_vvvv_kernel(SysBatch b, int o, int v, long long Pv, long long ld, __nv_bfloat16 *out) {
-  const int C2 = 2 * b.nsys;
-  const long long tot = (long long)o * C2 * Pv;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const long long ef = t % Pv, row = t / Pv;
-    const int c = (int)(row % C2), i = (int)(row / C2);
-    const Cz u = load_u(b, c >> 1, v + (long long)i * Pv + ef);
-    out[row * ld + ef] = __float2bfloat16((c & 1) ? u.i : u.r);
-  }
-}
-
-// rk[c][(m, x, y)] = y2[m, y, x] for the long-K contractions, rk[c][o v v + e] = y1[e], r1[c][e] = y1[e]
-__global__ void unpack_ea_k_kernel(SysBatch b, int o, int v, long long Pv, long long ldk, __nv_bfloat16 *rk,
-                                   long long ld1, __nv_bfloat16 *r1) {
-  const int C2 = 2 * b.nsys;
-  const long long ov2 = (long long)o * v * v;
-  const long long K = ov2 + v;
-  const long long tot = (long long)C2 * K;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const long long k = t % K;
-    const int c = (int)(t / K), s = c >> 1;
-    Cz u;
-    if (k < ov2) {
-      const int y = (int)(k % v);
-      const long long r = k / v;
-      u = y2_at(b, v, Pv, s, (int)(r / v), y, (int)(r % v));
-    } else {
-      u = load_u(b, s, k - ov2);
+  const bool below = e0 + 31 < a0;   // every a > e: packed pairs (e, a) run along a
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int a = below ? a0 + threadIdx.x : a0 + r, e = below ? e0 + r : e0 + threadIdx.x;
+    float2 val = make_float2(0.f, 0.f);
+    if (a < v && e < v) {
+      const Cz u = y2_at(b, v, Pv, s, m, a, e);
+      val = make_float2(u.r, u.i);
     }
-    const __nv_bfloat16 h = __float2bfloat16((c & 1) ? u.i : u.r);
-    rk[(long long)c * ldk + k] = h;
-    if (k >= ov2) r1[(long long)c * ld1 + (k - ov2)] = h;
+    if (below)
+      tile[threadIdx.x][r] = val;
+    else
+      tile[r][threadIdx.x] = val;
   }
+  __syncthreads();
+  const int e = e0 + threadIdx.x;
+  if (e >= v) return;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int a = a0 + r;
+    if (a >= v) break;
+    const float2 u = tile[r][threadIdx.x];
+    const long long ring = ((long long)a * C2 + 2 * s) * ld_ov + (long long)m * v + e;
+    r2e[ring] = __float2bfloat16(u.x);
+    r2e[ring + ld_ov] = __float2bfloat16(u.y);
+    const long long kk = (long long)(2 * s) * ldk + ((long long)m * v + a) * v + e;
+    rk[kk] = __float2bfloat16(-u.x);
+    rk[kk + ldk] = __float2bfloat16(-u.y);
+  }
+}
+
+// r2p[(i, c)][ef] = y2[i, e < f] (row i of the packed 2p1h block), both planes; grid
+// (cdiv(Pv, 256), o * nsys)
+__global__ void unpack_ea_pairs_kernel(SysBatch b, int o, int v, long long Pv, long long ld, __nv_bfloat16 *out) {
+  const int i = (int)(blockIdx.y % (unsigned)o), s = (int)(blockIdx.y / (unsigned)o);
+  const long long ef = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ef >= Pv) return;
+  const Cz u = load_u(b, s, v + (long long)i * Pv + ef);
+  const long long row = (long long)i * 2 * b.nsys + 2 * s;
+  out[row * ld + ef] = __float2bfloat16(u.r);
+  out[(row + 1) * ld + ef] = __float2bfloat16(u.i);
+}
+
+// rk[c][o v v + e] = y1[e] and r1[c][e] = y1[e], both planes; grid (cdiv(v, 256), nsys)
+__global__ void unpack_ea_y1_kernel(SysBatch b, int o, int v, long long ldk, __nv_bfloat16 *rk, long long ld1,
+                                    __nv_bfloat16 *r1) {
+  const int s = blockIdx.y, e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= v) return;
+  const long long ov2 = (long long)o * v * v;
+  const Cz u = load_u(b, s, e);
+  const __nv_bfloat16 hr = __float2bfloat16(u.r), hi = __float2bfloat16(u.i);
+  rk[(long long)(2 * s) * ldk + ov2 + e] = hr;
+  rk[(long long)(2 * s + 1) * ldk + ov2 + e] = hi;
+  r1[(long long)(2 * s) * ld1 + e] = hr;
+  r1[(long long)(2 * s + 1) * ld1 + e] = hi;
 }
 
 constexpr int KSPLIT = 64;   // split of the long-K contractions (Z, 1h row) into partial sums
 
 struct MixedWork {
-  __nv_bfloat16 *r2b, *r2o, *rk, *r1b, *Zb;
+  __nv_bfloat16 *r2b, *r2o, *rk, *rz;
   float *T, *Q, *U, *Zp, *S1p;
   long long bytes;
 };
@@ -299,8 +317,7 @@ MixedWork layout(const gfcc_ctx *c, int nsys, void *base) {
   w.r2b = reinterpret_cast<__nv_bfloat16 *>(take(o * C2 * c->ld_ov * 2));
   w.r2o = reinterpret_cast<__nv_bfloat16 *>(take(v * C2 * c->ld_o2 * 2));
   w.rk = reinterpret_cast<__nv_bfloat16 *>(take(C2 * c->ld_k1 * 2));
-  w.r1b = reinterpret_cast<__nv_bfloat16 *>(take(C2 * c->ld_o * 2));
-  w.Zb = reinterpret_cast<__nv_bfloat16 *>(take(C2 * c->ld_v * 2));
+  w.rz = reinterpret_cast<__nv_bfloat16 *>(take(C2 * c->ld_ot * 2));
   w.T = reinterpret_cast<float *>(take(o * v * o * C2 * 4));
   w.Q = reinterpret_cast<float *>(take(o * o * v * C2 * 4));
   w.U = reinterpret_cast<float *>(take(o * v * o * C2 * 4));
@@ -313,7 +330,7 @@ MixedWork layout(const gfcc_ctx *c, int nsys, void *base) {
 }  // namespace
 
 struct MixedWorkEA {
-  __nv_bfloat16 *r2e, *r2p, *rk, *r1, *Zb;
+  __nv_bfloat16 *r2e, *r2p, *rk, *rz;
   float *T, *Qp, *U, *Zp, *S1p;
   long long bytes;
 };
@@ -330,8 +347,7 @@ MixedWorkEA layout_ea(const gfcc_ctx *c, int nsys, void *base) {
   w.r2e = reinterpret_cast<__nv_bfloat16 *>(take(v * C2 * c->ld_ov * 2));
   w.r2p = reinterpret_cast<__nv_bfloat16 *>(take(o * C2 * c->ld_pv * 2));
   w.rk = reinterpret_cast<__nv_bfloat16 *>(take(C2 * c->ld_k1e * 2));
-  w.r1 = reinterpret_cast<__nv_bfloat16 *>(take(C2 * c->ld_v * 2));
-  w.Zb = reinterpret_cast<__nv_bfloat16 *>(take(C2 * c->ld_o * 2));
+  w.rz = reinterpret_cast<__nv_bfloat16 *>(take(C2 * c->ld_ot * 2));
   w.T = reinterpret_cast<float *>(take(o * v * v * C2 * 4));
   w.Qp = reinterpret_cast<float *>(take(std::max<long long>(Pv, 1) * o * C2 * 4));
   w.U = reinterpret_cast<float *>(take(ov2 * C2 * 4));
@@ -375,7 +391,7 @@ int apply_ip_mixed(gfcc_ctx *c, const SysBatch &b, double *work) {
                                                                                           c->ld_k1, w.rk);
     GFCC_LAUNCH_CHECK();
   }
-  unpack_r1_kernel<<<cdiv(C2 * o, 128), 128, 0, st>>>(b, (int)o, (int)v, c->ld_k1, w.rk, c->ld_o, w.r1b);
+  unpack_r1_kernel<<<cdiv(C2 * o, 128), 128, 0, st>>>(b, (int)o, (int)v, c->ld_k1, w.rk, c->ld_ot, w.rz);
   GFCC_LAUNCH_CHECK();
   }
   {
@@ -385,14 +401,14 @@ int apply_ip_mixed(gfcc_ctx *c, const SysBatch &b, double *work) {
   }
   GFCC_TRY(gemm_bf16_tn(st, c->Wq_bf, c->ld_o2, w.r2o, c->ld_o2, w.Q, v * C2, (int)oo, (int)(v * C2), (int)oo, 1.0f,
                         0.0f));
-  GFCC_TRY(gemm_bf16_tn(st, c->W1_bf, c->ld_o, w.r1b, c->ld_o, w.U, C2, (int)o2v, (int)C2, (int)o, 1.0f, 0.0f));
-  // three-body: Z (split K) -> BF16 transposed -> U += T3 Z
+  // three-body: Z (split K) -> BF16 transposed into rz[c][o + e]; then U = [W1 | T3] [r1 | Z]
   const int zs = umma_splits((int)o2v, KSPLIT);
   GFCC_TRY(gemm_bf16_tn(st, c->V3_bf, c->ld_o2v, w.rk, c->ld_k1, w.Zp, C2, (int)v, (int)C2, (int)o2v, 1.0f, 0.0f, zs,
                         v * C2));
-  reduce_splits_kernel<<<grid1d(v * C2), 256, 0, st>>>(w.Zp, zs, v, C2, v * C2, w.Zb, c->ld_v);
+  reduce_splits_kernel<<<grid1d(v * C2), 256, 0, st>>>(w.Zp, zs, v, C2, v * C2, w.rz + o, c->ld_ot);
   GFCC_LAUNCH_CHECK();
-  GFCC_TRY(gemm_bf16_tn(st, c->T3_bf, c->ld_v, w.Zb, c->ld_v, w.U, C2, (int)o2v, (int)C2, (int)v, 1.0f, 1.0f));
+  GFCC_TRY(gemm_bf16_tn(st, c->WT_bf, c->ld_ot, w.rz, c->ld_ot, w.U, C2, (int)o2v, (int)C2, (int)(o + v), 1.0f,
+                        0.0f));
   // 1h row (split K)
   const int ss = umma_splits((int)(o2v + o), KSPLIT);
   GFCC_TRY(gemm_bf16_tn(st, c->U1_bf, c->ld_k1, w.rk, c->ld_k1, w.S1p, C2, (int)o, (int)C2, (int)(o2v + o), 1.0f, 0.0f,
@@ -415,13 +431,16 @@ int apply_ea_mixed(gfcc_ctx *c, const SysBatch &b, double *work) {
   PhaseTimer tsig(c, PH_SIGMA, b.nsys * sigma_flops(c, GFCC_SECTOR_EA));
   {
     PhaseTimer tu(c, PH_UNPACK);
-    unpack_ea_ring_kernel<<<grid1d(v * C2 * ov), 256, 0, st>>>(b, (int)o, (int)v, Pv, c->ld_ov, w.r2e);
+    unpack_ea_tile_kernel<<<dim3(cdiv(v, 32), cdiv(v, 32), (unsigned)(o * b.nsys)), dim3(32, 8), 0, st>>>(
+        b, (int)o, (int)v, Pv, c->ld_ov, c->ld_k1e, w.r2e, w.rk);
     GFCC_LAUNCH_CHECK();
     if (Pv > 0) {
-      unpack_ea_vvvv_kernel<<<grid1d(o * C2 * Pv), 256, 0, st>>>(b, (int)o, (int)v, Pv, c->ld_pv, w.r2p);
+      unpack_ea_pairs_kernel<<<dim3(cdiv(Pv, 256), (unsigned)(o * b.nsys)), 256, 0, st>>>(b, (int)o, (int)v, Pv,
+                                                                                        c->ld_pv, w.r2p);
       GFCC_LAUNCH_CHECK();
     }
-    unpack_ea_k_kernel<<<grid1d(C2 * (ov2 + v)), 256, 0, st>>>(b, (int)o, (int)v, Pv, c->ld_k1e, w.rk, c->ld_v, w.r1);
+    unpack_ea_y1_kernel<<<dim3(cdiv(v, 256), (unsigned)b.nsys), 256, 0, st>>>(b, (int)o, (int)v, c->ld_k1e, w.rk,
+                                                                              c->ld_ot, w.rz);
     GFCC_LAUNCH_CHECK();
   }
   // T[(i,b)][(a,c)] = Wr_ea[(i,b)][(m,e)] y2[m,a,e]
@@ -436,14 +455,14 @@ int apply_ea_mixed(gfcc_ctx *c, const SysBatch &b, double *work) {
     GFCC_TRY(gemm_bf16_tn(st, c->Wp_bf, c->ld_pv, w.r2p, c->ld_pv, w.Qp, o * C2, (int)Pv, (int)(o * C2), (int)Pv,
                           1.0f, 0.0f));
   }
-  // U[(i,b,a)][c] = W3 y1 + T3e Z,  Z[m][c] = V3e[m][(n,f,e)] y2[n,e,f] (split K)
-  GFCC_TRY(gemm_bf16_tn(st, c->W3_bf, c->ld_v, w.r1, c->ld_v, w.U, C2, (int)ov2, (int)C2, (int)v, 1.0f, 0.0f));
+  // U[(i,b,a)][c] = [W3 | T3e] [y1 | Z],  Z[m][c] = V3e[m][(n,f,e)] y2[n,e,f] (split K, into rz[c][v + m])
   const int zs = umma_splits((int)ov2, KSPLIT);
   GFCC_TRY(gemm_bf16_tn(st, c->V3e_bf, c->ld_ov2, w.rk, c->ld_k1e, w.Zp, C2, (int)o, (int)C2, (int)ov2, 1.0f, 0.0f, zs,
                         o * C2));
-  reduce_splits_kernel<<<grid1d(o * C2), 256, 0, st>>>(w.Zp, zs, o, C2, o * C2, w.Zb, c->ld_o);
+  reduce_splits_kernel<<<grid1d(o * C2), 256, 0, st>>>(w.Zp, zs, o, C2, o * C2, w.rz + v, c->ld_ot);
   GFCC_LAUNCH_CHECK();
-  GFCC_TRY(gemm_bf16_tn(st, c->T3e_bf, c->ld_o, w.Zb, c->ld_o, w.U, C2, (int)ov2, (int)C2, (int)o, 1.0f, 1.0f));
+  GFCC_TRY(gemm_bf16_tn(st, c->WTe_bf, c->ld_ot, w.rz, c->ld_ot, w.U, C2, (int)ov2, (int)C2, (int)(v + o), 1.0f,
+                        0.0f));
   // 1p row: S1[a][c] = [U1e | Fvv off-diagonal][a] . [y2 | y1](c) (split K)
   const int ss = umma_splits((int)(ov2 + v), KSPLIT);
   GFCC_TRY(gemm_bf16_tn(st, c->U1e_bf, c->ld_k1e, w.rk, c->ld_k1e, w.S1p, C2, (int)v, (int)C2, (int)(ov2 + v), 1.0f,

@@ -24,7 +24,7 @@ PRECOND_NONE, PRECOND_DIAG = 0, 1
 OPT_SECTOR, OPT_PRECISION, OPT_RESTART, OPT_MAX_ITERS, OPT_PRECOND, OPT_BATCH, OPT_INNER_TOL = 1, 2, 3, 4, 5, 6, 7
 OPT_RESIDUAL, OPT_INNER_CYCLES, OPT_EMU_LEVEL = 8, 9, 10
 OPT_GUESS, OPT_KEEP_SOLUTIONS, OPT_INNER_KRYLOV, OPT_AUTOTUNE, OPT_GRAPHS, OPT_EMU_FUSED_N = 11, 12, 13, 14, 15, 16
-OPT_INCREMENTAL = 17
+OPT_INCREMENTAL, OPT_INNER_RESTART = 17, 18
 GUESS_ZERO, GUESS_LEARNED, GUESS_MINRES = 0, 1, 2
 MLP_FP32, MLP_FP64 = 0, 1
 MLP_FEATURES, MLP_OUTPUTS = 27, 16
