@@ -251,29 +251,31 @@ __global__ void __launch_bounds__(THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   // tcgen05.ld is warp-collective: take the decision per warp
   if (__all_sync(0xffffffffu, ready && !*abort_flag)) {
-    // Each 32-column chunk of the warp's 32 rows goes through shared memory (the pipeline buffers
-    // are idle once every MMA has completed) and out row by row with the whole warp, so every
-    // store instruction writes 128 contiguous bytes.
-    float *stg = reinterpret_cast<float *>(smem) + warp * 32 * 33;
-    const int rbase = m0 + warp * 32;
-    const int rmax = min(32, M - rbase);
+    const int row = m0 + warp * 32 + lane;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 32) {
-      if (n0 + c0 >= N) break;   // warp-uniform
       float v[32];
       tmem_ld_32(tmem + ((unsigned)(warp * 32) << 16) + c0, v);
+      if (row < M) {
+        float *dst = D + (long long)row * ldd + n0 + c0;
+        const int ncols = min(32, N - (n0 + c0));
+        if (ncols == 32 && beta == 0.0f && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
 #pragma unroll
-      for (int q = 0; q < 32; q++) stg[lane * 33 + q] = v[q];
-      __syncwarp();
-      const int col = n0 + c0 + lane;
-      if (col < N) {
-        for (int r = 0; r < rmax; r++) {
-          float *dst = D + (long long)(rbase + r) * ldd + col;
-          const float x = alpha * stg[r * 33 + lane];
-          *dst = beta != 0.0f ? x + beta * *dst : x;
+          for (int i = 0; i < 32; i += 4)
+            *reinterpret_cast<float4 *>(dst + i) = make_float4(alpha * v[i], alpha * v[i + 1], alpha * v[i + 2],
+                                                               alpha * v[i + 3]);
+        } else if (ncols == 32 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+#pragma unroll
+          for (int i = 0; i < 32; i += 4) {
+            const float4 d = *reinterpret_cast<const float4 *>(dst + i);
+            *reinterpret_cast<float4 *>(dst + i) =
+                make_float4(alpha * v[i] + beta * d.x, alpha * v[i + 1] + beta * d.y, alpha * v[i + 2] + beta * d.z,
+                            alpha * v[i + 3] + beta * d.w);
+          }
+        } else {
+          for (int i = 0; i < ncols; i++) dst[i] = alpha * v[i] + (beta != 0.0f ? beta * dst[i] : 0.0f);
         }
       }
-      __syncwarp();
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -405,14 +407,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   const bool ready = mbar_wait(smem_u32(done), 0, abort_flag);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (__all_sync(0xffffffffu, ready && !*abort_flag) && nk > 0) {
-    // levels summed per row in registers, then staged in shared memory (idle pipeline buffers) and
-    // written row by row with the whole warp (coalesced along the columns)
-    double *stg = reinterpret_cast<double *>(smem) + warp * 32 * 33;
-    const int rbase = m0 + warp * 32;
-    const int rmax = min(32, M - rbase);
+    const int row = m0 + warp * 32 + lane;
+    const int ea = row < M ? eA[row] : 0;
 #pragma unroll 1
     for (int c0 = 0; c0 < EMU_BN; c0 += 32) {
-      if (n0 + c0 >= N) break;   // warp-uniform
       double acc[32];
 #pragma unroll
       for (int q = 0; q < 32; q++) acc[q] = 0.0;
@@ -427,25 +425,21 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int q = 0; q < 32; q++) acc[q] += (double)v[q] * w;
       }
-#pragma unroll
-      for (int q = 0; q < 32; q++) stg[lane * 33 + q] = acc[q];
-      __syncwarp();
-      const int col = n0 + c0 + lane;
-      if (col < N) {
+      if (row < M) {
+        const int ncols = min(32, N - (n0 + c0));
         if (part != nullptr) {
-          for (int r = 0; r < rmax; r++) part[((long long)blockIdx.z * M + rbase + r) * N + col] = stg[r * 33 + lane];
+          double *dst = part + ((long long)blockIdx.z * M + row) * N + n0 + c0;
+          for (int q = 0; q < ncols; q++) dst[q] = acc[q];
         } else {
-          const int eb = eB[col];
-          const long long offc = imap_apply(cn, n0g + col);
-          for (int r = 0; r < rmax; r++) {
-            const int row = rbase + r;
-            const long long off = imap_apply(cm, row) + offc;
-            const double val = alpha * ldexp(stg[r * 33 + lane], eA[row] + eb);
+          const long long ro = imap_apply(cm, row);
+          for (int q = 0; q < ncols; q++) {
+            const int col = n0 + c0 + q;
+            const long long off = ro + imap_apply(cn, n0g + col);
+            const double val = alpha * ldexp(acc[q], ea + eB[col]);
             C[off] = beta != 0.0 ? val + beta * C[off] : val;
           }
         }
       }
-      __syncwarp();
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
