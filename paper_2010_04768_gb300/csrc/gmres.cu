@@ -687,195 +687,6 @@ int Gmres::op_t(const T *x, long long ldx, T *yout, long long ldy) {
   }
 }
 
-// ---------------------------------------------------------------- FP32, even n: 16-byte loads
-// The same two passes for FP32 Krylov vectors of even length, where two adjacent complex elements
-// form one aligned float4.
-// * dots: the 8 warps of a block split the chunk (512 elements each); a lane keeps its 16
-//   elements of w in registers and streams every basis vector over them, two vectors per round
-//   (16 independent 16-byte loads per lane in flight); per-vector sums: warp shuffle, then the 8
-//   warps through shared memory.  Every warp does the same work whatever the vector count.
-// * update: a thread owns two float4 pairs (4 elements) and accumulates sum_i c_i V_i over batches
-//   of CGS_BATCH vectors (16 independent 16-byte loads per thread in flight).
-constexpr int CGS_MAXV = 72;                                       // vectors per pass (m + 2 <= 66)
-constexpr int F4_SLICE = CGS_CHUNK / (CGS_THREADS / 32);           // elements per warp
-constexpr int F4_PER_LANE = F4_SLICE / 64;                         // float4 pairs per lane
-
-__device__ __forceinline__ void dot_pair(const float4 a, const float4 x, float &ar, float &ai) {
-  ar += a.x * x.x + a.y * x.y + a.z * x.z + a.w * x.w;
-  ai += a.x * x.y - a.y * x.x + a.z * x.w - a.w * x.z;
-}
-__device__ __forceinline__ void warp_sum2(float &a, float &b) {
-  for (int off = 16; off > 0; off >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, off);
-    b += __shfl_xor_sync(0xffffffffu, b, off);
-  }
-}
-
-__global__ __launch_bounds__(CGS_THREADS) void cgs_dots_f4_kernel(const float *V, long long vs, long long vi, int nv,
-                                                                  const float *w, long long n, int nch,
-                                                                  const int *state, int want, double *partial,
-                                                                  int NV) {
-  __shared__ double2 red[CGS_THREADS / 32][CGS_MAXV];
-  const int s = blockIdx.y, chunk = blockIdx.x;
-  if (state[s] != want) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long np = n / 2;
-  const long long p0 = ((long long)chunk * CGS_CHUNK + (long long)warp * F4_SLICE) / 2 + lane;
-  const float4 *ws = reinterpret_cast<const float4 *>(w + 2 * s * vs);
-  const float4 *Vs = reinterpret_cast<const float4 *>(V + 2 * s * vs);
-  const long long vip = vi / 2;
-  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 x[F4_PER_LANE];
-#pragma unroll
-  for (int u = 0; u < F4_PER_LANE; u++) {
-    const long long p = p0 + 32 * u;
-    x[u] = p < np ? ws[p] : z4;
-  }
-  int i = 0;
-  for (; i + 1 < nv; i += 2) {
-    const float4 *va = Vs + i * vip, *vb = va + vip;
-    float4 a[F4_PER_LANE], b[F4_PER_LANE];
-#pragma unroll
-    for (int u = 0; u < F4_PER_LANE; u++) {
-      const long long p = p0 + 32 * u;
-      a[u] = p < np ? va[p] : z4;
-      b[u] = p < np ? vb[p] : z4;
-    }
-    float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
-#pragma unroll
-    for (int u = 0; u < F4_PER_LANE; u++) {
-      dot_pair(a[u], x[u], ar, ai);
-      dot_pair(b[u], x[u], br, bi);
-    }
-    warp_sum2(ar, ai);
-    warp_sum2(br, bi);
-    if (lane == 0) {
-      red[warp][i] = make_double2(ar, ai);
-      red[warp][i + 1] = make_double2(br, bi);
-    }
-  }
-  if (i < nv) {
-    const float4 *va = Vs + i * vip;
-    float4 a[F4_PER_LANE];
-#pragma unroll
-    for (int u = 0; u < F4_PER_LANE; u++) {
-      const long long p = p0 + 32 * u;
-      a[u] = p < np ? va[p] : z4;
-    }
-    float ar = 0.f, ai = 0.f;
-#pragma unroll
-    for (int u = 0; u < F4_PER_LANE; u++) dot_pair(a[u], x[u], ar, ai);
-    warp_sum2(ar, ai);
-    if (lane == 0) red[warp][i] = make_double2(ar, ai);
-  }
-  {   // slot nv: ||w||^2
-    float nn = 0.f, zz = 0.f;
-#pragma unroll
-    for (int u = 0; u < F4_PER_LANE; u++) nn += x[u].x * x[u].x + x[u].y * x[u].y + x[u].z * x[u].z + x[u].w * x[u].w;
-    warp_sum2(nn, zz);
-    if (lane == 0) red[warp][nv] = make_double2(nn, 0.0);
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k <= nv; k += CGS_THREADS) {
-    double2 t = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int q = 0; q < CGS_THREADS / 32; q++) {
-      t.x += red[q][k].x;
-      t.y += red[q][k].y;
-    }
-    reinterpret_cast<double2 *>(partial)[((long long)s * NV + k) * nch + chunk] = t;
-  }
-}
-
-__global__ __launch_bounds__(CGS_THREADS) void cgs_update_f4_kernel(const float *V, long long vs, long long vi, int nv,
-                                                                    float *w, long long n, int nch, const int *state,
-                                                                    int want, const double *h2, double *partial,
-                                                                    int NV) {
-  __shared__ float2 hh[CGS_MAXV];
-  __shared__ double sh[CGS_THREADS / 32];
-  const int s = blockIdx.y, chunk = blockIdx.x;
-  if (state[s] != want) return;
-  for (int k = threadIdx.x; k < nv; k += CGS_THREADS) {
-    const double2 c = reinterpret_cast<const double2 *>(h2)[(long long)s * NV + k];
-    hh[k] = make_float2((float)c.x, (float)c.y);
-  }
-  __syncthreads();
-  const long long np = n / 2;
-  const long long q0 = (long long)chunk * CGS_CHUNK / 2;
-  const long long q1 = q0 + CGS_CHUNK / 2 < np ? q0 + CGS_CHUNK / 2 : np;
-  float4 *ws = reinterpret_cast<float4 *>(w + 2 * s * vs);
-  const float4 *Vs = reinterpret_cast<const float4 *>(V + 2 * s * vs);
-  const long long vip = vi / 2;
-  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  float nn = 0.f;
-  for (long long p = q0 + threadIdx.x; p < q1; p += 2 * CGS_THREADS) {
-    const long long pf = p + CGS_THREADS;
-    const bool inf = pf < q1;
-    const long long pl = inf ? pf : p;   // past the chunk: repeat p (result not stored), loads stay unconditional
-    float4 acc0 = z4, acc1 = z4;
-    int i0 = 0;
-    for (; i0 + CGS_BATCH <= nv; i0 += CGS_BATCH) {
-      float4 a0[CGS_BATCH], a1[CGS_BATCH];
-#pragma unroll
-      for (int j = 0; j < CGS_BATCH; j++) {
-        const float4 *vp = Vs + (long long)(i0 + j) * vip;
-        a0[j] = vp[p];
-        a1[j] = vp[pl];
-      }
-#pragma unroll
-      for (int j = 0; j < CGS_BATCH; j++) {
-        const float2 c = hh[i0 + j];
-        acc0.x += c.x * a0[j].x - c.y * a0[j].y;
-        acc0.y += c.x * a0[j].y + c.y * a0[j].x;
-        acc0.z += c.x * a0[j].z - c.y * a0[j].w;
-        acc0.w += c.x * a0[j].w + c.y * a0[j].z;
-        acc1.x += c.x * a1[j].x - c.y * a1[j].y;
-        acc1.y += c.x * a1[j].y + c.y * a1[j].x;
-        acc1.z += c.x * a1[j].z - c.y * a1[j].w;
-        acc1.w += c.x * a1[j].w + c.y * a1[j].z;
-      }
-    }
-    for (; i0 < nv; i0++) {
-      const float4 *vp = Vs + (long long)i0 * vip;
-      const float4 a0 = vp[p], a1 = vp[pl];
-      const float2 c = hh[i0];
-      acc0.x += c.x * a0.x - c.y * a0.y;
-      acc0.y += c.x * a0.y + c.y * a0.x;
-      acc0.z += c.x * a0.z - c.y * a0.w;
-      acc0.w += c.x * a0.w + c.y * a0.z;
-      acc1.x += c.x * a1.x - c.y * a1.y;
-      acc1.y += c.x * a1.y + c.y * a1.x;
-      acc1.z += c.x * a1.z - c.y * a1.w;
-      acc1.w += c.x * a1.w + c.y * a1.z;
-    }
-    float4 x0 = ws[p];
-    x0.x -= acc0.x;
-    x0.y -= acc0.y;
-    x0.z -= acc0.z;
-    x0.w -= acc0.w;
-    ws[p] = x0;
-    nn += x0.x * x0.x + x0.y * x0.y + x0.z * x0.z + x0.w * x0.w;
-    if (inf) {
-      float4 x1 = ws[pf];
-      x1.x -= acc1.x;
-      x1.y -= acc1.y;
-      x1.z -= acc1.z;
-      x1.w -= acc1.w;
-      ws[pf] = x1;
-      nn += x1.x * x1.x + x1.y * x1.y + x1.z * x1.z + x1.w * x1.w;
-    }
-  }
-  double t = (double)nn;
-  for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int k = 0; k < CGS_THREADS / 32; k++) tot += sh[k];
-    reinterpret_cast<double2 *>(partial)[((long long)s * NV) * nch + chunk] = make_double2(tot, 0.0);
-  }
-}
-
 // dots of vectors [0, nv) of each system's basis (V + s*vs + i*vi) with w (w + s*ws) -> out
 template <typename T>
 int Gmres::mdot_t(const T *Vb, long long vs, long long vi, int nv, const T *w, long long ws, double *out, int want,
@@ -902,23 +713,7 @@ int Gmres::cgs2_t(const T *Vb, long long vs, int nv, T *w, cudaStream_t st) {
   dim3 grid(nchc, nsys);
   const int TH = 256;
   // pass p (0: dots and norm, 2: update and norm) over the systems whose filter array equals `want`
-  // FP32 vectors of even length (every vector starts 16-byte aligned): the float4 kernels
-  bool f4 = false;
-  if constexpr (sizeof(T) == sizeof(float))
-    f4 = n % 2 == 0 && nv + 1 <= CGS_MAXV && (reinterpret_cast<uintptr_t>(Vb) & 15) == 0 &&
-         (reinterpret_cast<uintptr_t>(w) & 15) == 0;
   auto pass = [&](int p, const double *coef, const int *filt, int want) -> int {
-    if constexpr (sizeof(T) == sizeof(float)) {
-      if (f4) {
-        if (p == 0)
-          cgs_dots_f4_kernel<<<grid, CGS_THREADS, 0, st>>>(Vb, vs, n, nv, w, n, nchc, filt, want, partial, NV);
-        else
-          cgs_update_f4_kernel<<<grid, CGS_THREADS, 0, st>>>(Vb, vs, n, nv, w, n, nchc, filt, want, coef, partial,
-                                                             NV);
-        GFCC_LAUNCH_CHECK();
-        return GFCC_OK;
-      }
-    }
     if (p == 0)
       cgs_dots_kernel<T><<<grid, CGS_THREADS, 0, st>>>(Vb, vs, n, nv, w, n, nchc, filt, want, partial, NV);
     else
