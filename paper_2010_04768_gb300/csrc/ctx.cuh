@@ -89,7 +89,7 @@ struct gfcc_ctx {
 
   // digit planes of the FP64 IP operands for the FP64-accurate residual on the tensor cores
   // (full Fock folding, same GEMM roles as the BF16 operands; V3 padded to the K of U1x)
-  gfcc::EmuOperand eWr, eWq, eW1, eV3, eT3, eU1;
+  gfcc::EmuOperand eWr, eWq, eWT, eV3, eU1;   // eWT: [W1 | T3] over K = o + v
   int emu_S = 8, emu_P = 9;
   int residual_emulated = 1;   // 0: refinement residuals with the FP64 (DFMA) sigma
   int incremental = 1;         // 1: r -= A d at the digit level the correction needs (after the first step)
@@ -113,7 +113,7 @@ struct gfcc_ctx {
   __nv_bfloat16 *U1e_bf = nullptr;  // [a][(m,x,y) | e] U1e and the off-diagonal Fbar_vv of the 1p row, ld_k1e
   long long ld_pv = 0, ld_ov2 = 0, ld_k1e = 0;
   // digit planes of the FP64 EA operands (full Fock folding) for the FP64-accurate residual
-  gfcc::EmuOperand eWre, eWp, eW3, eV3e, eT3e, eU1e;
+  gfcc::EmuOperand eWre, eWp, eWTe, eV3e, eU1e;   // eWTe: [W3 | T3e] over K = v + o
 
   std::vector<void *> allocs;
 

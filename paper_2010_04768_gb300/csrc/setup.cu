@@ -146,6 +146,16 @@ __global__ void to_bf16_kernel(const double *in, long long rows, long long cols,
   }
 }
 
+// out[r] = [in1[r][0..k1) | in2[r][0..k2)] (rows of k1 + k2)
+__global__ void concat_f64_kernel(const double *in1, long long k1, const double *in2, long long k2, long long rows,
+                                  double *out) {
+  const long long K = k1 + k2, tot = rows * K;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < tot; x += (long long)gridDim.x * blockDim.x) {
+    const long long r = x / K, c = x - r * K;
+    out[x] = c < k1 ? in1[r * k1 + c] : in2[r * k2 + (c - k1)];
+  }
+}
+
 // out[r] = [bf16(in1[r][0..k1)) | bf16(in2[r][0..k2)) | 0 ...] (ld_out >= k1 + k2)
 __global__ void concat_bf16_kernel(const double *in1, long long k1, const double *in2, long long k2, long long rows,
                                    __nv_bfloat16 *out, long long ld_out) {
@@ -605,8 +615,14 @@ int build_hbar(gfcc_ctx *c, const double *d_fock, const double *d_chol) {
       GFCC_TRY(permute4(st, d, c->Woooo, is, t, os, 0.5, 0.0));
     }
     GFCC_TRY(slice(t, oo, oo, oo, c->eWq));
-    GFCC_TRY(slice(c->W1, o2v, o, o, c->eW1));
-    GFCC_TRY(slice(c->T3, o2v, v, v, c->eT3));
+    {
+      // [W1 | T3] with one exponent per row over K = o + v (one product with [r1 | Z])
+      double *wt;
+      GFCC_TRY(tmp.get(&wt, o2v * (o + v)));
+      concat_f64_kernel<<<grid1d(o2v * (o + v)), 256, 0, st>>>(c->W1, o, c->T3, v, o2v, wt);
+      GFCC_LAUNCH_CHECK();
+      GFCC_TRY(slice(wt, o2v, o + v, o + v, c->eWT));
+    }
     double *t2x;
     GFCC_TRY(tmp.get(&t2x, std::max(v, o) * (o2v + o)));
     {
@@ -665,10 +681,16 @@ int build_hbar(gfcc_ctx *c, const double *d_fock, const double *d_chol) {
     GFCC_TRY(alloc_bf16(c, &c->WTe_bf, ov2 * c->ld_ot));
     concat_bf16_kernel<<<grid1d(ov2 * c->ld_ot), 256, 0, st>>>(c->W3, v, c->T3e, o, ov2, c->WTe_bf, c->ld_ot);
     GFCC_LAUNCH_CHECK();
-    GFCC_TRY(slice(c->W3, ov2, v, v, c->eW3));
+    {
+      // [W3 | T3e] with one exponent per row over K = v + o
+      double *wt;
+      GFCC_TRY(tmp.get(&wt, ov2 * (v + o)));
+      concat_f64_kernel<<<grid1d(ov2 * (v + o)), 256, 0, st>>>(c->W3, v, c->T3e, o, ov2, wt);
+      GFCC_LAUNCH_CHECK();
+      GFCC_TRY(slice(wt, ov2, v + o, v + o, c->eWTe));
+    }
     GFCC_TRY(alloc_bf16(c, &c->V3e_bf, o * c->ld_ov2));
     GFCC_TRY(to_bf16(st, c->V3e, o, ov2, ov2, 1.0, c->V3e_bf, c->ld_ov2));
-    GFCC_TRY(slice(c->T3e, ov2, o, o, c->eT3e));
     // [V3e | 0]: padded to the K of the 1p row
     {
       const long long d[4] = {1, 1, o, ov2};

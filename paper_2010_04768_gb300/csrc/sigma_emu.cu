@@ -138,12 +138,14 @@ __global__ void digits_k1_kernel(const double *x, long long ldx, int C2, int o, 
   }
 }
 
-// Zt[c][e] = Z[e][c]
-__global__ void transpose_kernel(const double *Z, long long rows, long long cols, double *Zt) {
-  const long long tot = rows * cols;
+// Rz[c] = [plane c of x[s][0..k1) | Z[0..k2)[c]]: the B rows of the concatenated product
+// [W1 | T3] (IP: x's 1h block, then Z over v) or [W3 | T3e] (EA: x's 1p block, then Z over o)
+__global__ void rz_fill_kernel(const double *x, long long ldx, int C2, int k1, const double *Z, int k2, double *Rz) {
+  const long long K = (long long)k1 + k2, tot = (long long)C2 * K;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const long long r = t / cols, c = t - r * cols;
-    Zt[c * rows + r] = Z[t];
+    const int c = (int)(t / K);
+    const long long k = t - (long long)c * K;
+    Rz[t] = k < k1 ? x[2 * ((long long)(c >> 1) * ldx + k) + (c & 1)] : Z[(k - k1) * C2 + c];
   }
 }
 
@@ -249,20 +251,19 @@ EmuWorkEA emu_layout_ea(const gfcc_ctx *c, int nsub, void *base) {
   op(w.r2p, o * C2, std::max<long long>(Pv, 1));
   op(w.rk, C2, ov2 + v);
   op(w.r1, C2, v);
-  op(w.Zo, C2, o);
+  op(w.Zo, C2, v + o);
   w.ec = reinterpret_cast<int *>(take(C2 * 4));
   w.T = reinterpret_cast<double *>(take(ov * v * C2 * 8));
   w.Qp = reinterpret_cast<double *>(take(std::max<long long>(Pv, 1) * o * C2 * 8));
   w.U = reinterpret_cast<double *>(take(ov2 * C2 * 8));
   w.S1 = reinterpret_cast<double *>(take(v * C2 * 8));
   w.Z = reinterpret_cast<double *>(take(o * C2 * 8));
-  w.Zt = reinterpret_cast<double *>(take(o * C2 * 8));
+  w.Zt = reinterpret_cast<double *>(take((v + o) * C2 * 8));
   long long g = 0;
   g = std::max(g, emu_gemm_work_bytes(ov, v * C2, ov));
   g = std::max(g, emu_gemm_work_bytes(std::max<long long>(Pv, 1), o * C2, std::max<long long>(Pv, 1)));
-  g = std::max(g, emu_gemm_work_bytes(ov2, C2, v));
+  g = std::max(g, emu_gemm_work_bytes(ov2, C2, v + o));
   g = std::max(g, emu_gemm_work_bytes(o, C2, ov2 + v));
-  g = std::max(g, emu_gemm_work_bytes(ov2, C2, o));
   g = std::max(g, emu_gemm_work_bytes(v, C2, ov2 + v));
   w.gw = take(g);
   w.bytes = p - static_cast<unsigned char *>(base);
@@ -299,20 +300,19 @@ EmuWork emu_layout(const gfcc_ctx *c, int nsub, void *base) {
   op(w.r2o, v * C2, o * o);
   op(w.rk, C2, o2v + o);
   op(w.r1b, C2, o);
-  op(w.Zo, C2, v);
+  op(w.Zo, C2, o + v);
   w.ec = reinterpret_cast<int *>(take(C2 * 4));
   w.T = reinterpret_cast<double *>(take(o * v * o * C2 * 8));
   w.Q = reinterpret_cast<double *>(take(o * o * v * C2 * 8));
   w.U = reinterpret_cast<double *>(take(o * v * o * C2 * 8));
   w.S1 = reinterpret_cast<double *>(take(o * C2 * 8));
   w.Z = reinterpret_cast<double *>(take(v * C2 * 8));
-  w.Zt = reinterpret_cast<double *>(take(v * C2 * 8));
+  w.Zt = reinterpret_cast<double *>(take((o + v) * C2 * 8));
   long long g = 0;
   g = std::max(g, emu_gemm_work_bytes(o * v, o * C2, o * v));
   g = std::max(g, emu_gemm_work_bytes(o * o, v * C2, o * o));
-  g = std::max(g, emu_gemm_work_bytes(o2v, C2, o));
+  g = std::max(g, emu_gemm_work_bytes(o2v, C2, o + v));
   g = std::max(g, emu_gemm_work_bytes(v, C2, o2v + o));
-  g = std::max(g, emu_gemm_work_bytes(o2v, C2, v));
   g = std::max(g, emu_gemm_work_bytes(o, C2, o2v + o));
   w.gw = take(g);
   w.bytes = p - static_cast<unsigned char *>(base);
@@ -376,12 +376,12 @@ int apply_ip_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_do
       GFCC_TRY(emu_gemm(st, c->eWr, w.r2b, P, 1.0, 0.0, w.T, imap1(o * C2), imap1(1), w.gw));
     }
     GFCC_TRY(emu_gemm(st, c->eWq, w.r2o, P, 1.0, 0.0, w.Q, imap1(v * C2), imap1(1), w.gw));
-    GFCC_TRY(emu_gemm(st, c->eW1, w.r1b, P, 1.0, 0.0, w.U, imap1(C2), imap1(1), w.gw));
+    // three-body Z = V3 rk, then U = [W1 | T3] [r1 | Z] in one product over K = o + v
     GFCC_TRY(emu_gemm(st, c->eV3, w.rk, P, 1.0, 0.0, w.Z, imap1(C2), imap1(1), w.gw));
-    transpose_kernel<<<grid1d(v * C2), 256, 0, st>>>(w.Z, v, C2, w.Zt);
+    rz_fill_kernel<<<grid1d(C2 * (o + v)), 256, 0, st>>>(x, b.ldx, C2, (int)o, w.Z, (int)v, w.Zt);
     GFCC_LAUNCH_CHECK();
-    GFCC_TRY(emu_slice(st, w.Zt, C2, v, v, S, w.Zo.dig, w.Zo));
-    GFCC_TRY(emu_gemm(st, c->eT3, w.Zo, P, 1.0, 1.0, w.U, imap1(C2), imap1(1), w.gw));
+    GFCC_TRY(emu_slice(st, w.Zt, C2, o + v, o + v, S, w.Zo.dig, w.Zo));
+    GFCC_TRY(emu_gemm(st, c->eWT, w.Zo, P, 1.0, 0.0, w.U, imap1(C2), imap1(1), w.gw));
     GFCC_TRY(emu_gemm(st, c->eU1, w.rk, P, 1.0, 0.0, w.S1, imap1(C2), imap1(1), w.gw));
     SysBatch bb = b;
     bb.nsys = ns;
@@ -438,12 +438,12 @@ int apply_ea_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_do
       GFCC_TRY(emu_gemm(st, c->eWre, w.r2e, P, 1.0, 0.0, w.T, imap1(v * C2), imap1(1), w.gw));
     }
     if (Pv > 0) GFCC_TRY(emu_gemm(st, c->eWp, w.r2p, P, 1.0, 0.0, w.Qp, imap1(o * C2), imap1(1), w.gw));
-    GFCC_TRY(emu_gemm(st, c->eW3, w.r1, P, 1.0, 0.0, w.U, imap1(C2), imap1(1), w.gw));
+    // Z = V3e rk, then U = [W3 | T3e] [y1 | Z] in one product over K = v + o
     GFCC_TRY(emu_gemm(st, c->eV3e, w.rk, P, 1.0, 0.0, w.Z, imap1(C2), imap1(1), w.gw));
-    transpose_kernel<<<grid1d(o * C2), 256, 0, st>>>(w.Z, o, C2, w.Zt);
+    rz_fill_kernel<<<grid1d(C2 * (v + o)), 256, 0, st>>>(x, b.ldx, C2, (int)v, w.Z, (int)o, w.Zt);
     GFCC_LAUNCH_CHECK();
-    GFCC_TRY(emu_slice(st, w.Zt, C2, o, o, S, w.Zo.dig, w.Zo));
-    GFCC_TRY(emu_gemm(st, c->eT3e, w.Zo, P, 1.0, 1.0, w.U, imap1(C2), imap1(1), w.gw));
+    GFCC_TRY(emu_slice(st, w.Zt, C2, v + o, v + o, S, w.Zo.dig, w.Zo));
+    GFCC_TRY(emu_gemm(st, c->eWTe, w.Zo, P, 1.0, 0.0, w.U, imap1(C2), imap1(1), w.gw));
     GFCC_TRY(emu_gemm(st, c->eU1e, w.rk, P, 1.0, 0.0, w.S1, imap1(C2), imap1(1), w.gw));
     SysBatch bb = b;
     bb.nsys = ns;

@@ -298,8 +298,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 // the 512 columns).  A stage holds the tile of one A plane i and the tiles of the B planes
 // j = 1 .. min(SB, P - i), so every level of pair (i, j) is fed from the same stage.  A level
 // accumulates at most 8 pairs x 32 K blocks x 64 = 2^14 products of magnitude <= 2^10, so its FP32
-// sums are exact integers; the epilogue adds the levels in FP64 (smallest weight first) and writes
-// the FP64 result (or, with a K split, an FP64 partial per split).
+// sums are exact integers; the epilogue adds the levels exactly in two int64 accumulators, forms
+// the FP64 value and writes the FP64 result (or, with a K split, an FP64 partial per split).
 constexpr int EMU_BN = 64, EMU_STAGES = 2, EMU_MAXS = 8;
 constexpr int EMU_A_BYTES = BM * BK * 2, EMU_B_BYTES = EMU_BN * BK * 2;
 constexpr int EMU_STAGE_BYTES = EMU_A_BYTES + EMU_MAXS * EMU_B_BYTES;
@@ -409,30 +409,56 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (__all_sync(0xffffffffu, ready && !*abort_flag) && nk > 0) {
     const int row = m0 + warp * 32 + lane;
     const int ea = row < M ? eA[row] : 0;
+    // The level sums are exact integers below 2^24: they are added in two int64 accumulators,
+    // levels Lhi+1..P with weights 64^(P-L) and 2..Lhi with 64^(Lhi-L) (below 2^45 each), on the
+    // integer pipes; FP64 work is two conversions and one scaled add per output.
+    const int Lhi = min(P, 5);
 #pragma unroll 1
     for (int c0 = 0; c0 < EMU_BN; c0 += 32) {
       double acc[32];
+      long long ia[32];
 #pragma unroll
-      for (int q = 0; q < 32; q++) acc[q] = 0.0;
+      for (int q = 0; q < 32; q++) ia[q] = 0;
 #pragma unroll 1
-      for (int L = P; L >= 2; L--) {
-        // a level receives products when some pair i + j = L exists
+      for (int L = P; L > Lhi; L--) {
+        const int ilo = max(1, L - SB), ihi = min(SAe, L - 1);   // a level holds products if some i + j = L
+        if (ilo > ihi) continue;
+        float v[32];
+        tmem_ld_32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)((L - 2) * EMU_BN + c0), v);
+        const int sh = 6 * (P - L);
+#pragma unroll
+        for (int q = 0; q < 32; q++) ia[q] += (long long)__float2int_rn(v[q]) << sh;
+      }
+      const double wlo = ldexp(1.0, -6 * P), whi = ldexp(1.0, -6 * Lhi);
+#pragma unroll
+      for (int q = 0; q < 32; q++) {
+        acc[q] = (double)ia[q] * wlo;
+        ia[q] = 0;
+      }
+#pragma unroll 1
+      for (int L = Lhi; L >= 2; L--) {
         const int ilo = max(1, L - SB), ihi = min(SAe, L - 1);
         if (ilo > ihi) continue;
         float v[32];
         tmem_ld_32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)((L - 2) * EMU_BN + c0), v);
-        const double w = ldexp(1.0, -6 * L);
+        const int sh = 6 * (Lhi - L);
 #pragma unroll
-        for (int q = 0; q < 32; q++) acc[q] += (double)v[q] * w;
+        for (int q = 0; q < 32; q++) ia[q] += (long long)__float2int_rn(v[q]) << sh;
       }
+#pragma unroll
+      for (int q = 0; q < 32; q++) acc[q] = fma((double)ia[q], whi, acc[q]);
       if (row < M) {
         const int ncols = min(32, N - (n0 + c0));
         if (part != nullptr) {
           double *dst = part + ((long long)blockIdx.z * M + row) * N + n0 + c0;
-          for (int q = 0; q < ncols; q++) dst[q] = acc[q];
+#pragma unroll
+          for (int q = 0; q < 32; q++)
+            if (q < ncols) dst[q] = acc[q];
         } else {
           const long long ro = imap_apply(cm, row);
-          for (int q = 0; q < ncols; q++) {
+#pragma unroll
+          for (int q = 0; q < 32; q++) {
+            if (q >= ncols) continue;
             const int col = n0 + c0 + q;
             const long long off = ro + imap_apply(cn, n0g + col);
             const double val = alpha * ldexp(acc[q], ea + eB[col]);
