@@ -339,6 +339,7 @@ __global__ void coef_add_kernel(int nsys, int nv, double *h, const double *h2, i
 // * update: every thread owns two elements and accumulates sum_i c_i V_i over batches of
 //   CGS_BATCH vectors whose loads are predicated (not branched), so they issue together.
 constexpr int CGS_THREADS = 256, CGS_CHUNK = 4096, CGS_UNROLL = 8, CGS_BATCH = 8;
+constexpr double REORTH_THETA_F32 = 0.01;   // FP32 Krylov vectors: second pass where ||w'|| < 0.1 ||w||
 
 template <typename T>
 __global__ __launch_bounds__(CGS_THREADS) void cgs_dots_kernel(const T *V, long long vs, long long vi, int nv,
@@ -463,12 +464,12 @@ __global__ __launch_bounds__(CGS_THREADS) void cgs_update_norm_kernel(const T *V
 // Selective reorthogonalisation (Daniel, Gragg, Kaufman & Stewart 1976): a second Gram-Schmidt
 // pass only where the first one cancelled more than half of w (||w'||^2 < ||w||^2 / 2).
 __global__ void reorth_flag_kernel(int nsys, const int *state, int want, const double *h, const double *w2, int NV,
-                                   int nv, int *flag) {
+                                   int nv, double theta, int *flag) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nsys) return;
   const double before = h[2 * ((long long)s * NV + nv)];    // ||w||^2 from the first pass
   const double after = w2[2 * ((long long)s * NV)];          // ||w'||^2
-  flag[s] = (state[s] == want && after < 0.5 * before) ? 1 : 0;
+  flag[s] = (state[s] == want && after < theta * before) ? 1 : 0;
 }
 
 // h[s][i] += h2[s][i] (i < nv) and h[s][nv] = ||w||^2 for the flagged systems; copy the final norm
@@ -736,7 +737,13 @@ int Gmres::cgs2_t(const T *Vb, long long vs, int nv, T *w, cudaStream_t st) {
   GFCC_TRY(pass(2, h, state, ST_IN_CYCLE));
   GFCC_TRY(final(1, nrm, state, ST_IN_CYCLE));
   // passes 3-4 only where the first pass cancelled most of w
-  reorth_flag_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, state, ST_IN_CYCLE, h, nrm, NV, nv, flag);
+  // Second pass where ||w'||^2 < theta ||w||^2.  The orthogonality lost by the new vector is about
+  // the relative rounding error of the pass times ||w|| / ||w'||: FP64 solves reorthogonalise below
+  // 1/sqrt(2) (the usual twice-is-enough test); the FP32 inner solves of the refinement, which stop
+  // at a relative residual of 1e-4 and are corrected by the FP64-accurate outer residual, only where
+  // the first pass cancelled more than 90% of w (orthogonality loss <= 10 x about 1e-6 per vector).
+  const double theta = sizeof(T) == sizeof(float) ? REORTH_THETA_F32 : 0.5;
+  reorth_flag_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, state, ST_IN_CYCLE, h, nrm, NV, nv, theta, flag);
   GFCC_LAUNCH_CHECK();
   GFCC_TRY(pass(0, nullptr, flag, 1));
   GFCC_TRY(final(nv, h2, flag, 1));
