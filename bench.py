@@ -62,6 +62,11 @@ WORKLOADS = {
 DEFAULT_WORKLOAD = "medium-ipea-mixed"
 FREQ_STRIDE = 17   # timed step k takes grid frequency (k * 17) mod n_omega (coprime with 64: covers the grid)
 INNER_RESTART = 60   # restart length of the inner GMRES of the mixed-precision refinement (library default)
+# DRAM traffic of one digit-pair GEMM launch (umma_bf16_gemm_kernel<256, 0>) at the IP ring shape
+# M = K = 8000, N = 3200, from one ncu --set full capture (profiles/umma_digit_pairs_ring_ip_medium.md;
+# mean of two launches); null once that kernel changes
+RING_EMU_TRAFFIC = {"traffic": 621.7e6, "traffic_unit": "DRAM bytes per digit-pair GEMM launch at M=K=8000, "
+                    "N=3200 (ncu --set full)", "algorithmic_bytes_per_launch": [281e6, 383e6]}
 
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 flops x max clock
 
@@ -471,6 +476,7 @@ def main():
             ach = fl / (ms / 1e3) / 1e12
             rf[ph] = {"bound": bound, "kernel": kernel, "achieved": ach, "peak": peak, "unit": unit,
                       "frac": ach / peak, "traffic": None, "launches": n_l, "ms_total": ms,
+                      **(RING_EMU_TRAFFIC if ph == "ring_emu" else {}),
                       "peak_note": ("FP64 FMA units: 152 SMs x 2 DFMA/clk x 2070 MHz (derived); cuBLAS DGEMM "
                                     "measured 1.10 TFLOP/s on this pool") if bound == "alu" else
                                    "bf16_tflops_sustained of measured (kernel timed inside a long step); the "

@@ -81,9 +81,17 @@ void dfree(void *p) {
 }
 
 static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
-void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static thread_local long long t_launches = 0;   // this thread's launches (graph capture bookkeeping)
+void count_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  t_launches++;
+}
+void count_launches(long long n) {
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  t_launches += n;
+}
 long long launch_count() { return g_launches.load(); }
+long long thread_launch_count() { return t_launches; }
 
 static cudaEvent_t take_event(gfcc_ctx *c) {
   if (!c->ev_pool.empty()) {

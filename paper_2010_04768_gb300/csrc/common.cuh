@@ -44,6 +44,7 @@ void dfree(void *p);                           // unreg_alloc + cudaFree
 void count_launch();
 void count_launches(long long n);   // kernels replayed from a CUDA graph
 long long launch_count();
+long long thread_launch_count();   // the calling thread's share (concurrent solves of gfcc_solve_batch)
 #define GFCC_LAUNCH_CHECK()   \
   do {                        \
     ::gfcc::count_launch();   \

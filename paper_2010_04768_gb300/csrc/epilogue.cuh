@@ -105,9 +105,10 @@ __global__ __launch_bounds__(THREADS) void ip2_kernel(SysBatch b, int o, int v, 
   long long i, j;
   pair_decode(p, o, i, j);
   const long long Cl = 2LL * ns, ld = Cl + 1, c0 = 2LL * s0;
-  for (long long t = threadIdx.x; t < A * Cl; t += THREADS) {
-    const int al = (int)(t / Cl);
-    const long long c = t - al * Cl;
+  const int cl = (int)Cl;   // at most 2 max_systems()
+  for (int t = threadIdx.x; t < A * cl; t += THREADS) {
+    const int al = t / cl;
+    const long long c = t - al * cl;
     const long long a = a0 + al;
     if (a >= v) continue;
     const long long tij = ((i * v + a) * o + j) * C2 + c0 + c;
@@ -133,16 +134,24 @@ __global__ __launch_bounds__(THREADS) void ea2_kernel(SysBatch b, int o, int v, 
   extern __shared__ __align__(16) unsigned char smem[];
   TIn *tile = reinterpret_cast<TIn *>(smem);
   constexpr int A = run_len<TIn>();
+  __shared__ int pa[A], pb[A];   // the block's pairs (a < b), decoded once
   const long long i = blockIdx.x;
   const long long ab0 = (long long)blockIdx.y * A;
   const long long Cl = 2LL * ns, ld = Cl + 1, c0 = 2LL * s0;
-  for (long long t = threadIdx.x; t < A * Cl; t += THREADS) {
-    const int al = (int)(t / Cl);
-    const long long c = t - al * Cl;
+  if (threadIdx.x < A && ab0 + threadIdx.x < Pv) {
+    long long a, bb;
+    pair_decode(ab0 + threadIdx.x, v, a, bb);
+    pa[threadIdx.x] = (int)a;
+    pb[threadIdx.x] = (int)bb;
+  }
+  __syncthreads();
+  const int cl = (int)Cl;   // at most 2 max_systems()
+  for (int t = threadIdx.x; t < A * cl; t += THREADS) {
+    const int al = t / cl;
+    const long long c = t - al * cl;
     const long long ab = ab0 + al;
     if (ab >= Pv) continue;
-    long long a, bb;
-    pair_decode(ab, v, a, bb);
+    const long long a = pa[al], bb = pb[al];
     const long long tiba = ((i * v + bb) * v + a) * C2 + c0 + c;
     const long long tiab = ((i * v + a) * v + bb) * C2 + c0 + c;
     const long long qq = (ab * o + i) * C2 + c0 + c;

@@ -869,7 +869,7 @@ int Gmres::solve_t(double tol, int max_iters, int *h_state, int max_cycles, bool
           // capture the step once (its launches are counted as they are recorded; the launch right
           // after the capture runs them), replay it afterwards.  A capture that fails leaves the
           // graphs off for this solver and the step runs directly.
-          const long long l0 = launch_count();
+          const long long l0 = thread_launch_count();   // other threads may launch meanwhile
           cudaGraph_t gr = nullptr;
           cudaError_t ec = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
           int rc = GFCC_ERR_CUDA;
@@ -879,14 +879,14 @@ int Gmres::solve_t(double tol, int max_iters, int *h_state, int max_cycles, bool
           }
           if (rc == GFCC_OK && ec == cudaSuccess && gr != nullptr &&
               cudaGraphInstantiate(&gexec[k], gr, 0) == cudaSuccess) {
-            glaunch[k] = launch_count() - l0;
+            glaunch[k] = thread_launch_count() - l0;
             GFCC_CUDA(cudaGraphLaunch(gexec[k], st));
             done_step = true;
           } else {
             cudaGetLastError();
             gexec[k] = nullptr;
             gbroken = true;
-            count_launches(l0 - launch_count());   // nothing of the failed capture ran
+            count_launches(l0 - thread_launch_count());   // nothing of the failed capture ran
           }
           if (gr) cudaGraphDestroy(gr);
         } else {
