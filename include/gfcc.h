@@ -65,7 +65,7 @@ extern "C" {
 #define GFCC_OPT_MAX_ITERS   4    /* max sigma products per system; default 1500                         */
 #define GFCC_OPT_PRECOND     5    /* GFCC_PRECOND_*; default DIAG                                        */
 #define GFCC_OPT_BATCH       6    /* systems solved together (0 = chosen from free memory); default 0   */
-#define GFCC_OPT_INNER_TOL   7    /* mixed precision: inner GMRES relative tolerance; default 1e-4       */
+#define GFCC_OPT_INNER_TOL   7    /* mixed precision: inner GMRES relative tolerance; default 3e-4       */
 #define GFCC_OPT_RESIDUAL    8    /* mixed precision refinement residual: 1 (default) FP64-accurate from
                                      digit planes on the tensor cores, 0 the FP64 (DFMA) sigma          */
 #define GFCC_OPT_INNER_CYCLES 9   /* mixed precision: GMRES restart cycles per refinement step; default 1 */

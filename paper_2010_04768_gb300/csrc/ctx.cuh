@@ -54,7 +54,7 @@ struct gfcc_ctx {
   int precond = GFCC_PRECOND_DIAG;
   int batch = 0;
   double mem_share = 1.0;    // fraction of the free device memory a solve may plan its batch for
-  double inner_tol = 1e-4;
+  double inner_tol = 3e-4;
   int inner_cycles = 1;      // GMRES restart cycles per refinement step (each ends with an FP64-accurate residual)
   int inner_fp64 = 0;        // 1: FP64 Krylov vectors in the inner solves (default FP32)
   int use_graphs = 1;        // replay the Arnoldi steps of the inner solves from CUDA graphs

@@ -740,7 +740,7 @@ int Gmres::cgs2_t(const T *Vb, long long vs, int nv, T *w, cudaStream_t st) {
   // Second pass where ||w'||^2 < theta ||w||^2.  The orthogonality lost by the new vector is about
   // the relative rounding error of the pass times ||w|| / ||w'||: FP64 solves reorthogonalise below
   // 1/sqrt(2) (the usual twice-is-enough test); the FP32 inner solves of the refinement, which stop
-  // at a relative residual of 1e-4 and are corrected by the FP64-accurate outer residual, only where
+  // at a relative residual of 3e-4 and are corrected by the FP64-accurate outer residual, only where
   // the first pass cancelled more than 90% of w (orthogonality loss <= 10 x about 1e-6 per vector).
   const double theta = sizeof(T) == sizeof(float) ? REORTH_THETA_F32 : 0.5;
   reorth_flag_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, state, ST_IN_CYCLE, h, nrm, NV, nv, theta, flag);
