@@ -149,6 +149,35 @@ def dist_setup():
     return world, rank, local
 
 
+def step_frequency_indices(step, world, rank, per, nw, sweep=False):
+    """Grid indices of the frequencies rank `rank` of `world` solves in step `step` (`per` per step on
+    a grid of `nw`).  The (omega, p) tasks are independent, so the ranks shard the frequencies and
+    share nothing on the data path.  Sweeps: timed step k takes the window of `per` consecutive grid
+    frequencies starting at (k world + r) per; single-frequency steps take grid frequency
+    ((k world + r) per + j) FREQ_STRIDE mod nw (FREQ_STRIDE coprime with nw, so distinct steps and ranks
+    land on distinct frequencies until the grid is used up).  Warm-up steps (negative k) take the top
+    end of the grid."""
+    if step < 0:
+        return [(nw + step * per + j) % nw for j in range(per)]
+    base = (step * world + rank) * per
+    if sweep:
+        return [(base + j) % nw for j in range(per)]
+    return [((base + j) * FREQ_STRIDE) % nw for j in range(per)]
+
+
+def reduce_over_ranks(dist, seconds, columns, device):
+    """(slowest rank's time, columns of all ranks): the only collective of a multi-rank run, on the
+    timings after the timed region."""
+    if dist is None:
+        return seconds, columns
+    import torch
+    t = torch.tensor([seconds, float(columns)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), int(round(float(t[1])))
+
+
 def sectors_of(spec):
     return ("IP", "EA") if spec["sector"] in ("IP+EA", "BOTH") else (spec["sector"],)
 
@@ -269,7 +298,7 @@ def uneven_specs(seed=4, count=16):
     return out
 
 
-def run_uneven(args, spec, world, rank):
+def run_uneven(args, spec, world, rank, dist=None):
     """Uneven multi-molecule batch: one context per molecule, every step one frequency of each
     molecule x its orbitals, solved concurrently by gfcc_solve_batch (host API: G read back every
     step; the value is host-timed around the synchronous call)."""
@@ -291,7 +320,10 @@ def run_uneven(args, spec, world, rank):
     eta, tol = 0.005, 1e-8
 
     def step(k):
-        reqs = [(grids[i][[(k * 7 + i) % grids[i].size]], eta, orbs[i], tol) for i in range(len(ctxs))]
+        # rank r, step k: molecule i solves its grid frequency ((k world + r) 7 + i) mod n_freq (warm-up
+        # steps, negative k, stay off the timed ones); ranks share nothing on the data path
+        kk = k * world + rank if k >= 0 else k
+        reqs = [(grids[i][[(kk * 7 + i) % grids[i].size]], eta, orbs[i], tol) for i in range(len(ctxs))]
         Gs, codes = gfcc.solve_batch(ctxs, reqs)
         cols = 0
         for g in ctxs:
@@ -302,12 +334,17 @@ def run_uneven(args, spec, world, rank):
         step(-1 - k)
     launches0 = gfcc.launch_count()
     torch.cuda.synchronize()
-    with Clocks(0) as clk:
+    if dist is not None:
+        dist.barrier()
+    with Clocks(torch.cuda.current_device()) as clk:
         t0 = time.perf_counter()
         cols = sum(step(k) for k in range(args.steps))
         torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
         dt = time.perf_counter() - t0
     launches = gfcc.launch_count() - launches0
+    dt, cols = reduce_over_ranks(dist, dt, cols, "cuda")
     line = {
         "metric": "converged G(omega) columns/sec", "value": cols / dt, "unit": "columns/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
@@ -356,7 +393,7 @@ def main():
 
     spec = WORKLOADS[args.workload]
     if spec.get("uneven"):
-        return run_uneven(args, spec, world, rank)
+        return run_uneven(args, spec, world, rank, dist)
     wl = workload(spec["base"])
     problem = wl.problem()
     t0 = time.perf_counter()
@@ -383,16 +420,7 @@ def main():
         ctx.set_option(gfcc.OPT_GUESS, gfcc.GUESS_LEARNED)
 
     def freqs(step):
-        # sweeps: rank r, timed step k takes the window of `per` consecutive grid frequencies starting at
-        # ((k * world + r) * per) mod n_omega; single-frequency steps take grid frequency
-        # ((k * world + r) * per + j) * FREQ_STRIDE mod n_omega.  Warm-up steps (negative k) take the top
-        # end of the grid.
-        if step < 0:
-            return np.array([wl.omegas[(nw + step * per + j) % nw] for j in range(per)])
-        base = (step * world + rank) * per
-        if spec.get("sweep"):
-            return np.array([wl.omegas[(base + j) % nw] for j in range(per)])
-        return np.array([wl.omegas[((base + j) * FREQ_STRIDE) % nw] for j in range(per)])
+        return wl.omegas[step_frequency_indices(step, world, rank, per, nw, bool(spec.get("sweep")))]
 
     iter_log = []
 
@@ -427,13 +455,7 @@ def main():
     dt = ev0.elapsed_time(ev1) / 1e3
     prof = ctx.profile_read()
     ctx.profile(False)
-    total_cols = converged
-    if dist is not None:
-        t = torch.tensor([dt, float(converged)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        dt, total_cols = float(tmax[0]), int(t[1])
+    dt, total_cols = reduce_over_ranks(dist, dt, converged, "cuda")
     value = total_cols / dt
 
     # end to end through the host C ABI: host omegas / orbitals in pinned memory, G read back every step
@@ -450,12 +472,7 @@ def main():
         e2e_cols += int(np.sum(ctx.stats()[2] == 0))
     barrier()
     e2e_dt = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_dt, float(e2e_cols)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        e2e_dt, e2e_cols = float(tmax[0]), int(t[1])
+    e2e_dt, e2e_cols = reduce_over_ranks(dist, e2e_dt, e2e_cols, "cuda")
 
     # roofline of the dominant kernel: the FP64 (DFMA) or BF16 (tcgen05) ring or EA vvvv contraction,
     # or the Arnoldi orthogonalisation, whichever took the most device time inside the timed region
