@@ -47,6 +47,9 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert typed.gfcc_create(0, 4, 4, None, None, None, None, None, ctypes.byref(h)) == gfcc.ERR_ARG
     assert b"o >= 1" in typed.gfcc_last_error()
     assert typed.gfcc_set_option(None, 1, 1.0) == gfcc.ERR_ARG
+    assert typed.gfcc_residual_stats(None, None, None, None) == gfcc.ERR_ARG
+    cnt = ctypes.c_int(0)
+    assert typed.gfcc_refine_stats(None, ctypes.byref(cnt), None) == gfcc.ERR_ARG
     typed.gfcc_destroy(None)
 
 
