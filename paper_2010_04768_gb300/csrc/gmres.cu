@@ -924,12 +924,6 @@ __global__ void rsub_kernel(const double *a, double *y, long long tot) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
     y[t] = a[t] - y[t];
 }
-// x += d (all systems)
-template <typename T>
-__global__ void add_kernel(double *x, const T *d, long long tot) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
-    x[t] += (double)d[t];
-}
 // y = x rounded to FP32
 __global__ void to_f32_kernel(const double *x, float *y, long long tot) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
@@ -1033,6 +1027,11 @@ int Gmres::reset_slots(const int *d_mask) {
 }
 
 int Gmres::refine_residual(int *h_done, double *h_relres) {
+  GFCC_TRY(residual_update());
+  return refine_residual_free(h_done, h_relres);
+}
+
+int Gmres::residual_update() {
   cudaStream_t st = c->stream;
   const long long tot = 2LL * nsys * n;
   const bool emu = c->residual_emulated && (sector == GFCC_SECTOR_IP ? c->eWr.dig : c->eWre.dig) != nullptr;
@@ -1073,14 +1072,14 @@ int Gmres::refine_residual(int *h_done, double *h_relres) {
       c->res_inc++;
       c->res_inc_levels += level;
     }
-    return refine_residual_free(h_done, h_relres);
+    return GFCC_OK;
   }
   have_d = false;
   GFCC_TRY(op_fp64(X, n, R, n));
   rsub_kernel<<<grid1d(tot), 256, 0, st>>>(B0, R, tot);
   GFCC_LAUNCH_CHECK();
   c->res_full++;
-  return refine_residual_free(h_done, h_relres);
+  return GFCC_OK;
 }
 
 int Gmres::refine_residual_free(int *h_done, double *h_relres) {
@@ -1131,6 +1130,7 @@ int Gmres::solve_refined(double tol, double inner_tol, int max_iters, int *h_sta
   if (h_outer)
     for (int s = 0; s < nsys; s++) h_outer[s] = 0;
   // B0 holds the right-hand sides (FP64), X the initial iterate when use_x0
+  have_d = false;
   if (!use_x0) GFCC_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * tot, st));
   GFCC_TRY(mdot(B0, n, 0, 1, B0, n, nrm, -1, 0));
   int *done = kcyc;   // reused: per-system done flags between inner solves
@@ -1139,14 +1139,11 @@ int Gmres::solve_refined(double tol, double inner_tol, int max_iters, int *h_sta
   const int max_outer = 400;
   bool all_done = false;
   for (int outer = 0; outer <= max_outer; outer++) {
-    // FP64-accurate residual r = b - A x
+    // FP64-accurate residual r = b - A x (after a correction: r -= A d, see residual_update)
     if (outer == 0 && !use_x0) {
       GFCC_CUDA(cudaMemcpyAsync(R, B0, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
     } else {
-      GFCC_TRY(op_fp64(X, n, R, n));
-      c->res_full++;
-      rsub_kernel<<<grid1d(tot), TH, 0, st>>>(B0, R, tot);
-      GFCC_LAUNCH_CHECK();
+      GFCC_TRY(residual_update());
     }
     GFCC_TRY(mdot(R, n, 0, 1, R, n, nrm, -1, 0));
     refine_check_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, nrm, NV, b0norm, tol, done, relres);
@@ -1179,10 +1176,11 @@ int Gmres::solve_refined(double tol, double inner_tol, int max_iters, int *h_sta
     GFCC_CUDA(cudaStreamSynchronize(st));
     for (int s = 0; s < nsys; s++) h_iters[s] += it[s];
     if (f32)
-      add_kernel<float><<<grid1d(tot), TH, 0, st>>>(X, reinterpret_cast<const float *>(U), tot);
+      add_keep_kernel<float><<<grid1d(tot), TH, 0, st>>>(X, D, reinterpret_cast<const float *>(U), tot);
     else
-      add_kernel<double><<<grid1d(tot), TH, 0, st>>>(X, U, tot);
+      add_keep_kernel<double><<<grid1d(tot), TH, 0, st>>>(X, D, U, tot);
     GFCC_LAUNCH_CHECK();
+    have_d = true;
   }
   // final state: converged where the FP64 residual met tol; the solution stays in X
   for (int s = 0; s < nsys; s++) h_state[s] = h_done[s] == 1 ? 3 : 4;

@@ -68,6 +68,9 @@ struct Gmres {
   int refine_norms();
   int refine_residual(int *h_done, double *h_relres);
   int refine_residual_free(int *h_done, double *h_relres);   // the checks on R as it is (no operator)
+  // R = B0 - A X (FP64-accurate), or R -= A D at the digit level max|D| / max|X| allows when the
+  // last step left its correction in D (incremental option, digit-plane residuals)
+  int residual_update();
   int refine_correct(const int *h_done, int *h_state, int *h_iters);
   // X[s] = 0 and R[s] = B0[s] for the slots with mask[s] != 0 (device mask)
   int reset_slots(const int *d_mask);
