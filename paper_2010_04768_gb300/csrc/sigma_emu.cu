@@ -115,8 +115,8 @@ __global__ void digits_k2_kernel(const double *x, long long ldx, int C2, int o, 
   }
 }
 
-// digit planes of the r1 part: rk[c][o2v + m] (and the zero padding of rk up to ldk), r1b[c][m]
-// (zero up to ld1); exponents of both operands
+// digit planes of the r1 part: rk[c][o2v + m] (and the zero padding of rk up to ldk) and, when ld1 > 0,
+// r1b[c][m] (zero up to ld1); exponents of the operands written
 __global__ void digits_k1_kernel(const double *x, long long ldx, int C2, int o, int v, const int *ec, int S,
                                  long long ldk, __nv_bfloat16 *digk, int *rexpk, long long ld1, __nv_bfloat16 *dig1,
                                  int *rexp1) {
@@ -133,7 +133,7 @@ __global__ void digits_k1_kernel(const double *x, long long ldx, int C2, int o, 
     if (q < ld1) put_digits(val, ec[c], S, dig1 + (long long)c * ld1 + q, plane1);
     if (q == 0) {
       rexpk[c] = ec[c];
-      rexp1[c] = ec[c];
+      if (rexp1 != nullptr) rexp1[c] = ec[c];
     }
   }
 }
@@ -187,8 +187,8 @@ __global__ void digits_ea_vvvv_kernel(const double *x, long long ldx, int C2, in
   }
 }
 
-// digit planes of rk[c][(m,x,y)] = y2[m,y,x], rk[c][o v v + e] = y1[e] (zero padding to ldk), and
-// r1[c][e] = y1[e] (zero padding to ld1); exponents of both operands
+// digit planes of rk[c][(m,x,y)] = y2[m,y,x], rk[c][o v v + e] = y1[e] (zero padding to ldk), and,
+// when ld1 > 0, r1[c][e] = y1[e] (zero padding to ld1); exponents of the operands written
 __global__ void digits_ea_k_kernel(const double *x, long long ldx, int C2, int o, int v, long long Pv, const int *ec,
                                    int S, long long ldk, __nv_bfloat16 *digk, int *rexpk, long long ld1,
                                    __nv_bfloat16 *dig1, int *rexp1) {
@@ -216,13 +216,13 @@ __global__ void digits_ea_k_kernel(const double *x, long long ldx, int C2, int o
     }
     if (k == 0) {
       rexpk[c] = ec[c];
-      rexp1[c] = ec[c];
+      if (rexp1 != nullptr) rexp1[c] = ec[c];
     }
   }
 }
 
 struct EmuWorkEA {
-  EmuOperand r2e, r2p, rk, r1, Zo;
+  EmuOperand r2e, r2p, rk, Zo;
   int *ec;
   double *T, *Qp, *U, *S1, *Z, *Zt;
   void *gw;
@@ -250,7 +250,6 @@ EmuWorkEA emu_layout_ea(const gfcc_ctx *c, int nsub, void *base) {
   op(w.r2e, v * C2, ov);
   op(w.r2p, o * C2, std::max<long long>(Pv, 1));
   op(w.rk, C2, ov2 + v);
-  op(w.r1, C2, v);
   op(w.Zo, C2, v + o);
   w.ec = reinterpret_cast<int *>(take(C2 * 4));
   w.T = reinterpret_cast<double *>(take(ov * v * C2 * 8));
@@ -271,7 +270,7 @@ EmuWorkEA emu_layout_ea(const gfcc_ctx *c, int nsub, void *base) {
 }
 
 struct EmuWork {
-  EmuOperand r2b, r2o, rk, r1b, Zo;
+  EmuOperand r2b, r2o, rk, Zo;
   int *ec;
   double *T, *Q, *U, *S1, *Z, *Zt;
   void *gw;     // emu_gemm workspace
@@ -299,7 +298,6 @@ EmuWork emu_layout(const gfcc_ctx *c, int nsub, void *base) {
   op(w.r2b, o * C2, o * v);
   op(w.r2o, v * C2, o * o);
   op(w.rk, C2, o2v + o);
-  op(w.r1b, C2, o);
   op(w.Zo, C2, o + v);
   w.ec = reinterpret_cast<int *>(take(C2 * 4));
   w.T = reinterpret_cast<double *>(take(o * v * o * C2 * 8));
@@ -362,8 +360,9 @@ int apply_ip_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_do
     digits_k2_kernel<<<dim3(cdiv(o, 32), cdiv(v, 32), o * C2), dim3(32, 8), 0, st>>>(x, b.ldx, C2, (int)o, (int)v,
                                                                                     w.ec, S, w.rk.ld, w.rk.dig);
     GFCC_LAUNCH_CHECK();
-    digits_k1_kernel<<<grid1d((long long)C2 * std::max(w.rk.ld - o2v, w.r1b.ld)), 256, 0, st>>>(
-        x, b.ldx, C2, (int)o, (int)v, w.ec, S, w.rk.ld, w.rk.dig, w.rk.exp2, w.r1b.ld, w.r1b.dig, w.r1b.exp2);
+    // (the 1h block also enters [r1 | Z] of the concatenated ovoo / three-body product, sliced there)
+    digits_k1_kernel<<<grid1d((long long)C2 * (w.rk.ld - o2v)), 256, 0, st>>>(
+        x, b.ldx, C2, (int)o, (int)v, w.ec, S, w.rk.ld, w.rk.dig, w.rk.exp2, 0, nullptr, nullptr);
     GFCC_LAUNCH_CHECK();
     }
     {
@@ -425,8 +424,9 @@ int apply_ea_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_do
       digits_ea_vvvv_kernel<<<grid1d(w.r2p.rows * w.r2p.ld), 256, 0, st>>>(x, b.ldx, C2, (int)o, (int)v, Pv, w.ec, S,
                                                                             w.r2p.ld, w.r2p.dig, w.r2p.exp2);
       GFCC_LAUNCH_CHECK();
-      digits_ea_k_kernel<<<grid1d((long long)C2 * std::max(w.rk.ld, w.r1.ld)), 256, 0, st>>>(
-          x, b.ldx, C2, (int)o, (int)v, Pv, w.ec, S, w.rk.ld, w.rk.dig, w.rk.exp2, w.r1.ld, w.r1.dig, w.r1.exp2);
+      // (the 1p block also enters [y1 | Z] of the concatenated product, sliced there)
+      digits_ea_k_kernel<<<grid1d((long long)C2 * w.rk.ld), 256, 0, st>>>(
+          x, b.ldx, C2, (int)o, (int)v, Pv, w.ec, S, w.rk.ld, w.rk.dig, w.rk.exp2, 0, nullptr, nullptr);
       GFCC_LAUNCH_CHECK();
     }
     {
