@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -89,7 +90,9 @@ class Clocks:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # the raw samples: GFCC_CLOCKS_DIR if set, else the temporary directory
+        self.path = os.path.join(os.environ.get("GFCC_CLOCKS_DIR") or tempfile.gettempdir(),
+                                 f"clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         try:
