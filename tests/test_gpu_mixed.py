@@ -178,6 +178,29 @@ def test_incremental_residual_matches_full_residuals(sector):
             assert np.linalg.norm(Gf[w, a] - G64[w, a]) <= 1e-6 * ref
 
 
+def test_full_size_sampled_row_matches_oracle():
+    """Full size in the bench's launch configuration: the medium workload (o=40 v=200 L=800), IP,
+    mixed precision, one frequency x the 40 orbitals of the list in one batch.  The G row of one
+    sampled orbital (the bench's CPU sample: grid frequency 17, first orbital) against the oracle's
+    preconditioned GMRES for that (omega, p) and the oracle's left vectors (about two minutes of CPU)."""
+    from oracle.gfcc_ref import gmres
+    wl = workload("medium")
+    pr = wl.problem()
+    om = wl.omegas[17]
+    g = gfcc.GFCC(pr, sectors="IP", precision="mixed")
+    G, code = g.solve(np.array([om]), wl.eta, wl.orbitals, 1e-10)
+    it, rr, st = g.stats()
+    g.close()
+    assert code in (gfcc.OK, gfcc.WARN_NOT_CONVERGED) and rr[0] <= 1e-9
+    orc = GFCCOracle(pr.fock, pr.chol, pr.t1, pr.t2, o=wl.o, sectors=("IP",))
+    p = int(wl.orbitals[0])
+    D = (om - 1j * wl.eta) + orc.ip_diag()
+    x, its, rel, ok = gmres(orc.ip_apply(om, wl.eta), orc.ip_rhs(p), 1e-10, 30, 50, diag=D)
+    assert ok
+    row = np.stack([orc.ip_left(int(q)) for q in wl.orbitals]) @ x
+    assert np.linalg.norm(G[0, 0] - row) <= 1e-6 * np.linalg.norm(row)
+
+
 @pytest.mark.parametrize("krylov", [32, 64])
 def test_inner_krylov_precision_does_not_change_the_result(krylov):
     # the inner GMRES of the refinement runs on FP32 (default) or FP64 Krylov vectors; the FP64
