@@ -3,7 +3,13 @@
 
 One step = one batch of (omega, p) linear systems of eq. xplin solved by GMRES to
 tol through the C ABI, including right-hand sides, left vectors and the G overlaps
-(every row of the hot path after the one-time setup of gfcc_create).
+(every row of the hot path after the one-time setup of gfcc_create).  The default
+workload is the C60-shaped one (o=90 v=450 L=1800, IP, the 30 highest occupied
+orbitals, eta 0.005, tol 1e-8): mixed precision (BF16 tensor-core sigma products
+inside FP64-accurate iterative refinement), one frequency x 30 orbitals per step.
+Beside it the line carries the plain FP64 GPU path on a sample of the same systems
+(its columns/s and the mixed path's multiple of it), a check of the mixed G rows
+against those FP64 rows, and the CPU oracle's rate.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl gb300|reference]
 
@@ -59,15 +65,26 @@ WORKLOADS = {
     # C60-shaped: o=90 v=450 L=1800, the 30 highest occupied orbitals, 128 frequencies in [-1.0, -0.3]
     "c60-ip-mixed": dict(base="c60", sector="IP", precision="mixed", per_step=1),
     "c60-ip-fp64": dict(base="c60", sector="IP", precision="fp64", per_step=1),
+    # learned initial guesses on the C60-shaped problem (256 frequencies in [-1.0, -0.3]: spacing 0.55
+    # eta): each step solves 8 consecutive grid frequencies x 30 orbitals in one call, each system
+    # started from the guess named; the model is trained beforehand on two other seeds of the same shape
+    "c60x256-ip-mixed-sweep": dict(base="c60x256", sector="IP", precision="mixed", per_step=8, sweep=True),
+    "c60x256-ip-mixed-sweep-minres": dict(base="c60x256", sector="IP", precision="mixed", per_step=8, sweep=True,
+                                          guess="minres"),
+    "c60x256-ip-mixed-sweep-learned": dict(base="c60x256", sector="IP", precision="mixed", per_step=8, sweep=True,
+                                           guess="learned"),
 }
-DEFAULT_WORKLOAD = "medium-ipea-mixed"
+DEFAULT_WORKLOAD = "c60-ip-mixed"
+E2E_STEPS = 5        # steps of the end-to-end (host API) measurement: min(steps, E2E_STEPS)
+PLAIN_STEP = 1       # plain FP64 leg: the frequency of this timed step (the step's own G rows compared)
+ROW_TOL = 1e-6       # mixed vs plain FP64 G rows (relative 2-norm per row)
 FREQ_STRIDE = 17   # timed step k takes grid frequency (k * 17) mod n_omega (coprime with 64: covers the grid)
 INNER_RESTART = 60   # restart length of the inner GMRES of the mixed-precision refinement (library default)
-# DRAM traffic of one digit-pair GEMM launch (umma_bf16_gemm_kernel<256, 0>) at the IP ring shape
-# M = K = 8000, N = 3200, from one ncu --set full capture (profiles/umma_digit_pairs_ring_ip_medium.md;
-# mean of two launches); null once that kernel changes
-RING_EMU_TRAFFIC = {"traffic": 621.7e6, "traffic_unit": "DRAM bytes per digit-pair GEMM launch at M=K=8000, "
-                    "N=3200 (ncu --set full)", "algorithmic_bytes_per_launch": [281e6, 383e6]}
+# DRAM traffic of the tensor-core GEMM launches from ncu captures of the current kernels (profiles/),
+# keyed by roofline phase: {"traffic": DRAM bytes per launch, "algorithmic_bytes": bytes one launch
+# must move (operands once, output once), "case": the captured shape}.  A phase without a capture of
+# its current kernel reports traffic null.
+NCU_TRAFFIC = {}
 
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 flops x max clock
 
@@ -185,6 +202,67 @@ def sectors_of(spec):
     return ("IP", "EA") if spec["sector"] in ("IP+EA", "BOTH") else (spec["sector"],)
 
 
+class MediumOracle:
+    """The CPU oracle as it stands on the medium workload's IP sector (o=40 v=200 L=800): the
+    stand-in for the C60-shaped workload, whose dense oracle intermediates (the ovvv block alone is
+    66 GB) do not fit the host.  column(c) solves one (omega, p) IP system with the oracle's GMRES
+    (same eta / tol / restart / preconditioner as the workload) and forms its G row; times are
+    scaled to the C60-shaped size by the ratio of the IP sigma flops and, when known, of the FP64
+    GMRES iteration counts."""
+
+    def __init__(self):
+        from oracle.gfcc_ref import GFCCOracle
+        self.med = workload("medium")
+        pr = self.med.problem()
+        t0 = time.perf_counter()
+        self.orc = GFCCOracle(pr.fock, pr.chol, pr.t1, pr.t2, o=self.med.o, sectors=("IP",))
+        self.t_setup = time.perf_counter() - t0
+        self.omega = self.med.omegas[FREQ_STRIDE % self.med.omegas.size]
+
+    def warm(self):
+        """One sigma product (a bounded warm-up of the oracle's code path)."""
+        self.orc.ip_apply(self.omega, self.med.eta)(self.orc.ip_rhs(int(self.med.orbitals[0])).astype(complex))
+
+    def column(self, c):
+        from oracle.gfcc_ref import gmres
+        med, orc = self.med, self.orc
+        p = int(med.orbitals[c % med.orbitals.size])
+        t0 = time.perf_counter()
+        D = (self.omega - 1j * med.eta) + orc.ip_diag()
+        x, its, rel, ok = gmres(orc.ip_apply(self.omega, med.eta), orc.ip_rhs(p), med.tol, med.restart, 50, diag=D)
+        np.stack([orc.ip_left(int(q)) for q in med.orbitals]) @ x
+        return time.perf_counter() - t0, its, bool(ok)
+
+    def extrapolate(self, wl, t_cols, its_cols, its_target=None):
+        t_col = float(np.mean(t_cols))
+        its_med = float(np.mean(its_cols))
+        scale = ip_sigma_flops(wl.o, wl.v) / ip_sigma_flops(self.med.o, self.med.v)
+        it_scale = (its_target / its_med) if its_target else 1.0
+        t_est = t_col * scale * it_scale
+        sample = (f"extrapolated: {len(t_cols)} IP column(s) of the medium workload (o=40 v=200 L=800; omega "
+                  f"{self.omega:.4f}, eta {self.med.eta}, tol {self.med.tol}, GMRES({self.med.restart}), diagonal "
+                  f"preconditioner) solved by the numpy FP64 oracle, {t_col:.2f} s per column ({its_med:.0f} "
+                  f"iterations; oracle setup {self.t_setup:.1f} s excluded like gfcc_create), scaled by the IP "
+                  f"sigma flop ratio {scale:.1f} (o={wl.o} v={wl.v} vs o=40 v=200)" +
+                  (f" and the iteration ratio {its_target:.1f} / {its_med:.0f} (FP64 GMRES iterations of the "
+                   f"C60-shaped systems on the plain FP64 GPU path)" if its_target else
+                   " (iteration count taken equal)") +
+                  "; the oracle cannot hold the C60-shaped intermediates")
+        return {"value": 1.0 / t_est, "unit": "columns/s", "cores": os.cpu_count(), "kind": "oracle",
+                "sample": sample, "seconds": t_est}
+
+
+def cpu_baseline_extrapolated(wl, its_target=None, columns=1):
+    """cpu_baseline for the C60-shaped workload: MediumOracle columns scaled to the C60 size."""
+    mo = MediumOracle()
+    t_cols, its_cols = [], []
+    for c in range(columns):
+        t, its, ok = mo.column(c)
+        t_cols.append(t)
+        its_cols.append(its)
+    return mo.extrapolate(wl, t_cols, its_cols, its_target)
+
+
 def cpu_baseline(wl, spec, problem, max_columns=1):
     """The CPU oracle as it stands, on a bounded sample of the same workload: `max_columns` IP columns
     solved by its GMRES (same tolerance, restart and preconditioner); for the EA sector, whose oracle
@@ -233,15 +311,22 @@ def cpu_baseline(wl, spec, problem, max_columns=1):
 
 def train_guess_model(gfcc, spec, wl, seed=1, n_freq=24):
     """Train the learned-guess model on the method's own converged solutions of another problem of
-    the same shape (seed `seed`): a zero-guess sweep over n_freq spread frequencies with the solutions
-    kept, 3 samples per system, 1500 Adam steps.  Excluded from the timed region like gfcc_create."""
+    the same shape (seed `seed`): a zero-guess sweep over n_freq frequencies with the solutions kept,
+    3 samples per system, 1500 Adam steps.  The frequencies are spread over the grid, or, on grids
+    finer than the broadening (spacing < eta), n_freq consecutive grid frequencies from a quarter of
+    the way in, so that the neighbour distances of the training samples are those of a sweep.
+    Excluded from the timed region like gfcc_create."""
     from paper_2010_04768_gb300.synthetic import make_problem, mlp_init_params
     t0 = time.perf_counter()
     pr = make_problem(wl.o, wl.v, wl.L, seed=seed)
     g = gfcc.GFCC(pr, sectors=spec["sector"], precision=spec["precision"])
     g.set_option(gfcc.OPT_RESTART, wl.restart)
     g.set_option(gfcc.OPT_KEEP_SOLUTIONS, 1)
-    om = wl.omegas[np.linspace(0, wl.omegas.size - 1, n_freq).round().astype(int)]
+    if wl.omegas[1] - wl.omegas[0] < wl.eta:
+        q = wl.omegas.size // 4
+        om = wl.omegas[q:q + n_freq]
+    else:
+        om = wl.omegas[np.linspace(0, wl.omegas.size - 1, n_freq).round().astype(int)]
     g.solve(om, wl.eta, wl.orbitals, wl.tol)
     model = gfcc.MLP(mlp_init_params(256, seed), 256, gfcc.MLP_FP32)
     added = model.collect(g, samples_per_system=3, seed=seed)
@@ -255,7 +340,10 @@ def train_guess_model(gfcc, spec, wl, seed=1, n_freq=24):
 
 
 def run_reference(args, world, rank):
-    """--impl reference: the CPU oracle (the baseline of this hot path) on rank 0 only."""
+    """--impl reference: the CPU oracle (the baseline of this hot path) on rank 0 only.  Each step
+    is a bounded sample of the workload: one (omega, p) column solved by the oracle (for the
+    C60-shaped workload: one medium-workload IP column, extrapolated; see MediumOracle); each
+    warm-up step is one oracle sigma product."""
     if rank != 0:
         return 0
     spec = WORKLOADS[args.workload]
@@ -264,12 +352,23 @@ def run_reference(args, world, rank):
                           "reference arm on a single-molecule workload"}), flush=True)
         return 0
     wl = workload(spec["base"])
-    problem = wl.problem()
-    for _ in range(args.warmup):
-        pass   # the oracle has no warm-up state; its setup is excluded from the timing
-    res = cpu_baseline(wl, spec, problem, max_columns=max(1, args.steps))
+    if wl.name == "c60":
+        mo = MediumOracle()
+        for _ in range(args.warmup):
+            mo.warm()
+        t_cols, its_cols = [], []
+        for k in range(args.steps):
+            t, its, ok = mo.column(k)
+            t_cols.append(t)
+            its_cols.append(its)
+        res = mo.extrapolate(wl, t_cols, its_cols)
+        seconds = res["seconds"] * args.steps
+    else:
+        problem = wl.problem()
+        res = cpu_baseline(wl, spec, problem, max_columns=max(1, args.steps))
+        seconds = res["seconds"]
     line = {"metric": "converged G(omega) columns/sec", "value": res["value"], "unit": "columns/s", "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * res["seconds"] / max(1, args.steps),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * seconds / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference", "config": config_of(spec, wl, 1),
             "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")},
@@ -376,6 +475,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain-fp64", action="store_true")
+    ap.add_argument("--no-mor", action="store_true")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -462,56 +563,39 @@ def main():
     value = total_cols / dt
 
     # end to end through the host C ABI: host omegas / orbitals in pinned memory, G read back every step
+    # (the first min(steps, E2E_STEPS) timed steps' frequencies)
+    e2e_steps = max(1, min(args.steps, E2E_STEPS))
     om_pin = torch.empty(per, dtype=torch.float64, pin_memory=True)
     orb_pin = torch.tensor(wl.orbitals, dtype=torch.int32).pin_memory()
     G_pin = torch.empty((per, no, no, 2), dtype=torch.float64, pin_memory=True)
+    G_e2e = []
     barrier()
     t0 = time.perf_counter()
     e2e_cols = 0
-    for k in range(args.steps):
+    for k in range(e2e_steps):
         om_pin.numpy()[:] = freqs(k)
         G, code = ctx.solve(om_pin.numpy(), wl.eta, orb_pin.numpy(), wl.tol)
         G_pin.numpy().reshape(-1)[:] = G.view(np.float64).reshape(-1)
+        if k <= PLAIN_STEP:
+            G_e2e.append(G.copy())
         e2e_cols += int(np.sum(ctx.stats()[2] == 0))
     barrier()
     e2e_dt = time.perf_counter() - t0
     e2e_dt, e2e_cols = reduce_over_ranks(dist, e2e_dt, e2e_cols, "cuda")
 
-    # roofline of the dominant kernel: the FP64 (DFMA) or BF16 (tcgen05) ring or EA vvvv contraction,
-    # or the Arnoldi orthogonalisation, whichever took the most device time inside the timed region
+    # plain FP64 GPU path on a sample of the same systems (mixed workloads only): the rows of PLAIN_SAMPLE
+    # orbitals of the list at the frequency of timed step 0, solved by FP64 GMRES with the FP64 sigma
+    # product on the same context (gfcc_solve_block: rows over the sample, columns over the whole list)
+    plain = row_check = None
+    ks = min(PLAIN_STEP, len(G_e2e) - 1)
+    if spec["precision"] == "mixed" and rank == 0 and not args.no_plain_fp64:
+        plain, row_check = plain_fp64_leg(gfcc, ctx, wl, freqs(ks)[:1], G_e2e[ks][:1], stream)
+    mor = None
+    if rank == 0 and not args.no_mor and len(sectors_of(spec)) == 1 and not spec.get("sweep"):
+        mor = mor_leg(gfcc, ctx, wl, spec, freqs(0)[0], G_e2e[0][0])
+
     peaks = measured_peaks()
-    rf = {}
-    for ph, bound, peak, unit, kernel in (
-            ("ring", "alu", FP64_PEAK_TFLOPS, "TFLOP/s", "contract_f64_kernel (FP64 ring contraction)"),
-            ("ring_bf16", "tensor", peaks.get("bf16_tflops_sustained", 1727.1), "TFLOP/s",
-             "umma_bf16_gemm_kernel (BF16 ring contraction)"),
-            ("ring_emu", "tensor", peaks.get("bf16_tflops_sustained", 1727.1), "TFLOP/s",
-             "umma_bf16_gemm_kernel (digit-pair products of the FP64-accurate residual ring contraction)"),
-            ("vvvv",) + (("alu", FP64_PEAK_TFLOPS, "TFLOP/s", "contract_f64_kernel (FP64 EA vvvv contraction)")
-                         if spec["precision"] == "fp64" else
-                         ("tensor", peaks.get("bf16_tflops_sustained", 1727.1), "TFLOP/s",
-                          "umma_bf16_gemm_kernel (BF16 EA vvvv contraction)"))):
-        ms, n_l, fl = prof[ph]
-        if ms > 0:
-            ach = fl / (ms / 1e3) / 1e12
-            rf[ph] = {"bound": bound, "kernel": kernel, "achieved": ach, "peak": peak, "unit": unit,
-                      "frac": ach / peak, "traffic": None, "launches": n_l, "ms_total": ms,
-                      **(RING_EMU_TRAFFIC if ph == "ring_emu" else {}),
-                      "peak_note": ("FP64 FMA units: 152 SMs x 2 DFMA/clk x 2070 MHz (derived); cuBLAS DGEMM "
-                                    "measured 1.10 TFLOP/s on this pool") if bound == "alu" else
-                                   "bf16_tflops_sustained of measured (kernel timed inside a long step); the "
-                                   "achieved figure counts the tensor-core work of the launches (all digit "
-                                   "pairs for the residual)"}
-    # Arnoldi orthogonalisation (HBM): algorithmic bytes of one classical Gram-Schmidt pass per step
-    ms, n_l, nbytes = prof["arnoldi"]
-    if ms > 0:
-        ach = nbytes / (ms / 1e3) / 1e9
-        hbm = peaks.get("hbm_gbs", 6761.6)
-        rf["arnoldi"] = {"bound": "hbm", "kernel": "cgs_dots_kernel + cgs_update_norm_kernel (+ vscale) of the "
-                         "Arnoldi step", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                         "traffic": None, "launches": n_l, "ms_total": ms,
-                         "peak_note": "hbm_gbs of measured; algorithmic bytes = (2(k+1) + 5) vectors x n x "
-                                      "bytes per complex element per system in cycle at Arnoldi step k"}
+    rf = roofline_entries(prof, spec, peaks)
     dominant = max(rf, key=lambda k: rf[k]["ms_total"]) if rf else None
     # sigma TFLOP/s: algorithmic flops of every complex sigma product (inner BF16, FP64 and the
     # FP64-accurate residuals) at F_IP / F_EA each, over the device time of the sigma products
@@ -527,7 +611,8 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if spec["precision"] == "fp64" else "bf16+f64",
         "data": "synthetic", "config": config_of(spec, wl, world),
         "e2e": {"value": e2e_cols / e2e_dt, "unit": "columns/s", "h2d_bytes_per_step": 8 * per + 4 * no,
-                "d2h_bytes_per_step": 16 * per * no * no},
+                "d2h_bytes_per_step": 16 * per * no * no, "steps": e2e_steps,
+                "note": f"the first {e2e_steps} timed steps' frequencies through gfcc_solve (host arrays in and out)"},
         "roofline": rf.get(dominant),
         "roofline_other": {k: v for k, v in rf.items() if k != dominant},
         "sigma_tflops": sigma_tflops,
@@ -542,9 +627,24 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
+    # device time of the solve calls inside the timed phases (sigma products, Arnoldi, least squares,
+    # right-hand sides / left vectors / overlaps, guesses); the rest is launch and host-read gaps
+    inside = sum(prof[k][0] for k in ("sigma", "arnoldi", "lsq", "overlap", "guess"))
+    if prof["solve"][0] > 0:
+        line["solve_time_in_phases"] = {"solve_ms": prof["solve"][0], "phases_ms": inside,
+                                        "fraction": inside / prof["solve"][0]}
+    if mor is not None:
+        line["mor"] = mor
+    if plain is not None:
+        line["plain_fp64"] = plain
+        line["vs_plain_fp64"] = value / plain["value"] if plain["value"] else None
+        line["sampled_row_check"] = row_check
     if not args.no_cpu_baseline:
         try:
-            cb = cpu_baseline(wl, spec, problem, max_columns=1)
+            if wl.name == "c60":
+                cb = cpu_baseline_extrapolated(wl, plain["iterations_per_column"] if plain else None)
+            else:
+                cb = cpu_baseline(wl, spec, problem, max_columns=1)
             line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
         except Exception as e:  # report, do not hide, a failing baseline
             line["cpu_baseline"] = {"value": None, "error": repr(e)}
@@ -553,6 +653,140 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def plain_fp64_leg(gfcc, ctx, wl, om, G_mixed, stream):
+    """Plain FP64 GPU path (FP64 sigma products, FP64 GMRES, same preconditioner, restart and tol) on
+    one row of G, the highest orbital of the list (the HOMO for the valence list), at frequency om
+    (a timed step's), on the mixed context's FP64 operators; its columns/s, and the relative 2-norm
+    error of the mixed G row (G_mixed[0][row]) against it.  (The FP64 path runs at the rate of the
+    FP64 units, about 0.9 s per sigma product of one C60-shaped system, so a sample of one system keeps
+    this leg to about a minute at a frequency of average difficulty.)"""
+    import torch
+    no = int(wl.orbitals.size)
+    rows = [no - 1]
+    P = wl.orbitals[rows]
+    ctx.set_option(gfcc.OPT_PRECISION, gfcc.PREC_FP64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    G64, code = ctx.solve_block(om, wl.eta, P, wl.orbitals, wl.tol)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    it, rr, st = ctx.stats()
+    ctx.set_option(gfcc.OPT_PRECISION, gfcc.PREC_MIXED_BF16)
+    cols = int(np.sum(st == 0))
+    errs = [float(np.linalg.norm(G_mixed[0, r] - G64[0, a]) / np.linalg.norm(G64[0, a])) for a, r in enumerate(rows)]
+    plain = {"value": cols / dt, "unit": "columns/s", "columns": cols, "seconds": dt,
+             "iterations_per_column": float(np.mean(it)), "max_relres": float(np.max(rr)),
+             "sample": f"{len(rows)} (omega, p) IP system(s) of the same workload (omega of timed step {PLAIN_STEP} = "
+                       f"{om[0]:.5f}, "
+                       f"orbitals {P.tolist()}) with their G rows over all {no} orbitals, solved in one call "
+                       f"(gfcc_solve_block) by FP64 GMRES({wl.restart}) with FP64 sigma products (DFMA "
+                       f"contractions), same tol / preconditioner, on the same context; host-timed"}
+    check = {"rows": P.tolist(), "omega": float(om[0]), "max_rel_err": max(errs), "rel_err": errs, "tol": ROW_TOL,
+             "passed": bool(max(errs) <= ROW_TOL and cols == len(rows))}
+    return plain, check
+
+
+MOR_SAMPLES = 3       # model-order reduction leg: frequencies whose solutions span the subspace
+MOR_GRID = 1000       # model G evaluated on this many frequencies over the workload's window
+
+
+def mor_leg(gfcc, ctx, wl, spec, om0, G0):
+    """Model-order reduction (eq. model) on the workload: the full systems of MOR_SAMPLES frequencies of
+    the grid (its two ends and middle, all orbitals) span the subspace; the model G over MOR_GRID
+    frequencies of the window; its accuracy at the sampled frequencies (interpolation) and at the
+    frequency of timed step 0 (not sampled) against that step's full solve."""
+    import torch
+    sector = sectors_of(spec)[0]
+    samp = np.array([wl.omegas[0], wl.omegas[wl.omegas.size // 2], wl.omegas[-1]])
+    if np.any(np.abs(samp - om0) < 1e-12):
+        samp = samp + 0.5 * (wl.omegas[1] - wl.omegas[0])
+    mor = gfcc.MOR(ctx, sector)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Gs, code = mor.expand(samp, wl.eta, wl.orbitals, wl.tol)
+    torch.cuda.synchronize()
+    t_expand = time.perf_counter() - t0
+    grid = np.linspace(wl.omegas[0], wl.omegas[-1], MOR_GRID)
+    t0 = time.perf_counter()
+    Gm = mor.green(grid, wl.eta, wl.orbitals)
+    torch.cuda.synchronize()
+    t_model = time.perf_counter() - t0
+    Gi = mor.green(samp, wl.eta, wl.orbitals)
+    G0m = mor.green(np.array([om0]), wl.eta, wl.orbitals)[0]
+    m = mor.dim()
+    mor.close()
+    no = int(wl.orbitals.size)
+    return {"subspace_dim": m, "sampled_omegas": samp.tolist(), "expand_s": t_expand, "expand_code": int(code),
+            "grid_points": MOR_GRID, "model_s": t_model, "model_columns_per_s": MOR_GRID * no / t_model,
+            "interpolation_max_rel_err": float(np.abs(Gi - Gs).max() / np.abs(Gs).max()),
+            "unsampled_omega": float(om0),
+            "unsampled_max_rel_err": float(np.abs(G0m - G0).max() / np.abs(G0).max()),
+            "note": "expand = full solves of the sampled frequencies + Gram-Schmidt + projection (sigma products "
+                    "of the basis); model columns = G rows of the grid's (omega, p) from the dense model "
+                    "solves; errors relative to max |G|"}
+
+
+# roofline candidates: (phase, bound, kernel label, peak key); the FP64 ring phase runs on the DFMA
+# units, the tensor-core phases against the measured sustained BF16 rate (kernels timed inside a long
+# step), the HBM phases against the measured copy bandwidth
+def roofline_entries(prof, spec, peaks):
+    bf16 = peaks.get("bf16_tflops_sustained", 1727.1)
+    hbm = peaks.get("hbm_gbs", 6761.6)
+    fp64 = spec["precision"] == "fp64"
+    cands = [
+        ("ring", "alu", "contract_f64_kernel (FP64 ring contraction)"),
+        ("vvvv", "alu" if fp64 else "tensor", "contract_f64_kernel (FP64 EA vvvv contraction)" if fp64 else
+         "umma_bf16_gemm_kernel (BF16 EA vvvv contraction)"),
+        ("ring_bf16", "tensor", "umma_bf16_gemm_kernel (BF16 ring contraction of the inner sigma)"),
+        ("bf16_other", "tensor", "umma_bf16_gemm_kernel + reduce_splits_kernel (the other BF16 products of the "
+                                 "inner sigma: oooo, three-body, 1h row)"),
+        ("ring_emu", "tensor", "umma_bf16_gemm_kernel / umma_emu_kernel + combine_int_kernel + finalize_kernel "
+                               "(FP64-accurate ring contraction of the refinement residual from BF16 digit planes)"),
+        ("emu_other", "tensor", "umma_emu_kernel / umma_bf16_gemm_kernel + digit slicing (the other FP64-accurate "
+                                "products of the residual: oooo / vvvv, three-body, 1h / 1p row)"),
+        ("unpack", "hbm", "unpack_ip_kernel / unpack_ea_tile_kernel / digit kernels (packed vectors into the "
+                          "contraction layouts)"),
+        ("epilogue", "hbm", "epi::ip2_kernel / epi::ea2_kernel (sigma epilogues)"),
+        ("arnoldi", "hbm", "cgs_dots_kernel + cgs_update_norm_kernel (+ vscale) of the Arnoldi step"),
+    ]
+    rf = {}
+    for ph, bound, kernel in cands:
+        ms, n_l, work = prof[ph]
+        if ms <= 0:
+            continue
+        if bound == "hbm":
+            if ph == "unpack":
+                continue   # no algorithmic byte count is kept for this phase; its time shows in phases_ms
+            ach, peak, unit = work / (ms / 1e3) / 1e9, hbm, "GB/s"
+            note = "hbm_gbs of measured; achieved = algorithmic bytes / device time"
+        elif bound == "alu":
+            ach, peak, unit = work / (ms / 1e3) / 1e12, FP64_PEAK_TFLOPS, "TFLOP/s"
+            note = ("FP64 FMA units: 152 SMs x 2 DFMA/clk x 2070 MHz (derived); cuBLAS DGEMM measured 1.10 TFLOP/s "
+                    "on this pool")
+        else:
+            ach, peak, unit = work / (ms / 1e3) / 1e12, bf16, "TFLOP/s"
+            note = "bf16_tflops_sustained of measured (kernels timed inside a long step)"
+        e = {"bound": bound, "kernel": kernel, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+             "traffic": None, "launches": n_l, "ms_total": ms, "peak_note": note}
+        if ph in ("ring_emu", "emu_other"):
+            e["peak_note"] += ("; achieved counts the method's work, one FP64 product per FP64-accurate "
+                               "contraction (2 M N K), not the digit-pair products that evaluate it")
+        if ph == "ring_emu":
+            ms_w, _, work_w = prof["ring_emu_work"]
+            if ms_w > 0:
+                rate = work_w / (ms_w / 1e3) / 1e12
+                e["emulation_rate"] = {"achieved": rate, "unit": "TFLOP/s", "frac": rate / bf16,
+                                       "pairs_per_product": work_w / work if work > 0 else None,
+                                       "note": "BF16 tensor-core work of all digit pairs / device time"}
+        tr = NCU_TRAFFIC.get(ph)
+        if tr is not None:
+            e["traffic"] = tr["traffic"]
+            e["traffic_ratio"] = tr["traffic"] / tr["algorithmic_bytes"]
+            e["traffic_case"] = tr["case"]
+        rf[ph] = e
+    return rf
 
 
 if __name__ == "__main__":

@@ -70,7 +70,9 @@ extern "C" {
                                      digit planes on the tensor cores, 0 the FP64 (DFMA) sigma          */
 #define GFCC_OPT_INNER_CYCLES 9   /* mixed precision: GMRES restart cycles per refinement step; default 1 */
 #define GFCC_OPT_EMU_LEVEL  10    /* digit pairs i + j <= level in the FP64-accurate products (8 digits of
-                                     6 bits per operand); default 9                                      */
+                                     6 bits per operand, 2 <= level <= 16); default 9.  The products
+                                     evaluate the operator's couplings; its Fock-like diagonal is exact
+                                     in FP64                                                            */
 #define GFCC_OPT_GUESS      11    /* GFCC_GUESS_*: initial iterate of each GMRES solve; default ZERO     */
 #define GFCC_OPT_KEEP_SOLUTIONS 12 /* 1: keep the converged solutions of the last sector solved after
                                      gfcc_solve (for gfcc_mlp_collect); default 0                        */
@@ -93,6 +95,21 @@ extern "C" {
                                      correction d, its product taking only the digit levels that the
                                      ratio max|d| / max|x| leaves significant (at most the error of the
                                      full product A x); 0: every residual is b - A x at the full level */
+
+/* Process-wide option keys (gfcc_set_process_option; AUTOTUNE and EMU_FUSED_N above are also
+ * accepted there). */
+#define GFCC_OPT_SETUP_EMULATE_FLOPS 19 /* contexts created GFCC_PREC_MIXED_BF16 evaluate the setup
+                                     contractions of at least this many flops from digit planes on
+                                     the tensor cores (FP64-accurate); default 4e12, 0 = all of them   */
+#define GFCC_OPT_WAIT_NS    20    /* limit of the bounded waits of the tensor-core kernels in
+                                     nanoseconds (1 .. 1e11); default 1e9.  A wait that runs out makes
+                                     the call return GFCC_ERR_TIMEOUT                                   */
+#define GFCC_OPT_TEST_NO_LOADS 21 /* test only: 1 makes the tensor-core kernels issue no loads, so that
+                                     their first wait runs out (with nothing in flight) and the call
+                                     returns GFCC_ERR_TIMEOUT; default 0                               */
+#define GFCC_OPT_GEMM_PAIR  22    /* BF16 tensor-core products on CTA pairs (256 x 256 tiles over two
+                                     SMs, tcgen05 cta_group::2): 0 (default) the autotuner times them
+                                     beside the one-CTA tiles, 1 whenever they apply, 2 never          */
 
 /* Initial guesses (Algorithm 1, "compute initial guess").  With a guess other than ZERO, gfcc_solve
  * keeps every converged solution X_p(omega) (FP32 complex, n_omega * n_orb * dim * 8 bytes of device
@@ -145,6 +162,12 @@ int gfcc_create_ex(int o, int v, int L, const double *fock, const double *chol,
  * for an unknown key or a value out of range. */
 int gfcc_set_option(gfcc_ctx *ctx, int key, double value);
 
+/* gfcc_set_process_option - set a process-wide option (GFCC_OPT_AUTOTUNE, GFCC_OPT_EMU_FUSED_N,
+ * GFCC_OPT_SETUP_EMULATE_FLOPS, GFCC_OPT_WAIT_NS, GFCC_OPT_TEST_NO_LOADS, GFCC_OPT_GEMM_PAIR).  It applies to every
+ * later call of every context; do not change it while another thread is inside the library.
+ * Returns GFCC_ERR_ARG for an unknown key or a value out of range. */
+int gfcc_set_process_option(int key, double value);
+
 /* gfcc_set_stream - run all of the context's work on `stream` (a cudaStream_t; NULL = the
  * context's own stream). */
 int gfcc_set_stream(gfcc_ctx *ctx, void *stream);
@@ -160,6 +183,19 @@ int gfcc_set_stream(gfcc_ctx *ctx, void *stream);
  */
 int gfcc_solve(gfcc_ctx *ctx, int n_omega, const double *omegas, double eta,
                int n_orb, const int *orbitals, double tol, double *G);
+
+/*
+ * gfcc_solve_block - the block of G(omega) with rows p over p_orbitals and columns q over q_orbitals
+ * (eqs. gfxn2/gfxn3): G[w][a][b] = G^IP_{p_a q_b}(omega_w) + G^EA_{p_a q_b}(omega_w).  The IP systems
+ * X_p (eq. xp) are solved for the row orbitals and overlapped with the left vectors of the column
+ * orbitals; the EA systems Y_q (eq. yq) are solved for the column orbitals and overlapped with the
+ * left vectors of the row orbitals.  gfcc_solve(orbitals) is gfcc_solve_block(orbitals, orbitals).
+ *   G : out, host complex128 interleaved, [n_omega][n_p][n_q], caller-allocated.
+ * Statistics (gfcc_last_stats): the IP systems (omega-major over p_orbitals), then the EA systems
+ * (omega-major over q_orbitals).  Return codes and errors as gfcc_solve.
+ */
+int gfcc_solve_block(gfcc_ctx *ctx, int n_omega, const double *omegas, double eta, int n_p, const int *p_orbitals,
+                     int n_q, const int *q_orbitals, double tol, double *G);
 
 /* gfcc_solve_device - gfcc_solve with omegas, orbitals and G in DEVICE memory (same layouts);
  * the call is asynchronous on the context's stream except for the per-iteration
@@ -243,8 +279,12 @@ int gfcc_dims(gfcc_ctx *ctx, long long *dim_ip, long long *dim_ea);
  * 3 whole sigma products (contains 1 and 2), 4 Arnoldi orthogonalisation, 5 Givens / least squares,
  * 6 right-hand sides, left vectors and overlaps, 7 whole gfcc_solve calls, 8 ring contraction on the
  * BF16 tensor cores (mixed precision; phase 1 is the FP64 ring contraction), 9 FP64-accurate ring
- * contraction of the refinement residual (digit planes; flops counted as tensor-core work), 10 expansion
- * of packed vectors into contraction layouts, 11 initial guesses (Gram matrices, model, combination).
+ * contraction of the refinement residual (digit planes; flops of the one FP64 product it evaluates), 10
+ * expansion of packed vectors into contraction layouts, 11 initial guesses (Gram matrices, model,
+ * combination), 12 the other FP64-accurate products of the refinement residual (oooo / vvvv,
+ * three-body, 1h / 1p row; FP64 product flops), 13 the other BF16 products of the inner sigma (oooo,
+ * three-body, 1h / 1p row), 14 sigma epilogues (shift, diagonal, packing; count = algorithmic bytes),
+ * 15 the same region as phase 9 with the BF16 tensor-core work of all its digit pairs as the count.
  */
 int gfcc_profile(gfcc_ctx *ctx, int enable);
 int gfcc_profile_read(gfcc_ctx *ctx, int phase, double *ms, long long *count, double *flops);
@@ -350,6 +390,75 @@ int gfcc_mlp_train(gfcc_mlp *m, int steps, int minibatch, double lr, unsigned lo
 int gfcc_mlp_eval(gfcc_mlp *m, double *out);
 /* gfcc_set_guess_model - model used by GFCC_GUESS_LEARNED (not owned; NULL detaches). */
 int gfcc_set_guess_model(gfcc_ctx *ctx, gfcc_mlp *m);
+
+/*
+ * Model-order reduction (Theory section, eq. model; Algorithm 1: Gram-Schmidt, projection and the
+ * spectral function after the frequency loop of a level).  A gfcc_mor object holds, for one sector
+ * of a context, a real orthonormal subspace S = {v_1 .. v_m} of the packed space (spanned by the real
+ * and imaginary parts of converged solutions X_p(omega_k) or Y_q(omega_k); Hbar, b and c are real,
+ * so S^T of eq. model is the plain transpose), W = Hbar_N S and Hhat = S^T Hbar_N S (m x m).  The
+ * model systems
+ *     IP: (omega - i eta + Hhat) Xhat = S^T b_p,  G_pq = (S^T c_q)^T Xhat
+ *     EA: (omega + i eta - Hhat) Yhat = S^T b_q,  G_pq = (S^T c_p)^T Yhat
+ * are solved densely on the GPU for any frequency grid; at every frequency whose solutions entered S
+ * they reproduce the full G (to the solver tolerance).  The object uses its context's stream and
+ * must not be used concurrently with it; destroy it before the context.
+ */
+typedef struct gfcc_mor gfcc_mor;
+
+/* gfcc_mor_create - empty subspace for sector GFCC_SECTOR_IP or GFCC_SECTOR_EA of ctx (the sector must
+ * be built).  drop_tol (0 < drop_tol < 1): a new vector is kept when the norm left after two
+ * Gram-Schmidt passes exceeds drop_tol times its norm (1e-10 is a good default). */
+int gfcc_mor_create(gfcc_ctx *ctx, int sector, double drop_tol, gfcc_mor **out);
+/* gfcc_mor_destroy - free the object and its device memory.  NULL is a no-op. */
+void gfcc_mor_destroy(gfcc_mor *mor);
+/* gfcc_mor_dim - the subspace dimension m (-1 for NULL). */
+int gfcc_mor_dim(gfcc_mor *mor);
+/*
+ * gfcc_mor_expand - solve the full systems of the object's sector for every omega x orbital (the
+ * context's solver and options, as gfcc_solve with that sector only), then orthonormalise the real
+ * and imaginary parts of every converged solution into S (O(m^2 O^2 V)) and project the operator on
+ * the new basis vectors (their sigma products, O(m O^3 V^2)).  G (optional, host, as gfcc_solve for
+ * that sector alone) receives the full G at these frequencies.  Returns GFCC_OK or
+ * GFCC_WARN_NOT_CONVERGED (unconverged systems do not enter S; gfcc_last_stats says which), or an error.
+ */
+int gfcc_mor_expand(gfcc_mor *mor, int n_omega, const double *omegas, double eta, int n_orb, const int *orbitals,
+                    double tol, double *G);
+/*
+ * gfcc_mor_green - the model G block on a frequency grid: G[w][a][b] for rows p_orbitals[a] and columns
+ * q_orbitals[b] (host, complex128 interleaved, [n_omega][n_p][n_q]; the object's sector only), by one
+ * dense LU solve per frequency (O(N_omega m^3)).  relres (optional, host): the relative full-space
+ * residual ||b - A(omega) S Xhat|| / ||b|| of every model solution ([n_omega][n_p] for IP, [n_omega][n_q]
+ * for EA; from W, without a sigma product; needs m <= 1024).
+ */
+int gfcc_mor_green(gfcc_mor *mor, int n_omega, const double *omegas, double eta, int n_p, const int *p_orbitals,
+                   int n_q, const int *q_orbitals, double *G, double *relres);
+/* gfcc_mor_projected - host copies of Hhat (m x m row-major; may be NULL) and of the first row_count
+ * basis vectors (row_count x dim row-major; may be NULL). */
+int gfcc_mor_projected(gfcc_mor *mor, double *Hhat, double *S_rows, int row_count);
+
+/*
+ * gfcc_spectral_adaptive - the spectral function (eq. specfxn) over [omega_min, omega_max] from the
+ * model-order reduction built level by level (Algorithm 1's outer loop; Implementation Details,
+ * eq. Lmax).  Level 1 solves omega_min, the midpoint and omega_max; each later level L solves, for all
+ * orbitals, the midpoints of adjacent sampled frequencies (at most 2^(L-1); a midpoint is a candidate
+ * when its half-interval is at least d_omega, which bounds the levels by log2((omega_max -
+ * omega_min) / d_omega)) whose largest relative model residual over the orbitals and sectors exceeds
+ * level_tol, the largest first; it stops when no candidate exceeds level_tol or after max_levels
+ * (1..30).  Each level's solutions expand one subspace per sector in `sectors` (GFCC_SECTOR_*).
+ *   A            : out [n_fine], A(omega) = (1/pi) sum_p (Im G^IP_pp - Im G^EA_pp) over `orbitals`
+ *                  from the final models (the paper's -(1/pi) Tr Im G^R, with the IP resolvent's
+ *                  -i eta and the EA resolvent's +i eta of eq. gfxn1, so A > 0 near every pole).
+ *   n_levels     : out, levels run; level_sizes: out [max_levels], frequencies per level;
+ *   sampled      : out, the sampled frequencies in sampling order (up to sampled_cap);
+ *   mdim         : out [2], subspace dimensions (IP, EA; 0 for a sector not requested).
+ * Any output pointer but A may be NULL.  Returns GFCC_OK, GFCC_WARN_NOT_CONVERGED (a full system missed
+ * tol; its solution was left out of the subspace) or an error.
+ */
+int gfcc_spectral_adaptive(gfcc_ctx *ctx, int sectors, double omega_min, double omega_max, double d_omega,
+                           double eta, int n_orb, const int *orbitals, double tol, double level_tol, int max_levels,
+                           int n_fine, const double *fine_omegas, double *A, int *n_levels, int *level_sizes,
+                           double *sampled, int sampled_cap, int *mdim);
 
 /* gfcc_destroy - free the context and all its device memory.  NULL is a no-op. */
 void gfcc_destroy(gfcc_ctx *ctx);

@@ -354,22 +354,24 @@ __global__ void left_ea_1p_kernel(double *C, long long n, int np, const int *por
 }
 
 // ---------------------------------------------------------------- overlaps
-// part[z][(s,t)][q] summed over z -> G: IP row (w_s, a_s) gets columns q; EA column (w_s, a_s) gets rows q
-// G rows of systems s < count with tw[s] >= 0 from the split-K partial overlaps (batch of nsys systems)
-__global__ void overlap_scatter_kernel(const double *part, int nsplit, int nsys, int count, int nq, const int *tw,
-                                       const int *ta, int is_ip, double *G) {
-  const long long tot = (long long)count * nq;
+// part[z][(s,t)][q] summed over z -> G ([omega][nP][nQ]): the IP system (w_s, a_s) of row orbital a_s
+// gets row a_s, columns q < nl (nl = nQ left vectors); the EA system (w_s, a_s) of column orbital
+// a_s gets column a_s, rows q < nl (nl = nP left vectors).  Systems s < count with tw[s] >= 0 of a
+// batch of nsys systems, from the split-K partial overlaps.
+__global__ void overlap_scatter_kernel(const double *part, int nsplit, int nsys, int count, int nl, const int *tw,
+                                       const int *ta, int is_ip, int nP, int nQ, double *G) {
+  const long long tot = (long long)count * nl;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(t / nq), q = (int)(t % nq);
+    const int s = (int)(t / nl), q = (int)(t % nl);
     if (tw[s] < 0) continue;
     double re = 0.0, im = 0.0;
-    const long long zs = 2LL * nsys * nq;
+    const long long zs = 2LL * nsys * nl;
     for (int z = 0; z < nsplit; z++) {
-      re += part[z * zs + (2LL * s) * nq + q];
-      im += part[z * zs + (2LL * s + 1) * nq + q];
+      re += part[z * zs + (2LL * s) * nl + q];
+      im += part[z * zs + (2LL * s + 1) * nl + q];
     }
     const long long w = tw[s], a = ta[s];
-    const long long idx = is_ip ? (w * nq + a) * nq + q : (w * nq + q) * nq + a;
+    const long long idx = is_ip ? (w * nP + a) * nQ + q : (w * nP + q) * nQ + a;
     G[2 * idx] += re;
     G[2 * idx + 1] += im;
   }
@@ -526,8 +528,22 @@ int create_impl(int o, int v, int L, const double *fock, const double *chol, con
   return GFCC_OK;
 }
 
-int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, int n_orb, const int *d_orb,
-                     const int *h_orb, double tol, double *d_G);
+// The orbital lists of a solve: rows p of G run over P, columns q over Q.  IP systems are solved for
+// the row orbitals (X_p, eq. xp) and overlapped with the left vectors of the columns; EA systems
+// are solved for the column orbitals (Y_q, eq. yq) and overlapped with the left vectors of the rows.
+struct OrbLists {
+  int nP = 0, nQ = 0;
+  const int *dP = nullptr, *dQ = nullptr;   // device
+  const int *hP = nullptr, *hQ = nullptr;   // host copies of the same lists
+  int n_sys(bool ip) const { return ip ? nP : nQ; }
+  const int *sys(bool ip) const { return ip ? dP : dQ; }
+  int n_left(bool ip) const { return ip ? nQ : nP; }
+  const int *left(bool ip) const { return ip ? dQ : dP; }
+  const int *left_host(bool ip) const { return ip ? hQ : hP; }
+};
+
+int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, const OrbLists &ol, double tol,
+                     double *d_G);
 
 int choose_batch(gfcc_ctx *c, int sector, long long n, long long ntasks) {
   if (c->batch > 0) return (int)std::min<long long>(c->batch, ntasks);
@@ -559,13 +575,13 @@ int grow_scratch(gfcc_ctx *c, size_t bytes) {
   return GFCC_OK;
 }
 
-int solve_impl(gfcc_ctx *c, int n_omega, const double *d_om, double eta, int n_orb, const int *d_orb,
-               const int *h_orb, double tol, double *d_G) {
+int solve_impl(gfcc_ctx *c, int n_omega, const double *d_om, double eta, const OrbLists &ol, double tol,
+               double *d_G) {
   cudaStream_t st = c->stream;
   int rc;
   {
     PhaseTimer tm(c, PH_SOLVE);
-    rc = solve_impl_inner(c, n_omega, d_om, eta, n_orb, d_orb, h_orb, tol, d_G);
+    rc = solve_impl_inner(c, n_omega, d_om, eta, ol, tol, d_G);
   }
   if (c->prof) {
     GFCC_CUDA(cudaStreamSynchronize(st));
@@ -604,34 +620,42 @@ int prepare_kept(gfcc_ctx *c, int sector, long long n, int n_omega, int n_orb, c
   return GFCC_OK;
 }
 
-int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, int n_orb, const int *d_orb,
-                     const int *h_orb, double tol, double *d_G) {
+int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, const OrbLists &ol, double tol,
+                     double *d_G) {
   cudaStream_t st = c->stream;
   const int sectors[2] = {GFCC_SECTOR_IP, GFCC_SECTOR_EA};
-  const long long ntasks = (long long)n_omega * n_orb;
-  const int nsec = (c->sectors & GFCC_SECTOR_IP ? 1 : 0) + (c->sectors & GFCC_SECTOR_EA ? 1 : 0);
   const int guess = c->guess;
   if (guess == GFCC_GUESS_LEARNED && c->mlp == nullptr) {
     set_error("gfcc_solve: GFCC_GUESS_LEARNED needs a model (gfcc_set_guess_model)");
     return GFCC_ERR_STATE;
   }
   const bool keep = guess != GFCC_GUESS_ZERO || c->keep_solutions;
-  c->st_iters.assign(ntasks * nsec, 0);
-  c->st_status.assign(ntasks * nsec, GFCC_STATUS_NOT_CONVERGED);
-  c->st_relres.assign(ntasks * nsec, 0.0);
-  c->st_guess.assign(ntasks * nsec, GFCC_GUESS_ZERO);
-  c->st_guess_pred.assign(ntasks * nsec, 1.0);
-  c->st_relres0.assign(ntasks * nsec, 1.0);
-  c->st_outer.assign(ntasks * nsec, 0);
+  // statistics entries: the IP systems (omega-major over the row orbitals), then the EA systems
+  // (omega-major over the column orbitals)
+  long long nstat = 0;
+  for (int sector : sectors)
+    if (c->sectors & sector) nstat += (long long)n_omega * ol.n_sys(sector == GFCC_SECTOR_IP);
+  c->st_iters.assign(nstat, 0);
+  c->st_status.assign(nstat, GFCC_STATUS_NOT_CONVERGED);
+  c->st_relres.assign(nstat, 0.0);
+  c->st_guess.assign(nstat, GFCC_GUESS_ZERO);
+  c->st_guess_pred.assign(nstat, 1.0);
+  c->st_relres0.assign(nstat, 1.0);
+  c->st_outer.assign(nstat, 0);
   c->res_full = c->res_inc = c->res_inc_levels = 0;
-  GFCC_CUDA(cudaMemsetAsync(d_G, 0, sizeof(double) * 2 * n_omega * n_orb * n_orb, st));
-  int sec_slot = 0;
+  GFCC_CUDA(cudaMemsetAsync(d_G, 0, sizeof(double) * 2 * n_omega * (long long)ol.nP * ol.nQ, st));
+  long long stat_off = 0;   // first statistics entry of the current sector
   bool all_ok = true;
-  (void)h_orb;
   for (int sector : sectors) {
     if (!(c->sectors & sector)) continue;
     const bool ip = sector == GFCC_SECTOR_IP;
     const long long n = ip ? c->dim_ip : c->dim_ea;
+    const int n_orb = ol.n_sys(ip);     // orbitals of the systems solved in this sector
+    const int *d_orb = ol.sys(ip);
+    const int n_left = ol.n_left(ip);   // orbitals of the left vectors they are overlapped with
+    const int *d_left = ol.left(ip);
+    const long long ntasks = (long long)n_omega * n_orb;
+    if (ntasks == 0) continue;
     // mixed precision: BF16 operator inside FP64-accurate refinement, in every sector whose BF16
     // operands were built
     const bool mixed = c->precision == GFCC_PREC_MIXED_BF16 && (ip ? c->Wr_bf : c->Wre_bf) != nullptr;
@@ -645,17 +669,41 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
     const long long gq = keep ? 2LL * nsys * GUESS_G + (long long)nsys * (GUESS_NF + 2 * GUESS_NO + 1 + GUESS_K + 1) +
                                     guess_gram_work_doubles(nsys, n) + (long long)nsys * (GUESS_K + 3) / 2 + 64
                               : 0;
-    const long long work = gw + (long long)n_orb * n + nsplit * 2LL * nsys * n_orb + 4LL * nsys + 64 + gq;
+    const long long work = gw + nsplit * 2LL * nsys * n_left + 4LL * nsys + 64 + gq;
     GFCC_TRY(grow_scratch(c, sizeof(double) * work));
     double *base = static_cast<double *>(c->scratch);
     Gmres gm;
     GFCC_TRY(gm.init(c, sector, n, nsys, m, base, mixed));
-    double *Cl = base + gw;
-    double *part = Cl + (long long)n_orb * n;
-    int *d_tw = reinterpret_cast<int *>(part + nsplit * 2LL * nsys * n_orb);
+    // left vectors: cached per sector and orbital list (computed on the first solve over the list)
+    double *Cl = nullptr;
+    bool left_ready = false;
+    {
+      gfcc_ctx::LeftCache &lc = c->left_cache[ip ? 0 : 1];
+      const int *hl = ol.left_host(ip);
+      const size_t lbytes = sizeof(double) * (size_t)n_left * (size_t)n;
+      left_ready = lc.C != nullptr && (int)lc.orb.size() == n_left &&
+                   std::equal(lc.orb.begin(), lc.orb.end(), hl);
+      if (!left_ready) {
+        lc.orb.clear();
+        if (lc.bytes < lbytes) {
+          if (lc.C) dfree(lc.C);
+          lc.C = nullptr;
+          lc.bytes = 0;
+          if (lbytes > 0 && dmalloc(reinterpret_cast<void **>(&lc.C), lbytes) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cannot allocate %.3f GB for the left vectors", lbytes / 1e9);
+            return GFCC_ERR_OOM;
+          }
+          lc.bytes = lbytes;
+        }
+      }
+      Cl = lc.C;
+    }
+    double *part = base + gw;
+    int *d_tw = reinterpret_cast<int *>(part + nsplit * 2LL * nsys * n_left);
     int *d_ta = d_tw + nsys;
     int *d_porb = d_ta + nsys;
-    double *g_Gm = part + nsplit * 2LL * nsys * n_orb + 4LL * nsys + 64;
+    double *g_Gm = part + nsplit * 2LL * nsys * n_left + 4LL * nsys + 64;
     double *g_feat = g_Gm + 2LL * nsys * GUESS_G;
     double *g_y = g_feat + (long long)nsys * GUESS_NF;
     double *g_coef = g_y + (long long)nsys * GUESS_NO;
@@ -669,26 +717,12 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
     int *g_slot = g_kind + nsys;
     gm.eta = eta;
     gm.use_precond = c->precond == GFCC_PRECOND_DIAG;
-    // left vectors for all orbitals of the list
-    {
+    // left vectors for all orbitals of the overlap list (unless cached from an earlier solve)
+    if (n_left > 0 && !left_ready) {
     PhaseTimer tleft(c, PH_OVERLAP);
-    if (ip) {
-      left_ip_1h_kernel<<<n_orb * c->o, 256, 0, st>>>(Cl, n, n_orb, d_orb, c->o, c->v, c->t1, c->t2, c->l1, c->l2);
-      GFCC_LAUNCH_CHECK();
-      if (n > c->o) {
-        left_ip_2h1p_kernel<<<grid1d((n - c->o) * n_orb), 256, 0, st>>>(Cl, n, n_orb, d_orb, c->o, c->v, c->t1,
-                                                                          c->l1, c->l2);
-        GFCC_LAUNCH_CHECK();
-      }
-    } else {
-      left_ea_1p_kernel<<<n_orb * c->v, 256, 0, st>>>(Cl, n, n_orb, d_orb, c->o, c->v, c->t1, c->t2, c->l1, c->l2);
-      GFCC_LAUNCH_CHECK();
-      if (n > c->v) {
-        left_ea_2p1h_kernel<<<grid1d((n - c->v) * n_orb), 256, 0, st>>>(Cl, n, n_orb, d_orb, c->o, c->v, c->Pv, c->t1,
-                                                                          c->l1, c->l2);
-        GFCC_LAUNCH_CHECK();
-      }
-    }
+    GFCC_TRY(build_left_vectors(c, sector, n_left, d_left, Cl, st));
+    const int *hl = ol.left_host(ip);
+    c->left_cache[ip ? 0 : 1].orb.assign(hl, hl + n_left);
     }
     if (mixed && guess == GFCC_GUESS_ZERO) {
       // continuous batching: a slot whose system has converged (or spent its budget) after a
@@ -762,7 +796,7 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
           }
           // finalise the slot
           const long long t = task[s];
-          const long long idx = sec_slot * ntasks + t;
+          const long long idx = stat_off + t;
           c->st_iters[idx] = sl_it[s];
           c->st_relres[idx] = h_rel[s];
           c->st_relres0[idx] = 1.0;
@@ -772,27 +806,35 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
           h_twf[s] = h_tw[s];
           any_fin = true;
         }
-        if (any_fin) {
+        if (any_fin && n_left > 0) {
           GFCC_CUDA(cudaMemcpyAsync(d_twf, h_twf.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
           {
             PhaseTimer tov(c, PH_OVERLAP);
             Contract k;
             k.A = gm.solution(); k.am = imap2(2, 1, 2 * n); k.ak = imap1(2);
             k.B = Cl; k.bk = imap1(1); k.bn = imap1(n);
-            k.C = part; k.cm = imap1(n_orb); k.cn = imap1(1);
-            k.M = 2LL * ns; k.N = n_orb; k.K = n;
-            k.nsplit = nsplit; k.kchunk = 8192; k.scz = 2LL * ns * n_orb;
+            k.C = part; k.cm = imap1(n_left); k.cn = imap1(1);
+            k.M = 2LL * ns; k.N = n_left; k.K = n;
+            k.nsplit = nsplit; k.kchunk = 8192; k.scz = 2LL * ns * n_left;
             GFCC_TRY(contract_f64(k, st));
-            overlap_scatter_kernel<<<grid1d((long long)ns * n_orb), 256, 0, st>>>(part, (int)nsplit, ns, ns, n_orb,
-                                                                                   d_twf, d_ta, ip ? 1 : 0, d_G);
+            overlap_scatter_kernel<<<grid1d((long long)ns * n_left), 256, 0, st>>>(
+                part, (int)nsplit, ns, ns, n_left, d_twf, d_ta, ip ? 1 : 0, ol.nP, ol.nQ, d_G);
             GFCC_LAUNCH_CHECK();
           }
+        }
+        if (any_fin) {
           if (keep) {
             for (int s = 0; s < ns; s++) h_slot[s] = h_twf[s] >= 0 ? h_tw[s] * n_orb + h_ta[s] : -1;
             GFCC_CUDA(cudaMemcpyAsync(g_slot, h_slot.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
             GFCC_TRY(guess_store_put(st, ns, n, gm.solution(), n, g_slot, c->kept.X));
             for (int s = 0; s < ns; s++)
               if (h_twf[s] >= 0 && h_done[s] == 1) c->kept.done[(size_t)h_tw[s] * n_orb + h_ta[s]] = 1;
+          }
+          if (c->sink != nullptr) {
+            for (int s = 0; s < ns; s++)
+              if (h_twf[s] >= 0)
+                GFCC_CUDA(cudaMemcpyAsync(c->sink + 2 * task[s] * n, gm.solution() + 2LL * s * n,
+                                          sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice, st));
           }
           // refill the finished slots while tasks remain
           bool refill = false;
@@ -843,7 +885,7 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
       }
       GFCC_TRY(umma_error_check(st));
       gm.nsys = nsys;
-      sec_slot++;
+      stat_off += ntasks;
       continue;
     }
     // task order: frequency-major; with initial guesses the frequencies go in the order of
@@ -907,18 +949,25 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
         GFCC_TRY(gm.solve(tol, c->max_iters, h_state.data(), 0, use_x0));
       }
       // overlaps: part[z][(s,t)][q] = sum_{mu in chunk z} x_s[mu] C[q][mu]
-      {
+      if (n_left > 0) {
       PhaseTimer tov(c, PH_OVERLAP);
       Contract k;
       k.A = gm.solution(); k.am = imap2(2, 1, 2 * n); k.ak = imap1(2);
       k.B = Cl; k.bk = imap1(1); k.bn = imap1(n);
-      k.C = part; k.cm = imap1(n_orb); k.cn = imap1(1);
-      k.M = 2LL * nsys; k.N = n_orb; k.K = n;
-      k.nsplit = nsplit; k.kchunk = 8192; k.scz = 2LL * nsys * n_orb;
+      k.C = part; k.cm = imap1(n_left); k.cn = imap1(1);
+      k.M = 2LL * nsys; k.N = n_left; k.K = n;
+      k.nsplit = nsplit; k.kchunk = 8192; k.scz = 2LL * nsys * n_left;
       GFCC_TRY(contract_f64(k, st));
-      overlap_scatter_kernel<<<grid1d((long long)nb * n_orb), 256, 0, st>>>(part, (int)nsplit, nsys, nb, n_orb, d_tw,
-                                                                             d_ta, ip ? 1 : 0, d_G);
+      overlap_scatter_kernel<<<grid1d((long long)nb * n_left), 256, 0, st>>>(part, (int)nsplit, nsys, nb, n_left,
+                                                                              d_tw, d_ta, ip ? 1 : 0, ol.nP, ol.nQ,
+                                                                              d_G);
       GFCC_LAUNCH_CHECK();
+      }
+      if (c->sink != nullptr) {
+        for (int s = 0; s < nb; s++)
+          GFCC_CUDA(cudaMemcpyAsync(c->sink + 2 * ((long long)h_tw[s] * n_orb + h_ta[s]) * n,
+                                    gm.solution() + 2LL * s * n, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice,
+                                    st));
       }
       if (keep) {
         for (int s = 0; s < nsys; s++) h_slot[s] = s < nb ? h_tw[s] * n_orb + h_ta[s] : -1;
@@ -936,7 +985,7 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
       GFCC_CUDA(cudaStreamSynchronize(st));
       for (int s = 0; s < nb; s++) {
         // statistics in (omega, orbital) order of the request
-        const long long idx = sec_slot * ntasks + (long long)h_tw[s] * n_orb + h_ta[s];
+        const long long idx = stat_off + (long long)h_tw[s] * n_orb + h_ta[s];
         c->st_iters[idx] = h_it[s];
         c->st_relres[idx] = h_rel[s];
         c->st_relres0[idx] = h_rel0[s];
@@ -951,7 +1000,7 @@ int solve_impl_inner(gfcc_ctx *c, int n_omega, const double *d_om, double eta, i
         all_ok &= h_state[s] == 3;
       }
     }
-    sec_slot++;
+    stat_off += ntasks;
   }
   return all_ok ? GFCC_OK : GFCC_WARN_NOT_CONVERGED;
 }
@@ -966,6 +1015,73 @@ int check_solve_args(gfcc_ctx *c, int n_omega, double eta, int n_orb, double tol
     return GFCC_ERR_ARG;
   }
   return GFCC_OK;
+}
+
+// gfcc_solve / gfcc_solve_block on host arrays: device copies of the frequencies, the two orbital
+// lists and G around solve_impl
+int solve_host(gfcc_ctx *c, int n_omega, const double *omegas, double eta, int nP, const int *P, int nQ, const int *Q,
+               double tol, double *G) {
+  // G == nullptr: the solve runs and G stays on the device (internal callers that only want the
+  // solutions); the entry points reject a NULL G themselves
+  if (omegas == nullptr || P == nullptr || Q == nullptr) {
+    set_error("gfcc_solve: NULL omegas or orbitals");
+    return GFCC_ERR_ARG;
+  }
+  for (int pass = 0; pass < 2; pass++) {
+    const int cnt = pass ? nQ : nP;
+    const int *lst = pass ? Q : P;
+    for (int a = 0; a < cnt; a++)
+      if (lst[a] < 0 || lst[a] >= c->n) {
+        set_error("gfcc_solve: orbital index %d out of range [0, %d)", lst[a], c->n);
+        return GFCC_ERR_ARG;
+      }
+  }
+  for (int w = 0; w < n_omega; w++)
+    if (!std::isfinite(omegas[w])) {
+      set_error("gfcc_solve: omega[%d] is not finite", w);
+      return GFCC_ERR_ARG;
+    }
+  double *d_om = nullptr, *d_G = nullptr;
+  int *d_P = nullptr, *d_Q = nullptr;
+  const size_t gbytes = sizeof(double) * 2 * (size_t)n_omega * nP * nQ;
+  if (dmalloc((void **)&d_om, sizeof(double) * n_omega) != cudaSuccess ||
+      dmalloc((void **)&d_P, sizeof(int) * nP) != cudaSuccess || dmalloc((void **)&d_Q, sizeof(int) * nQ) != cudaSuccess ||
+      dmalloc((void **)&d_G, gbytes) != cudaSuccess) {
+    cudaGetLastError();
+    dfree(d_om);
+    dfree(d_P);
+    dfree(d_Q);
+    dfree(d_G);
+    set_error("gfcc_solve: cannot allocate the frequency / orbital / G buffers");
+    return GFCC_ERR_OOM;
+  }
+  int s = GFCC_OK;
+  if (cudaMemcpyAsync(d_om, omegas, sizeof(double) * n_omega, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(d_P, P, sizeof(int) * nP, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(d_Q, Q, sizeof(int) * nQ, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+    set_error("gfcc_solve: host-to-device copy failed");
+    s = GFCC_ERR_CUDA;
+  }
+  OrbLists ol;
+  ol.nP = nP;
+  ol.nQ = nQ;
+  ol.dP = d_P;
+  ol.dQ = d_Q;
+  ol.hP = P;
+  ol.hQ = Q;
+  if (s == GFCC_OK) s = solve_impl(c, n_omega, d_om, eta, ol, tol, d_G);
+  if (s >= 0) {
+    if ((G != nullptr && cudaMemcpyAsync(G, d_G, gbytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      set_error("gfcc_solve: device-to-host copy of G failed");
+      s = GFCC_ERR_CUDA;
+    }
+  }
+  dfree(d_om);
+  dfree(d_P);
+  dfree(d_Q);
+  dfree(d_G);
+  return s;
 }
 
 }  // namespace
@@ -986,6 +1102,44 @@ int build_rhs_masked(gfcc_ctx *c, int sector, int nsys, const int *d_porb, const
 
 int build_rhs(gfcc_ctx *c, int sector, int nsys, const int *d_porb, double *B, cudaStream_t st) {
   return build_rhs_masked(c, sector, nsys, d_porb, nullptr, B, st);
+}
+
+// left vectors C[q][mu] (real, [nq][dim]) of the orbitals d_orb (device) of one sector (eq. gfxn2)
+int build_left_vectors(gfcc_ctx *c, int sector, int nq, const int *d_orb, double *C, cudaStream_t st) {
+  if (nq <= 0) return GFCC_OK;
+  if (sector == GFCC_SECTOR_IP) {
+    const long long n = c->dim_ip;
+    left_ip_1h_kernel<<<nq * c->o, 256, 0, st>>>(C, n, nq, d_orb, c->o, c->v, c->t1, c->t2, c->l1, c->l2);
+    GFCC_LAUNCH_CHECK();
+    if (n > c->o) {
+      left_ip_2h1p_kernel<<<grid1d((n - c->o) * nq), 256, 0, st>>>(C, n, nq, d_orb, c->o, c->v, c->t1, c->l1, c->l2);
+      GFCC_LAUNCH_CHECK();
+    }
+  } else {
+    const long long n = c->dim_ea;
+    left_ea_1p_kernel<<<nq * c->v, 256, 0, st>>>(C, n, nq, d_orb, c->o, c->v, c->t1, c->t2, c->l1, c->l2);
+    GFCC_LAUNCH_CHECK();
+    if (n > c->v) {
+      left_ea_2p1h_kernel<<<grid1d((n - c->v) * nq), 256, 0, st>>>(C, n, nq, d_orb, c->o, c->v, c->Pv, c->t1, c->l1,
+                                                                     c->l2);
+      GFCC_LAUNCH_CHECK();
+    }
+  }
+  return GFCC_OK;
+}
+
+// gfcc_solve over one sector (rows and columns over the same orbital list) with every finished
+// system's FP64 solution copied to d_sink ([omega][orbital][dim] complex); G to the host if h_G.
+// The statistics of the solve stay in the context.
+int solve_for_sink(gfcc_ctx *c, int sector, int n_omega, const double *h_om, double eta, int n_orb,
+                   const int *h_orb, double tol, double *d_sink, double *h_G) {
+  const int saved = c->sectors;
+  c->sectors = sector;
+  c->sink = d_sink;
+  const int rc = solve_host(c, n_omega, h_om, eta, n_orb, h_orb, n_orb, h_orb, tol, h_G);
+  c->sink = nullptr;
+  c->sectors = saved;
+  return rc;
 }
 
 }  // namespace gfcc
@@ -1094,6 +1248,46 @@ int gfcc_set_option(gfcc_ctx *c, int key, double value) {
   return GFCC_ERR_ARG;
 }
 
+int gfcc_set_process_option(int key, double value) {
+  switch (key) {
+    case GFCC_OPT_AUTOTUNE:
+      if (value != 0.0 && value != 1.0) break;
+      umma_set_autotune(value == 1.0);
+      return GFCC_OK;
+    case GFCC_OPT_EMU_FUSED_N:
+      if (!(value >= 0.0)) break;
+      emu_set_fused_max_n((long long)value);
+      return GFCC_OK;
+    case GFCC_OPT_GEMM_PAIR:
+      if (value != 0.0 && value != 1.0 && value != 2.0) break;
+      umma_set_pair_mode((int)value);
+      return GFCC_OK;
+    case GFCC_OPT_SETUP_EMULATE_FLOPS:
+      if (!(value >= 0.0)) break;
+      g_emulate_min_flops = value;
+      return GFCC_OK;
+    case GFCC_OPT_WAIT_NS:
+    case GFCC_OPT_TEST_NO_LOADS: {
+      static unsigned long long wait_ns = 1000000000ULL;
+      static bool no_loads = false;
+      if (key == GFCC_OPT_WAIT_NS) {
+        if (!(value >= 1.0 && value <= 1e11)) break;
+        wait_ns = (unsigned long long)value;
+      } else {
+        if (value != 0.0 && value != 1.0) break;
+        no_loads = value == 1.0;
+      }
+      umma_set_wait(wait_ns, no_loads);
+      return GFCC_OK;
+    }
+    default:
+      set_error("gfcc_set_process_option: unknown key %d", key);
+      return GFCC_ERR_ARG;
+  }
+  set_error("gfcc_set_process_option: value %g out of range for key %d", value, key);
+  return GFCC_ERR_ARG;
+}
+
 int gfcc_set_stream(gfcc_ctx *c, void *stream) {
   if (c == nullptr) {
     set_error("gfcc_set_stream: ctx is NULL");
@@ -1116,57 +1310,38 @@ int gfcc_solve_device(gfcc_ctx *c, int n_omega, const double *omegas_dev, double
       set_error("gfcc_solve: orbital index %d out of range [0, %d)", x, c->n);
       return GFCC_ERR_ARG;
     }
-  return solve_impl(c, n_omega, omegas_dev, eta, n_orb, orbitals_dev, h_orb.data(), tol, G_dev);
+  OrbLists ol;
+  ol.nP = ol.nQ = n_orb;
+  ol.dP = ol.dQ = orbitals_dev;
+  ol.hP = ol.hQ = h_orb.data();
+  return solve_impl(c, n_omega, omegas_dev, eta, ol, tol, G_dev);
 }
+
 
 int gfcc_solve(gfcc_ctx *c, int n_omega, const double *omegas, double eta, int n_orb, const int *orbitals, double tol,
                double *G) {
   GFCC_TRY(check_solve_args(c, n_omega, eta, n_orb, tol));
   if (n_omega == 0 || n_orb == 0) return GFCC_OK;
-  if (omegas == nullptr || orbitals == nullptr || G == nullptr) {
-    set_error("gfcc_solve: NULL omegas, orbitals or G");
+  if (G == nullptr) {
+    set_error("gfcc_solve: G is NULL");
     return GFCC_ERR_ARG;
   }
-  for (int a = 0; a < n_orb; a++)
-    if (orbitals[a] < 0 || orbitals[a] >= c->n) {
-      set_error("gfcc_solve: orbital index %d out of range [0, %d)", orbitals[a], c->n);
-      return GFCC_ERR_ARG;
-    }
-  for (int w = 0; w < n_omega; w++)
-    if (!std::isfinite(omegas[w])) {
-      set_error("gfcc_solve: omega[%d] is not finite", w);
-      return GFCC_ERR_ARG;
-    }
-  double *d_om = nullptr, *d_G = nullptr;
-  int *d_orb = nullptr;
-  const size_t gbytes = sizeof(double) * 2 * (size_t)n_omega * n_orb * n_orb;
-  if (dmalloc((void **)&d_om, sizeof(double) * n_omega) != cudaSuccess ||
-      dmalloc((void **)&d_orb, sizeof(int) * n_orb) != cudaSuccess || dmalloc((void **)&d_G, gbytes) != cudaSuccess) {
-    cudaGetLastError();
-    dfree(d_om);
-    dfree(d_orb);
-    dfree(d_G);
-    set_error("gfcc_solve: cannot allocate the frequency / orbital / G buffers");
-    return GFCC_ERR_OOM;
+  return solve_host(c, n_omega, omegas, eta, n_orb, orbitals, n_orb, orbitals, tol, G);
+}
+
+int gfcc_solve_block(gfcc_ctx *c, int n_omega, const double *omegas, double eta, int n_p, const int *p_orbitals,
+                     int n_q, const int *q_orbitals, double tol, double *G) {
+  GFCC_TRY(check_solve_args(c, n_omega, eta, n_p, tol));
+  if (n_q < 0) {
+    set_error("gfcc_solve_block: need n_q >= 0");
+    return GFCC_ERR_ARG;
   }
-  int s = GFCC_OK;
-  if (cudaMemcpyAsync(d_om, omegas, sizeof(double) * n_omega, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
-      cudaMemcpyAsync(d_orb, orbitals, sizeof(int) * n_orb, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
-    set_error("gfcc_solve: host-to-device copy failed");
-    s = GFCC_ERR_CUDA;
+  if (n_omega == 0 || n_p == 0 || n_q == 0) return GFCC_OK;
+  if (G == nullptr) {
+    set_error("gfcc_solve_block: G is NULL");
+    return GFCC_ERR_ARG;
   }
-  if (s == GFCC_OK) s = solve_impl(c, n_omega, d_om, eta, n_orb, d_orb, orbitals, tol, d_G);
-  if (s >= 0) {
-    if (cudaMemcpyAsync(G, d_G, gbytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
-        cudaStreamSynchronize(c->stream) != cudaSuccess) {
-      set_error("gfcc_solve: device-to-host copy of G failed");
-      s = GFCC_ERR_CUDA;
-    }
-  }
-  dfree(d_om);
-  dfree(d_orb);
-  dfree(d_G);
-  return s;
+  return solve_host(c, n_omega, omegas, eta, n_p, p_orbitals, n_q, q_orbitals, tol, G);
 }
 
 int gfcc_last_stats(gfcc_ctx *c, int *count, int *iters, double *relres, int *status) {
@@ -1353,6 +1528,8 @@ void gfcc_destroy(gfcc_ctx *c) {
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (void *p : c->allocs) dfree(p);
   if (c->scratch) dfree(c->scratch);
+  for (auto &lc : c->left_cache)
+    if (lc.C) dfree(lc.C);
   if (c->kept.X) dfree(c->kept.X);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;

@@ -21,7 +21,13 @@ enum GfccPhase {
   PH_RING_EMU = 9,    // the FP64-accurate ring contraction of the refinement residual (digit planes)
   PH_UNPACK = 10,     // expansion of packed vectors into the contraction layouts (BF16 / digits)
   PH_GUESS = 11,      // initial guesses: neighbour Gram matrices, model, coefficients, combination
-  PH_COUNT = 12
+  PH_EMU_OTHER = 12,  // the other FP64-accurate products of the refinement residual (oooo / vvvv,
+                      // three-body, 1h / 1p row), digit slicing of their inputs included
+  PH_BF16_OTHER = 13, // the other BF16 products of the inner sigma (oooo, three-body, 1h / 1p row)
+  PH_EPILOGUE = 14,   // sigma epilogues (shift, diagonal, packing of y); "flops" = algorithmic bytes
+  PH_RING_EMU_WORK = 15,  // same region as PH_RING_EMU; "flops" = the BF16 tensor-core work of all
+                          // its digit pairs (PH_RING_EMU counts the one FP64 product it evaluates)
+  PH_COUNT = 16
 };
 
 struct gfcc_mlp;
@@ -143,6 +149,18 @@ struct gfcc_ctx {
   // scratch reused across solves (grown on demand)
   void *scratch = nullptr;
   size_t scratch_bytes = 0;
+
+  // when set, every solve copies each finished system's solution (FP64 complex) to sink[task][dim]
+  // (task = omega index x number of orbitals + orbital index; the subspace builder of mor.cu)
+  double *sink = nullptr;
+
+  // left vectors c_q (eq. gfxn2) of the last orbital list of each sector ([0] IP, [1] EA): they depend
+  // on the list and the amplitudes only, so repeated solves over the same list reuse them
+  struct LeftCache {
+    std::vector<int> orb;
+    double *C = nullptr;   // [n_orb][dim]
+    size_t bytes = 0;
+  } left_cache[2];
 };
 
 namespace gfcc {

@@ -34,6 +34,7 @@ constexpr int max_systems() {
 }
 
 __device__ __forceinline__ void load_x(const SysBatch &b, int s, long long mu, double &xr, double &xi) {
+  s = sysv(b, s);
   if (b.xf != nullptr) {
     const float2 t = reinterpret_cast<const float2 *>(b.xf)[s * b.ldx + mu];
     xr = t.x;
@@ -46,6 +47,8 @@ __device__ __forceinline__ void load_x(const SysBatch &b, int s, long long mu, d
 }
 
 __device__ __forceinline__ void store_y(const SysBatch &b, int s, long long mu, double yr, double yi) {
+  if (!sys_stores(b, s)) return;
+  s = sysv(b, s);
   if (b.yf != nullptr)
     reinterpret_cast<float2 *>(b.yf)[s * b.ldy + mu] = make_float2((float)yr, (float)yi);
   else
@@ -66,12 +69,12 @@ __device__ __forceinline__ void combine(const SysBatch &b, int s, long long mu, 
     } else {
       double ur = xr, ui = xi;
       if (b.diag != nullptr) {
-        const double dr = b.omega[s] + b.dsign * b.diag[mu], di = b.zsign * b.eta;
+        const double dr = b.omega[sysv(b, s)] + b.dsign * b.diag[mu], di = b.zsign * b.eta;
         const double d2 = dr * dr + di * di;
         ur = (xr * dr + xi * di) / d2;
         ui = (xi * dr - xr * di) / d2;
       }
-      const double zr = b.omega[s], zi = b.zsign * b.eta;
+      const double zr = b.omega[sysv(b, s)], zi = b.zsign * b.eta;
       yr = zr * ur - zi * ui + sgn * sr;
       yi = zr * ui + zi * ur + sgn * si;
     }
@@ -84,7 +87,7 @@ __device__ __forceinline__ void combine(const SysBatch &b, int s, long long mu, 
       yr = xr + sgn * sr;
       yi = xi + sgn * si;
     } else {
-      const double dr = b.omega[s] + sgn * d, di = b.zsign * b.eta;
+      const double dr = b.omega[sysv(b, s)] + sgn * d, di = b.zsign * b.eta;
       yr = dr * xr - di * xi + sgn * sr;
       yi = dr * xi + di * xr + sgn * si;
     }

@@ -557,7 +557,8 @@ long long gmres_work_doubles(const gfcc_ctx *c, int sector, long long n, int nsy
   w += 2LL * nsys * NV * 5;                 // h, h2, y, nrm (two slots)
   w += 2LL * nsys * (m + 1) * m;            // H
   w += 2LL * nsys * (2 * m + (m + 1));      // cs, sn, g
-  w += 8LL * nsys + 512;                    // bnorm, relres, relres0, est, omega, int state/kcyc/iters, alignment
+  w += 9LL * nsys + 512;                    // bnorm, relres, relres0, est, omega, int state/kcyc/iters/rflag/act,
+                                            // alignment
   w += sigma_work_doubles(c, sector, nsys);
   if (mixed) {
     w += 5 * 2LL * nsys * n + nsys + 64;     // X, R, B0, D, A D, ||b0||
@@ -604,11 +605,12 @@ int Gmres::init(gfcc_ctx *ctx, int sec, long long dim, int ns, int mm, double *w
   take(est, nsys);
   take(omega, nsys);
   double *ip;
-  take(ip, 4LL * nsys);
+  take(ip, 5LL * nsys);
   state = reinterpret_cast<int *>(ip);
   kcyc = state + nsys;
   iters = kcyc + nsys;
   rflag = iters + nsys;
+  act = rflag + nsys;
   if (mixed) {
     take(X, 2LL * nsys * n);
     take(R, 2LL * nsys * n);
@@ -659,9 +661,10 @@ int Gmres::op_fp64(const double *x, long long ldx, double *yout, long long ldy, 
 }
 
 template <typename T>
-int Gmres::op_t(const T *x, long long ldx, T *yout, long long ldy) {
+int Gmres::op_t(const T *x, long long ldx, T *yout, long long ldy, int nact, const int *idx) {
   SysBatch b;
-  b.nsys = nsys;
+  b.nsys = nact > 0 ? nact : nsys;
+  b.idx = nact > 0 ? idx : nullptr;
   if constexpr (sizeof(T) == sizeof(float)) {
     b.xf = x;
     b.yf = yout;
@@ -841,11 +844,30 @@ int Gmres::solve_t(double tol, int max_iters, int *h_state, int max_cycles, bool
     // Arnoldi steps
     int active = 0;
     for (int s = 0; s < nsys; s++) active += h_state[s] == ST_IN_CYCLE;
+    // Systems whose cycle has ended stay in the batch until the cycle of every system has: the
+    // operator then runs on the systems in cycle only (their list, padded to a multiple of 4 with
+    // entries that read an active system and store nothing, so that the contraction widths repeat)
+    int nact = -1;
+    std::vector<int> h_act;
+    auto plan_active = [&]() -> int {
+      nact = -1;
+      if (active >= nsys || active == 0) return GFCC_OK;
+      h_act.clear();
+      for (int s = 0; s < nsys; s++)
+        if (h_state[s] == ST_IN_CYCLE) h_act.push_back(s);
+      const int padded = std::min(nsys, (active + 3) / 4 * 4);
+      while ((int)h_act.size() < padded) h_act.push_back(-1 - h_act[0]);
+      if (padded >= nsys) return GFCC_OK;   // no narrower than the batch: run it whole
+      GFCC_CUDA(cudaMemcpyAsync(act, h_act.data(), sizeof(int) * padded, cudaMemcpyHostToDevice, st));
+      nact = padded;
+      return GFCC_OK;
+    };
+    GFCC_TRY(plan_active());
     for (int k = 0; k < m; k++) {
       T *vk = Vt + 2 * (long long)k * n;
       T *w = Vt + 2 * (long long)(k + 1) * n;
       auto step = [&]() -> int {
-        GFCC_TRY(op_t<T>(vk, vs, w, vs));
+        GFCC_TRY(op_t<T>(vk, vs, w, vs, nact, act));
         // Gram-Schmidt against the basis: one classical pass (dots with ||w||^2, then update with
         // ||w'||^2), a second pass only where needed, then w /= ||w||.  Algorithmic bytes of one
         // classical pass per system: dots read k+1 basis vectors and w, the update reads k+1 basis
@@ -864,7 +886,7 @@ int Gmres::solve_t(double tol, int max_iters, int *h_state, int max_cycles, bool
         return GFCC_OK;
       };
       bool done_step = false;
-      if (use_graphs && gseen > 1 && !gbroken) {
+      if (use_graphs && gseen > 1 && !gbroken && nact < 0) {
         if (!gexec[k]) {
           // capture the step once (its launches are counted as they are recorded; the launch right
           // after the capture runs them), replay it afterwards.  A capture that fails leaves the
@@ -901,6 +923,7 @@ int Gmres::solve_t(double tol, int max_iters, int *h_state, int max_cycles, bool
       active = 0;
       for (int s = 0; s < nsys; s++) active += h_state[s] == ST_IN_CYCLE;
       if (active == 0) break;
+      GFCC_TRY(plan_active());
     }
     // x += V y
     backsolve_kernel<<<cdiv(nsys, TH), TH, 0, st>>>(nsys, m, H, g, state, kcyc, y, NV);

@@ -36,6 +36,7 @@ struct Gmres {
   double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr;
   double *bnorm = nullptr, *relres = nullptr, *est = nullptr, *omega = nullptr;
   int *state = nullptr, *kcyc = nullptr, *iters = nullptr, *rflag = nullptr;
+  int *act = nullptr;   // the systems the operator runs on in an Arnoldi step (see solve_t)
   double *relres0 = nullptr;   // relative residual of the initial iterate (first true residual)
   double *sigma_work = nullptr;
 
@@ -86,8 +87,9 @@ struct Gmres {
   int gnsys = -1, gseen = 0;
   bool gbroken = false;
   void drop_graphs();
+  // y = A x for the batch (nact < 0) or for the nact systems listed in the device array idx (SysBatch::idx)
   template <typename T>
-  int op_t(const T *x, long long ldx, T *y, long long ldy);
+  int op_t(const T *x, long long ldx, T *y, long long ldy, int nact = -1, const int *idx = nullptr);
   template <typename T>
   int mdot_t(const T *Vb, long long vs, long long vi, int nv, const T *w, long long ws, double *out, int want,
              int accumulate);

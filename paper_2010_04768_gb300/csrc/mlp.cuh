@@ -26,6 +26,8 @@ struct gfcc_mlp {
 namespace gfcc {
 // y[s] = model(feat[s]) with the inference copy, s < nb (device arrays, FP64 in and out).
 int mlp_infer(gfcc_mlp *m, cudaStream_t st, int nb, const double *feat, double *y);
+// left vectors C[q][mu] (real, [nq][dim]) of the orbitals d_orb (device) of one sector (api.cu)
+int build_left_vectors(gfcc_ctx *c, int sector, int nq, const int *d_orb, double *C, cudaStream_t st);
 // Right-hand sides of orbitals porb[s] (device) of one sector into B ([s][n] complex).
 int build_rhs(gfcc_ctx *c, int sector, int nsys, const int *d_porb, double *B, cudaStream_t st);
 // the same for the systems with d_mask[s] != 0 only

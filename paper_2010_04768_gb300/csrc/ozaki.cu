@@ -146,8 +146,37 @@ long long emu_gemm_work_bytes(long long M, long long N, long long K) {
 
 void emu_set_fused_max_n(long long n) { g_fused_max_n = n; }
 
+namespace {
+__global__ void max_int_kernel(const int *x, long long n, int *out) {
+  int m = -(1 << 30);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    m = max(m, x[t]);
+  for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+}  // namespace
+
+int emu_max_exponent(cudaStream_t st, const EmuOperand &e, int *out) {
+  int *d = nullptr;
+  const int init = -(1 << 30);
+  GFCC_CUDA(cudaMalloc(&d, sizeof(int)));
+  GFCC_CUDA(cudaMemcpyAsync(d, &init, sizeof(int), cudaMemcpyHostToDevice, st));
+  max_int_kernel<<<grid1d(e.rows), 256, 0, st>>>(e.exp2, e.rows, d);
+  cudaError_t er = cudaGetLastError();
+  count_launch();
+  if (er == cudaSuccess) er = cudaMemcpyAsync(out, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (er == cudaSuccess) er = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (er != cudaSuccess) {
+    set_error("emu_max_exponent: %s", cudaGetErrorString(er));
+    return GFCC_ERR_CUDA;
+  }
+  return GFCC_OK;
+}
+
 int emu_gemm(cudaStream_t st, const EmuOperand &A, const EmuOperand &B, int P, double alpha, double beta, double *C,
              IMap cm, IMap cn, void *work, long long n0) {
+  P = std::max(2, P - A.drop);
   const long long M = A.rows, N = B.rows, K = A.K;
   if (M <= 0 || N <= 0) return GFCC_OK;
   if (B.K != K || A.ld != B.ld) {

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include <cmath>
+
 #include "common.cuh"
 
 namespace gfcc {
@@ -13,7 +15,20 @@ struct EmuOperand {
   int *exp2 = nullptr;            // [rows]
   long long rows = 0, K = 0, ld = 0;
   int S = 0;
+  // levels this operand's products may drop (as the A operand of emu_gemm) while keeping the error
+  // bound of the level-P product of the operator with its Fock-like diagonal (set at setup: see
+  // emu_level_drop)
+  int drop = 0;
 };
+// Largest row scale exponent of an operand (max over rows of exp2[r]); host value, synchronises st.
+int emu_max_exponent(cudaStream_t st, const EmuOperand &e, int *out);
+// Levels an operand may drop: every product term of the operand is bounded by 2^-(6P-4) times its
+// row scale (at most 2^e_max), while the bound of the level-P product of the ring operator with the
+// diagonal folded in is at least 2^-(6P-4) times the smallest diagonal entry of its rows; one level
+// (6 bits) may go when 2^(e_max + 6) <= min_diag.  At most one level is dropped.
+static inline int emu_level_drop(int e_max, double min_diag) {
+  return (min_diag > 0.0 && std::ldexp(1.0, e_max + 6) <= min_diag) ? 1 : 0;
+}
 
 long long emu_operand_bytes(long long rows, long long K, int S);
 int emu_slice(cudaStream_t st, const double *A, long long rows, long long K, long long lda, int S, void *mem,

@@ -19,7 +19,11 @@
 // Every contraction below is one call of the strided FP64 contraction kernel; the
 // index maps place the result directly in the layout the sigma product reads.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <initializer_list>
+#include <vector>
+
 
 #include "ctx.cuh"
 #include "kernels.cuh"
@@ -189,6 +193,28 @@ __global__ void u1_foo_kernel(double *U1x, int o, long long o2v, long long ld, c
   if (t >= o * o) return;
   const int i = t / o, m = t % o;
   U1x[(long long)i * ld + o2v + m] = (m == i) ? 0.0 : -Foo[(long long)m * o + i];
+}
+
+// Digit-level drops of a sector's digit-plane operands (see emu_level_drop): the smallest magnitude of
+// the Fock-like diagonal entries cvv Fvv[a][a] + coo Foo[i][i] that the ring rows carried before the
+// diagonal was taken out, against each operand's largest row scale.
+int set_level_drops(gfcc_ctx *c, double cvv, double coo, std::initializer_list<EmuOperand *> ops) {
+  const int o = c->o, v = c->v;
+  std::vector<double> foo((size_t)o * o), fvv((size_t)v * v);
+  GFCC_CUDA(cudaMemcpyAsync(foo.data(), c->Foo, sizeof(double) * o * o, cudaMemcpyDeviceToHost, c->stream));
+  GFCC_CUDA(cudaMemcpyAsync(fvv.data(), c->Fvv, sizeof(double) * v * v, cudaMemcpyDeviceToHost, c->stream));
+  GFCC_CUDA(cudaStreamSynchronize(c->stream));
+  double mn = HUGE_VAL;
+  for (int i = 0; i < o; i++)
+    for (int a = 0; a < v; a++)
+      mn = std::min(mn, std::fabs(cvv * fvv[(size_t)a * v + a] + coo * foo[(size_t)i * o + i]));
+  for (EmuOperand *e : ops) {
+    if (e->dig == nullptr || e->rows <= 0) continue;
+    int emax = 0;
+    GFCC_TRY(emu_max_exponent(c->stream, *e, &emax));
+    e->drop = emu_level_drop(emax, mn);
+  }
+  return GFCC_OK;
 }
 
 }  // namespace
@@ -572,6 +598,16 @@ int build_hbar(gfcc_ctx *c, const double *d_fock, const double *d_chol) {
     GFCC_LAUNCH_CHECK();
     GFCC_TRY(alloc_bf16(c, &c->Wr_bf, ov * c->ld_ov));
     GFCC_TRY(to_bf16(st, t, ov, ov, ov, 1.0, c->Wr_bf, c->ld_ov));
+    // Digit planes of the FP64 operands for the FP64-accurate residual: the same couplings as the BF16
+    // operands (the exact Fock-like diagonal is applied in FP64 by the epilogue), so that each row's
+    // scale, and with it the truncation error of the digit pairs, is set by the couplings
+    const int S = c->emu_S;
+    auto slice = [&](const double *A, long long rows, long long K, long long lda, EmuOperand &e) -> int {
+      double *mem;
+      GFCC_TRY(dev_alloc(c, &mem, emu_operand_bytes(rows, K, S) / 8 + 1));
+      return emu_slice(st, A, rows, K, lda, S, mem, e);
+    };
+    GFCC_TRY(slice(t, ov, ov, ov, c->eWr));
     // Wq[(i,j)][(m,n)] = 1/2 Woooo[m][n][i][j]
     {
       const long long d[4] = {o, o, o, o};          // (i, j, m, n)
@@ -600,14 +636,7 @@ int build_hbar(gfcc_ctx *c, const double *d_fock, const double *d_chol) {
     GFCC_TRY(alloc_bf16(c, &c->U1_bf, o * c->ld_k1));
     GFCC_TRY(to_bf16(st, t, o, o2v + o, o2v + o, 1.0, c->U1_bf, c->ld_k1));
 
-    // digit planes of the FP64 operands (full Fock folding) for the FP64-accurate residual
-    const int S = c->emu_S;
-    auto slice = [&](const double *A, long long rows, long long K, long long lda, EmuOperand &e) -> int {
-      double *mem;
-      GFCC_TRY(dev_alloc(c, &mem, emu_operand_bytes(rows, K, S) / 8 + 1));
-      return emu_slice(st, A, rows, K, lda, S, mem, e);
-    };
-    GFCC_TRY(slice(c->Wr_ip, ov, ov, ov, c->eWr));
+    // the other digit-plane operands (oooo, [ovoo | three-body], three-body Z, 1h row)
     {
       const long long d[4] = {o, o, o, o};          // (i, j, m, n)
       const long long is[4] = {o, 1, o * oo, oo};
@@ -635,17 +664,16 @@ int build_hbar(gfcc_ctx *c, const double *d_fock, const double *d_chol) {
     }
     GFCC_TRY(slice(t2x, v, o2v + o, o2v + o, c->eV3));
     {
-      // [U1 | -Fbar_oo^T]: the 1h row with the full Fbar_oo
+      // [U1 | -Fbar_oo^T off the diagonal]: the 1h row without its diagonal -Fbar_oo[i][i]
       const long long d[4] = {1, 1, o, o2v};
       const long long is[4] = {0, 0, o2v, 1};
       const long long os[4] = {0, 0, o2v + o, 1};
       GFCC_TRY(permute4(st, d, c->U1, is, t2x, os, 1.0, 0.0));
-      const long long d2[4] = {1, 1, o, o};             // (i, m): t2x[i][o2v + m] = -Foo[m][i]
-      const long long is2[4] = {0, 0, 1, o};
-      const long long os2[4] = {0, 0, o2v + o, 1};
-      GFCC_TRY(permute4(st, d2, c->Foo, is2, t2x + o2v, os2, -1.0, 0.0));
+      u1_foo_kernel<<<cdiv(oo, 128), 128, 0, st>>>(t2x, o, o2v, o2v + o, c->Foo);
+      GFCC_LAUNCH_CHECK();
     }
     GFCC_TRY(slice(t2x, o, o2v + o, o2v + o, c->eU1));
+    GFCC_TRY(set_level_drops(c, 0.5, -1.0, {&c->eWr, &c->eWq, &c->eWT, &c->eV3, &c->eU1}));
   }
   if (want_ea && c->precision == GFCC_PREC_MIXED_BF16) {
     // BF16 EA operands (the Fock-like diagonal stays in FP64) and their FP64 digit planes
@@ -670,7 +698,8 @@ int build_hbar(gfcc_ctx *c, const double *d_fock, const double *d_chol) {
     GFCC_LAUNCH_CHECK();
     GFCC_TRY(alloc_bf16(c, &c->Wre_bf, ov * c->ld_ov));
     GFCC_TRY(to_bf16(st, t, ov, ov, ov, 1.0, c->Wre_bf, c->ld_ov));
-    GFCC_TRY(slice(c->Wr_ea, ov, ov, ov, c->eWre));
+    // digit planes of the same couplings (the exact diagonal is applied in FP64 by the epilogue)
+    GFCC_TRY(slice(t, ov, ov, ov, c->eWre));
     if (Pv > 0) {
       GFCC_TRY(alloc_bf16(c, &c->Wp_bf, Pv * c->ld_pv));
       GFCC_TRY(to_bf16(st, c->Wp, Pv, Pv, Pv, 1.0, c->Wp_bf, c->ld_pv));
@@ -700,7 +729,8 @@ int build_hbar(gfcc_ctx *c, const double *d_fock, const double *d_chol) {
       GFCC_TRY(permute4(st, d, c->V3e, is, t, os, 1.0, 0.0));
     }
     GFCC_TRY(slice(t, o, ov2 + v, ov2 + v, c->eV3e));
-    // 1p row: [U1e | Fbar_vv] (full, for the digit planes) and [U1e | Fbar_vv off-diagonal] (BF16)
+    // 1p row: [U1e | Fbar_vv off the diagonal] (the diagonal Fbar_vv[a][a] is applied in FP64), for the
+    // digit planes and the BF16 operand
     {
       const long long d[4] = {1, 1, v, ov2};
       const long long is[4] = {0, 0, ov2, 1};
@@ -711,9 +741,10 @@ int build_hbar(gfcc_ctx *c, const double *d_fock, const double *d_chol) {
       const long long os2[4] = {0, 0, ov2 + v, 1};
       GFCC_TRY(permute4(st, d2, c->Fvv, is2, t + ov2, os2, 1.0, 0.0));
     }
-    GFCC_TRY(slice(t, v, ov2 + v, ov2 + v, c->eU1e));
     diag_zero_kernel<<<cdiv(v, 128), 128, 0, st>>>(t + ov2, v, ov2 + v + 1);
     GFCC_LAUNCH_CHECK();
+    GFCC_TRY(slice(t, v, ov2 + v, ov2 + v, c->eU1e));
+    GFCC_TRY(set_level_drops(c, 1.0, -0.5, {&c->eWre, &c->eWp, &c->eWTe, &c->eV3e, &c->eU1e}));
     GFCC_TRY(alloc_bf16(c, &c->U1e_bf, v * c->ld_k1e));
     GFCC_TRY(to_bf16(st, t, v, ov2 + v, ov2 + v, 1.0, c->U1e_bf, c->ld_k1e));
   }

@@ -41,7 +41,7 @@ __device__ __forceinline__ Cplx cdivz(Cplx a, Cplx b) {
 __device__ __forceinline__ Cplx precond_in(const double *x, long long idx, const SysBatch &b, int s, long long mu) {
   Cplx u{x[2 * idx], x[2 * idx + 1]};
   if (b.diag != nullptr && b.omega != nullptr) {
-    const Cplx D{b.omega[s] + b.dsign * b.diag[mu], b.zsign * b.eta};
+    const Cplx D{b.omega[sysv(b, s)] + b.dsign * b.diag[mu], b.zsign * b.eta};
     u = cdivz(u, D);
   }
   return u;
@@ -63,7 +63,7 @@ __global__ void unpack_ip_kernel(SysBatch b, int o, int v, long long C2, double 
       if (m != j) {
         const long long lo = m < j ? m : j, hi = m < j ? j : m;
         const long long mu = o + pair_index(lo, hi, o) * v + e;
-        u = precond_in(b.x, s * b.ldx + mu, b, s, mu);
+        u = precond_in(b.x, (long long)sysv(b, s) * b.ldx + mu, b, s, mu);
         if (m > j) { u.r = -u.r; u.i = -u.i; }
       }
       double *dst = r2u + (((long long)m * v + e) * o + j) * C2 + 2 * s;
@@ -73,7 +73,7 @@ __global__ void unpack_ip_kernel(SysBatch b, int o, int v, long long C2, double 
       const long long q = t - tot2;
       const int s = (int)(q % ns);
       const int m = (int)(q / ns);
-      const Cplx u = precond_in(b.x, s * b.ldx + m, b, s, m);
+      const Cplx u = precond_in(b.x, (long long)sysv(b, s) * b.ldx + m, b, s, m);
       r1u[(long long)m * C2 + 2 * s] = u.r;
       r1u[(long long)m * C2 + 2 * s + 1] = u.i;
     }
@@ -100,7 +100,7 @@ __global__ void unpack_ea_kernel(SysBatch b, int o, int v, long long Pv, long lo
       if (a != e) {
         const long long lo = a < e ? a : e, hi = a < e ? e : a;
         const long long mu = v + (long long)m * Pv + pair_index(lo, hi, v);
-        u = precond_in(b.x, s * b.ldx + mu, b, s, mu);
+        u = precond_in(b.x, (long long)sysv(b, s) * b.ldx + mu, b, s, mu);
         if (a > e) { u.r = -u.r; u.i = -u.i; }
       }
       double *dst = y2u + (((long long)m * v + e) * v + a) * C2 + 2 * s;
@@ -114,7 +114,7 @@ __global__ void unpack_ea_kernel(SysBatch b, int o, int v, long long Pv, long lo
       const long long i = r % o;
       const long long ef = r / o;
       const long long mu = v + i * Pv + ef;
-      const Cplx u = precond_in(b.x, s * b.ldx + mu, b, s, mu);
+      const Cplx u = precond_in(b.x, (long long)sysv(b, s) * b.ldx + mu, b, s, mu);
       double *dst = y2p + (ef * o + i) * C2 + 2 * s;
       dst[0] = u.r;
       dst[1] = u.i;
@@ -122,7 +122,7 @@ __global__ void unpack_ea_kernel(SysBatch b, int o, int v, long long Pv, long lo
       const long long q = t - totu - totp;
       const int s = (int)(q % ns);
       const int a = (int)(q / ns);
-      const Cplx u = precond_in(b.x, s * b.ldx + a, b, s, a);
+      const Cplx u = precond_in(b.x, (long long)sysv(b, s) * b.ldx + a, b, s, a);
       y1u[(long long)a * C2 + 2 * s] = u.r;
       y1u[(long long)a * C2 + 2 * s + 1] = u.i;
     }
@@ -132,16 +132,16 @@ __global__ void unpack_ea_kernel(SysBatch b, int o, int v, long long Pv, long lo
 }  // namespace
 
 int launch_epilogue_ip(gfcc_ctx *c, const SysBatch &b, const double *S1, const double *T, const double *Q,
-                       const double *U) {
-  const long long C2 = 2LL * b.nsys;
-  (void)C2;
+                       const double *U, const double *diag) {
+  if (diag != nullptr)
+    return epi::launch_ip<double, epi::MODE_OFFDIAG>(c->stream, b, c->o, c->v, S1, T, Q, U, diag);
   return epi::launch_ip<double, epi::MODE_FULL>(c->stream, b, c->o, c->v, S1, T, Q, U, nullptr);
 }
 
 int launch_epilogue_ea(gfcc_ctx *c, const SysBatch &b, const double *S1, const double *T, const double *Qp,
-                       const double *U) {
-  const long long C2 = 2LL * b.nsys;
-  (void)C2;
+                       const double *U, const double *diag) {
+  if (diag != nullptr)
+    return epi::launch_ea<double, epi::MODE_OFFDIAG>(c->stream, b, c->o, c->v, c->Pv, S1, T, Qp, U, diag);
   return epi::launch_ea<double, epi::MODE_FULL>(c->stream, b, c->o, c->v, c->Pv, S1, T, Qp, U, nullptr);
 }
 

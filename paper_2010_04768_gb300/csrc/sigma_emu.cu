@@ -1,8 +1,11 @@
 // FP64-accurate IP operator y = (omega - i eta) x + sigma(x) evaluated from base-64 digit
 // planes on the BF16 tensor cores (ozaki.cu), for the residuals of the mixed-precision
-// refinement.  Same contractions and layouts as the BF16 operator of sigma_mixed.cu, but the
-// operator matrices carry the full Fock folding (the diagonal included) and every product is
-// FP64-accurate, so the refinement converges to the FP64 solution.
+// refinement.  Same contractions, layouts and operator couplings as the BF16 operator of
+// sigma_mixed.cu: the exact Fock-like diagonal and the shift are applied in FP64 by the epilogue,
+// and every coupling product is FP64-accurate, so the refinement converges to the FP64 solution.
+// Leaving the diagonal (orbital energies, order 1 Hartree) out of the digit planes lets each row's
+// power-of-two scale follow its couplings (about three orders of magnitude smaller on the synthetic
+// workloads), which lowers the truncation error of a given digit level by the same factor.
 //
 // Each vector plane (system s, re/im) shares one power-of-two scale: its packed entries are
 // written as digits of x 2^-e_c directly by the unpack kernels, so no FP64 copy of the
@@ -368,27 +371,38 @@ int apply_ip_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_do
     {
       // tensor-core work: one BF16 GEMM per digit pair (i, j), i + j <= P
       int pairs = 0;
-      for (int L = 2; L <= P; L++)
+      const int Pr = std::max(2, P - c->eWr.drop);
+      for (int L = 2; L <= Pr; L++)
         for (int i = 1; i <= S; i++)
           if (L - i >= 1 && L - i <= S) pairs++;
-      PhaseTimer tr(c, PH_RING_EMU, pairs * 2.0 * (double)(o * v) * (double)(o * v) * (double)(o * C2));
+      const double prod = 2.0 * (double)(o * v) * (double)(o * v) * (double)(o * C2);
+      PhaseTimer tr(c, PH_RING_EMU, prod);
+      PhaseTimer tw(c, PH_RING_EMU_WORK, pairs * prod);
       GFCC_TRY(emu_gemm(st, c->eWr, w.r2b, P, 1.0, 0.0, w.T, imap1(o * C2), imap1(1), w.gw));
     }
-    GFCC_TRY(emu_gemm(st, c->eWq, w.r2o, P, 1.0, 0.0, w.Q, imap1(v * C2), imap1(1), w.gw));
-    // three-body Z = V3 rk, then U = [W1 | T3] [r1 | Z] in one product over K = o + v
-    GFCC_TRY(emu_gemm(st, c->eV3, w.rk, P, 1.0, 0.0, w.Z, imap1(C2), imap1(1), w.gw));
-    rz_fill_kernel<<<grid1d(C2 * (o + v)), 256, 0, st>>>(x, b.ldx, C2, (int)o, w.Z, (int)v, w.Zt);
-    GFCC_LAUNCH_CHECK();
-    GFCC_TRY(emu_slice(st, w.Zt, C2, o + v, o + v, S, w.Zo.dig, w.Zo));
-    GFCC_TRY(emu_gemm(st, c->eWT, w.Zo, P, 1.0, 0.0, w.U, imap1(C2), imap1(1), w.gw));
-    GFCC_TRY(emu_gemm(st, c->eU1, w.rk, P, 1.0, 0.0, w.S1, imap1(C2), imap1(1), w.gw));
+    {
+      // oooo, three-body Z, [ovoo | three-body] U and the 1h row, one FP64 product each
+      PhaseTimer te(c, PH_EMU_OTHER, 2.0 * C2 * ((double)oo * oo * v + (double)v * o2v + (double)o2v * (o + v) +
+                                                 (double)o * (o2v + o)));
+      GFCC_TRY(emu_gemm(st, c->eWq, w.r2o, P, 1.0, 0.0, w.Q, imap1(v * C2), imap1(1), w.gw));
+      // three-body Z = V3 rk, then U = [W1 | T3] [r1 | Z] in one product over K = o + v
+      GFCC_TRY(emu_gemm(st, c->eV3, w.rk, P, 1.0, 0.0, w.Z, imap1(C2), imap1(1), w.gw));
+      rz_fill_kernel<<<grid1d(C2 * (o + v)), 256, 0, st>>>(x, b.ldx, C2, (int)o, w.Z, (int)v, w.Zt);
+      GFCC_LAUNCH_CHECK();
+      GFCC_TRY(emu_slice(st, w.Zt, C2, o + v, o + v, S, w.Zo.dig, w.Zo));
+      GFCC_TRY(emu_gemm(st, c->eWT, w.Zo, P, 1.0, 0.0, w.U, imap1(C2), imap1(1), w.gw));
+      GFCC_TRY(emu_gemm(st, c->eU1, w.rk, P, 1.0, 0.0, w.S1, imap1(C2), imap1(1), w.gw));
+    }
     SysBatch bb = b;
     bb.nsys = ns;
     bb.x = x;
     bb.y = b.y + 2 * (long long)s0 * b.ldy;
     bb.omega = b.omega ? b.omega + s0 : nullptr;
     bb.diag = nullptr;
-    GFCC_TRY(launch_epilogue_ip(c, bb, w.S1, w.T, w.Q, w.U));
+    {
+      PhaseTimer tp(c, PH_EPILOGUE, 8.0 * C2 * (3.0 * o2v + o) + 32.0 * ns * n);
+      GFCC_TRY(launch_epilogue_ip(c, bb, w.S1, w.T, w.Q, w.U, c->diag_ip));
+    }
   }
   return GFCC_OK;
 }
@@ -431,27 +445,38 @@ int apply_ea_emu(gfcc_ctx *c, const SysBatch &b, double *work, long long work_do
     }
     {
       int pairs = 0;
-      for (int L = 2; L <= P; L++)
+      const int Pr = std::max(2, P - c->eWre.drop);
+      for (int L = 2; L <= Pr; L++)
         for (int i = 1; i <= S; i++)
           if (L - i >= 1 && L - i <= S) pairs++;
-      PhaseTimer tr(c, PH_RING_EMU, pairs * 2.0 * (double)ov * (double)ov * (double)(v * C2));
+      const double prod = 2.0 * (double)ov * (double)ov * (double)(v * C2);
+      PhaseTimer tr(c, PH_RING_EMU, prod);
+      PhaseTimer tw(c, PH_RING_EMU_WORK, pairs * prod);
       GFCC_TRY(emu_gemm(st, c->eWre, w.r2e, P, 1.0, 0.0, w.T, imap1(v * C2), imap1(1), w.gw));
     }
-    if (Pv > 0) GFCC_TRY(emu_gemm(st, c->eWp, w.r2p, P, 1.0, 0.0, w.Qp, imap1(o * C2), imap1(1), w.gw));
-    // Z = V3e rk, then U = [W3 | T3e] [y1 | Z] in one product over K = v + o
-    GFCC_TRY(emu_gemm(st, c->eV3e, w.rk, P, 1.0, 0.0, w.Z, imap1(C2), imap1(1), w.gw));
-    rz_fill_kernel<<<grid1d(C2 * (v + o)), 256, 0, st>>>(x, b.ldx, C2, (int)v, w.Z, (int)o, w.Zt);
-    GFCC_LAUNCH_CHECK();
-    GFCC_TRY(emu_slice(st, w.Zt, C2, v + o, v + o, S, w.Zo.dig, w.Zo));
-    GFCC_TRY(emu_gemm(st, c->eWTe, w.Zo, P, 1.0, 0.0, w.U, imap1(C2), imap1(1), w.gw));
-    GFCC_TRY(emu_gemm(st, c->eU1e, w.rk, P, 1.0, 0.0, w.S1, imap1(C2), imap1(1), w.gw));
+    {
+      // vvvv, three-body Z, [vvvo | three-body] U and the 1p row, one FP64 product each
+      PhaseTimer te(c, PH_EMU_OTHER, 2.0 * C2 * ((double)Pv * Pv * o + (double)o * ov2 + (double)ov2 * (v + o) +
+                                                 (double)v * (ov2 + v)));
+      if (Pv > 0) GFCC_TRY(emu_gemm(st, c->eWp, w.r2p, P, 1.0, 0.0, w.Qp, imap1(o * C2), imap1(1), w.gw));
+      // Z = V3e rk, then U = [W3 | T3e] [y1 | Z] in one product over K = v + o
+      GFCC_TRY(emu_gemm(st, c->eV3e, w.rk, P, 1.0, 0.0, w.Z, imap1(C2), imap1(1), w.gw));
+      rz_fill_kernel<<<grid1d(C2 * (v + o)), 256, 0, st>>>(x, b.ldx, C2, (int)v, w.Z, (int)o, w.Zt);
+      GFCC_LAUNCH_CHECK();
+      GFCC_TRY(emu_slice(st, w.Zt, C2, v + o, v + o, S, w.Zo.dig, w.Zo));
+      GFCC_TRY(emu_gemm(st, c->eWTe, w.Zo, P, 1.0, 0.0, w.U, imap1(C2), imap1(1), w.gw));
+      GFCC_TRY(emu_gemm(st, c->eU1e, w.rk, P, 1.0, 0.0, w.S1, imap1(C2), imap1(1), w.gw));
+    }
     SysBatch bb = b;
     bb.nsys = ns;
     bb.x = x;
     bb.y = b.y + 2 * (long long)s0 * b.ldy;
     bb.omega = b.omega ? b.omega + s0 : nullptr;
     bb.diag = nullptr;
-    GFCC_TRY(launch_epilogue_ea(c, bb, w.S1, w.T, w.Qp, w.U));
+    {
+      PhaseTimer tp(c, PH_EPILOGUE, 8.0 * C2 * (2.0 * ov2 + (double)Pv * o + v) + 32.0 * ns * n);
+      GFCC_TRY(launch_epilogue_ea(c, bb, w.S1, w.T, w.Qp, w.U, c->diag_ea));
+    }
   }
   return GFCC_OK;
 }

@@ -36,6 +36,7 @@ struct Cz {
 };
 
 __device__ __forceinline__ Cz load_u(const SysBatch &b, int s, long long mu) {
+  s = sysv(b, s);
   Cz u;
   if (b.xf != nullptr) {
     const float2 t = reinterpret_cast<const float2 *>(b.xf)[s * b.ldx + mu];
@@ -399,23 +400,30 @@ int apply_ip_mixed(gfcc_ctx *c, const SysBatch &b, double *work) {
     GFCC_TRY(gemm_bf16_tn(st, c->Wr_bf, c->ld_ov, w.r2b, c->ld_ov, w.T, o * C2, (int)ov, (int)(o * C2), (int)ov, 1.0f,
                           0.0f));
   }
-  GFCC_TRY(gemm_bf16_tn(st, c->Wq_bf, c->ld_o2, w.r2o, c->ld_o2, w.Q, v * C2, (int)oo, (int)(v * C2), (int)oo, 1.0f,
-                        0.0f));
-  // three-body: Z (split K) -> BF16 transposed into rz[c][o + e]; then U = [W1 | T3] [r1 | Z]
-  const int zs = umma_splits((int)o2v, KSPLIT);
-  GFCC_TRY(gemm_bf16_tn(st, c->V3_bf, c->ld_o2v, w.rk, c->ld_k1, w.Zp, C2, (int)v, (int)C2, (int)o2v, 1.0f, 0.0f, zs,
-                        v * C2));
-  reduce_splits_kernel<<<grid1d(v * C2), 256, 0, st>>>(w.Zp, zs, v, C2, v * C2, w.rz + o, c->ld_ot);
-  GFCC_LAUNCH_CHECK();
-  GFCC_TRY(gemm_bf16_tn(st, c->WT_bf, c->ld_ot, w.rz, c->ld_ot, w.U, C2, (int)o2v, (int)C2, (int)(o + v), 1.0f,
-                        0.0f));
-  // 1h row (split K)
-  const int ss = umma_splits((int)(o2v + o), KSPLIT);
-  GFCC_TRY(gemm_bf16_tn(st, c->U1_bf, c->ld_k1, w.rk, c->ld_k1, w.S1p, C2, (int)o, (int)C2, (int)(o2v + o), 1.0f, 0.0f,
-                        ss, o * C2));
-  reduce_splits_kernel<<<grid1d(o * C2), 256, 0, st>>>(w.S1p, ss, o, C2, o * C2, nullptr, 0);
-  GFCC_LAUNCH_CHECK();
-  GFCC_TRY((epi::launch_ip<float, epi::MODE_OFFDIAG>(st, b, (int)o, (int)v, w.S1p, w.T, w.Q, w.U, c->diag_ip)));
+  {
+    PhaseTimer tob(c, PH_BF16_OTHER, 2.0 * C2 * ((double)oo * oo * v + (double)v * o2v + (double)o2v * (o + v) +
+                                                 (double)o * (o2v + o)));
+    GFCC_TRY(gemm_bf16_tn(st, c->Wq_bf, c->ld_o2, w.r2o, c->ld_o2, w.Q, v * C2, (int)oo, (int)(v * C2), (int)oo, 1.0f,
+                          0.0f));
+    // three-body: Z (split K) -> BF16 transposed into rz[c][o + e]; then U = [W1 | T3] [r1 | Z]
+    const int zs = umma_splits((int)o2v, KSPLIT);
+    GFCC_TRY(gemm_bf16_tn(st, c->V3_bf, c->ld_o2v, w.rk, c->ld_k1, w.Zp, C2, (int)v, (int)C2, (int)o2v, 1.0f, 0.0f, zs,
+                          v * C2));
+    reduce_splits_kernel<<<grid1d(v * C2), 256, 0, st>>>(w.Zp, zs, v, C2, v * C2, w.rz + o, c->ld_ot);
+    GFCC_LAUNCH_CHECK();
+    GFCC_TRY(gemm_bf16_tn(st, c->WT_bf, c->ld_ot, w.rz, c->ld_ot, w.U, C2, (int)o2v, (int)C2, (int)(o + v), 1.0f,
+                          0.0f));
+    // 1h row (split K)
+    const int ss = umma_splits((int)(o2v + o), KSPLIT);
+    GFCC_TRY(gemm_bf16_tn(st, c->U1_bf, c->ld_k1, w.rk, c->ld_k1, w.S1p, C2, (int)o, (int)C2, (int)(o2v + o), 1.0f, 0.0f,
+                          ss, o * C2));
+    reduce_splits_kernel<<<grid1d(o * C2), 256, 0, st>>>(w.S1p, ss, o, C2, o * C2, nullptr, 0);
+    GFCC_LAUNCH_CHECK();
+  }
+  {
+    PhaseTimer tp(c, PH_EPILOGUE, 4.0 * C2 * (3.0 * o2v + o) + (b.xf ? 16.0 : 32.0) * b.nsys * c->dim_ip);
+    GFCC_TRY((epi::launch_ip<float, epi::MODE_OFFDIAG>(st, b, (int)o, (int)v, w.S1p, w.T, w.Q, w.U, c->diag_ip)));
+  }
   return GFCC_OK;
 }
 
@@ -455,22 +463,28 @@ int apply_ea_mixed(gfcc_ctx *c, const SysBatch &b, double *work) {
     GFCC_TRY(gemm_bf16_tn(st, c->Wp_bf, c->ld_pv, w.r2p, c->ld_pv, w.Qp, o * C2, (int)Pv, (int)(o * C2), (int)Pv,
                           1.0f, 0.0f));
   }
-  // U[(i,b,a)][c] = [W3 | T3e] [y1 | Z],  Z[m][c] = V3e[m][(n,f,e)] y2[n,e,f] (split K, into rz[c][v + m])
-  const int zs = umma_splits((int)ov2, KSPLIT);
-  GFCC_TRY(gemm_bf16_tn(st, c->V3e_bf, c->ld_ov2, w.rk, c->ld_k1e, w.Zp, C2, (int)o, (int)C2, (int)ov2, 1.0f, 0.0f, zs,
-                        o * C2));
-  reduce_splits_kernel<<<grid1d(o * C2), 256, 0, st>>>(w.Zp, zs, o, C2, o * C2, w.rz + v, c->ld_ot);
-  GFCC_LAUNCH_CHECK();
-  GFCC_TRY(gemm_bf16_tn(st, c->WTe_bf, c->ld_ot, w.rz, c->ld_ot, w.U, C2, (int)ov2, (int)C2, (int)(v + o), 1.0f,
-                        0.0f));
-  // 1p row: S1[a][c] = [U1e | Fvv off-diagonal][a] . [y2 | y1](c) (split K)
-  const int ss = umma_splits((int)(ov2 + v), KSPLIT);
-  GFCC_TRY(gemm_bf16_tn(st, c->U1e_bf, c->ld_k1e, w.rk, c->ld_k1e, w.S1p, C2, (int)v, (int)C2, (int)(ov2 + v), 1.0f,
-                        0.0f, ss, v * C2));
-  reduce_splits_kernel<<<grid1d(v * C2), 256, 0, st>>>(w.S1p, ss, v, C2, v * C2, nullptr, 0);
-  GFCC_LAUNCH_CHECK();
-  GFCC_TRY((epi::launch_ea<float, epi::MODE_OFFDIAG>(st, b, (int)o, (int)v, Pv, w.S1p, w.T, w.Qp, w.U,
-                                                     c->diag_ea)));
+  {
+    PhaseTimer tob(c, PH_BF16_OTHER, 2.0 * C2 * ((double)o * ov2 + (double)ov2 * (v + o) + (double)v * (ov2 + v)));
+    // U[(i,b,a)][c] = [W3 | T3e] [y1 | Z],  Z[m][c] = V3e[m][(n,f,e)] y2[n,e,f] (split K, into rz[c][v + m])
+    const int zs = umma_splits((int)ov2, KSPLIT);
+    GFCC_TRY(gemm_bf16_tn(st, c->V3e_bf, c->ld_ov2, w.rk, c->ld_k1e, w.Zp, C2, (int)o, (int)C2, (int)ov2, 1.0f, 0.0f,
+                          zs, o * C2));
+    reduce_splits_kernel<<<grid1d(o * C2), 256, 0, st>>>(w.Zp, zs, o, C2, o * C2, w.rz + v, c->ld_ot);
+    GFCC_LAUNCH_CHECK();
+    GFCC_TRY(gemm_bf16_tn(st, c->WTe_bf, c->ld_ot, w.rz, c->ld_ot, w.U, C2, (int)ov2, (int)C2, (int)(v + o), 1.0f,
+                          0.0f));
+    // 1p row: S1[a][c] = [U1e | Fvv off-diagonal][a] . [y2 | y1](c) (split K)
+    const int ss = umma_splits((int)(ov2 + v), KSPLIT);
+    GFCC_TRY(gemm_bf16_tn(st, c->U1e_bf, c->ld_k1e, w.rk, c->ld_k1e, w.S1p, C2, (int)v, (int)C2, (int)(ov2 + v), 1.0f,
+                          0.0f, ss, v * C2));
+    reduce_splits_kernel<<<grid1d(v * C2), 256, 0, st>>>(w.S1p, ss, v, C2, v * C2, nullptr, 0);
+    GFCC_LAUNCH_CHECK();
+  }
+  {
+    PhaseTimer tp(c, PH_EPILOGUE, 4.0 * C2 * (2.0 * ov2 + (double)Pv * o + v) + (b.xf ? 16.0 : 32.0) * b.nsys * c->dim_ea);
+    GFCC_TRY((epi::launch_ea<float, epi::MODE_OFFDIAG>(st, b, (int)o, (int)v, Pv, w.S1p, w.T, w.Qp, w.U,
+                                                       c->diag_ea)));
+  }
   return GFCC_OK;
 }
 

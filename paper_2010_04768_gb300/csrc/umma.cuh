@@ -26,7 +26,14 @@ long long emu_fused_work_bytes(long long M, long long N, long long K);
 // Tile autotuning (on by default): the first call of each GEMM shape with beta == 0 times the
 // 64 / 128 / 256-column tiles and every later call of the shape uses the fastest.
 void umma_set_autotune(bool on);
+// CTA-pair tile (cta_group::2, 256 x 256 per pair): 0 timed by the autotuner beside the one-CTA tiles
+// (default), 1 used whenever it applies, 2 never
+void umma_set_pair_mode(int mode);
 int umma_tuned_tile(int M, int N, int K, int nsplit);   // 0 if the shape was not tuned yet
+// Limit of the bounded pipeline waits of the tensor-core kernels (process-wide; default 1 s) and a
+// test-only switch under which their producers issue no loads (the wait then runs out with nothing
+// in flight and the kernel returns the GFCC_ERR_TIMEOUT status).
+void umma_set_wait(unsigned long long wait_ns, bool skip_loads);
 int umma_error_reset(cudaStream_t st);
 int umma_error_check(cudaStream_t st);   // GFCC_ERR_TIMEOUT if a bounded wait gave up
 

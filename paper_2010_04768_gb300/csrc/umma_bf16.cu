@@ -43,7 +43,19 @@ struct Tile {
   static constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
 };
-constexpr unsigned long long WAIT_NS = 1000000000ULL;   // bounded waits: 1 s
+// Bounded waits.  The limit of the pipeline waits is a launch parameter (default 1 s, settable
+// process-wide so that a test can make a wait run out); the waits of the abort path, for work
+// this CTA has already issued, always keep the fixed DRAIN_NS.
+constexpr unsigned long long DRAIN_NS = 1000000000ULL;
+// Launch-time control of the pipeline: wait limit, and (test only) a producer that issues no
+// loads, so that the consumer's wait runs out with no asynchronous copy outstanding.
+struct UmmaCtl {
+  unsigned long long wait_ns;
+  int skip_loads;
+};
+unsigned long long g_wait_ns = 1000000000ULL;
+bool g_skip_loads = false;
+UmmaCtl umma_ctl() { return UmmaCtl{g_wait_ns, g_skip_loads ? 1 : 0}; }
 
 __device__ unsigned int g_umma_error = 0;
 
@@ -77,14 +89,16 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned addr, unsigned parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase of the given parity; false on time-out or abort.
-__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity, volatile int *abort_flag) {
+// Bounded wait (limit_ns of %globaltimer) for the phase of the given parity; false on time-out or
+// abort.
+__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity, volatile int *abort_flag,
+                                          unsigned long long limit_ns) {
   if (mbar_try_wait(addr, parity)) return true;
   const unsigned long long t0 = globaltimer();
   while (true) {
     if (mbar_try_wait(addr, parity)) return true;
     if (*abort_flag) return false;
-    if (globaltimer() - t0 > WAIT_NS) {
+    if (globaltimer() - t0 > limit_ns) {
       *abort_flag = 1;
       atomicOr(&g_umma_error, 1u);
       return false;
@@ -153,7 +167,7 @@ template <int BN, int ST>
 __global__ void __launch_bounds__(THREADS, 1)
     umma_bf16_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, float *D,
                           long long ldd, int M, int N, int K, float alpha, float beta, int kb_per_split,
-                          long long split_stride) {
+                          long long split_stride, UmmaCtl ctl) {
   constexpr int STAGES = Tile<BN, ST>::STAGES, A_BYTES = Tile<BN, ST>::A_BYTES,
                 STAGE_BYTES = Tile<BN, ST>::STAGE_BYTES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -209,10 +223,10 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
-    for (int kb = 0; kb < nk; kb++) {
+    for (int kb = 0; kb < nk && !ctl.skip_loads; kb++) {
       const int s = kb % STAGES;
       const unsigned ph = (kb / STAGES) & 1;
-      if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag)) break;
+      if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag, ctl.wait_ns)) break;
       unsigned char *sa = smem + s * STAGE_BYTES;
       unsigned char *sb = sa + A_BYTES;
       mbar_expect_tx(smem_u32(&full[s]), STAGE_BYTES);
@@ -227,7 +241,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int kb = 0; kb < nk && ok; kb++) {
       const int s = kb % STAGES;
       const unsigned ph = (kb / STAGES) & 1;
-      if (!mbar_wait(smem_u32(&full[s]), ph, abort_flag)) {
+      if (!mbar_wait(smem_u32(&full[s]), ph, abort_flag, ctl.wait_ns)) {
         ok = false;
         break;
       }
@@ -247,7 +261,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncwarp();
 
   // ---------------- epilogue: all 4 warps
-  const bool ready = mbar_wait(smem_u32(done), 0, abort_flag);
+  const bool ready = mbar_wait(smem_u32(done), 0, abort_flag, ctl.wait_ns);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   // tcgen05.ld is warp-collective: take the decision per warp
   if (__all_sync(0xffffffffu, ready && !*abort_flag)) {
@@ -281,13 +295,228 @@ __global__ void __launch_bounds__(THREADS, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (threadIdx.x == 0 && *abort_flag) {
-    // after a time-out: let the TMA copies this CTA issued land before its shared memory goes away
+    // after a time-out: the MMA warp always commits `done` once its issued products have completed
+    // (wait for it, so that no tcgen05.mma still reads shared memory or writes TMEM when the TMEM is
+    // freed), then let the TMA copies this CTA issued land before its shared memory goes away.
+    // These waits keep the fixed DRAIN_NS limit; if one of them runs out as well, the CTA exits with
+    // that work in flight (the error flag is already set).
     volatile int never = 0;
-    for (int kb = *consumed; kb < *issued; kb++) mbar_wait(smem_u32(&full[kb % STAGES]), (kb / STAGES) & 1, &never);
+    mbar_wait(smem_u32(done), 0, &never, DRAIN_NS);
+    for (int kb = *consumed; kb < *issued; kb++)
+      mbar_wait(smem_u32(&full[kb % STAGES]), (kb / STAGES) & 1, &never, DRAIN_NS);
   }
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// The same product on CTA pairs (tcgen05 cta_group::2): a cluster of two CTAs on two SMs computes a
+// 256 x 256 output tile with M = 256 MMAs.  Each CTA stages its own 128 rows of A and one half (128
+// columns) of the B tile, so per SM the shared memory holds and the tensor core reads half of the B
+// tile of the one-CTA kernel: with a 128 x 256 tile per SM the operand traffic through shared
+// memory (TMA writes plus MMA reads, about 1.5x the shared-memory bandwidth at the full MMA rate in
+// the one-CTA kernel) drops to about the bandwidth.  The leader CTA (cluster rank 0) issues the MMAs
+// for the pair; both CTAs' loads complete on the leader's barriers; the MMA commits arrive on the
+// barriers of both CTAs (multicast); each CTA's TMEM holds its own 128 rows of the accumulator and
+// each CTA writes them.  Same bounded waits and abort path as the one-CTA kernel; the pair meets at a
+// cluster barrier before either frees its TMEM and exits.
+constexpr int PAIR_BN = 256, PAIR_HALF = 128, PAIR_STAGES = 6;
+constexpr int PAIR_A_BYTES = BM * BK * 2, PAIR_B_BYTES = PAIR_HALF * BK * 2;
+constexpr int PAIR_STAGE_BYTES = PAIR_A_BYTES + PAIR_B_BYTES;
+constexpr int PAIR_SMEM_BYTES = PAIR_STAGES * PAIR_STAGE_BYTES + 1024 + 256;
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// shared::cluster address of a shared::cta address in CTA `rank` of the cluster
+__device__ __forceinline__ unsigned map_to_rank(unsigned addr, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+// TMA tile load into this CTA's shared memory, completion on an mbarrier of either CTA of the pair
+__device__ __forceinline__ void tma_load_2d_pair(unsigned dst, const CUtensorMap *map, unsigned mbar_cluster, int x,
+                                                 int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(mbar_cluster), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16_pair(unsigned d_tmem, unsigned long long a, unsigned long long b,
+                                               unsigned idesc, unsigned accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.u32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// arrive (once all earlier MMAs of this thread have completed) on the mbarrier at this shared
+// offset in both CTAs of the pair
+__device__ __forceinline__ void umma_commit_pair(unsigned mbar) {
+  const unsigned short mask = 0x3;
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(mbar),
+      "h"(mask)
+      : "memory");
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
+    umma_pair_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, float *D,
+                          long long ldd, int M, int N, int K, float alpha, float beta, int kb_per_split,
+                          long long split_stride, UmmaCtl ctl) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + PAIR_STAGES * PAIR_STAGE_BYTES);
+  unsigned long long *full = bars, *empty = bars + PAIR_STAGES, *done = bars + 2 * PAIR_STAGES;
+  unsigned *tmem_slot = reinterpret_cast<unsigned *>(bars + 2 * PAIR_STAGES + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  volatile int *issued = reinterpret_cast<volatile int *>(tmem_slot + 2);
+  volatile int *consumed = reinterpret_cast<volatile int *>(tmem_slot + 3);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned rank = cluster_rank();
+  const bool leader = rank == 0;
+  // pair tile order as in the one-CTA kernel, over 256-row pair tiles
+  int mp_tile, n_tile;
+  {
+    const int nM = gridDim.x / 2, nN = gridDim.y;
+    const int id = blockIdx.y * nM + (int)(blockIdx.x / 2);
+    const int first_m = (id / (RASTER_GM * nN)) * RASTER_GM;
+    const int gm = min(nM - first_m, RASTER_GM);
+    const int r = id - first_m * nN;
+    mp_tile = first_m + r % gm;
+    n_tile = r / gm;
+  }
+  const int m0 = mp_tile * (2 * BM) + (int)rank * BM;        // this CTA's rows
+  const int n0 = n_tile * PAIR_BN;                            // the pair's columns
+  const int nb0 = n0 + (int)rank * PAIR_HALF;                 // this CTA's half of the B tile
+  const int nk_all = (K + BK - 1) / BK;
+  const int kb0 = blockIdx.z * kb_per_split;
+  const int kb1 = min(nk_all, kb0 + kb_per_split);
+  const int nk = kb1 - kb0;
+  D += (long long)blockIdx.z * split_stride;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < PAIR_STAGES; s++) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(done), 1);
+    *abort_flag = 0;
+    *issued = 0;
+    *consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {   // TMEM of both CTAs: 256 FP32 columns x 128 lanes each (one warp per CTA)
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(PAIR_BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  cluster_sync_all();   // both CTAs' barriers initialised and TMEM allocated before any remote arrive
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer (both CTAs): loads complete on the leader's full barriers
+    for (int kb = 0; kb < nk && !ctl.skip_loads; kb++) {
+      const int s = kb % PAIR_STAGES;
+      const unsigned ph = (kb / PAIR_STAGES) & 1;
+      if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag, ctl.wait_ns)) break;
+      unsigned char *sa = smem + s * PAIR_STAGE_BYTES;
+      unsigned char *sb = sa + PAIR_A_BYTES;
+      if (leader) mbar_expect_tx(smem_u32(&full[s]), 2 * PAIR_STAGE_BYTES);
+      const unsigned fb = map_to_rank(smem_u32(&full[s]), 0);
+      tma_load_2d_pair(smem_u32(sa), &tmA, fb, (kb0 + kb) * BK, m0);
+      tma_load_2d_pair(smem_u32(sb), &tmB, fb, (kb0 + kb) * BK, nb0);
+      *issued = kb + 1;
+    }
+  } else if (warp == 1 && lane == 0 && leader) {
+    // ---------------- MMA issuer (leader only): M = 256 over the pair, N = 256
+    const unsigned idesc = idesc_bf16(2 * BM, PAIR_BN);
+    bool ok = true;
+    for (int kb = 0; kb < nk && ok; kb++) {
+      const int s = kb % PAIR_STAGES;
+      const unsigned ph = (kb / PAIR_STAGES) & 1;
+      if (!mbar_wait(smem_u32(&full[s]), ph, abort_flag, ctl.wait_ns)) {
+        ok = false;
+        break;
+      }
+      *consumed = kb + 1;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const unsigned sa = smem_u32(smem + s * PAIR_STAGE_BYTES);
+      const unsigned sb = sa + PAIR_A_BYTES;
+#pragma unroll
+      for (int k = 0; k < BK / 16; k++)
+        umma_bf16_pair(tmem, smem_desc(sa + 32 * k), smem_desc(sb + 32 * k), idesc, (kb > 0 || k > 0) ? 1u : 0u);
+      umma_commit_pair(smem_u32(&empty[s]));
+    }
+    umma_commit_pair(smem_u32(done));   // both CTAs: every MMA issued above has completed
+  }
+  __syncwarp();
+
+  // ---------------- epilogue: all 4 warps of each CTA, its own 128 rows (skipped once any CTA of the
+  // launch has given up, so that a pair whose leader aborted writes nothing)
+  const bool ready = mbar_wait(smem_u32(done), 0, abort_flag, ctl.wait_ns);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const bool failed = *reinterpret_cast<volatile unsigned *>(&g_umma_error) != 0;
+  if (__all_sync(0xffffffffu, ready && !*abort_flag && !failed) && nk > 0) {
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < PAIR_BN; c0 += 32) {
+      float v[32];
+      tmem_ld_32(tmem + ((unsigned)(warp * 32) << 16) + c0, v);
+      if (row < M && n0 + c0 < N) {
+        float *dst = D + (long long)row * ldd + n0 + c0;
+        const int ncols = min(32, N - (n0 + c0));
+        if (ncols == 32 && beta == 0.0f && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+#pragma unroll
+          for (int i = 0; i < 32; i += 4)
+            *reinterpret_cast<float4 *>(dst + i) = make_float4(alpha * v[i], alpha * v[i + 1], alpha * v[i + 2],
+                                                               alpha * v[i + 3]);
+        } else if (ncols == 32 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+#pragma unroll
+          for (int i = 0; i < 32; i += 4) {
+            const float4 d = *reinterpret_cast<const float4 *>(dst + i);
+            *reinterpret_cast<float4 *>(dst + i) =
+                make_float4(alpha * v[i] + beta * d.x, alpha * v[i + 1] + beta * d.y, alpha * v[i + 2] + beta * d.z,
+                            alpha * v[i + 3] + beta * d.w);
+          }
+        } else {
+          for (int i = 0; i < ncols; i++) dst[i] = alpha * v[i] + (beta != 0.0f ? beta * dst[i] : 0.0f);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0 && leader && *abort_flag) {
+    // leader after a time-out: the committed MMAs (done), then the loads it waited for of both CTAs
+    // (the pair's copies complete on the leader's barriers), each with the fixed DRAIN_NS limit
+    volatile int never = 0;
+    mbar_wait(smem_u32(done), 0, &never, DRAIN_NS);
+    for (int kb = *consumed; kb < *issued; kb++)
+      mbar_wait(smem_u32(&full[kb % PAIR_STAGES]), (kb / PAIR_STAGES) & 1, &never, DRAIN_NS);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  cluster_sync_all();   // neither CTA frees its TMEM or shared memory while the pair's work is in flight
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(PAIR_BN));
   }
 }
 
@@ -313,7 +542,7 @@ struct EmuMaps {
 __global__ void __launch_bounds__(THREADS, 1)
     umma_emu_kernel(const __grid_constant__ EmuMaps maps, int SA, int SB, int P, int M, int N, int K,
                     int kb_per_split, const int *eA, const int *eB, double alpha, double beta, double *C, IMap cm,
-                    IMap cn, long long n0g, double *part) {
+                    IMap cn, long long n0g, double *part, UmmaCtl ctl) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + EMU_STAGES * EMU_STAGE_BYTES);
@@ -355,10 +584,10 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer: stage t = (K block t / SAe, A plane t % SAe + 1)
-    for (int t = 0; t < iters; t++) {
+    for (int t = 0; t < iters && !ctl.skip_loads; t++) {
       const int s = t % EMU_STAGES;
       const unsigned ph = (t / EMU_STAGES) & 1;
-      if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag)) break;
+      if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag, ctl.wait_ns)) break;
       const int kb = kb0 + t / SAe, i = t % SAe + 1;
       const int nb = min(SB, P - i);
       unsigned char *sa = smem + s * EMU_STAGE_BYTES;
@@ -377,7 +606,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int t = 0; t < iters && ok; t++) {
       const int s = t % EMU_STAGES;
       const unsigned ph = (t / EMU_STAGES) & 1;
-      if (!mbar_wait(smem_u32(&full[s]), ph, abort_flag)) {
+      if (!mbar_wait(smem_u32(&full[s]), ph, abort_flag, ctl.wait_ns)) {
         ok = false;
         break;
       }
@@ -404,7 +633,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncwarp();
 
   // ---------------- epilogue: all 4 warps, one row per thread
-  const bool ready = mbar_wait(smem_u32(done), 0, abort_flag);
+  const bool ready = mbar_wait(smem_u32(done), 0, abort_flag, ctl.wait_ns);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (__all_sync(0xffffffffu, ready && !*abort_flag) && nk > 0) {
     const int row = m0 + warp * 32 + lane;
@@ -471,8 +700,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (threadIdx.x == 0 && *abort_flag) {
+    // as in umma_bf16_gemm_kernel: the committed products, then the issued copies (fixed limit)
     volatile int never = 0;
-    for (int t = *consumed; t < *issued; t++) mbar_wait(smem_u32(&full[t % EMU_STAGES]), (t / EMU_STAGES) & 1, &never);
+    mbar_wait(smem_u32(done), 0, &never, DRAIN_NS);
+    for (int t = *consumed; t < *issued; t++)
+      mbar_wait(smem_u32(&full[t % EMU_STAGES]), (t / EMU_STAGES) & 1, &never, DRAIN_NS);
   }
   __syncthreads();
   if (warp == 0) {
@@ -559,6 +791,9 @@ int umma_error_check(cudaStream_t st) {
 namespace {
 // tile autotuner state: (device, M, N, K, split) -> tile width
 bool g_autotune = true;
+// 0: the autotuner also times the CTA-pair tile; 1: the pair tile whenever it applies; 2: never
+int g_pair_mode = 0;
+constexpr int TILE_PAIR = 512;   // autotuner key of the 256 x 256 CTA-pair tile
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, int> g_tune;
 
@@ -583,7 +818,33 @@ int launch_umma_st(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const
   }
   dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, nsplit);
   umma_bf16_gemm_kernel<BN, ST><<<grid, THREADS, Tile<BN, ST>::SMEM_BYTES, st>>>(ma, mb, D, ldd, M, N, K, alpha, beta, kbs,
-                                                                         split_stride);
+                                                                         split_stride, umma_ctl());
+  GFCC_LAUNCH_CHECK();
+  return GFCC_OK;
+}
+
+int launch_umma_pair(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const __nv_bfloat16 *B, long long ldb,
+                     float *D, long long ldd, int M, int N, int K, float alpha, float beta, int nsplit, int kbs,
+                     long long split_stride) {
+  CUtensorMap ma, mb;
+  GFCC_TRY(make_map(&ma, A, M, K, lda, BM));
+  GFCC_TRY(make_map(&mb, B, N, K, ldb, PAIR_HALF));
+  static bool attr[64] = {false};
+  int dev = 0;
+  GFCC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64 || !attr[dev]) {
+    GFCC_CUDA(cudaFuncSetAttribute(umma_pair_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   PAIR_SMEM_BYTES));
+    if (dev >= 0 && dev < 64) attr[dev] = true;
+  }
+  const long long mp = (M + 2 * BM - 1) / (2 * BM);
+  if ((N + PAIR_BN - 1) / PAIR_BN > 65535 || nsplit > 65535 || 2 * mp > 0x7fffffffLL) {
+    set_error("gemm_bf16_tn: grid too large (M=%d, N=%d, nsplit=%d)", M, N, nsplit);
+    return GFCC_ERR_ARG;
+  }
+  dim3 grid((unsigned)(2 * mp), (N + PAIR_BN - 1) / PAIR_BN, nsplit);
+  umma_pair_gemm_kernel<<<grid, THREADS, PAIR_SMEM_BYTES, st>>>(ma, mb, D, ldd, M, N, K, alpha, beta, kbs,
+                                                                 split_stride, umma_ctl());
   GFCC_LAUNCH_CHECK();
   return GFCC_OK;
 }
@@ -622,11 +883,17 @@ int gemm_bf16_tn(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const _
   GFCC_TRY(check_extent_bytes(B, (long long)(N - 1) * ldb * 2 + (long long)K * 2, "bf16 GEMM operand B"));
   GFCC_TRY(check_extent_bytes(D, ((long long)(M - 1) * ldd + N + (long long)(nsplit - 1) * split_stride) * 4,
                               "bf16 GEMM output D"));
+  // tile widths: 64 / 128 / 256 columns per CTA, or TILE_PAIR (256 x 256 over a CTA pair)
   auto run = [&](int bn) -> int {
     if (bn == 64) return launch_umma<64>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
     if (bn == 128) return launch_umma<128>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
+    if (bn == TILE_PAIR)
+      return launch_umma_pair(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
     return launch_umma<256>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
   };
+  // the pair kernel needs two row tiles and pays off on wide products with a long K loop
+  const bool pair_ok = g_pair_mode != 2 && M > BM && N > 128 && kbs >= 8;
+  if (g_pair_mode == 1) return pair_ok ? run(TILE_PAIR) : run(N <= 64 ? 64 : (N <= 128 ? 128 : 256));
   // default: the narrowest tile that covers N (wide N keeps the 256-column tile)
   int bn = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
   if (g_autotune && beta != 0.0f) {
@@ -650,8 +917,8 @@ int gemm_bf16_tn(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const _
       GFCC_CUDA(cudaEventCreate(&e0));
       GFCC_CUDA(cudaEventCreate(&e1));
       float best_ms = 0.0f;
-      for (int cand : {64, 128, 256}) {
-        if (cand > 64 && cand / 2 >= N) continue;   // wider than twice the columns: never better
+      for (int cand : {64, 128, 256, TILE_PAIR}) {
+        if (cand == TILE_PAIR ? !pair_ok : (cand > 64 && cand / 2 >= N)) continue;   // never better
         GFCC_TRY(run(cand));
         GFCC_CUDA(cudaEventRecord(e0, st));
         GFCC_TRY(run(cand));
@@ -716,7 +983,7 @@ int emu_gemm_fused(cudaStream_t st, const __nv_bfloat16 *Adig, long long plA, in
     return GFCC_ERR_ARG;
   }
   umma_emu_kernel<<<grid, THREADS, EMU_SMEM_BYTES, st>>>(maps, SA, SB, P, M, N, K, 32, eA, eB, alpha, beta, C, cm, cn,
-                                                          n0, part);
+                                                          n0, part, umma_ctl());
   GFCC_LAUNCH_CHECK();
   if (nz > 1) {
     emu_split_reduce_kernel<<<grid1d((long long)M * N), 256, 0, st>>>(part, nz, M, N, eA, eB, alpha, beta, C, cm, cn,
@@ -727,6 +994,13 @@ int emu_gemm_fused(cudaStream_t st, const __nv_bfloat16 *Adig, long long plA, in
 }
 
 void umma_set_autotune(bool on) { g_autotune = on; }
+
+void umma_set_pair_mode(int mode) { g_pair_mode = mode; }
+
+void umma_set_wait(unsigned long long wait_ns, bool skip_loads) {
+  g_wait_ns = wait_ns;
+  g_skip_loads = skip_loads;
+}
 
 int umma_tuned_tile(int M, int N, int K, int nsplit) {
   int dev = 0;

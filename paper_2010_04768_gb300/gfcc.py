@@ -25,6 +25,7 @@ OPT_SECTOR, OPT_PRECISION, OPT_RESTART, OPT_MAX_ITERS, OPT_PRECOND, OPT_BATCH, O
 OPT_RESIDUAL, OPT_INNER_CYCLES, OPT_EMU_LEVEL = 8, 9, 10
 OPT_GUESS, OPT_KEEP_SOLUTIONS, OPT_INNER_KRYLOV, OPT_AUTOTUNE, OPT_GRAPHS, OPT_EMU_FUSED_N = 11, 12, 13, 14, 15, 16
 OPT_INCREMENTAL, OPT_INNER_RESTART = 17, 18
+OPT_SETUP_EMULATE_FLOPS, OPT_WAIT_NS, OPT_TEST_NO_LOADS, OPT_GEMM_PAIR = 19, 20, 21, 22
 GUESS_ZERO, GUESS_LEARNED, GUESS_MINRES = 0, 1, 2
 MLP_FP32, MLP_FP64 = 0, 1
 MLP_FEATURES, MLP_OUTPUTS = 27, 16
@@ -66,6 +67,9 @@ def load():
     lib.gfcc_set_stream.argtypes = [P, P]
     lib.gfcc_solve.argtypes = [P, ctypes.c_int, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.c_double, dp]
     lib.gfcc_solve_device.argtypes = [P, ctypes.c_int, P, ctypes.c_double, ctypes.c_int, P, ctypes.c_double, P]
+    lib.gfcc_solve_block.argtypes = [P, ctypes.c_int, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.c_int, ip,
+                                     ctypes.c_double, dp]
+    lib.gfcc_set_process_option.argtypes = [ctypes.c_int, ctypes.c_double]
     lib.gfcc_last_stats.argtypes = [P, ip, ip, dp, ip]
     lib.gfcc_sigma.argtypes = [P, ctypes.c_int, ctypes.c_int, dp, dp]
     lib.gfcc_sigma_ex.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
@@ -107,17 +111,35 @@ def load():
     lib.gfcc_mlp_train.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ull, dp]
     lib.gfcc_mlp_eval.argtypes = [P, dp]
     lib.gfcc_mlp_get_samples.argtypes = [P, ctypes.c_longlong, ctypes.c_int, dp, dp]
+    lib.gfcc_mor_create.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(P)]
+    lib.gfcc_mor_destroy.argtypes = [P]
+    lib.gfcc_mor_destroy.restype = None
+    lib.gfcc_mor_dim.argtypes = [P]
+    lib.gfcc_mor_expand.argtypes = [P, ctypes.c_int, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.c_double, dp]
+    lib.gfcc_mor_green.argtypes = [P, ctypes.c_int, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.c_int, ip, dp, dp]
+    lib.gfcc_mor_projected.argtypes = [P, dp, dp, ctypes.c_int]
+    lib.gfcc_spectral_adaptive.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int, ip, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_int, ctypes.c_int, dp, dp, ip, ip, dp, ctypes.c_int, ip]
+    lib.gfcc_spectral_adaptive.restype = ctypes.c_int
     lib.gfcc_last_error.restype = ctypes.c_char_p
     for name in ("gfcc_create", "gfcc_create_ex", "gfcc_set_option", "gfcc_set_stream", "gfcc_solve",
+                 "gfcc_solve_block", "gfcc_set_process_option",
                  "gfcc_solve_device", "gfcc_last_stats", "gfcc_sigma", "gfcc_dims", "gfcc_profile",
                  "gfcc_profile_read", "gfcc_guess_stats", "gfcc_set_guess_model", "gfcc_refine_stats",
                  "gfcc_residual_stats", "gfcc_solve_batch", "gfcc_mlp_create",
                  "gfcc_mlp_get_params", "gfcc_mlp_set_params", "gfcc_mlp_forward", "gfcc_mlp_loss_grad",
                  "gfcc_mlp_train_batch", "gfcc_mlp_collect", "gfcc_mlp_train", "gfcc_mlp_eval",
-                 "gfcc_mlp_get_samples"):
+                 "gfcc_mlp_get_samples", "gfcc_mor_create", "gfcc_mor_dim", "gfcc_mor_expand", "gfcc_mor_green",
+                 "gfcc_mor_projected"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
+
+
+def set_process_option(key: int, value: float):
+    """gfcc_set_process_option: a process-wide option (applies to every context)."""
+    _check(load().gfcc_set_process_option(int(key), float(value)))
 
 
 def launch_count() -> int:
@@ -215,6 +237,19 @@ class GFCC:
                                         G.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return G, code
 
+    def solve_block(self, omegas, eta: float, p_orbitals, q_orbitals, tol: float):
+        """G[w][a][b] = G_{p_a q_b} (complex128) for rows p over p_orbitals and columns q over q_orbitals,
+        and the return code."""
+        om = _f64(omegas).reshape(-1)
+        P = np.ascontiguousarray(p_orbitals, dtype=np.int32).reshape(-1)
+        Q = np.ascontiguousarray(q_orbitals, dtype=np.int32).reshape(-1)
+        G = np.zeros((om.size, P.size, Q.size), dtype=np.complex128)
+        ip = ctypes.POINTER(ctypes.c_int)
+        code = _check(load().gfcc_solve_block(self._h, om.size, _dp(om), float(eta), P.size, P.ctypes.data_as(ip),
+                                              Q.size, Q.ctypes.data_as(ip), float(tol),
+                                              G.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return G, code
+
     def solve_device(self, omegas_ptr: int, n_omega: int, eta: float, orbitals_ptr: int, n_orb: int, tol: float,
                      G_ptr: int):
         """gfcc_solve_device on caller-owned device buffers (e.g. torch tensors' data_ptr())."""
@@ -276,7 +311,7 @@ class GFCC:
         _check(load().gfcc_set_guess_model(self._h, None if model is None else model.handle))
 
     PHASES = ("setup", "ring", "vvvv", "sigma", "arnoldi", "lsq", "overlap", "solve", "ring_bf16", "ring_emu",
-              "unpack", "guess")
+              "unpack", "guess", "emu_other", "bf16_other", "epilogue", "ring_emu_work")
 
     def profile(self, enable: bool = True):
         _check(load().gfcc_profile(self._h, 1 if enable else 0))
@@ -417,3 +452,87 @@ class MLP:
         out = np.zeros(4)
         _check(load().gfcc_mlp_eval(self._h, _dp(out)))
         return {"loss": out[0], "loss_fallback": out[1], "loss_minres": out[2], "frac_better_than_zero": out[3]}
+
+
+class MOR:
+    """One gfcc_mor: the model-order reduction of one sector of a context (eq. model)."""
+
+    def __init__(self, ctx: GFCC, sector: str = "IP", drop_tol: float = 1e-10):
+        h = ctypes.c_void_p()
+        _check(load().gfcc_mor_create(ctx.handle, _SECTORS[sector], float(drop_tol), ctypes.byref(h)))
+        self._h = h
+        self._ctx = ctx   # the context outlives the object
+        self.sector = sector
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().gfcc_mor_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def dim(self) -> int:
+        return int(load().gfcc_mor_dim(self._h))
+
+    def expand(self, omegas, eta: float, orbitals, tol: float):
+        """Solve the full systems and add their solutions to the subspace; (G of those systems, code)."""
+        om = _f64(omegas).reshape(-1)
+        orb = np.ascontiguousarray(orbitals, dtype=np.int32).reshape(-1)
+        G = np.zeros((om.size, orb.size, orb.size), dtype=np.complex128)
+        code = _check(load().gfcc_mor_expand(self._h, om.size, _dp(om), float(eta), orb.size,
+                                             orb.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), float(tol),
+                                             G.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return G, code
+
+    def green(self, omegas, eta: float, p_orbitals, q_orbitals=None, residuals: bool = False):
+        """Model G[w][a][b] (rows p, columns q) and, with residuals=True, the model solutions' relative
+        full-space residuals."""
+        om = _f64(omegas).reshape(-1)
+        P = np.ascontiguousarray(p_orbitals, dtype=np.int32).reshape(-1)
+        Q = P if q_orbitals is None else np.ascontiguousarray(q_orbitals, dtype=np.int32).reshape(-1)
+        G = np.zeros((om.size, P.size, Q.size), dtype=np.complex128)
+        rr = np.zeros((om.size, P.size if self.sector == "IP" else Q.size)) if residuals else None
+        ip = ctypes.POINTER(ctypes.c_int)
+        _check(load().gfcc_mor_green(self._h, om.size, _dp(om), float(eta), P.size, P.ctypes.data_as(ip), Q.size,
+                                     Q.ctypes.data_as(ip), G.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     _dp(rr) if rr is not None else None))
+        return (G, rr) if residuals else G
+
+    def projected(self, rows: int = 0):
+        """(Hhat m x m, the first `rows` basis vectors)."""
+        m = self.dim()
+        H = np.zeros((m, m))
+        _, de = self._ctx.dims()
+        di, _ = self._ctx.dims()
+        n = di if self.sector == "IP" else de
+        S = np.zeros((min(rows, m), n)) if rows > 0 else None
+        _check(load().gfcc_mor_projected(self._h, _dp(H), _dp(S) if S is not None else None, int(min(rows, m))))
+        return H, S
+
+
+def spectral_adaptive(ctx: GFCC, sectors: str, omega_min: float, omega_max: float, d_omega: float, eta: float,
+                      orbitals, tol: float, level_tol: float, fine_omegas, max_levels: int = 30):
+    """gfcc_spectral_adaptive: (A on fine_omegas, levels [list of frequency lists], (m_IP, m_EA), code)."""
+    orb = np.ascontiguousarray(orbitals, dtype=np.int32).reshape(-1)
+    fine = _f64(fine_omegas).reshape(-1)
+    A = np.zeros(fine.size)
+    nlev = ctypes.c_int(0)
+    sizes = np.zeros(max_levels, dtype=np.int32)
+    cap = 4096
+    samp = np.zeros(cap)
+    mdim = np.zeros(2, dtype=np.int32)
+    ip = ctypes.POINTER(ctypes.c_int)
+    code = _check(load().gfcc_spectral_adaptive(ctx.handle, _SECTORS[sectors], float(omega_min), float(omega_max),
+                                                float(d_omega), float(eta), orb.size, orb.ctypes.data_as(ip),
+                                                float(tol), float(level_tol), int(max_levels), fine.size, _dp(fine),
+                                                _dp(A), ctypes.byref(nlev), sizes.ctypes.data_as(ip), _dp(samp), cap,
+                                                mdim.ctypes.data_as(ip)))
+    levels, k = [], 0
+    for L in range(nlev.value):
+        levels.append(list(samp[k:k + sizes[L]]))
+        k += sizes[L]
+    return A, levels, (int(mdim[0]), int(mdim[1])), code

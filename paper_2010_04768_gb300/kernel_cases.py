@@ -13,6 +13,9 @@ Shapes (M rows of the operator, N planar columns, K contraction length):
   vvvv-ea-medium   EA vvvv contraction, 40 systems: M = K = v (v - 1) / 2, N = 2 * 40 * o
   ring-ip-medium-emu   the IP ring contraction as an FP64-accurate product from 8 digit planes
                        per operand, digit pairs i + j <= 9
+  ring-ip-c60-half     the IP ring contraction of the C60-shaped workload (o=90 v=450, 30 systems:
+                       N = 2 * 30 * o = 5400) with M = K = o v / 2 = 20250, so that the operator
+                       (820 MB in BF16) is far larger than L2 as at full size (3.3 GB)
 """
 from __future__ import annotations
 
@@ -28,6 +31,7 @@ CASES = {
     "ring-ea-medium": (8000, 16000, 8000, None),
     "vvvv-ea-medium": (19900, 3200, 19900, None),
     "ring-ip-medium-emu": (8000, 3200, 8000, (8, 9)),
+    "ring-ip-c60-half": (20250, 5400, 20250, None),
 }
 
 

@@ -252,7 +252,7 @@ def orbitals_nearest_gap(eps_o: np.ndarray, eps_v: np.ndarray, count: int) -> np
 
 def workload(name: str) -> Workload:
     """The named workload.  'tiny' (o=4 v=12 L=48), 'medium' (o=40 v=200 L=800),
-    'c60' (o=90 v=450 L=1800)."""
+    'c60' (o=90 v=450 L=1800, 128 frequencies), 'c60x256' (the same problem, 256 frequencies)."""
     if name == "tiny":
         return Workload("tiny", 4, 12, 48, np.linspace(-1.0, -0.2, 4), 0.01,
                         np.arange(16, dtype=np.int32), 1e-8, 30, "IP")
@@ -265,5 +265,10 @@ def workload(name: str) -> Workload:
     if name == "c60":
         o, v = 90, 450
         return Workload("c60", o, v, 1800, np.linspace(-1.0, -0.3, 128), 0.005,
+                        np.arange(o - 30, o, dtype=np.int32), 1e-8, 30, "IP", precision="mixed")
+    if name == "c60x256":
+        # the C60-shaped problem on the denser grid of the learned-guess workload: 256 frequencies
+        o, v = 90, 450
+        return Workload("c60x256", o, v, 1800, np.linspace(-1.0, -0.3, 256), 0.005,
                         np.arange(o - 30, o, dtype=np.int32), 1e-8, 30, "IP", precision="mixed")
     raise KeyError(name)

@@ -64,3 +64,20 @@ def test_guess_model_arguments_are_rejected_without_a_gpu(lib):
     assert typed.gfcc_set_guess_model(None, None) == gfcc.ERR_ARG
     assert typed.gfcc_mlp_num_params(None) == 0
     typed.gfcc_mlp_destroy(None)
+
+
+def test_process_options_and_block_solve_arguments_without_a_gpu(lib):
+    # process-wide options are host state; bad keys, values and NULL contexts are rejected before any
+    # CUDA call
+    typed = gfcc.load()
+    assert typed.gfcc_set_process_option(999, 1.0) == gfcc.ERR_ARG
+    assert typed.gfcc_set_process_option(gfcc.OPT_WAIT_NS, 0.0) == gfcc.ERR_ARG
+    assert typed.gfcc_set_process_option(gfcc.OPT_TEST_NO_LOADS, 2.0) == gfcc.ERR_ARG
+    assert typed.gfcc_set_process_option(gfcc.OPT_SETUP_EMULATE_FLOPS, -1.0) == gfcc.ERR_ARG
+    assert typed.gfcc_set_process_option(gfcc.OPT_WAIT_NS, 1e9) == gfcc.OK
+    assert typed.gfcc_set_process_option(gfcc.OPT_TEST_NO_LOADS, 0.0) == gfcc.OK
+    assert typed.gfcc_set_process_option(gfcc.OPT_SETUP_EMULATE_FLOPS, 4e12) == gfcc.OK
+    om = (ctypes.c_double * 1)(0.1)
+    orb = (ctypes.c_int * 1)(0)
+    G = (ctypes.c_double * 2)()
+    assert typed.gfcc_solve_block(None, 1, om, 0.01, 1, orb, 1, orb, 1e-8, G) == gfcc.ERR_ARG

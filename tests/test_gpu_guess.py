@@ -84,9 +84,24 @@ def test_forward_fp16_weights_matches_rounded_oracle():
     r = []
     for a, half in ((W1, 1), (b1, 0), (W2, 1), (b2, 0), (W3, 1), (b3, 0), (mu, 0), (sd, 0)):
         r.append(a.astype(np.float16 if half else np.float32).astype(np.float64).ravel())
-    ref = M.MLPRef(np.concatenate(r), 256).forward(F)[-1]
-    # FP32 accumulation over 256 hidden units of O(1) activations
-    assert np.max(np.abs(y - ref)) <= 1e-4 * np.max(np.abs(ref))
+    rnet = M.MLPRef(np.concatenate(r), 256)
+    ref = rnet.forward(F)[-1]
+    # A-priori bound of the FP32 evaluation (both sides use the same FP16 weights): the input
+    # (x - mu) / sd is rounded once to FP32 (|dx| <= u |x|); each layer z = b + W h sums n terms in FP32
+    # (fused or not, any order), so |fl(z) - z| <= |W| e_in + gamma_n (|b| + |W| (|h| + e_in)) with
+    # gamma_n = n u / (1 - n u), u = 2^-24 (Higham, Accuracy and Stability of Numerical Algorithms, 3.1);
+    # ReLU is 1-Lipschitz, so the bound e of a layer's output is the input bound of the next.
+    u = 2.0 ** -24
+    gam = lambda n: n * u / (1 - n * u)
+    W1r, b1r, W2r, b2r, W3r, b3r, mur, sdr = rnet.unpack()
+    xh = (F - mur) / sdr
+    h1 = np.maximum(xh @ W1r.T + b1r, 0.0)
+    h2 = np.maximum(h1 @ W2r.T + b2r, 0.0)
+    e0 = u * np.abs(xh)
+    e1 = e0 @ np.abs(W1r).T + gam(W1r.shape[1]) * (np.abs(b1r) + (np.abs(xh) + e0) @ np.abs(W1r).T)
+    e2 = e1 @ np.abs(W2r).T + gam(W2r.shape[1]) * (np.abs(b2r) + (h1 + e1) @ np.abs(W2r).T)
+    e3 = e2 @ np.abs(W3r).T + gam(W3r.shape[1]) * (np.abs(b3r) + (h2 + e2) @ np.abs(W3r).T)
+    assert np.all(np.abs(y - ref) <= e3 + 1e-12 * np.abs(ref))
     ref64 = net.forward(F)[-1]
     assert np.max(np.abs(y - ref64)) <= 5e-3 * np.max(np.abs(ref64))
 

@@ -1,0 +1,158 @@
+"""Model-order reduction on the GPU (gfcc_mor_*) against the CPU oracle (oracle/mor_ref.py).
+
+* a subspace that spans the whole packed space reproduces the exact G (dense LU of the oracle's
+  operator) at any frequency, FP64 to 1e-10;
+* the projected operator Hhat = S^T Hbar S of the GPU's own basis against the oracle's dense operator;
+  the basis is orthonormal;
+* interpolation: at the sampled frequencies the model G equals the full G of the same solves;
+* between the samples the model depends only on the span of the subspace, so the GPU model G equals
+  the oracle's model built from its own dense solutions at the same sampled frequencies;
+* the model residuals (from W = Hbar S) against the oracle's dense residual of the lifted solution;
+* a mixed-precision context builds the same model (FP64-accurate sigma products for W).
+"""
+import numpy as np
+import pytest
+
+from oracle import mor_ref as R
+from oracle.gfcc_ref import GFCCOracle, ip_dim, ea_dim
+from paper_2010_04768_gb300 import gfcc
+from paper_2010_04768_gb300.synthetic import make_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built():
+    from paper_2010_04768_gb300 import build
+    build.build()
+    gfcc.load()
+
+
+def rel_err(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("sector", ["IP", "EA"])
+def test_whole_space_model_is_exact(sector):
+    o, v, L = 3, 5, 6
+    pr = make_problem(o, v, L, seed=4, t1_std=0.05, t2_std=0.05, chol_sigma=0.3)
+    g = gfcc.GFCC(pr, sectors=sector)
+    mor = gfcc.MOR(g, sector)
+    orbs = np.arange(o + v, dtype=np.int32)
+    n = ip_dim(o, v) if sector == "IP" else ea_dim(o, v)
+    _, code = mor.expand(np.array([-0.7, 0.2, 1.1]), 0.05, orbs, 1e-13)
+    assert code == gfcc.OK and mor.dim() == n
+    om = np.linspace(-1.5, 2.0, 9)
+    G = mor.green(om, 0.02, orbs)
+    orc = GFCCOracle(pr.fock, pr.chol, pr.t1, pr.t2, o=o, sectors=(sector,))
+    ref = orc.green_dense(om, 0.02, list(orbs), sectors=(sector,))
+    assert rel_err(G, ref) <= 1e-10
+    H, S = mor.projected(rows=n)
+    assert np.abs(S @ S.T - np.eye(n)).max() <= 1e-12
+    M = orc.ip_matrix() if sector == "IP" else orc.ea_matrix()
+    assert np.abs(H - S @ M @ S.T).max() <= 1e-12 * np.abs(H).max()
+    mor.close()
+    g.close()
+
+
+@pytest.mark.parametrize("sector", ["IP", "EA"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_model_interpolates_and_matches_oracle_model(sector, precision):
+    o, v, L = 4, 16, 30
+    pr = make_problem(o, v, L, seed=7)
+    eta = 0.02
+    samp = np.array([-0.9, -0.3] if sector == "IP" else [0.15, 0.6])
+    orbs = np.array([o - 2, o - 1, o, o + 1], dtype=np.int32)
+    g = gfcc.GFCC(pr, sectors=sector, precision=precision)
+    mor = gfcc.MOR(g, sector)
+    Gfull, code = mor.expand(samp, eta, orbs, 1e-12)
+    assert code == gfcc.OK
+    m = mor.dim()
+    assert 0 < m <= 2 * samp.size * orbs.size
+    # interpolation at the sampled frequencies
+    Gm = mor.green(samp, eta, orbs)
+    assert rel_err(Gm, Gfull) <= 1e-9
+    # between the samples: the oracle's model from its own dense solutions at the same frequencies
+    orc = GFCCOracle(pr.fock, pr.chol, pr.t1, pr.t2, o=o, sectors=(sector,))
+    Mx = orc.ip_matrix() if sector == "IP" else orc.ea_matrix()
+    n = Mx.shape[0]
+    B = np.stack([(orc.ip_rhs(p) if sector == "IP" else orc.ea_rhs(p)) for p in orbs], axis=1).astype(complex)
+    C = np.stack([(orc.ip_left(p) if sector == "IP" else orc.ea_left(p)) for p in orbs], axis=1)
+    X = []
+    for om in samp:
+        A = ((om - 1j * eta) * np.eye(n) + Mx) if sector == "IP" else ((om + 1j * eta) * np.eye(n) - Mx)
+        X += list(np.linalg.solve(A, B).T)
+    S = R.orthonormal_extend(None, R.real_parts(X))
+    assert S.shape[1] == m
+    Hh, W = R.project(orc.ip_sigma if sector == "IP" else orc.ea_sigma, S)
+    mid = np.linspace(samp[0], samp[1], 5)
+    Gmid, rr = mor.green(mid, eta, orbs, residuals=True)
+    ref = R.model_green(Hh, S, B.real, C, mid, eta, sector)
+    assert rel_err(Gmid, ref) <= 1e-8
+    # the model residuals against the oracle's
+    for w, om in enumerate(mid):
+        for a in range(orbs.size):
+            r_ref = R.model_relres(Hh, S, W, B[:, a].real, om, eta, sector)
+            assert rr[w, a] == pytest.approx(r_ref, rel=1e-6, abs=1e-10)
+    assert np.all(rr[[0, -1]] <= 1e-9)   # the sampled frequencies themselves
+    mor.close()
+    g.close()
+
+
+def test_adaptive_levels_and_spectral_function_match_oracle():
+    # the level driver (gfcc_spectral_adaptive) against the oracle's driver with dense solves and the
+    # same indicator (largest relative model residual over orbitals and sectors at each midpoint)
+    # (4 levels of 3, 2, 4, 8 frequencies; subspaces of 59 of 64 IP and 134 of 190 EA dimensions)
+    o, v, L = 4, 10, 12
+    pr = make_problem(o, v, L, seed=11, t1_std=0.05, t2_std=0.05, chol_sigma=0.3)
+    orbs = np.array([o - 2, o - 1, o, o + 1], dtype=np.int32)
+    eta, wmin, wmax, dw, ltol = 0.05, -1.6, 2.0, 0.02, 1e-2
+    fine = np.linspace(wmin, wmax, 181)
+    g = gfcc.GFCC(pr, sectors="IP+EA")
+    A, levels, mdim, code = gfcc.spectral_adaptive(g, "IP+EA", wmin, wmax, dw, eta, orbs, 1e-12, ltol, fine)
+    g.close()
+    assert code == gfcc.OK and len(levels) >= 3 and levels[0] == [wmin, 0.5 * (wmin + wmax), wmax]
+    assert len(levels) <= R.l_max_bound(wmin, wmax, dw)
+    assert all(len(lv) <= R.n_max(k + 1) for k, lv in enumerate(levels))
+    orc = GFCCOracle(pr.fock, pr.chol, pr.t1, pr.t2, o=o)
+    mats = {"IP": orc.ip_matrix(), "EA": orc.ea_matrix()}
+    rhs = {"IP": np.stack([orc.ip_rhs(p) for p in orbs], axis=1), "EA": np.stack([orc.ea_rhs(p) for p in orbs], axis=1)}
+    lefts = {"IP": np.stack([orc.ip_left(p) for p in orbs], axis=1),
+             "EA": np.stack([orc.ea_left(p) for p in orbs], axis=1)}
+
+    def model(sector, sampled):
+        Mx, B = mats[sector], rhs[sector].astype(complex)
+        n = Mx.shape[0]
+        X = []
+        for om in sampled:
+            Az = ((om - 1j * eta) * np.eye(n) + Mx) if sector == "IP" else ((om + 1j * eta) * np.eye(n) - Mx)
+            X += list(np.linalg.solve(Az, B).T)
+        S = R.orthonormal_extend(None, R.real_parts(X))
+        Hh, W = R.project(orc.ip_sigma if sector == "IP" else orc.ea_sigma, S)
+        return S, Hh, W
+
+    margins = []
+
+    def indicator(w, sampled):
+        e = 0.0
+        for sector in ("IP", "EA"):
+            S, Hh, W = model(sector, sampled)
+            for a in range(orbs.size):
+                e = max(e, R.model_relres(Hh, S, W, rhs[sector][:, a], w, eta, sector))
+        margins.append(abs(np.log10(max(e, 1e-300) / ltol)))
+        return e
+
+    ref_levels = R.adaptive_levels(indicator, wmin, wmax, dw, ltol)
+    assert min(margins) > 0.1   # no midpoint within 25% of the tolerance: the comparison is not borderline
+    assert len(ref_levels) == len(levels)
+    for a, b in zip(ref_levels, levels):
+        assert np.allclose(sorted(a), sorted(b), rtol=0, atol=1e-12)
+    sampled = [w for lv in ref_levels for w in lv]
+    Gd = {}
+    for sector in ("IP", "EA"):
+        S, Hh, W = model(sector, sampled)
+        Gs = R.model_green(Hh, S, rhs[sector], lefts[sector], fine, eta, sector)
+        Gd[sector] = np.einsum("wpp->wp", Gs)
+        assert S.shape[1] == mdim[0 if sector == "IP" else 1]
+    Aref = R.spectral_function(Gd["IP"], Gd["EA"])
+    assert np.abs(A - Aref).max() <= 1e-8 * np.abs(Aref).max()

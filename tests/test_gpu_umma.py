@@ -81,3 +81,47 @@ def test_tile_autotuner_gives_the_same_products():
                 assert np.max(np.abs(D - out[(M, N, K)][0])) <= 1e-5 * np.max(np.abs(D))
     g.set_option(gfcc.OPT_AUTOTUNE, 1)
     g.close()
+
+
+@pytest.fixture
+def pair_mode():
+    # force the CTA-pair (cta_group::2) kernel where it applies; restore autotuning afterwards
+    gfcc.set_process_option(gfcc.OPT_GEMM_PAIR, 1.0)
+    yield
+    gfcc.set_process_option(gfcc.OPT_GEMM_PAIR, 0.0)
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 256, 512), (300, 520, 700), (640, 300, 4096), (129, 257, 520),
+                                   (1024, 1024, 8192)])
+def test_pair_gemm_matches_reference(pair_mode, M, N, K):
+    # 256 x 256 tiles over CTA pairs: row tails inside a pair and past it, column tails inside a half
+    A = normal(3, 1, M * K).reshape(M, K).astype(np.float32)
+    B = normal(4, 1, N * K).reshape(N, K).astype(np.float32)
+    D = gfcc.selftest_gemm_bf16(A, B)
+    Ab, Bb = bf16_round(A), bf16_round(B)
+    ref = Ab @ Bb.T
+    scale = np.abs(Ab) @ np.abs(Bb).T
+    err = np.abs(D.astype(np.float64) - ref) / scale
+    assert err.max() <= 4 * K * 2.0**-24 + 1e-7
+
+
+def test_pair_gemm_integer_products_are_exact(pair_mode):
+    M, N, K = 512, 384, 16384
+    rng = np.random.default_rng(6)
+    A = rng.integers(-32, 33, size=(M, K)).astype(np.float32)
+    B = rng.integers(-32, 33, size=(N, K)).astype(np.float32)
+    A[0, :] = 32
+    B[0, :] = 32
+    D = gfcc.selftest_gemm_bf16(A, B)
+    ref = A.astype(np.int64) @ B.astype(np.int64).T
+    assert np.array_equal(D.astype(np.int64), ref)
+
+
+def test_pair_emulated_product_is_fp64_accurate(pair_mode):
+    # the wide digit-pair products of the FP64 emulation on the pair kernel
+    rng = np.random.default_rng(9)
+    M, N, K = 600, 700, 3000
+    A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-3, 3, size=(M, 1)))
+    B = rng.standard_normal((N, K)) * np.exp(rng.uniform(-3, 3, size=(N, 1)))
+    C = gfcc.selftest_gemm_f64emu(A, B, S=8, P=9)
+    assert (np.abs(C - A @ B.T) / (np.abs(A) @ np.abs(B).T)).max() <= 1e-13
