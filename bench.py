@@ -66,13 +66,21 @@ WORKLOADS = {
     "c60-ip-mixed": dict(base="c60", sector="IP", precision="mixed", per_step=1),
     "c60-ip-fp64": dict(base="c60", sector="IP", precision="fp64", per_step=1),
     # learned initial guesses on the C60-shaped problem (256 frequencies in [-1.0, -0.3]: spacing 0.55
-    # eta): each step solves 8 consecutive grid frequencies x 30 orbitals in one call, each system
-    # started from the guess named; the model is trained beforehand on two other seeds of the same shape
-    "c60x256-ip-mixed-sweep": dict(base="c60x256", sector="IP", precision="mixed", per_step=8, sweep=True),
-    "c60x256-ip-mixed-sweep-minres": dict(base="c60x256", sector="IP", precision="mixed", per_step=8, sweep=True,
+    # eta): each step solves 16 consecutive grid frequencies x 30 orbitals in one call, each system
+    # started from the guess named (the learned model needs 8 converged neighbours, so the first
+    # frequencies of a window start from zero); the model is trained beforehand on another seed of the
+    # same shape
+    "c60x256-ip-mixed-sweep": dict(base="c60x256", sector="IP", precision="mixed", per_step=16, sweep=True),
+    "c60x256-ip-mixed-sweep-minres": dict(base="c60x256", sector="IP", precision="mixed", per_step=16, sweep=True,
                                           guess="minres"),
-    "c60x256-ip-mixed-sweep-learned": dict(base="c60x256", sector="IP", precision="mixed", per_step=8, sweep=True,
+    "c60x256-ip-mixed-sweep-learned": dict(base="c60x256", sector="IP", precision="mixed", per_step=16, sweep=True,
                                            guess="learned"),
+    # closed-shell spin-adapted IP (spatial orbitals, FP64), beside the spin-orbital FP64 path on the
+    # spin-orbital embedding of the same system
+    "medium-closed-shell-ip-fp64": dict(base="medium-closed-shell", sector="IP", precision="fp64", per_step=1),
+    # ground-state CCSD (the step before the Green's function): one step = one T iteration
+    "ccsd-medium": dict(ccsd=(40, 200, 800), emulate=True),
+    "ccsd-medium-fp64": dict(ccsd=(40, 200, 800), emulate=False),
 }
 DEFAULT_WORKLOAD = "c60-ip-mixed"
 E2E_STEPS = 5        # steps of the end-to-end (host API) measurement: min(steps, E2E_STEPS)
@@ -84,7 +92,16 @@ INNER_RESTART = 60   # restart length of the inner GMRES of the mixed-precision 
 # keyed by roofline phase: {"traffic": DRAM bytes per launch, "algorithmic_bytes": bytes one launch
 # must move (operands once, output once), "case": the captured shape}.  A phase without a capture of
 # its current kernel reports traffic null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    "ring_bf16": {"traffic": 8.094e9, "algorithmic_bytes": 1.476e9,
+                  "case": "umma_pair_gemm_kernel at the C60-shaped ring contraction with M = K = 20250, N = 5400 "
+                          "(kernel_cases ring-ip-c60-half; profiles/umma_pair_ring_ip_c60half.md): DRAM bytes of one "
+                          "launch of that case, not of a bench launch"},
+    "ring_emu": {"traffic": 0.710e9, "algorithmic_bytes": 0.332e9,
+                 "case": "umma_pair_gemm_kernel on one digit pair at the medium ring shape M = K = 8000, N = 3200 "
+                         "(kernel_cases ring-ip-medium-emu; profiles/umma_pair_digit_pairs_ring_ip_medium.md): mean "
+                         "of two pair launches, algorithmic bytes 281-383 MB"},
+}
 
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 flops x max clock
 
@@ -351,6 +368,38 @@ def run_reference(args, world, rank):
         print(json.dumps({"impl": "reference", "unavailable": "the oracle has no multi-molecule batch; run the "
                           "reference arm on a single-molecule workload"}), flush=True)
         return 0
+    if spec.get("ccsd"):
+        # the oracle's T residual at half the shape, scaled by the o^2 v^4 ratio (the oracle's vvvv
+        # block at the full shape alone would be 12.8 GB); each step is one such residual
+        from oracle import ccsd_ref
+        from paper_2010_04768_gb300.synthetic import make_problem
+        o, v, L = spec["ccsd"]
+        so, sv, sL = o // 2, v // 2, L // 2
+        sp = make_problem(so, sv, sL, seed=0, with_t=False)
+        rng = np.random.default_rng(0)
+        st1 = 0.01 * rng.standard_normal((so, sv))
+        g = 0.02 * rng.standard_normal((so, so, sv, sv))
+        st2 = 0.25 * (g - g.transpose(1, 0, 2, 3) - g.transpose(0, 1, 3, 2) + g.transpose(1, 0, 3, 2))
+        for _ in range(args.warmup):
+            ccsd_ref.t_residuals(sp.fock, sp.chol, st1, st2, so)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ccsd_ref.t_residuals(sp.fock, sp.chol, st1, st2, so)
+        ts = (time.perf_counter() - t0) / max(1, args.steps)
+        scale = (o / so) ** 2 * (v / sv) ** 4
+        val = 1.0 / (ts * scale)
+        sample = (f"extrapolated: oracle T residuals at o={so} v={sv} L={sL}, {ts:.2f} s each, scaled by the "
+                  f"o^2 v^4 ratio {scale:.0f}")
+        print(json.dumps({"impl": "reference", "metric": "CCSD T iterations/sec", "value": val, "unit": "iterations/s",
+                          "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * ts * scale,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic",
+                          "config": {"workload": f"ground-state CCSD o={o} v={v} L={L} (medium shape)"},
+                          "cpu_baseline": {"value": val, "unit": "iterations/s", "cores": os.cpu_count(),
+                                           "kind": "oracle", "sample": sample},
+                          "e2e": {"value": val, "unit": "iterations/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return 0
     wl = workload(spec["base"])
     if wl.name == "c60":
         mo = MediumOracle()
@@ -467,6 +516,84 @@ def run_uneven(args, spec, world, rank, dist=None):
     return 0
 
 
+def run_ccsd(args, spec, world, rank, dist=None):
+    """Ground-state CCSD on the device (gfcc_ccsd): warm-up iterations from zero amplitudes, then
+    exactly `steps` T iterations (residual, Jacobi step, DIIS) from the warmed-up amplitudes, timed by
+    the library around its iteration loop (stream-synchronised).  The e2e figure is the same call
+    host-timed (Hamiltonian and amplitudes uploaded, amplitudes read back).  Each rank solves its own
+    problem (seed = rank): replicas, no collective.  A full T + Lambda solve of the same problem is
+    reported beside it, and the CPU oracle's T residual on a smaller problem, scaled."""
+    import torch
+    from paper_2010_04768_gb300 import gfcc
+    from paper_2010_04768_gb300.synthetic import make_problem
+    o, v, L = spec["ccsd"]
+    pr = make_problem(o, v, L, seed=rank, with_t=False)
+    t1, t2, _, _, info_w, _ = gfcc.ccsd(pr.fock, pr.chol, o, tol=1e-14, max_iter=max(1, args.warmup),
+                                        want_lambda=False, emulate=spec["emulate"])
+    launches0 = gfcc.launch_count()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    with Clocks(torch.cuda.current_device()) as clk:
+        t0 = time.perf_counter()
+        g1, g2, _, _, info, code = gfcc.ccsd(pr.fock, pr.chol, o, tol=1e-14, max_iter=args.steps, want_lambda=False,
+                                             emulate=spec["emulate"], guess=(t1, t2))
+        e2e_s = time.perf_counter() - t0
+    launches = gfcc.launch_count() - launches0
+    dt, iters = reduce_over_ranks(dist, info["t_seconds"], int(info["t_iters"]), "cuda")
+    peaks = measured_peaks()
+    flops = info["t_flops_per_iter"]
+    achieved = flops * args.steps / info["t_seconds"] / 1e12
+    if spec["emulate"]:
+        peak, bound = peaks.get("bf16_tflops_sustained", 1727.1), "tensor"
+        pnote = ("bf16_tflops_sustained of measured; achieved = the iteration's counted FP64 contraction flops "
+                 "(method flops, one product per FP64-accurate contraction) / iteration time")
+    else:
+        peak, bound = FP64_PEAK_TFLOPS, "alu"
+        pnote = "FP64 DFMA peak derived from 152 SMs x 2 FMA/clk x 2070 MHz; achieved = counted flops / time"
+    # a full T + Lambda solve of the same problem (not timed as steps)
+    _, _, _, _, full, fcode = gfcc.ccsd(pr.fock, pr.chol, o, tol=1e-8, max_iter=100, emulate=spec["emulate"])
+    line = {
+        "metric": "CCSD T iterations/sec", "value": iters / dt, "unit": "iterations/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, iters), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16-digit-planes+f64" if spec["emulate"] else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"ground-state CCSD o={o} v={v} L={L} (medium shape), T iterations from warmed-up "
+                               "amplitudes", "emulate": bool(spec["emulate"]), "l2": "inputs larger than L2"},
+        "e2e": {"value": args.steps / e2e_s, "unit": "iterations/s",
+                "h2d_bytes_per_step": int(8 * (pr.fock.size + pr.chol.size + t1.size + t2.size) / args.steps),
+                "d2h_bytes_per_step": int(8 * (t1.size + t2.size) / args.steps),
+                "note": "host-timed gfcc_ccsd call: upload, setup of the call, the iterations, read-back"},
+        "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "note": pnote, "flops_per_iteration": flops},
+        "full_solve": {"code": fcode, "e_corr": full["e_corr"], "t_iters": full["t_iters"],
+                       "t_seconds": full["t_seconds"], "lambda_iters": full["lambda_iters"],
+                       "lambda_seconds": full["lambda_seconds"], "tol": 1e-8},
+        "gpu_launches": int(launches), "clocks": clk.summary(), "code": code,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        # the oracle's T residual (numpy FP64, all host cores) at o/2, v/2, L/2, scaled by the
+        # o^2 v^4 ratio of the dominant ladder term
+        from oracle import ccsd_ref
+        so, sv, sL = o // 2, v // 2, L // 2
+        sp = make_problem(so, sv, sL, seed=0, with_t=False)
+        rng = np.random.default_rng(0)
+        st1 = 0.01 * rng.standard_normal((so, sv))
+        g = 0.02 * rng.standard_normal((so, so, sv, sv))
+        st2 = 0.25 * (g - g.transpose(1, 0, 2, 3) - g.transpose(0, 1, 3, 2) + g.transpose(1, 0, 3, 2))
+        t0 = time.perf_counter()
+        ccsd_ref.t_residuals(sp.fock, sp.chol, st1, st2, so)
+        ts = time.perf_counter() - t0
+        scale = (o / so) ** 2 * (v / sv) ** 4
+        line["cpu_baseline"] = {"value": 1.0 / (ts * scale), "unit": "iterations/s", "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": f"extrapolated: one oracle T residual at o={so} v={sv} L={sL} took {ts:.2f} s, "
+                                          f"scaled by the o^2 v^4 ratio {scale:.0f}"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -498,10 +625,17 @@ def main():
     spec = WORKLOADS[args.workload]
     if spec.get("uneven"):
         return run_uneven(args, spec, world, rank, dist)
+    if spec.get("ccsd"):
+        return run_ccsd(args, spec, world, rank, dist)
     wl = workload(spec["base"])
+    model = guess_train = None
+    if spec.get("guess") == "learned":
+        # trained (and its context freed) before the timed context exists: two C60-shaped contexts
+        # and their setup temporaries do not fit on the device together
+        model, guess_train = train_guess_model(gfcc, spec, wl)
     problem = wl.problem()
     t0 = time.perf_counter()
-    ctx = gfcc.GFCC(problem, sectors=spec["sector"], precision=spec["precision"])
+    ctx = gfcc.GFCC(problem, sectors=spec["sector"], precision=spec["precision"], closed_shell=wl.closed_shell)
     setup_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream.cuda_stream)
@@ -513,13 +647,11 @@ def main():
     per = spec["per_step"]
     orb_dev = torch.tensor(wl.orbitals, dtype=torch.int32, device="cuda")
     G_dev = torch.zeros((per, no, no, 2), dtype=torch.float64, device="cuda")
-    guess_train = None
     if spec.get("sweep"):
         ctx.set_option(gfcc.OPT_BATCH, no)
     if spec.get("guess") == "minres":
         ctx.set_option(gfcc.OPT_GUESS, gfcc.GUESS_MINRES)
     elif spec.get("guess") == "learned":
-        model, guess_train = train_guess_model(gfcc, spec, wl)
         ctx.set_guess_model(model)
         ctx.set_option(gfcc.OPT_GUESS, gfcc.GUESS_LEARNED)
 
@@ -590,8 +722,12 @@ def main():
     ks = min(PLAIN_STEP, len(G_e2e) - 1)
     if spec["precision"] == "mixed" and rank == 0 and not args.no_plain_fp64:
         plain, row_check = plain_fp64_leg(gfcc, ctx, wl, freqs(ks)[:1], G_e2e[ks][:1], stream)
+    spin_orbital = None
+    if wl.closed_shell and rank == 0 and not args.no_plain_fp64:
+        spin_orbital = spin_orbital_leg(gfcc, problem, wl, freqs(ks)[:1], G_e2e[ks][:1])
     mor = None
-    if rank == 0 and not args.no_mor and len(sectors_of(spec)) == 1 and not spec.get("sweep"):
+    if (rank == 0 and not args.no_mor and len(sectors_of(spec)) == 1 and not spec.get("sweep")
+            and not wl.closed_shell):
         mor = mor_leg(gfcc, ctx, wl, spec, freqs(0)[0], G_e2e[0][0])
 
     peaks = measured_peaks()
@@ -635,6 +771,9 @@ def main():
                                         "fraction": inside / prof["solve"][0]}
     if mor is not None:
         line["mor"] = mor
+    if spin_orbital is not None:
+        line["spin_orbital_fp64"] = spin_orbital
+        line["vs_spin_orbital_fp64"] = value / spin_orbital["value"] if spin_orbital["value"] else None
     if plain is not None:
         line["plain_fp64"] = plain
         line["vs_plain_fp64"] = value / plain["value"] if plain["value"] else None
@@ -643,6 +782,8 @@ def main():
         try:
             if wl.name == "c60":
                 cb = cpu_baseline_extrapolated(wl, plain["iterations_per_column"] if plain else None)
+            elif wl.closed_shell:
+                cb = cpu_baseline_closed_shell(wl, problem)
             else:
                 cb = cpu_baseline(wl, spec, problem, max_columns=1)
             line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
@@ -686,6 +827,78 @@ def plain_fp64_leg(gfcc, ctx, wl, om, G_mixed, stream):
     check = {"rows": P.tolist(), "omega": float(om[0]), "max_rel_err": max(errs), "rel_err": errs, "tol": ROW_TOL,
              "passed": bool(max(errs) <= ROW_TOL and cols == len(rows))}
     return plain, check
+
+
+def spin_orbital_leg(gfcc, problem, wl, om, G_cs):
+    """The same system through the spin-orbital FP64 path: the spin-orbital embedding of the closed-shell
+    problem (2o occupied, 2v virtual spin-orbitals), one row of G (the highest orbital of the list, alpha
+    spin) at frequency om (a timed step's) by gfcc_solve_block with the columns over the alpha spin-orbitals
+    of the list; its columns/s (host-timed, setup excluded) and the relative 2-norm difference of the
+    closed-shell G row (G_cs[0][row]) from it."""
+    import torch
+    from paper_2010_04768_gb300.synthetic import Problem
+    o, v = wl.o, wl.v
+    n = o + v
+    al = np.where(np.arange(n) < o, np.arange(n), 2 * o + (np.arange(n) - o))   # alpha spin-orbital of p
+    be = np.where(np.arange(n) < o, o + np.arange(n), 2 * o + v + (np.arange(n) - o))
+    F = np.zeros((2 * n, 2 * n))
+    F[np.ix_(al, al)] = problem.fock
+    F[np.ix_(be, be)] = problem.fock
+    Ls = np.zeros((problem.L, 2 * n, 2 * n))
+    Ls[:, al[:, None], al[None, :]] = problem.chol
+    Ls[:, be[:, None], be[None, :]] = problem.chol
+    # spin-orbital amplitudes: T_IJ^AB = d(sI,sA) d(sJ,sB) t_ij^ab - d(sI,sB) d(sJ,sA) t_ij^ba
+    so_o, so_v = np.repeat([0, 1], o), np.repeat([0, 1], v)
+    io, iv = np.tile(np.arange(o), 2), np.tile(np.arange(v), 2)
+    T1 = (so_o[:, None] == so_v[None, :]) * problem.t1[io][:, iv]
+    t = problem.t2[io][:, io][:, :, iv][:, :, :, iv]
+    d1 = (so_o[:, None, None, None] == so_v[None, None, :, None]) & (so_o[None, :, None, None] == so_v[None, None, None, :])
+    d2 = (so_o[:, None, None, None] == so_v[None, None, None, :]) & (so_o[None, :, None, None] == so_v[None, None, :, None])
+    T2 = np.ascontiguousarray(d1 * t - d2 * np.swapaxes(t, 2, 3))
+    del t, d1, d2
+    t0 = time.perf_counter()
+    g = gfcc.GFCC(Problem(o=2 * o, v=2 * v, L=problem.L, fock=F, chol=Ls, t1=T1, t2=T2), sectors="IP")
+    setup_s = time.perf_counter() - t0
+    g.set_option(gfcc.OPT_RESTART, wl.restart)
+    g.set_option(gfcc.OPT_PRECOND, gfcc.PRECOND_DIAG)
+    no = int(wl.orbitals.size)
+    row = no - 1
+    cols = al[wl.orbitals].astype(np.int32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Gso, code = g.solve_block(om, wl.eta, cols[row:row + 1], cols, wl.tol)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    it, rr, st = g.stats()
+    g.close()
+    done = int(np.sum(st == 0))
+    err = float(np.linalg.norm(G_cs[0, row] - Gso[0, 0]) / np.linalg.norm(Gso[0, 0]))
+    return {"value": done / dt, "unit": "columns/s", "columns": done, "seconds": dt, "setup_s": setup_s,
+            "iterations_per_column": float(np.mean(it)), "g_row_rel_diff": err,
+            "sample": f"1 (omega, p) IP system (omega {om[0]:.5f}, spatial orbital {int(wl.orbitals[row])} alpha) of "
+                      f"the spin-orbital embedding (o={2 * o} v={2 * v} spin-orbitals, FP64 sigma and GMRES({wl.restart}),"
+                      f" same tol and preconditioner), its G row over the list's alpha spin-orbitals; host-timed"}
+
+
+def cpu_baseline_closed_shell(wl, problem):
+    """The closed-shell oracle (closed-form spatial equations, numpy FP64) on one column of the workload:
+    the first orbital of the list at the frequency of timed step 1, GMRES with the same tol, restart and
+    preconditioner; its setup excluded like gfcc_create."""
+    from oracle.rhf_ref import RHFClosed
+    from oracle.gfcc_ref import gmres
+    t0 = time.perf_counter()
+    C = RHFClosed(problem.fock, problem.chol, problem.t1, problem.t2, o=wl.o)
+    t_setup = time.perf_counter() - t0
+    om = wl.omegas[FREQ_STRIDE % wl.omegas.size]
+    z = om - 1j * wl.eta
+    t0 = time.perf_counter()
+    x, its, rel, ok = gmres(lambda y: z * y + C.sigma(y), C.rhs(int(wl.orbitals[0])), wl.tol, wl.restart, 50,
+                            diag=z + C.diag())
+    np.stack([C.left(int(q)) for q in wl.orbitals]) @ x
+    dt = time.perf_counter() - t0
+    return {"value": (1 if ok else 0) / dt, "unit": "columns/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"1 closed-shell IP column (omega {om:.5f}, orbital {int(wl.orbitals[0])}): {its} GMRES iterations "
+                      f"in {dt:.1f} s; oracle setup {t_setup:.1f} s excluded", "seconds": dt}
 
 
 MOR_SAMPLES = 3       # model-order reduction leg: frequencies whose solutions span the subspace

@@ -110,6 +110,10 @@ extern "C" {
 #define GFCC_OPT_GEMM_PAIR  22    /* BF16 tensor-core products on CTA pairs (256 x 256 tiles over two
                                      SMs, tcgen05 cta_group::2): 0 (default) the autotuner times them
                                      beside the one-CTA tiles, 1 whenever they apply, 2 never          */
+#define GFCC_OPT_GEMM_PERSIST 23  /* BF16 tensor-core products with a persistent tile loop (one CTA per
+                                     SM, two TMEM accumulators): 0 (default) timed by the autotuner on
+                                     launches of several waves, 1 always (unless GFCC_OPT_GEMM_PAIR is
+                                     1), 2 never                                                        */
 
 /* Initial guesses (Algorithm 1, "compute initial guess").  With a guess other than ZERO, gfcc_solve
  * keeps every converged solution X_p(omega) (FP32 complex, n_omega * n_orb * dim * 8 bytes of device
@@ -158,12 +162,29 @@ int gfcc_create_ex(int o, int v, int L, const double *fock, const double *chol,
                    const double *t1, const double *t2, const double *lambda,
                    int sectors, int precision, gfcc_ctx **out);
 
+/* gfcc_create_rhf - closed-shell spin-adapted IP context (the paper's closed-shell GFCCSD-IP, Table 2:
+ * alpha amplitudes only).  Spatial orbitals: o doubly occupied, v virtual; the Hamiltonian is the
+ * spin-free one of a closed-shell reference (fock, chol spatial, as for gfcc_create).
+ *   t1 [o][v] = t_i^a (alpha), t2 [o][o][v][v] = t_ij^ab = T_{i alpha, j beta}^{a alpha, b beta}, with
+ *   t2[i][j][a][b] == t2[j][i][b][a] (checked); lambda: NULL (Lambda = T^dagger) or [lambda1 | lambda2]
+ *   in the same spatial layout.
+ * Sector IP, FP64.  G_pq(omega) over spatial orbitals equals the spin-orbital G of orbitals
+ * p alpha, q alpha.  The systems are solved in the doublet coordinates r_i = R_{i alpha},
+ * r_ij^a = R_{i alpha, j beta}^{a beta} (dimension o + o^2 v; gfcc_dims reports it, gfcc_sigma and
+ * the solves take vectors in it: [r_i | r_ij^a at [i][j][a]]), with the spin-summed Hbar elements.
+ * Zero initial guesses only; model-order reduction is not offered for these contexts.  Errors as
+ * gfcc_create.
+ */
+int gfcc_create_rhf(int o, int v, int L, const double *fock, const double *chol, const double *t1, const double *t2,
+                    const double *lambda, gfcc_ctx **out);
+
 /* gfcc_set_option - set one GFCC_OPT_* option (value cast from double).  Returns GFCC_ERR_ARG
  * for an unknown key or a value out of range. */
 int gfcc_set_option(gfcc_ctx *ctx, int key, double value);
 
 /* gfcc_set_process_option - set a process-wide option (GFCC_OPT_AUTOTUNE, GFCC_OPT_EMU_FUSED_N,
- * GFCC_OPT_SETUP_EMULATE_FLOPS, GFCC_OPT_WAIT_NS, GFCC_OPT_TEST_NO_LOADS, GFCC_OPT_GEMM_PAIR).  It applies to every
+ * GFCC_OPT_SETUP_EMULATE_FLOPS, GFCC_OPT_WAIT_NS, GFCC_OPT_TEST_NO_LOADS, GFCC_OPT_GEMM_PAIR,
+ * GFCC_OPT_GEMM_PERSIST).  It applies to every
  * later call of every context; do not change it while another thread is inside the library.
  * Returns GFCC_ERR_ARG for an unknown key or a value out of range. */
 int gfcc_set_process_option(int key, double value);
@@ -459,6 +480,41 @@ int gfcc_spectral_adaptive(gfcc_ctx *ctx, int sectors, double omega_min, double 
                            double eta, int n_orb, const int *orbitals, double tol, double level_tol, int max_levels,
                            int n_fine, const double *fine_omegas, double *A, int *n_levels, int *level_sizes,
                            double *sampled, int sampled_cap, int *mdim);
+
+/* ---------------------------------------------------------------- ground state (the step before G)
+ * gfcc_ccsd - solve the ground-state CCSD equations for T and, when lambda is given, the Lambda-CCSD
+ * equations for the de-excitation amplitudes, on the device (FP64; Theory section: T and Lambda come
+ * from the conventional CC equations, which the Green's function then takes as fixed inputs;
+ * Workflow section and Table 1: Cholesky-decomposed CCSD, O(O^2 V^4) per iteration).  The integrals
+ * enter only through the Cholesky vectors; the vvvv ladder term is formed block by block.
+ *   o, v, L, fock, chol : the Hamiltonian, as for gfcc_create (host, row-major; fock symmetric, chol
+ *                 symmetric in its orbital pair; checked on the device).
+ *   tol         : convergence when max |residual| <= tol (every singles and doubles equation).
+ *   max_iter    : iterations per equation set (>= 1); Jacobi steps with the Fock-diagonal denominators
+ *                 f_ii (+ f_jj) - f_aa (- f_bb), extrapolated by DIIS over the last 8 iterates.
+ *   flags       : GFCC_CCSD_EMULATE - contractions of at least the setup threshold
+ *                 (GFCC_OPT_SETUP_EMULATE_FLOPS) through the FP64-accurate digit-plane products on the
+ *                 BF16 tensor cores; GFCC_CCSD_GUESS - t1, t2 (and lambda) hold initial iterates on entry
+ *                 (else both start from zero, Lambda from T).
+ *   t1 [o][v], t2 [o][o][v][v] : out (in with GFCC_CCSD_GUESS), host; t2 antisymmetric.
+ *   lambda      : NULL (T only) or out [lambda1 (o x v) | lambda2 (o x o x v x v)], the layout
+ *                 gfcc_create takes (lambda_a^i at [i][a], lambda_ab^ij at [i][j][a][b]).
+ *   info        : out [8], may be NULL: E_corr (Hartree; f_ia t_i^a + 1/4 <ij||ab> t_ij^ab +
+ *                 1/2 <ij||ab> t_i^a t_j^b), T iterations, final max |T residual|, Lambda iterations,
+ *                 final max |Lambda residual|, seconds in the T iterations, seconds in the Lambda
+ *                 iterations (both host-timed, stream-synchronised), FP64 multiply-adds x 2 of one T
+ *                 iteration (the counted contraction flops).
+ * Both equation sets are taken in their T1 = 0 forms for the T1-rotated Hamiltonian (whose T2
+ * transform is e^-T H e^T exactly); the Lambda residuals leave out the terms that vanish when T
+ * solves its equations.
+ * Returns GFCC_OK, GFCC_WARN_NOT_CONVERGED (outputs hold the last iterate), GFCC_ERR_ARG (sizes, NULL
+ * inputs, tol <= 0, bad symmetry), GFCC_ERR_OOM or GFCC_ERR_CUDA.  Device memory: about
+ * (2 * 8 + 6) o^2 v^2 + o v^3 + 2 L (o + v)^2 doubles plus a 4 GB vvvv block; freed before returning.
+ */
+#define GFCC_CCSD_EMULATE 1
+#define GFCC_CCSD_GUESS 2
+int gfcc_ccsd(int o, int v, int L, const double *fock, const double *chol, double tol, int max_iter, int flags,
+              double *t1, double *t2, double *lambda, double *info);
 
 /* gfcc_destroy - free the context and all its device memory.  NULL is a no-op. */
 void gfcc_destroy(gfcc_ctx *ctx);

@@ -421,7 +421,7 @@ int upload(gfcc_ctx *c, double **dst, const double *src, long long count) {
 }
 
 int create_impl(int o, int v, int L, const double *fock, const double *chol, const double *t1, const double *t2,
-                const double *lambda, int sectors, int precision, gfcc_ctx **out) {
+                const double *lambda, int sectors, int precision, gfcc_ctx **out, int rhf = 0) {
   if (out == nullptr) {
     set_error("gfcc_create: out is NULL");
     return GFCC_ERR_ARG;
@@ -441,6 +441,8 @@ int create_impl(int o, int v, int L, const double *fock, const double *chol, con
   c->Pv = (long long)v * (v - 1) / 2;
   c->dim_ip = o + c->Po * v;
   c->dim_ea = v + (long long)o * c->Pv;
+  c->rhf = rhf;
+  if (rhf) c->dim_ip = o + (long long)o * o * v;   // spatial 1h + 2h1p coordinates, no pair packing
   c->sectors = sectors;
   c->precision = precision;
   int s = GFCC_OK;
@@ -488,15 +490,17 @@ int create_impl(int o, int v, int L, const double *fock, const double *chol, con
   if ((s = check_tensor(c->stream, d_fock, 1, 1, n, n, 0, 1, 1.0, 1e-12, "fock")) < 0 ||
       (s = check_tensor(c->stream, d_chol, 1, L, n, n, 0, 1, 1.0, 1e-12, "chol")) < 0 ||
       (s = check_tensor(c->stream, c->t1, 1, 1, o, v, 0, 0, 1.0, 1e300, "t1")) < 0 ||
-      (s = check_tensor(c->stream, c->t2, o, o, v, v, 1, 0, -1.0, 1e-12, "t2 (i<->j)")) < 0 ||
-      (s = check_tensor(c->stream, c->t2, o, o, v, v, 0, 1, -1.0, 1e-12, "t2 (a<->b)")) < 0) {
+      (!rhf && (s = check_tensor(c->stream, c->t2, o, o, v, v, 1, 0, -1.0, 1e-12, "t2 (i<->j)")) < 0) ||
+      (!rhf && (s = check_tensor(c->stream, c->t2, o, o, v, v, 0, 1, -1.0, 1e-12, "t2 (a<->b)")) < 0) ||
+      (rhf && (s = check_tensor(c->stream, c->t2, o, o, v, v, 1, 1, 1.0, 1e-12, "t2 (ia<->jb)")) < 0)) {
     free_tmp();
     return fail(s);
   }
   if (lambda != nullptr &&
       ((s = check_tensor(c->stream, c->l1, 1, 1, o, v, 0, 0, 1.0, 1e300, "lambda1")) < 0 ||
-       (s = check_tensor(c->stream, c->l2, o, o, v, v, 1, 0, -1.0, 1e-12, "lambda2 (i<->j)")) < 0 ||
-       (s = check_tensor(c->stream, c->l2, o, o, v, v, 0, 1, -1.0, 1e-12, "lambda2 (a<->b)")) < 0)) {
+       (!rhf && (s = check_tensor(c->stream, c->l2, o, o, v, v, 1, 0, -1.0, 1e-12, "lambda2 (i<->j)")) < 0) ||
+       (!rhf && (s = check_tensor(c->stream, c->l2, o, o, v, v, 0, 1, -1.0, 1e-12, "lambda2 (a<->b)")) < 0) ||
+       (rhf && (s = check_tensor(c->stream, c->l2, o, o, v, v, 1, 1, 1.0, 1e-12, "lambda2 (ia<->jb)")) < 0))) {
     free_tmp();
     return fail(s);
   }
@@ -507,7 +511,7 @@ int create_impl(int o, int v, int L, const double *fock, const double *chol, con
     // mixed-precision contexts build their large FP64 intermediates from digit planes on the
     // tensor cores (FP64-accurate); FP64 contexts keep every contraction on the FP64 units
     g_emulate_big = precision == GFCC_PREC_MIXED_BF16;
-    s = build_hbar(c, d_fock, d_chol);
+    s = rhf ? build_hbar_rhf(c, d_fock, d_chol) : build_hbar(c, d_fock, d_chol);
     g_emulate_big = false;
     if (timed) {
       cudaEventRecord(e1, c->stream);
@@ -1086,9 +1090,15 @@ int solve_host(gfcc_ctx *c, int n_omega, const double *omegas, double eta, int n
 
 }  // namespace
 
+int check_input_tensor(cudaStream_t st, const double *x, long long d0, long long d1, long long d2, long long d3,
+                       int s01, int s23, double sign, double rel, const char *name) {
+  return check_tensor(st, x, d0, d1, d2, d3, s01, s23, sign, rel, name);
+}
+
 int build_rhs_masked(gfcc_ctx *c, int sector, int nsys, const int *d_porb, const int *d_mask, double *B,
                      cudaStream_t st) {
   if (nsys <= 0) return GFCC_OK;
+  if (c->rhf) return build_rhs_rhf(c, nsys, d_porb, d_mask, B, st);
   if (sector == GFCC_SECTOR_IP) {
     rhs_ip_kernel<<<grid1d(c->dim_ip * nsys), 256, 0, st>>>(B, c->dim_ip, nsys, d_porb, c->o, c->v, c->t1, c->t2,
                                                             d_mask);
@@ -1107,6 +1117,7 @@ int build_rhs(gfcc_ctx *c, int sector, int nsys, const int *d_porb, double *B, c
 // left vectors C[q][mu] (real, [nq][dim]) of the orbitals d_orb (device) of one sector (eq. gfxn2)
 int build_left_vectors(gfcc_ctx *c, int sector, int nq, const int *d_orb, double *C, cudaStream_t st) {
   if (nq <= 0) return GFCC_OK;
+  if (c->rhf) return build_left_rhf(c, nq, d_orb, C, st);
   if (sector == GFCC_SECTOR_IP) {
     const long long n = c->dim_ip;
     left_ip_1h_kernel<<<nq * c->o, 256, 0, st>>>(C, n, nq, d_orb, c->o, c->v, c->t1, c->t2, c->l1, c->l2);
@@ -1156,6 +1167,11 @@ int gfcc_create(int o, int v, int L, const double *fock, const double *chol, con
 int gfcc_create_ex(int o, int v, int L, const double *fock, const double *chol, const double *t1, const double *t2,
                    const double *lambda, int sectors, int precision, gfcc_ctx **out) {
   return create_impl(o, v, L, fock, chol, t1, t2, lambda, sectors, precision, out);
+}
+
+int gfcc_create_rhf(int o, int v, int L, const double *fock, const double *chol, const double *t1, const double *t2,
+                    const double *lambda, gfcc_ctx **out) {
+  return create_impl(o, v, L, fock, chol, t1, t2, lambda, GFCC_SECTOR_IP, GFCC_PREC_FP64, out, 1);
 }
 
 int gfcc_set_option(gfcc_ctx *c, int key, double value) {
@@ -1214,6 +1230,10 @@ int gfcc_set_option(gfcc_ctx *c, int key, double value) {
       return GFCC_OK;
     case GFCC_OPT_GUESS:
       if (iv != GFCC_GUESS_ZERO && iv != GFCC_GUESS_LEARNED && iv != GFCC_GUESS_MINRES) break;
+      if (c->rhf && iv != GFCC_GUESS_ZERO) {
+        set_error("gfcc_set_option: closed-shell contexts solve from the zero guess only");
+        return GFCC_ERR_ARG;
+      }
       c->guess = iv;
       return GFCC_OK;
     case GFCC_OPT_INNER_KRYLOV:
@@ -1261,6 +1281,10 @@ int gfcc_set_process_option(int key, double value) {
     case GFCC_OPT_GEMM_PAIR:
       if (value != 0.0 && value != 1.0 && value != 2.0) break;
       umma_set_pair_mode((int)value);
+      return GFCC_OK;
+    case GFCC_OPT_GEMM_PERSIST:
+      if (value != 0.0 && value != 1.0 && value != 2.0) break;
+      umma_set_persist_mode((int)value);
       return GFCC_OK;
     case GFCC_OPT_SETUP_EMULATE_FLOPS:
       if (!(value >= 0.0)) break;

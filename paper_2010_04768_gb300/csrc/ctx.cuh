@@ -83,6 +83,13 @@ struct gfcc_ctx {
   double *T3 = nullptr;      // [(i,a,j)][e]    t2[i,j,a,e]
   double *U1 = nullptr;      // [i][(m,e,n)]    -d_in Fov[m,e] + 1/2 Wooov[n,m,i,e]
   double *diag_ip = nullptr; // packed Fock-like diagonal
+  // closed-shell spin-adapted IP context (gfcc_create_rhf; rhf.cu): spatial orbitals, vectors
+  // [r_i (o) | r_ij^a ([i][j][a], o^2 v)], every element alpha-beta spin-summed
+  int rhf = 0;
+  double *rM1 = nullptr, *rM2 = nullptr, *rM3 = nullptr;   // ring matrices [(i,a)][(m,e)] (ov x ov)
+  double *rWT = nullptr;    // [(i,j,a)][e | m]: -t_ij^ea | -W_maij  (o^2 v x (v + o))
+  double *rVz = nullptr;    // [e][(m,n,f)]: 2 u_mnef - u_mnfe  (v x o^2 v)
+  double *rU1 = nullptr;    // [i][m | (m,n,e)]: the 1h row (o x (o + o^2 v))
 
   // mixed-precision IP operands: BF16, K-major, row strides padded to multiples of 8.  The exact
   // Fock-like diagonal d (diag_ip) is left out of them and applied in FP64 by the epilogue.
@@ -178,4 +185,12 @@ void prof_resolve(gfcc_ctx *c);   // after a stream synchronisation: fold pendin
 int dev_alloc(gfcc_ctx *c, double **p, long long count);      // owned by the context
 int dev_alloc_tmp(double **p, long long count);                  // caller frees with cudaFree
 int build_hbar(gfcc_ctx *c, const double *d_fock, const double *d_chol);
+// closed-shell spin-adapted elements (rhf.cu); c->t1, c->t2, c->l1, c->l2 are spatial
+int build_hbar_rhf(gfcc_ctx *c, const double *d_fock, const double *d_chol);
+int build_rhs_rhf(gfcc_ctx *c, int nsys, const int *d_porb, const int *d_mask, double *B, cudaStream_t st);
+int build_left_rhf(gfcc_ctx *c, int nq, const int *d_orb, double *C, cudaStream_t st);
+// Device-side input check of a [d0][d1][d2][d3] tensor: finite entries and, where s01 / s23 is set,
+// x[i][j][.][.] == sign * x[j][i][.][.] / x[.][.][a][b] == sign * x[.][.][b][a] to rel * max(1, max|x|)
+int check_input_tensor(cudaStream_t st, const double *x, long long d0, long long d1, long long d2, long long d3,
+                       int s01, int s23, double sign, double rel, const char *name);
 }  // namespace gfcc

@@ -26,6 +26,18 @@ int gemm_f64(cudaStream_t st, long long M, long long N, long long K, double alph
              double *C, IMap cm, IMap cn, long long batch = 1, long long sab = 0, long long sbb = 0,
              long long scb = 0);
 
+// ---------------------------------------------------------------- Cholesky-vector building blocks
+// C((p,r),(q,s)) (+)= alpha * sum_K Lt[K][P0+p][R0+r] Lt[K][Q0+q][S0+s] for Cholesky vectors Lt [L][n][n]
+// (GEMM row index p * nr + r, column index q * ns + s, placed through cm / cn)
+int chol_eri(cudaStream_t st, const double *Lt, int n, int L, long long P0, long long np, long long R0, long long nr,
+             long long Q0, long long nq, long long S0, long long ns, double alpha, double beta, double *C, IMap cm,
+             IMap cn);
+// M <- (1 - t) M (1 + t) in place for `batch` n x n matrices spaced `stride` apart, t[o+a][i] = t1[i][a]
+// (the T1 similarity transformation of a one-body operator, n = o + v)
+int t1_dress(cudaStream_t st, const double *t1, int o, int v, double *M, long long batch, long long stride);
+// F[p][q] += aj * sum_K M[K][p][q] tr_o(M[K]) + ak * sum_K sum_{j<o} M[K][p][j] M[K][j][q]
+int chol_coulomb_exchange(cudaStream_t st, const double *M, int n, int o, int L, double *F, double aj, double ak);
+
 // ---------------------------------------------------------------- elementwise helpers
 // For every index (i0, i1, i2, i3) < d:
 //   out[sum i_k * os[k]] = alpha * in[sum i_k * is[k]] + beta * out[sum i_k * os[k]]

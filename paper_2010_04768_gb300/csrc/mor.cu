@@ -606,6 +606,10 @@ int gfcc_mor_create(gfcc_ctx *ctx, int sector, double drop_tol, gfcc_mor **out) 
     set_error("gfcc_mor_create: need a context with the sector built and 0 < drop_tol < 1");
     return GFCC_ERR_ARG;
   }
+  if (ctx->rhf) {
+    set_error("gfcc_mor_create: model-order reduction is not offered for closed-shell contexts");
+    return GFCC_ERR_ARG;
+  }
   gfcc_mor *M = new gfcc_mor();
   M->c = ctx;
   M->sector = sector;

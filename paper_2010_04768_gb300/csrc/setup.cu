@@ -272,6 +272,42 @@ int dev_alloc_tmp(double **p, long long count) {
   return GFCC_OK;
 }
 
+int chol_eri(cudaStream_t st, const double *Lt, int n, int L, long long P0, long long np, long long R0, long long nr,
+             long long Q0, long long nq, long long S0, long long ns, double alpha, double beta, double *C, IMap cm,
+             IMap cn) {
+  const long long nn = (long long)n * n;
+  return gemm_f64(st, np * nr, nq * ns, L, alpha, Lt + P0 * n + R0, imap2(nr, 1, n), imap1(nn), Lt + Q0 * n + S0,
+                  imap1(nn), imap2(ns, 1, n), beta, C, cm, cn);
+}
+
+int t1_dress(cudaStream_t st, const double *t1, int o, int v, double *M, long long batch, long long stride) {
+  const int n = o + v;
+  // M[p][i] += sum_a M[p][o+a] t1[i][a]
+  GFCC_TRY(gemm_f64(st, n, o, v, 1.0, M + o, imap1(n), imap1(1), t1, imap1(1), imap1(v), 1.0, M, imap1(n), imap1(1),
+                    batch, stride, 0, stride));
+  // M[o+a][q] -= sum_i t1[i][a] M[i][q]
+  GFCC_TRY(gemm_f64(st, v, n, o, -1.0, t1, imap1(1), imap1(v), M, imap1(n), imap1(1), 1.0, M + (long long)o * n,
+                    imap1(n), imap1(1), batch, 0, stride, stride));
+  return GFCC_OK;
+}
+
+int chol_coulomb_exchange(cudaStream_t st, const double *M, int n, int o, int L, double *F, double aj, double ak) {
+  double *d;
+  GFCC_TRY(dev_alloc_tmp(&d, L));
+  chol_trace_kernel<<<cdiv(L, 128), 128, 0, st>>>(M, L, n, o, d);
+  int s = cudaGetLastError() == cudaSuccess ? GFCC_OK : GFCC_ERR_CUDA;
+  count_launch();
+  const long long nn = (long long)n * n;
+  if (s == GFCC_OK)
+    s = gemm_f64(st, nn, 1, L, aj, M, imap1(1), imap1(nn), d, imap1(1), imap1(0), 1.0, F, imap1(1), imap1(0));
+  if (s == GFCC_OK)
+    s = gemm_f64(st, n, n, (long long)L * o, ak, M, imap1(n), imap2(o, 1, nn), M, imap2(o, n, nn), imap1(1), 1.0, F,
+                 imap1(n), imap1(1));
+  if (s == GFCC_ERR_CUDA) set_error("Coulomb/exchange build: %s", cudaGetErrorString(cudaGetLastError()));
+  dfree(d);   // cudaFree waits for the launches above
+  return s;
+}
+
 namespace {
 
 int alloc_bf16(gfcc_ctx *c, __nv_bfloat16 **p, long long count) {
@@ -318,32 +354,15 @@ struct Builder {
   // C((p,r),(q,s)) (+)= alpha * sum_K L'[K][P0+p][R0+r] L'[K][Q0+q][S0+s]
   int eri(long long P0, long long np, long long R0, long long nr, long long Q0, long long nq, long long S0,
           long long ns, double alpha, double beta, double *C, IMap cm, IMap cn) {
-    return gemm_f64(st, np * nr, nq * ns, L, alpha, lt_block(P0, R0), lt_pair(nr), imap1((long long)n * n),
-                    lt_block(Q0, S0), imap1((long long)n * n), lt_pair(ns), beta, C, cm, cn);
+    return chol_eri(st, Lt, n, L, P0, np, R0, nr, Q0, nq, S0, ns, alpha, beta, C, cm, cn);
   }
 
   // M <- (1 - t) M (1 + t) in place for `batch` n x n matrices spaced `stride` apart.
-  int dress(double *M, long long batch, long long stride) {
-    // M[p][i] += sum_a M[p][o+a] t1[i][a]
-    GFCC_TRY(gemm_f64(st, n, o, v, 1.0, M + o, imap1(n), imap1(1), c->t1, imap1(1), imap1(v), 1.0, M, imap1(n),
-                      imap1(1), batch, stride, 0, stride));
-    // M[o+a][q] -= sum_i t1[i][a] M[i][q]
-    GFCC_TRY(gemm_f64(st, v, n, o, -1.0, c->t1, imap1(1), imap1(v), M, imap1(n), imap1(1), 1.0,
-                      M + (long long)o * n, imap1(n), imap1(1), batch, 0, stride, stride));
-    return GFCC_OK;
-  }
+  int dress(double *M, long long batch, long long stride) { return t1_dress(st, c->t1, o, v, M, batch, stride); }
 
   // F[p][q] += alpha_j * sum_K M[K][p][q] tr_o(M[K]) + alpha_k * sum_K sum_j M[K][p][j] M[K][j][q]
-  int coulomb_exchange(const double *M, double *F, double aj, double ak, Tmp &tmp) {
-    double *d;
-    GFCC_TRY(tmp.get(&d, L));
-    chol_trace_kernel<<<cdiv(L, 128), 128, 0, st>>>(M, L, n, o, d);
-    GFCC_LAUNCH_CHECK();
-    const long long nn = (long long)n * n;
-    GFCC_TRY(gemm_f64(st, nn, 1, L, aj, M, imap1(1), imap1(nn), d, imap1(1), imap1(0), 1.0, F, imap1(1), imap1(0)));
-    GFCC_TRY(gemm_f64(st, n, n, (long long)L * o, ak, M, imap1(n), imap2(o, 1, nn), M, imap2(o, n, nn), imap1(1), 1.0,
-                      F, imap1(n), imap1(1)));
-    return GFCC_OK;
+  int coulomb_exchange(const double *M, double *F, double aj, double ak, Tmp &) {
+    return chol_coulomb_exchange(st, M, n, o, L, F, aj, ak);
   }
 
   int copy_block(const double *src, long long ld_src, long long rows, long long cols, double *dst, double alpha,

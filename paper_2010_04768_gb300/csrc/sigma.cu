@@ -146,6 +146,7 @@ int launch_epilogue_ea(gfcc_ctx *c, const SysBatch &b, const double *S1, const d
 }
 
 double sigma_flops(const gfcc_ctx *c, int sector) {
+  if (c->rhf) return rhf_sigma_flops(c);
   const double o = c->o, v = c->v;
   if (sector == GFCC_SECTOR_IP)
     return 2.0 * (2 * o * o * o * v * v + 0.5 * o * o * o * o * v + 3 * o * o * v * v + 4 * o * o * o * v +
@@ -155,12 +156,14 @@ double sigma_flops(const gfcc_ctx *c, int sector) {
 
 long long sigma_work_doubles(const gfcc_ctx *c, int sector, int nsys) {
   const long long o = c->o, v = c->v, C2 = 2LL * nsys;
+  if (c->rhf) return rhf_work_doubles(c, nsys) + 64;
   if (sector == GFCC_SECTOR_IP) return (o + 4 * o * o * v + v + o) * C2 + 64;
   const long long Pv = c->Pv;
   return (v + 3 * o * v * v + 2 * Pv * o + o + v) * C2 + 64;
 }
 
 int apply_ip(gfcc_ctx *c, const SysBatch &b, double *work) {
+  if (c->rhf) return apply_ip_rhf(c, b, work);
   cudaStream_t st = c->stream;
   const long long o = c->o, v = c->v, ov = o * v, C2 = 2LL * b.nsys;
   double *r1u = work;

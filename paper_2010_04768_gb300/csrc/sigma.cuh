@@ -42,6 +42,10 @@ long long sigma_mixed_work_doubles(const gfcc_ctx *c, int nsys);
 // mixed precision (IP): BF16 tensor-core couplings + FP64 diagonal and shift (sigma_mixed.cu)
 int apply_ip_mixed(gfcc_ctx *c, const SysBatch &b, double *work);
 int apply_ip(gfcc_ctx *c, const SysBatch &b, double *work);
+// closed-shell spin-adapted IP operator (rhf.cu; apply_ip dispatches to it for such contexts)
+int apply_ip_rhf(gfcc_ctx *c, const SysBatch &b, double *work);
+long long rhf_work_doubles(const gfcc_ctx *c, int nsys);
+double rhf_sigma_flops(const gfcc_ctx *c);
 // the FP64 epilogue of the IP operator on given S1 / T / Q / U (FP64, layouts of sigma.cu); with diag
 // (the packed Fock-like diagonal) the outputs hold the couplings only and the diagonal is applied here
 int launch_epilogue_ip(gfcc_ctx *c, const SysBatch &b, const double *S1, const double *T, const double *Q,

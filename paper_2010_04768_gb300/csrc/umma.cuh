@@ -29,6 +29,9 @@ void umma_set_autotune(bool on);
 // CTA-pair tile (cta_group::2, 256 x 256 per pair): 0 timed by the autotuner beside the one-CTA tiles
 // (default), 1 used whenever it applies, 2 never
 void umma_set_pair_mode(int mode);
+// persistent tile loop (one CTA per SM, two TMEM accumulators): 0 timed by the autotuner (default),
+// 1 always, 2 never
+void umma_set_persist_mode(int mode);
 int umma_tuned_tile(int M, int N, int K, int nsplit);   // 0 if the shape was not tuned yet
 // Limit of the bounded pipeline waits of the tensor-core kernels (process-wide; default 1 s) and a
 // test-only switch under which their producers issue no loads (the wait then runs out with nothing

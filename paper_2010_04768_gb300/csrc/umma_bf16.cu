@@ -312,6 +312,200 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------------------------
+// The same product with a persistent tile loop: one CTA per SM walks the output tiles (and K splits)
+// of the launch; six warps: warp 0 the TMA producer, warp 1 the MMA issuer, warps 2-5 the epilogue
+// (warp w reads TMEM lanes 32 (w mod 4) .. + 31).  Two accumulators of BN columns in TMEM (ping-pong):
+// the epilogue of a tile overlaps the main loop of the next, and the load pipeline runs on across
+// tiles, so products with few K blocks per tile (the long thin contractions of the sigma product)
+// no longer pay a pipeline fill, a TMEM allocation and an unoverlapped epilogue per tile.
+constexpr int PERSIST_THREADS = 192;
+template <int BN>
+struct PTile {
+  static constexpr int STAGES = BN == 256 ? 4 : 6;
+  static constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 512;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(PERSIST_THREADS, 1)
+    umma_persist_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                             float *D, long long ldd, int M, int N, int K, float alpha, float beta, int kb_per_split,
+                             long long split_stride, int nM, int nN, int nsplit, UmmaCtl ctl) {
+  constexpr int STAGES = PTile<BN>::STAGES, A_BYTES = PTile<BN>::A_BYTES, STAGE_BYTES = PTile<BN>::STAGE_BYTES;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + STAGES * STAGE_BYTES);
+  unsigned long long *full = bars, *empty = bars + STAGES;
+  unsigned long long *accf = bars + 2 * STAGES, *acce = accf + 2, *drain = acce + 2;
+  unsigned *tmem_slot = reinterpret_cast<unsigned *>(drain + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  volatile int *issued = reinterpret_cast<volatile int *>(tmem_slot + 2);
+  volatile int *consumed = reinterpret_cast<volatile int *>(tmem_slot + 3);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk_all = (K + BK - 1) / BK;
+  const int tiles = nM * nN * nsplit;
+  // tile t: split z = t / (nM nN); within a split, groups of RASTER_GM row tiles sweep the column tiles
+  auto tile_of = [&](int t, int &m0, int &n0, int &kb0, int &nk, long long &zoff) {
+    const int z = t / (nM * nN), id = t - z * (nM * nN);
+    const int first_m = (id / (RASTER_GM * nN)) * RASTER_GM;
+    const int gm = min(nM - first_m, RASTER_GM);
+    const int r = id - first_m * nN;
+    m0 = (first_m + r % gm) * BM;
+    n0 = (r / gm) * BN;
+    kb0 = z * kb_per_split;
+    nk = min(nk_all, kb0 + kb_per_split) - kb0;
+    zoff = (long long)z * split_stride;
+  };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; s++) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int b = 0; b < 2; b++) {
+      mbar_init(smem_u32(&accf[b]), 1);
+      mbar_init(smem_u32(&acce[b]), 4);   // one arrive per epilogue warp
+    }
+    mbar_init(smem_u32(drain), 1);
+    *abort_flag = 0;
+    *issued = 0;
+    *consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {   // TMEM: two accumulators of BN FP32 columns x 128 lanes
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0 && !ctl.skip_loads) {
+      // ---------------- TMA producer: K blocks of the CTA's tiles, one continuous pipeline
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        int m0, n0, kb0, nk;
+        long long zoff;
+        tile_of(t, m0, n0, kb0, nk, zoff);
+        for (int kb = 0; kb < nk; kb++, it++) {
+          const int s = it % STAGES;
+          const unsigned ph = (it / STAGES) & 1;
+          if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag, ctl.wait_ns)) {
+            ok = false;
+            break;
+          }
+          unsigned char *sa = smem + s * STAGE_BYTES;
+          mbar_expect_tx(smem_u32(&full[s]), STAGE_BYTES);
+          tma_load_2d(smem_u32(sa), &tmA, smem_u32(&full[s]), (kb0 + kb) * BK, m0);
+          tma_load_2d(smem_u32(sa + A_BYTES), &tmB, smem_u32(&full[s]), (kb0 + kb) * BK, n0);
+          *issued = it + 1;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer: accumulator lt & 1 of the CTA's lt-th tile
+      const unsigned idesc = idesc_bf16(BM, BN);
+      int it = 0, lt = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, lt++) {
+        int m0, n0, kb0, nk;
+        long long zoff;
+        tile_of(t, m0, n0, kb0, nk, zoff);
+        const int buf = lt & 1;
+        if (!mbar_wait(smem_u32(&acce[buf]), ((lt >> 1) & 1) ^ 1, abort_flag, ctl.wait_ns)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned acc = tmem + (unsigned)(buf * BN);
+        for (int kb = 0; kb < nk; kb++, it++) {
+          const int s = it % STAGES;
+          const unsigned ph = (it / STAGES) & 1;
+          if (!mbar_wait(smem_u32(&full[s]), ph, abort_flag, ctl.wait_ns)) {
+            ok = false;
+            break;
+          }
+          *consumed = it + 1;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const unsigned sa = smem_u32(smem + s * STAGE_BYTES);
+          const unsigned sb = sa + A_BYTES;
+#pragma unroll
+          for (int k = 0; k < BK / 16; k++)
+            umma_bf16(acc, smem_desc(sa + 32 * k), smem_desc(sb + 32 * k), idesc, (kb > 0 || k > 0) ? 1u : 0u);
+          umma_commit(smem_u32(&empty[s]));
+        }
+        if (ok) umma_commit(smem_u32(&accf[buf]));
+      }
+      umma_commit(smem_u32(drain));   // arrives once every MMA issued above has completed
+    }
+  } else {
+    // ---------------- epilogue warps 2..5: rows 32 (warp mod 4) + lane of each tile
+    const int q = warp & 3;
+    int lt = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, lt++) {
+      int m0, n0, kb0, nk;
+      long long zoff;
+      tile_of(t, m0, n0, kb0, nk, zoff);
+      const int buf = lt & 1;
+      const bool ready = mbar_wait(smem_u32(&accf[buf]), (lt >> 1) & 1, abort_flag, ctl.wait_ns);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!__all_sync(0xffffffffu, ready && !*abort_flag)) break;
+      const int row = m0 + q * 32 + lane;
+      float *Dz = D + zoff;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        float v[32];
+        tmem_ld_32(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(buf * BN + c0), v);
+        if (row < M && n0 + c0 < N) {
+          float *dst = Dz + (long long)row * ldd + n0 + c0;
+          const int ncols = min(32, N - (n0 + c0));
+          if (ncols == 32 && beta == 0.0f && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+#pragma unroll
+            for (int i = 0; i < 32; i += 4)
+              *reinterpret_cast<float4 *>(dst + i) = make_float4(alpha * v[i], alpha * v[i + 1], alpha * v[i + 2],
+                                                                 alpha * v[i + 3]);
+          } else if (ncols == 32 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+#pragma unroll
+            for (int i = 0; i < 32; i += 4) {
+              const float4 d = *reinterpret_cast<const float4 *>(dst + i);
+              *reinterpret_cast<float4 *>(dst + i) =
+                  make_float4(alpha * v[i] + beta * d.x, alpha * v[i + 1] + beta * d.y, alpha * v[i + 2] + beta * d.z,
+                              alpha * v[i + 3] + beta * d.w);
+            }
+          } else {
+            for (int i = 0; i < ncols; i++) dst[i] = alpha * v[i] + (beta != 0.0f ? beta * dst[i] : 0.0f);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[buf])) : "memory");
+    }
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // every MMA the issuer committed has completed (the drain barrier); after a time-out also the TMA
+    // copies issued but not consumed land before the shared memory goes away (fixed DRAIN_NS limits)
+    volatile int never = 0;
+    mbar_wait(smem_u32(drain), 0, &never, DRAIN_NS);
+    if (*abort_flag)
+      for (int it = *consumed; it < *issued; it++)
+        mbar_wait(smem_u32(&full[it % STAGES]), (it / STAGES) & 1, &never, DRAIN_NS);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN));
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // The same product on CTA pairs (tcgen05 cta_group::2): a cluster of two CTAs on two SMs computes a
 // 256 x 256 output tile with M = 256 MMAs.  Each CTA stages its own 128 rows of A and one half (128
 // columns) of the B tile, so per SM the shared memory holds and the tensor core reads half of the B
@@ -794,6 +988,9 @@ bool g_autotune = true;
 // 0: the autotuner also times the CTA-pair tile; 1: the pair tile whenever it applies; 2: never
 int g_pair_mode = 0;
 constexpr int TILE_PAIR = 512;   // autotuner key of the 256 x 256 CTA-pair tile
+constexpr int TILE_PERSIST = 1024;   // autotuner key offset of the persistent kernel (+ its tile width)
+// 0: the autotuner also times the persistent kernel; 1: always the persistent kernel; 2: never
+int g_persist_mode = 0;
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, int> g_tune;
 
@@ -819,6 +1016,40 @@ int launch_umma_st(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const
   dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, nsplit);
   umma_bf16_gemm_kernel<BN, ST><<<grid, THREADS, Tile<BN, ST>::SMEM_BYTES, st>>>(ma, mb, D, ldd, M, N, K, alpha, beta, kbs,
                                                                          split_stride, umma_ctl());
+  GFCC_LAUNCH_CHECK();
+  return GFCC_OK;
+}
+
+template <int BN>
+int launch_umma_persist(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const __nv_bfloat16 *B, long long ldb,
+                        float *D, long long ldd, int M, int N, int K, float alpha, float beta, int nsplit, int kbs,
+                        long long split_stride) {
+  CUtensorMap ma, mb;
+  GFCC_TRY(make_map(&ma, A, M, K, lda, BM));
+  GFCC_TRY(make_map(&mb, B, N, K, ldb, BN));
+  static bool attr[64] = {false};
+  static int nsm[64] = {0};
+  int dev = 0;
+  GFCC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64 || !attr[dev]) {
+    GFCC_CUDA(cudaFuncSetAttribute(umma_persist_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   PTile<BN>::SMEM_BYTES));
+    int sms = 0;
+    GFCC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (dev >= 0 && dev < 64) {
+      attr[dev] = true;
+      nsm[dev] = sms;
+    }
+  }
+  const int sms = (dev >= 0 && dev < 64 && nsm[dev] > 0) ? nsm[dev] : 152;
+  const long long nM = (M + BM - 1) / BM, nN = (N + BN - 1) / BN, tiles = nM * nN * nsplit;
+  if (tiles > 0x7fffffffLL) {
+    set_error("gemm_bf16_tn: too many tiles (M=%d, N=%d, nsplit=%d)", M, N, nsplit);
+    return GFCC_ERR_ARG;
+  }
+  const unsigned grid = (unsigned)std::min<long long>(tiles, sms);
+  umma_persist_gemm_kernel<BN><<<grid, PERSIST_THREADS, PTile<BN>::SMEM_BYTES, st>>>(
+      ma, mb, D, ldd, M, N, K, alpha, beta, kbs, split_stride, (int)nM, (int)nN, nsplit, umma_ctl());
   GFCC_LAUNCH_CHECK();
   return GFCC_OK;
 }
@@ -883,17 +1114,29 @@ int gemm_bf16_tn(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const _
   GFCC_TRY(check_extent_bytes(B, (long long)(N - 1) * ldb * 2 + (long long)K * 2, "bf16 GEMM operand B"));
   GFCC_TRY(check_extent_bytes(D, ((long long)(M - 1) * ldd + N + (long long)(nsplit - 1) * split_stride) * 4,
                               "bf16 GEMM output D"));
-  // tile widths: 64 / 128 / 256 columns per CTA, or TILE_PAIR (256 x 256 over a CTA pair)
+  // tile widths: 64 / 128 / 256 columns per CTA, TILE_PAIR (256 x 256 over a CTA pair), or
+  // TILE_PERSIST + 64 / 128 / 256 (the persistent kernel with that width)
   auto run = [&](int bn) -> int {
     if (bn == 64) return launch_umma<64>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
     if (bn == 128) return launch_umma<128>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
     if (bn == TILE_PAIR)
       return launch_umma_pair(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
+    if (bn == TILE_PERSIST + 64)
+      return launch_umma_persist<64>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
+    if (bn == TILE_PERSIST + 128)
+      return launch_umma_persist<128>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
+    if (bn == TILE_PERSIST + 256)
+      return launch_umma_persist<256>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
     return launch_umma<256>(st, A, lda, B, ldb, D, ldd, M, N, K, alpha, beta, nsplit, kbs, split_stride);
   };
   // the pair kernel needs two row tiles and pays off on wide products with a long K loop
   const bool pair_ok = g_pair_mode != 2 && M > BM && N > 128 && kbs >= 8;
   if (g_pair_mode == 1) return pair_ok ? run(TILE_PAIR) : run(N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+  const int narrow = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
+  if (g_persist_mode == 1) return run(TILE_PERSIST + narrow);
+  // the persistent kernel pays off once a launch has several waves of tiles
+  const long long tiles_narrow = ((M + BM - 1) / BM) * ((N + narrow - 1) / narrow) * (long long)nsplit;
+  const bool persist_ok = g_persist_mode != 2 && tiles_narrow > 2 * 152;
   // default: the narrowest tile that covers N (wide N keeps the 256-column tile)
   int bn = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
   if (g_autotune && beta != 0.0f) {
@@ -917,8 +1160,11 @@ int gemm_bf16_tn(cudaStream_t st, const __nv_bfloat16 *A, long long lda, const _
       GFCC_CUDA(cudaEventCreate(&e0));
       GFCC_CUDA(cudaEventCreate(&e1));
       float best_ms = 0.0f;
-      for (int cand : {64, 128, 256, TILE_PAIR}) {
-        if (cand == TILE_PAIR ? !pair_ok : (cand > 64 && cand / 2 >= N)) continue;   // never better
+      for (int cand : {64, 128, 256, TILE_PAIR, TILE_PERSIST + 64, TILE_PERSIST + 128, TILE_PERSIST + 256}) {
+        const int w = cand > TILE_PERSIST ? cand - TILE_PERSIST : cand;
+        if (cand == TILE_PAIR ? !pair_ok
+                              : ((cand > TILE_PERSIST && !persist_ok) || (w > 64 && w / 2 >= N)))
+          continue;   // never better
         GFCC_TRY(run(cand));
         GFCC_CUDA(cudaEventRecord(e0, st));
         GFCC_TRY(run(cand));
@@ -996,6 +1242,7 @@ int emu_gemm_fused(cudaStream_t st, const __nv_bfloat16 *Adig, long long plA, in
 void umma_set_autotune(bool on) { g_autotune = on; }
 
 void umma_set_pair_mode(int mode) { g_pair_mode = mode; }
+void umma_set_persist_mode(int mode) { g_persist_mode = mode; }
 
 void umma_set_wait(unsigned long long wait_ns, bool skip_loads) {
   g_wait_ns = wait_ns;

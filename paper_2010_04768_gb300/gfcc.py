@@ -25,7 +25,7 @@ OPT_SECTOR, OPT_PRECISION, OPT_RESTART, OPT_MAX_ITERS, OPT_PRECOND, OPT_BATCH, O
 OPT_RESIDUAL, OPT_INNER_CYCLES, OPT_EMU_LEVEL = 8, 9, 10
 OPT_GUESS, OPT_KEEP_SOLUTIONS, OPT_INNER_KRYLOV, OPT_AUTOTUNE, OPT_GRAPHS, OPT_EMU_FUSED_N = 11, 12, 13, 14, 15, 16
 OPT_INCREMENTAL, OPT_INNER_RESTART = 17, 18
-OPT_SETUP_EMULATE_FLOPS, OPT_WAIT_NS, OPT_TEST_NO_LOADS, OPT_GEMM_PAIR = 19, 20, 21, 22
+OPT_SETUP_EMULATE_FLOPS, OPT_WAIT_NS, OPT_TEST_NO_LOADS, OPT_GEMM_PAIR, OPT_GEMM_PERSIST = 19, 20, 21, 22, 23
 GUESS_ZERO, GUESS_LEARNED, GUESS_MINRES = 0, 1, 2
 MLP_FP32, MLP_FP64 = 0, 1
 MLP_FEATURES, MLP_OUTPUTS = 27, 16
@@ -122,6 +122,11 @@ def load():
                                            ctypes.c_double, ctypes.c_int, ip, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_int, ctypes.c_int, dp, dp, ip, ip, dp, ctypes.c_int, ip]
     lib.gfcc_spectral_adaptive.restype = ctypes.c_int
+    lib.gfcc_create_rhf.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, ctypes.POINTER(P)]
+    lib.gfcc_create_rhf.restype = ctypes.c_int
+    lib.gfcc_ccsd.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_int,
+                              ctypes.c_int, dp, dp, dp, dp]
+    lib.gfcc_ccsd.restype = ctypes.c_int
     lib.gfcc_last_error.restype = ctypes.c_char_p
     for name in ("gfcc_create", "gfcc_create_ex", "gfcc_set_option", "gfcc_set_stream", "gfcc_solve",
                  "gfcc_solve_block", "gfcc_set_process_option",
@@ -187,7 +192,8 @@ def _f64(a) -> np.ndarray:
 class GFCC:
     """One gfcc_ctx: the problem on the device with its Hbar elements."""
 
-    def __init__(self, problem, sectors: str = "IP+EA", precision: str = "fp64"):
+    def __init__(self, problem, sectors: str = "IP+EA", precision: str = "fp64", closed_shell: bool = False):
+        """closed_shell=True: gfcc_create_rhf (spatial orbitals, spin-adapted IP; sectors "IP", FP64)."""
         lib = load()
         self.o, self.v, self.L = problem.o, problem.v, problem.L
         fock, chol, t1, t2 = (_f64(x) for x in (problem.fock, problem.chol, problem.t1, problem.t2))
@@ -195,9 +201,15 @@ class GFCC:
         if problem.lam1 is not None:
             lam = np.concatenate([_f64(problem.lam1).reshape(-1), _f64(problem.lam2).reshape(-1)])
         h = ctypes.c_void_p()
-        _check(lib.gfcc_create_ex(self.o, self.v, self.L, _dp(fock), _dp(chol), _dp(t1), _dp(t2),
-                                  None if lam is None else _dp(lam), _SECTORS[sectors], _PRECS[precision],
-                                  ctypes.byref(h)))
+        if closed_shell:
+            if sectors != "IP" or precision != "fp64":
+                raise ValueError("closed-shell contexts are IP-only and FP64")
+            _check(lib.gfcc_create_rhf(self.o, self.v, self.L, _dp(fock), _dp(chol), _dp(t1), _dp(t2),
+                                       None if lam is None else _dp(lam), ctypes.byref(h)))
+        else:
+            _check(lib.gfcc_create_ex(self.o, self.v, self.L, _dp(fock), _dp(chol), _dp(t1), _dp(t2),
+                                      None if lam is None else _dp(lam), _SECTORS[sectors], _PRECS[precision],
+                                      ctypes.byref(h)))
         self._h = h
         self.sectors = sectors
 
@@ -536,3 +548,40 @@ def spectral_adaptive(ctx: GFCC, sectors: str, omega_min: float, omega_max: floa
         levels.append(list(samp[k:k + sizes[L]]))
         k += sizes[L]
     return A, levels, (int(mdim[0]), int(mdim[1])), code
+
+
+CCSD_EMULATE, CCSD_GUESS = 1, 2
+
+
+def ccsd(fock, chol, o: int, tol: float = 1e-10, max_iter: int = 100, want_lambda: bool = True,
+         emulate: bool = False, guess=None):
+    """gfcc_ccsd: (t1, t2, lam1, lam2, info, code) for the Hamiltonian (fock, chol) with o occupied
+    orbitals.  guess = (t1, t2[, lam1, lam2]) starts from those iterates; lam1 / lam2 are None when
+    want_lambda is False.  info: dict of the call's info array."""
+    fock = _f64(fock)
+    chol = _f64(chol)
+    n = fock.shape[0]
+    L = chol.shape[0]
+    v = n - o
+    flags = (CCSD_EMULATE if emulate else 0) | (CCSD_GUESS if guess is not None else 0)
+    t1 = np.zeros((o, v))
+    t2 = np.zeros((o, o, v, v))
+    lam = np.zeros(o * v + (o * v) ** 2) if want_lambda else None
+    if guess is not None:
+        t1[...] = guess[0]
+        t2[...] = guess[1]
+        if want_lambda and len(guess) > 2:
+            lam[:o * v] = np.ravel(guess[2])
+            lam[o * v:] = np.ravel(guess[3])
+        elif want_lambda:
+            lam[:o * v] = np.ravel(guess[0])
+            lam[o * v:] = np.ravel(guess[1])
+    info = np.zeros(8)
+    code = _check(load().gfcc_ccsd(o, v, L, _dp(fock), _dp(chol), float(tol), int(max_iter), flags, _dp(t1), _dp(t2),
+                                   _dp(lam) if lam is not None else None, _dp(info)))
+    keys = ("e_corr", "t_iters", "t_residual", "lambda_iters", "lambda_residual", "t_seconds", "lambda_seconds",
+            "t_flops_per_iter")
+    d = {k: float(x) for k, x in zip(keys, info)}
+    lam1 = lam[:o * v].reshape(o, v) if lam is not None else None
+    lam2 = lam[o * v:].reshape(o, o, v, v) if lam is not None else None
+    return t1, t2, lam1, lam2, d, code

@@ -202,6 +202,28 @@ def make_problem(o: int, v: int, L: int, seed: int = 0, *, chol_sigma: float | N
     return Problem(o=o, v=v, L=L, fock=fock, chol=chol, t1=t1, t2=t2, lam1=lam1, lam2=lam2)
 
 
+def make_closed_shell_problem(o: int, v: int, L: int, seed: int = 0, *, chol_sigma: float | None = None,
+                              t1_std: float = 0.01, t2_std: float = 0.02, separate_lambda: bool = False) -> Problem:
+    """Closed-shell synthetic inputs over spatial orbitals (o doubly occupied, v virtual): Fock matrix
+    and Cholesky vectors by the recipe of make_problem (sigma_L = (2o * 2v)^(-1/2) unless given, the
+    width of the spin-orbital problem of the same system); t1[i][a] ~ N(0, t1_std^2) (alpha block);
+    t2[i][j][a][b] = (g[i][j][a][b] + g[j][i][b][a]) / 2 with g ~ N(0, t2_std^2), so that
+    t_ij^ab = t_ji^ba (the alpha-beta block of a spin-adapted T2).  Lambda = T^dagger unless
+    separate_lambda (its own streams, same widths and symmetry)."""
+    sig = (1.0 / math.sqrt(4 * o * v)) if chol_sigma is None else float(chol_sigma)
+    base = make_problem(o, v, L, seed=seed, chol_sigma=sig, with_t=False)
+    t1 = normal(seed, STREAM_T1, o * v, t1_std).reshape(o, v)
+    g = normal(seed, STREAM_T2, o * o * v * v, t2_std).reshape(o, o, v, v)
+    t2 = 0.5 * (g + g.transpose(1, 0, 3, 2))
+    lam1 = lam2 = None
+    if separate_lambda:
+        lam1 = normal(seed, STREAM_LAMBDA1, o * v, t1_std).reshape(o, v)
+        h = normal(seed, STREAM_LAMBDA2, o * o * v * v, t2_std).reshape(o, o, v, v)
+        lam2 = 0.5 * (h + h.transpose(1, 0, 3, 2))
+    return Problem(o=o, v=v, L=L, fock=base.fock, chol=base.chol, t1=t1, t2=np.ascontiguousarray(t2), lam1=lam1,
+                   lam2=None if lam2 is None else np.ascontiguousarray(lam2))
+
+
 def random_vector(seed: int, count: int, stream_offset: int = 0) -> np.ndarray:
     """count N(0,1) draws for test vectors (a stream separate from the problem tensors)."""
     return normal(seed, STREAM_VECTOR + 16 * stream_offset, count)
@@ -237,8 +259,11 @@ class Workload:
     sectors: str            # "IP", "EA" or "IP+EA"
     seed: int = 0
     precision: str = "fp64"
+    closed_shell: bool = False   # spatial orbitals (make_closed_shell_problem)
 
     def problem(self, **kw) -> Problem:
+        if self.closed_shell:
+            return make_closed_shell_problem(self.o, self.v, self.L, self.seed, **kw)
         return make_problem(self.o, self.v, self.L, self.seed, **kw)
 
 
@@ -252,7 +277,9 @@ def orbitals_nearest_gap(eps_o: np.ndarray, eps_v: np.ndarray, count: int) -> np
 
 def workload(name: str) -> Workload:
     """The named workload.  'tiny' (o=4 v=12 L=48), 'medium' (o=40 v=200 L=800),
-    'c60' (o=90 v=450 L=1800, 128 frequencies), 'c60x256' (the same problem, 256 frequencies)."""
+    'c60' (o=90 v=450 L=1800, 128 frequencies), 'c60x256' (the same problem, 256 frequencies),
+    closed-shell (spatial orbitals): 'medium-closed-shell' (o=30 v=150 L=600),
+    'c60-closed-shell' (o=45 v=225 L=1800)."""
     if name == "tiny":
         return Workload("tiny", 4, 12, 48, np.linspace(-1.0, -0.2, 4), 0.01,
                         np.arange(16, dtype=np.int32), 1e-8, 30, "IP")
@@ -271,4 +298,16 @@ def workload(name: str) -> Workload:
         o, v = 90, 450
         return Workload("c60x256", o, v, 1800, np.linspace(-1.0, -0.3, 256), 0.005,
                         np.arange(o - 30, o, dtype=np.int32), 1e-8, 30, "IP", precision="mixed")
+    if name == "c60-closed-shell":
+        # the C60-shaped system as a closed shell: 45 doubly occupied and 225 virtual spatial orbitals
+        # (the 90 / 450 spin-orbitals of 'c60'), the 30 highest occupied orbitals, spin-adapted IP
+        o, v = 45, 225
+        return Workload("c60-closed-shell", o, v, 1800, np.linspace(-1.0, -0.3, 128), 0.005,
+                        np.arange(o - 30, o, dtype=np.int32), 1e-8, 30, "IP", closed_shell=True)
+    if name == "medium-closed-shell":
+        # 30 doubly occupied and 150 virtual spatial orbitals (the 60 / 300 spin-orbitals of a
+        # medium-sized system), the 10 highest occupied orbitals, spin-adapted IP
+        o, v = 30, 150
+        return Workload("medium-closed-shell", o, v, 600, np.linspace(-1.2, -0.2, 64), 0.005,
+                        np.arange(o - 10, o, dtype=np.int32), 1e-8, 30, "IP", closed_shell=True)
     raise KeyError(name)

@@ -81,3 +81,27 @@ def test_process_options_and_block_solve_arguments_without_a_gpu(lib):
     orb = (ctypes.c_int * 1)(0)
     G = (ctypes.c_double * 2)()
     assert typed.gfcc_solve_block(None, 1, om, 0.01, 1, orb, 1, orb, 1e-8, G) == gfcc.ERR_ARG
+
+
+def test_ccsd_arguments_are_rejected_without_a_gpu(lib):
+    # sizes, NULL inputs, tol, max_iter and unknown flags are checked before any CUDA call
+    typed = gfcc.load()
+    f = (ctypes.c_double * 4)()
+    ch = (ctypes.c_double * 4)()
+    t1 = (ctypes.c_double * 1)()
+    t2 = (ctypes.c_double * 1)()
+    assert typed.gfcc_ccsd(0, 1, 1, f, ch, 1e-8, 10, 0, t1, t2, None, None) == gfcc.ERR_ARG
+    assert typed.gfcc_ccsd(1, 1, 1, None, ch, 1e-8, 10, 0, t1, t2, None, None) == gfcc.ERR_ARG
+    assert typed.gfcc_ccsd(1, 1, 1, f, ch, 0.0, 10, 0, t1, t2, None, None) == gfcc.ERR_ARG
+    assert typed.gfcc_ccsd(1, 1, 1, f, ch, 1e-8, 0, 0, t1, t2, None, None) == gfcc.ERR_ARG
+    assert typed.gfcc_ccsd(1, 1, 1, f, ch, 1e-8, 10, 4, t1, t2, None, None) == gfcc.ERR_ARG
+    assert typed.gfcc_ccsd(1, 1, 1, f, ch, 1e-8, 10, 0, None, t2, None, None) == gfcc.ERR_ARG
+
+
+def test_closed_shell_create_arguments_are_rejected_without_a_gpu(lib):
+    typed = gfcc.load()
+    h = ctypes.c_void_p()
+    f = (ctypes.c_double * 4)()
+    assert typed.gfcc_create_rhf(0, 1, 1, f, f, f, f, None, ctypes.byref(h)) == gfcc.ERR_ARG
+    assert typed.gfcc_create_rhf(1, 1, 1, None, f, f, f, None, ctypes.byref(h)) == gfcc.ERR_ARG
+    assert typed.gfcc_create_rhf(1, 1, 1, f, f, f, f, None, None) == gfcc.ERR_ARG

@@ -62,6 +62,22 @@ def test_bounded_wait_runs_out_and_the_context_recovers():
         assert np.array_equal(gfcc.selftest_gemm_bf16(A2, B2), ref2)
     finally:
         gfcc.set_process_option(gfcc.OPT_GEMM_PAIR, 0.0)
+    # the persistent kernel likewise
+    gfcc.set_process_option(gfcc.OPT_GEMM_PERSIST, 1.0)
+    try:
+        ref3 = gfcc.selftest_gemm_bf16(A2, B2)
+        gfcc.set_process_option(gfcc.OPT_WAIT_NS, 2000.0)
+        gfcc.set_process_option(gfcc.OPT_TEST_NO_LOADS, 1.0)
+        try:
+            with pytest.raises(gfcc.GFCCError) as e:
+                gfcc.selftest_gemm_bf16(A2, B2)
+            assert e.value.code == gfcc.ERR_TIMEOUT
+        finally:
+            gfcc.set_process_option(gfcc.OPT_TEST_NO_LOADS, 0.0)
+            gfcc.set_process_option(gfcc.OPT_WAIT_NS, 1e9)
+        assert np.array_equal(gfcc.selftest_gemm_bf16(A2, B2), ref3)
+    finally:
+        gfcc.set_process_option(gfcc.OPT_GEMM_PERSIST, 0.0)
     # a solver context on the same device works after the time-out
     pr = make_problem(3, 5, 7, seed=1)
     g = gfcc.GFCC(pr, sectors="IP", precision="mixed")

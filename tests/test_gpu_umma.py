@@ -125,3 +125,36 @@ def test_pair_emulated_product_is_fp64_accurate(pair_mode):
     B = rng.standard_normal((N, K)) * np.exp(rng.uniform(-3, 3, size=(N, 1)))
     C = gfcc.selftest_gemm_f64emu(A, B, S=8, P=9)
     assert (np.abs(C - A @ B.T) / (np.abs(A) @ np.abs(B).T)).max() <= 1e-13
+
+
+@pytest.fixture
+def persist_mode():
+    # force the persistent kernel (two TMEM accumulators, one CTA per SM); restore autotuning afterwards
+    gfcc.set_process_option(gfcc.OPT_GEMM_PERSIST, 1.0)
+    yield
+    gfcc.set_process_option(gfcc.OPT_GEMM_PERSIST, 0.0)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (300, 520, 700), (5000, 60, 540), (2000, 300, 64),
+                                   (1024, 1024, 4096), (77, 1000, 130), (40000, 100, 64), (20000, 300, 200)])
+def test_persistent_gemm_matches_reference(persist_mode, M, N, K):
+    # up to three tiles per CTA (both accumulators reused, their barriers in their second phase), one
+    # K block per tile, ragged edges
+    A = normal(5, 1, M * K).reshape(M, K).astype(np.float32)
+    B = normal(6, 1, N * K).reshape(N, K).astype(np.float32)
+    D = gfcc.selftest_gemm_bf16(A, B)
+    Ab, Bb = bf16_round(A), bf16_round(B)
+    ref = Ab @ Bb.T
+    scale = np.abs(Ab) @ np.abs(Bb).T
+    err = np.abs(D.astype(np.float64) - ref) / scale
+    assert err.max() <= 4 * K * 2.0**-24 + 1e-7
+
+
+def test_persistent_emulated_product_is_fp64_accurate(persist_mode):
+    # the digit-pair products (accumulating calls, split K) on the persistent kernel
+    rng = np.random.default_rng(10)
+    for M, N, K in ((600, 700, 3000), (130, 600, 20000)):
+        A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-3, 3, size=(M, 1)))
+        B = rng.standard_normal((N, K)) * np.exp(rng.uniform(-3, 3, size=(N, 1)))
+        C = gfcc.selftest_gemm_f64emu(A, B, S=8, P=9)
+        assert (np.abs(C - A @ B.T) / (np.abs(A) @ np.abs(B).T)).max() <= 1e-13
