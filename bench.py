@@ -73,11 +73,17 @@ WORKLOADS = {
     "c60x256-ip-mixed-sweep": dict(base="c60x256", sector="IP", precision="mixed", per_step=16, sweep=True),
     "c60x256-ip-mixed-sweep-minres": dict(base="c60x256", sector="IP", precision="mixed", per_step=16, sweep=True,
                                           guess="minres"),
+    "c60x1024-ip-mixed-sweep": dict(base="c60x1024", sector="IP", precision="mixed", per_step=16, sweep=True),
+    "c60x1024-ip-mixed-sweep-minres": dict(base="c60x1024", sector="IP", precision="mixed", per_step=16, sweep=True,
+                                           guess="minres"),
+    "c60x1024-ip-mixed-sweep-learned": dict(base="c60x1024", sector="IP", precision="mixed", per_step=16, sweep=True,
+                                            guess="learned"),
     "c60x256-ip-mixed-sweep-learned": dict(base="c60x256", sector="IP", precision="mixed", per_step=16, sweep=True,
                                            guess="learned"),
     # closed-shell spin-adapted IP (spatial orbitals, FP64), beside the spin-orbital FP64 path on the
     # spin-orbital embedding of the same system
     "medium-closed-shell-ip-fp64": dict(base="medium-closed-shell", sector="IP", precision="fp64", per_step=1),
+    "c60-closed-shell-ip-fp64": dict(base="c60-closed-shell", sector="IP", precision="fp64", per_step=1),
     # ground-state CCSD (the step before the Green's function): one step = one T iteration
     "ccsd-medium": dict(ccsd=(40, 200, 800), emulate=True),
     "ccsd-medium-fp64": dict(ccsd=(40, 200, 800), emulate=False),
@@ -434,7 +440,9 @@ def config_of(spec, wl, world):
             **({"inner_restart": INNER_RESTART} if spec["precision"] == "mixed" else {}), "preconditioner": "diag",
             "columns_per_step": spec["per_step"] * int(wl.orbitals.size) * len(sectors_of(spec)) * world,
             "parallelism": f"{world} independent GPU(s), frequencies sharded", "l2": "inputs larger than L2 "
-            "(ring matrix and Krylov basis are each > 129 MB)"}
+            "(ring matrix and Krylov basis are each > 129 MB)",
+            **({"closed_shell": "spin-adapted IP over spatial orbitals (gfcc_create_rhf); contractions of at least "
+                                "1e9 flops as FP64-accurate digit-plane products"} if wl.closed_shell else {})}
 
 
 def uneven_specs(seed=4, count=16):
@@ -551,8 +559,11 @@ def run_ccsd(args, spec, world, rank, dist=None):
     else:
         peak, bound = FP64_PEAK_TFLOPS, "alu"
         pnote = "FP64 DFMA peak derived from 152 SMs x 2 FMA/clk x 2070 MHz; achieved = counted flops / time"
-    # a full T + Lambda solve of the same problem (not timed as steps)
-    _, _, _, _, full, fcode = gfcc.ccsd(pr.fock, pr.chol, o, tol=1e-8, max_iter=100, emulate=spec["emulate"])
+    # a full T + Lambda solve of the same problem (not timed as steps; digit-plane contractions only:
+    # on the FP64 units a full solve of this shape takes several minutes)
+    full, fcode = {}, None
+    if spec["emulate"]:
+        _, _, _, _, full, fcode = gfcc.ccsd(pr.fock, pr.chol, o, tol=1e-8, max_iter=100, emulate=True)
     line = {
         "metric": "CCSD T iterations/sec", "value": iters / dt, "unit": "iterations/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, iters), "higher_is_better": True,
@@ -566,9 +577,9 @@ def run_ccsd(args, spec, world, rank, dist=None):
                 "note": "host-timed gfcc_ccsd call: upload, setup of the call, the iterations, read-back"},
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None, "note": pnote, "flops_per_iteration": flops},
-        "full_solve": {"code": fcode, "e_corr": full["e_corr"], "t_iters": full["t_iters"],
-                       "t_seconds": full["t_seconds"], "lambda_iters": full["lambda_iters"],
-                       "lambda_seconds": full["lambda_seconds"], "tol": 1e-8},
+        "full_solve": ({"code": fcode, "e_corr": full["e_corr"], "t_iters": full["t_iters"],
+                        "t_seconds": full["t_seconds"], "lambda_iters": full["lambda_iters"],
+                        "lambda_seconds": full["lambda_seconds"], "tol": 1e-8} if full else None),
         "gpu_launches": int(launches), "clocks": clk.summary(), "code": code,
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -731,7 +742,7 @@ def main():
         mor = mor_leg(gfcc, ctx, wl, spec, freqs(0)[0], G_e2e[0][0])
 
     peaks = measured_peaks()
-    rf = roofline_entries(prof, spec, peaks)
+    rf = roofline_entries(prof, spec, peaks, closed_shell=wl.closed_shell)
     dominant = max(rf, key=lambda k: rf[k]["ms_total"]) if rf else None
     # sigma TFLOP/s: algorithmic flops of every complex sigma product (inner BF16, FP64 and the
     # FP64-accurate residuals) at F_IP / F_EA each, over the device time of the sigma products
@@ -744,7 +755,8 @@ def main():
     line = {
         "metric": "converged G(omega) columns/sec", "value": value, "unit": "columns/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if spec["precision"] == "fp64" else "bf16+f64",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": ("bf16-digit-planes+f64" if wl.closed_shell else "f64" if spec["precision"] == "fp64" else "bf16+f64"),
         "data": "synthetic", "config": config_of(spec, wl, world),
         "e2e": {"value": e2e_cols / e2e_dt, "unit": "columns/s", "h2d_bytes_per_step": 8 * per + 4 * no,
                 "d2h_bytes_per_step": 16 * per * no * no, "steps": e2e_steps,
@@ -944,11 +956,13 @@ def mor_leg(gfcc, ctx, wl, spec, om0, G0):
 # roofline candidates: (phase, bound, kernel label, peak key); the FP64 ring phase runs on the DFMA
 # units, the tensor-core phases against the measured sustained BF16 rate (kernels timed inside a long
 # step), the HBM phases against the measured copy bandwidth
-def roofline_entries(prof, spec, peaks):
+def roofline_entries(prof, spec, peaks, closed_shell=False):
     bf16 = peaks.get("bf16_tflops_sustained", 1727.1)
     hbm = peaks.get("hbm_gbs", 6761.6)
     fp64 = spec["precision"] == "fp64"
     cands = [
+        ("ring", "tensor", "umma_bf16_gemm_kernel / umma_pair_gemm_kernel on digit planes + combine (the three "
+                           "FP64-accurate ring contractions of the closed-shell operator)") if closed_shell else
         ("ring", "alu", "contract_f64_kernel (FP64 ring contraction)"),
         ("vvvv", "alu" if fp64 else "tensor", "contract_f64_kernel (FP64 EA vvvv contraction)" if fp64 else
          "umma_bf16_gemm_kernel (BF16 EA vvvv contraction)"),
@@ -983,7 +997,7 @@ def roofline_entries(prof, spec, peaks):
             note = "bf16_tflops_sustained of measured (kernels timed inside a long step)"
         e = {"bound": bound, "kernel": kernel, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
              "traffic": None, "launches": n_l, "ms_total": ms, "peak_note": note}
-        if ph in ("ring_emu", "emu_other"):
+        if ph in ("ring_emu", "emu_other") or (ph == "ring" and closed_shell):
             e["peak_note"] += ("; achieved counts the method's work, one FP64 product per FP64-accurate "
                                "contraction (2 M N K), not the digit-pair products that evaluate it")
         if ph == "ring_emu":

@@ -114,6 +114,10 @@ extern "C" {
                                      SM, two TMEM accumulators): 0 (default) timed by the autotuner on
                                      launches of several waves, 1 always (unless GFCC_OPT_GEMM_PAIR is
                                      1), 2 never                                                        */
+#define GFCC_OPT_CLOSED_SHELL_EMULATE 24 /* closed-shell contexts (gfcc_create_rhf) only: 1 (default) the
+                                     contractions of the operator of at least 1e9 flops (the ring sums,
+                                     oooo) are FP64-accurate products of BF16 digit planes on the tensor
+                                     cores; 0 every contraction on the FP64 units                       */
 
 /* Initial guesses (Algorithm 1, "compute initial guess").  With a guess other than ZERO, gfcc_solve
  * keeps every converged solution X_p(omega) (FP32 complex, n_omega * n_orb * dim * 8 bytes of device
@@ -172,8 +176,9 @@ int gfcc_create_ex(int o, int v, int L, const double *fock, const double *chol,
  * p alpha, q alpha.  The systems are solved in the doublet coordinates r_i = R_{i alpha},
  * r_ij^a = R_{i alpha, j beta}^{a beta} (dimension o + o^2 v; gfcc_dims reports it, gfcc_sigma and
  * the solves take vectors in it: [r_i | r_ij^a at [i][j][a]]), with the spin-summed Hbar elements.
- * Zero initial guesses only; model-order reduction is not offered for these contexts.  Errors as
- * gfcc_create.
+ * The operator's large contractions run as FP64-accurate digit-plane products on the tensor cores
+ * unless GFCC_OPT_CLOSED_SHELL_EMULATE is 0.  Zero initial guesses only; model-order reduction is not
+ * offered for these contexts.  Errors as gfcc_create.
  */
 int gfcc_create_rhf(int o, int v, int L, const double *fock, const double *chol, const double *t1, const double *t2,
                     const double *lambda, gfcc_ctx **out);
@@ -492,9 +497,9 @@ int gfcc_spectral_adaptive(gfcc_ctx *ctx, int sectors, double omega_min, double 
  *   tol         : convergence when max |residual| <= tol (every singles and doubles equation).
  *   max_iter    : iterations per equation set (>= 1); Jacobi steps with the Fock-diagonal denominators
  *                 f_ii (+ f_jj) - f_aa (- f_bb), extrapolated by DIIS over the last 8 iterates.
- *   flags       : GFCC_CCSD_EMULATE - contractions of at least the setup threshold
- *                 (GFCC_OPT_SETUP_EMULATE_FLOPS) through the FP64-accurate digit-plane products on the
- *                 BF16 tensor cores; GFCC_CCSD_GUESS - t1, t2 (and lambda) hold initial iterates on entry
+ *   flags       : GFCC_CCSD_EMULATE - contractions of at least 1e10 flops (or the setup threshold
+ *                 GFCC_OPT_SETUP_EMULATE_FLOPS when that is lower) through the FP64-accurate digit-plane
+ *                 products on the BF16 tensor cores; GFCC_CCSD_GUESS - t1, t2 (and lambda) hold initial iterates on entry
  *                 (else both start from zero, Lambda from T).
  *   t1 [o][v], t2 [o][o][v][v] : out (in with GFCC_CCSD_GUESS), host; t2 antisymmetric.
  *   lambda      : NULL (T only) or out [lambda1 (o x v) | lambda2 (o x o x v x v)], the layout

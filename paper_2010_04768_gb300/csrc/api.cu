@@ -1228,6 +1228,10 @@ int gfcc_set_option(gfcc_ctx *c, int key, double value) {
       if (!(value > 0.0 && value < 1.0)) break;
       c->inner_tol = value;
       return GFCC_OK;
+    case GFCC_OPT_CLOSED_SHELL_EMULATE:
+      if (!c->rhf || (iv != 0 && iv != 1)) break;
+      c->rhf_emulate = iv;
+      return GFCC_OK;
     case GFCC_OPT_GUESS:
       if (iv != GFCC_GUESS_ZERO && iv != GFCC_GUESS_LEARNED && iv != GFCC_GUESS_MINRES) break;
       if (c->rhf && iv != GFCC_GUESS_ZERO) {

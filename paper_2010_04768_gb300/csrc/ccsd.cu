@@ -46,6 +46,7 @@ namespace {
 constexpr int RED_BLOCKS = 304;   // reduction grids: two blocks per SM
 constexpr int RED_THREADS = 256;
 constexpr int DIIS_CAP = 8;
+constexpr double CCSD_EMULATE_MIN_FLOPS = 1e10;   // GFCC_CCSD_EMULATE: digit planes from this size up
 
 __global__ void diag_copy_kernel(const double *F, int n, double *eps) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -606,7 +607,11 @@ int ccsd_impl(int o, int v, int L, const double *fock, const double *chol, doubl
     return GFCC_ERR_CUDA;
   }
   const bool prev_emulate = g_emulate_big;
+  const double prev_min = g_emulate_min_flops_local;
   g_emulate_big = (flags & GFCC_CCSD_EMULATE) != 0;
+  // the iteration's large contractions (the vvvv blocks and their ladder products, the ring, the
+  // Cholesky sums of the singles) are 1e11-1e12 flops each at medium sizes: below the setup threshold
+  if (g_emulate_big) g_emulate_min_flops_local = std::min(g_emulate_min_flops, CCSD_EMULATE_MIN_FLOPS);
   auto run = [&](Ccsd &C) -> int {
     GFCC_TRY(C.init(o, v, L, fock, chol));
     const long long ov = C.ov, N = C.N;
@@ -667,6 +672,7 @@ int ccsd_impl(int o, int v, int L, const double *fock, const double *chol, doubl
     cudaStreamSynchronize(st);
   }
   g_emulate_big = prev_emulate;
+  g_emulate_min_flops_local = prev_min;
   cudaGetLastError();
   cudaStreamDestroy(st);
   return s;

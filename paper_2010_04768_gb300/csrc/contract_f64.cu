@@ -146,6 +146,7 @@ std::map<cudaStream_t, SplitBuf> g_splitk;
 
 thread_local bool g_emulate_big = false;
 double g_emulate_min_flops = 4e12;
+thread_local double g_emulate_min_flops_local = -1.0;
 
 int gemm_f64(cudaStream_t st, long long M, long long N, long long K, double alpha,
              const double *A, IMap am, IMap ak, const double *B, IMap bk, IMap bn, double beta,
@@ -158,7 +159,8 @@ int gemm_f64(cudaStream_t st, long long M, long long N, long long K, double alph
   c.alpha = alpha; c.beta = beta;
   // Large contractions (setup of big problems) go to the FP64-accurate digit-plane path on the
   // tensor cores when enabled: at ~1 TFLOP/s of FP64 they would take minutes.
-  if (batch == 1 && g_emulate_big && 2.0 * (double)M * (double)N * (double)K >= g_emulate_min_flops)
+  const double emu_min = g_emulate_min_flops_local >= 0.0 ? g_emulate_min_flops_local : g_emulate_min_flops;
+  if (batch == 1 && g_emulate_big && 2.0 * (double)M * (double)N * (double)K >= emu_min)
     return gemm_f64_emulated(st, M, N, K, alpha, A, am, ak, B, bk, bn, beta, C, cm, cn, 8, 9);
   // Few output tiles and a long K would leave most SMs idle: split K into partial sums.
   const long long tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN) * batch;

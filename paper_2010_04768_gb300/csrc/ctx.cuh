@@ -86,6 +86,7 @@ struct gfcc_ctx {
   // closed-shell spin-adapted IP context (gfcc_create_rhf; rhf.cu): spatial orbitals, vectors
   // [r_i (o) | r_ij^a ([i][j][a], o^2 v)], every element alpha-beta spin-summed
   int rhf = 0;
+  int rhf_emulate = 1;      // GFCC_OPT_CLOSED_SHELL_EMULATE: its large contractions from digit planes
   double *rM1 = nullptr, *rM2 = nullptr, *rM3 = nullptr;   // ring matrices [(i,a)][(m,e)] (ov x ov)
   double *rWT = nullptr;    // [(i,j,a)][e | m]: -t_ij^ea | -W_maij  (o^2 v x (v + o))
   double *rVz = nullptr;    // [e][(m,n,f)]: 2 u_mnef - u_mnfe  (v x o^2 v)

@@ -21,6 +21,8 @@ int contract_f64(const Contract &c, cudaStream_t st);
 // path when g_emulate_big is set (mixed-precision contexts set it during their setup)
 extern thread_local bool g_emulate_big;
 extern double g_emulate_min_flops;
+// the calling thread's threshold instead of g_emulate_min_flops while >= 0 (closed-shell operator)
+extern thread_local double g_emulate_min_flops_local;
 int gemm_f64(cudaStream_t st, long long M, long long N, long long K, double alpha,
              const double *A, IMap am, IMap ak, const double *B, IMap bk, IMap bn, double beta,
              double *C, IMap cm, IMap cn, long long batch = 1, long long sab = 0, long long sbb = 0,

@@ -384,8 +384,29 @@ int build_hbar_rhf(gfcc_ctx *c, const double *d_fock, const double *d_chol) {
   return GFCC_OK;
 }
 
+// Contractions of at least this many flops run on the FP64-accurate digit-plane path when the
+// context's emulation option is on (the ring sums and the oooo term at useful sizes; the narrow ones
+// stay on the FP64 units)
+constexpr double RHF_EMULATE_MIN_FLOPS = 1e9;
+
+namespace {
+struct EmulateScope {
+  bool prev_big;
+  double prev_min;
+  explicit EmulateScope(bool on) : prev_big(g_emulate_big), prev_min(g_emulate_min_flops_local) {
+    g_emulate_big = on;
+    g_emulate_min_flops_local = on ? RHF_EMULATE_MIN_FLOPS : prev_min;
+  }
+  ~EmulateScope() {
+    g_emulate_big = prev_big;
+    g_emulate_min_flops_local = prev_min;
+  }
+};
+}  // namespace
+
 int apply_ip_rhf(gfcc_ctx *c, const SysBatch &b, double *work) {
   cudaStream_t st = c->stream;
+  EmulateScope emu(c->rhf_emulate != 0);
   const long long o = c->o, v = c->v, ov = o * v, oo = o * o, o2v = oo * v, C2 = 2LL * b.nsys, dim = c->dim_ip;
   double *P = work;                    // [z (v rows) | r1u (o) | r2u (o^2 v)] x C2
   double *r1u = P + v * C2;

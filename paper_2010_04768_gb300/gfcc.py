@@ -26,6 +26,7 @@ OPT_RESIDUAL, OPT_INNER_CYCLES, OPT_EMU_LEVEL = 8, 9, 10
 OPT_GUESS, OPT_KEEP_SOLUTIONS, OPT_INNER_KRYLOV, OPT_AUTOTUNE, OPT_GRAPHS, OPT_EMU_FUSED_N = 11, 12, 13, 14, 15, 16
 OPT_INCREMENTAL, OPT_INNER_RESTART = 17, 18
 OPT_SETUP_EMULATE_FLOPS, OPT_WAIT_NS, OPT_TEST_NO_LOADS, OPT_GEMM_PAIR, OPT_GEMM_PERSIST = 19, 20, 21, 22, 23
+OPT_CLOSED_SHELL_EMULATE = 24
 GUESS_ZERO, GUESS_LEARNED, GUESS_MINRES = 0, 1, 2
 MLP_FP32, MLP_FP64 = 0, 1
 MLP_FEATURES, MLP_OUTPUTS = 27, 16

@@ -298,6 +298,12 @@ def workload(name: str) -> Workload:
         o, v = 90, 450
         return Workload("c60x256", o, v, 1800, np.linspace(-1.0, -0.3, 256), 0.005,
                         np.arange(o - 30, o, dtype=np.int32), 1e-8, 30, "IP", precision="mixed")
+    if name == "c60x1024":
+        # the C60-shaped problem on a grid 4x denser than c60x256 (spacing 0.14 eta): how dense a grid
+        # the neighbour guesses need
+        o, v = 90, 450
+        return Workload("c60x1024", o, v, 1800, np.linspace(-1.0, -0.3, 1024), 0.005,
+                        np.arange(o - 30, o, dtype=np.int32), 1e-8, 30, "IP", precision="mixed")
     if name == "c60-closed-shell":
         # the C60-shaped system as a closed shell: 45 doubly occupied and 225 virtual spatial orbitals
         # (the 90 / 450 spin-orbitals of 'c60'), the 30 highest occupied orbitals, spin-adapted IP

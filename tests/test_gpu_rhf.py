@@ -9,7 +9,9 @@
   device code paths of different shape that must agree;
 * two electrons (one doubly occupied orbital) with the converged CCSD / Lambda amplitudes of the
   device's own ground-state step: the exact Lehmann G;
-* a sampled G row of the medium closed-shell workload (o=30 v=150 L=600) against the oracle's GMRES.
+* the operator with its large contractions on the digit-plane path against the FP64 units and the
+  oracle at the medium closed-shell shape, and a sampled G row of that workload (o=30 v=150 L=600,
+  digit-plane operator) against the oracle's GMRES.
 """
 import numpy as np
 import pytest
@@ -108,6 +110,22 @@ def test_two_electrons_from_the_device_ground_state_is_exact():
     al, _ = R.so_index(o, v)
     Gx = F.exact_green(Fs, Ls, 2 * o, om, 0.05, [int(a) for a in al], parts=("IP",))
     assert rel(G, Gx) <= 1e-9
+
+
+def test_digit_plane_operator_matches_fp64_operator_and_oracle():
+    # medium closed-shell shape: the ring sums and the oooo term (above 1e9 flops) from digit planes
+    wl = workload("medium-closed-shell")
+    pr = wl.problem()
+    g = gfcc.GFCC(pr, sectors="IP", closed_shell=True)
+    di, _ = g.dims()
+    X = np.stack([random_vector(21 + k, di) + 1j * random_vector(41 + k, di) for k in range(4)])
+    Ye = g.sigma("IP", X)
+    g.set_option(gfcc.OPT_CLOSED_SHELL_EMULATE, 0)
+    Yf = g.sigma("IP", X)
+    g.close()
+    assert rel(Ye, Yf) <= 1e-12
+    C = R.RHFClosed(pr.fock, pr.chol, pr.t1, pr.t2, o=wl.o)
+    assert rel(Ye[0], C.sigma(X[0])) <= 1e-12
 
 
 def test_medium_closed_shell_row_matches_oracle():
