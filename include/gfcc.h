@@ -521,6 +521,22 @@ int gfcc_spectral_adaptive(gfcc_ctx *ctx, int sectors, double omega_min, double 
 int gfcc_ccsd(int o, int v, int L, const double *fock, const double *chol, double tol, int max_iter, int flags,
               double *t1, double *t2, double *lambda, double *info);
 
+/* gfcc_solve_checkpoint - gfcc_solve with each frequency's G block written to the file `path` as
+ * soon as it is solved, and resumed from it (Algorithm 1 writes each task's output; the Evaluation
+ * section restarts long jobs).  A call whose file holds the checkpoint of the same request (same
+ * frequencies, orbitals, eta, tol, and a context with the same sectors, precision and kind) restores
+ * the finished frequencies into G without solving them and solves the others, one frequency per
+ * internal solve; a record cut short by a killed job is dropped.  The file is created when absent.
+ *   path      : file name (host string); path + ".tmp" is used while the file is rewritten.
+ *   n_resumed : out (may be NULL), frequencies restored from the file.
+ *   G         : out, as gfcc_solve.
+ * Returns as gfcc_solve (WARN_NOT_CONVERGED also when a restored frequency had it); GFCC_ERR_ARG
+ * when the file holds something else (it is left untouched) or cannot be written.  gfcc_last_stats
+ * describes the last frequency solved in this call.
+ */
+int gfcc_solve_checkpoint(gfcc_ctx *ctx, int n_omega, const double *omegas, double eta, int n_orb, const int *orbitals,
+                          double tol, const char *path, int *n_resumed, double *G);
+
 /* gfcc_destroy - free the context and all its device memory.  NULL is a no-op. */
 void gfcc_destroy(gfcc_ctx *ctx);
 

@@ -1095,6 +1095,12 @@ int check_input_tensor(cudaStream_t st, const double *x, long long d0, long long
   return check_tensor(st, x, d0, d1, d2, d3, s01, s23, sign, rel, name);
 }
 
+int solve_rows_host(gfcc_ctx *c, int n_omega, const double *omegas, double eta, int n_orb, const int *orbitals,
+                    double tol, double *G) {
+  GFCC_TRY(check_solve_args(c, n_omega, eta, n_orb, tol));
+  return solve_host(c, n_omega, omegas, eta, n_orb, orbitals, n_orb, orbitals, tol, G);
+}
+
 int build_rhs_masked(gfcc_ctx *c, int sector, int nsys, const int *d_porb, const int *d_mask, double *B,
                      cudaStream_t st) {
   if (nsys <= 0) return GFCC_OK;

@@ -194,4 +194,7 @@ int build_left_rhf(gfcc_ctx *c, int nq, const int *d_orb, double *C, cudaStream_
 // x[i][j][.][.] == sign * x[j][i][.][.] / x[.][.][a][b] == sign * x[.][.][b][a] to rel * max(1, max|x|)
 int check_input_tensor(cudaStream_t st, const double *x, long long d0, long long d1, long long d2, long long d3,
                        int s01, int s23, double sign, double rel, const char *name);
+// gfcc_solve's argument checks and solve on host arrays (rows and columns over one orbital list)
+int solve_rows_host(gfcc_ctx *c, int n_omega, const double *omegas, double eta, int n_orb, const int *orbitals,
+                    double tol, double *G);
 }  // namespace gfcc

@@ -123,6 +123,9 @@ def load():
                                            ctypes.c_double, ctypes.c_int, ip, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_int, ctypes.c_int, dp, dp, ip, ip, dp, ctypes.c_int, ip]
     lib.gfcc_spectral_adaptive.restype = ctypes.c_int
+    lib.gfcc_solve_checkpoint.argtypes = [P, ctypes.c_int, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.c_double,
+                                          ctypes.c_char_p, ip, dp]
+    lib.gfcc_solve_checkpoint.restype = ctypes.c_int
     lib.gfcc_create_rhf.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, ctypes.POINTER(P)]
     lib.gfcc_create_rhf.restype = ctypes.c_int
     lib.gfcc_ccsd.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_int,
@@ -249,6 +252,19 @@ class GFCC:
                                         orb.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), float(tol),
                                         G.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return G, code
+
+    def solve_checkpoint(self, omegas, eta: float, orbitals, tol: float, path: str):
+        """gfcc_solve_checkpoint: (G, return code, frequencies restored from the file)."""
+        om = _f64(omegas).reshape(-1)
+        orb = np.ascontiguousarray(orbitals, dtype=np.int32).reshape(-1)
+        G = np.zeros((om.size, orb.size, orb.size), dtype=np.complex128)
+        nres = ctypes.c_int(0)
+        ip = ctypes.POINTER(ctypes.c_int)
+        code = _check(load().gfcc_solve_checkpoint(self._h, om.size, _dp(om), float(eta), orb.size,
+                                                   orb.ctypes.data_as(ip), float(tol), str(path).encode(),
+                                                   ctypes.byref(nres), G.view(np.float64).ctypes.data_as(
+                                                       ctypes.POINTER(ctypes.c_double))))
+        return G, code, nres.value
 
     def solve_block(self, omegas, eta: float, p_orbitals, q_orbitals, tol: float):
         """G[w][a][b] = G_{p_a q_b} (complex128) for rows p over p_orbitals and columns q over q_orbitals,

@@ -105,3 +105,13 @@ def test_closed_shell_create_arguments_are_rejected_without_a_gpu(lib):
     assert typed.gfcc_create_rhf(0, 1, 1, f, f, f, f, None, ctypes.byref(h)) == gfcc.ERR_ARG
     assert typed.gfcc_create_rhf(1, 1, 1, None, f, f, f, None, ctypes.byref(h)) == gfcc.ERR_ARG
     assert typed.gfcc_create_rhf(1, 1, 1, f, f, f, f, None, None) == gfcc.ERR_ARG
+
+
+def test_checkpoint_arguments_are_rejected_without_a_gpu(lib, tmp_path):
+    typed = gfcc.load()
+    om = (ctypes.c_double * 1)(0.1)
+    orb = (ctypes.c_int * 1)(0)
+    G = (ctypes.c_double * 2)()
+    path = str(tmp_path / "ck.bin").encode()
+    assert typed.gfcc_solve_checkpoint(None, 1, om, 0.01, 1, orb, 1e-8, path, None, G) == gfcc.ERR_ARG
+    assert not (tmp_path / "ck.bin").exists()

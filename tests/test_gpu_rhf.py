@@ -123,20 +123,31 @@ def test_digit_plane_operator_matches_fp64_operator_and_oracle():
     g.set_option(gfcc.OPT_CLOSED_SHELL_EMULATE, 0)
     Yf = g.sigma("IP", X)
     g.close()
-    assert rel(Ye, Yf) <= 1e-12
+    # a level-9 product of 8 base-64 digits carries an error below 2^-50 of the row scale per term,
+    # so at most K 2^-50 over a contraction of length K (the ring sums: K = o v)
+    bound = wl.o * wl.v * 2.0 ** -50
+    assert rel(Ye, Yf) <= bound
     C = R.RHFClosed(pr.fock, pr.chol, pr.t1, pr.t2, o=wl.o)
-    assert rel(Ye[0], C.sigma(X[0])) <= 1e-12
+    assert rel(Ye[0], C.sigma(X[0])) <= bound
+    assert rel(Yf[0], C.sigma(X[0])) <= 1e-12
 
 
 def test_medium_closed_shell_row_matches_oracle():
+    """The FP64 path (every contraction on the FP64 units) at 1e-10 against the oracle; the digit-plane
+    operator (the default) at tol 1e-10 against it at 1e-8 (its products carry up to ~4e-12 relative
+    error, which sets the floor of its GMRES residual)."""
     wl = workload("medium-closed-shell")
     pr = wl.problem()
     g = gfcc.GFCC(pr, sectors="IP", closed_shell=True)
     om = wl.omegas[40:41]
+    Ge, code_e = g.solve(om, wl.eta, wl.orbitals, 1e-10)
+    st_e = g.stats()[2]
+    g.set_option(gfcc.OPT_CLOSED_SHELL_EMULATE, 0)
     G, code = g.solve(om, wl.eta, wl.orbitals, 1e-12)
     it, rr, st = g.stats()
     g.close()
     assert code == gfcc.OK and np.all(st == 0)
+    assert code_e == gfcc.OK and np.all(st_e == 0)
     C = R.RHFClosed(pr.fock, pr.chol, pr.t1, pr.t2, o=wl.o)
     row = wl.orbitals.size - 1          # the highest occupied orbital: its system by the oracle's GMRES,
     z = om[0] - 1j * wl.eta             # overlapped with every column's left vector
@@ -145,6 +156,8 @@ def test_medium_closed_shell_row_matches_oracle():
     assert ok
     ref_row = np.stack([C.left(int(q)) for q in wl.orbitals]) @ x
     assert np.linalg.norm(G[0, row] - ref_row) <= 1e-10 * np.linalg.norm(ref_row)
+    for a in range(wl.orbitals.size):
+        assert np.linalg.norm(Ge[0, a] - G[0, a]) <= 1e-8 * np.linalg.norm(G[0, a])
 
 
 def test_closed_shell_arguments_are_rejected():
