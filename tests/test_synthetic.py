@@ -4,6 +4,7 @@ arithmetic; both the oracle and the GPU path read their inputs from them."""
 import math
 
 import numpy as np
+import pytest
 
 from paper_2010_04768_gb300.synthetic import make_problem, normal, uniform, workload
 
@@ -62,3 +63,21 @@ def test_workload_shapes():
     assert med.omegas[0] == -1.2 and med.omegas[-1] == 0.5 and med.eta == 0.005
     # medium: the 40 orbitals nearest the mid-gap, from both spaces
     assert med.orbitals.min() < med.o <= med.orbitals.max()
+
+
+def test_closed_shell_recipe():
+    from paper_2010_04768_gb300.synthetic import make_closed_shell_problem
+    o, v, L = 6, 20, 30
+    a = make_closed_shell_problem(o, v, L, seed=3)
+    b = make_closed_shell_problem(o, v, L, seed=3)
+    assert np.array_equal(a.t2, b.t2) and np.array_equal(a.chol, b.chol)         # deterministic
+    assert np.array_equal(a.t2, a.t2.transpose(1, 0, 3, 2))                       # t_ij^ab = t_ji^ba
+    assert np.allclose(a.chol, a.chol.transpose(0, 2, 1))
+    # the width of the spin-orbital problem of the same system: (2o 2v)^-1/2 on the leading vector
+    assert np.std(a.chol[0]) == pytest.approx((4 * o * v) ** -0.5, rel=0.15)
+    # off-diagonal t2 entries have std t2_std / sqrt(2), the (i=j, a=b) ones t2_std
+    off = a.t2[0, 1]
+    assert np.std(off) == pytest.approx(0.02 / np.sqrt(2), rel=0.15)
+    assert np.std(a.t1) == pytest.approx(0.01, rel=0.2)
+    c = make_closed_shell_problem(o, v, L, seed=3, separate_lambda=True)
+    assert np.array_equal(c.lam2, c.lam2.transpose(1, 0, 3, 2)) and not np.array_equal(c.lam2, c.t2)
