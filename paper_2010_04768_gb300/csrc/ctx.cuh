@@ -91,6 +91,7 @@ struct gfcc_ctx {
   double *rWT = nullptr;    // [(i,j,a)][e | m]: -t_ij^ea | -W_maij  (o^2 v x (v + o))
   double *rVz = nullptr;    // [e][(m,n,f)]: 2 u_mnef - u_mnfe  (v x o^2 v)
   double *rU1 = nullptr;    // [i][m | (m,n,e)]: the 1h row (o x (o + o^2 v))
+  gfcc::EmuOperand rM1e, rM2e, rM3e;   // digit planes of the ring matrices (when they fit)
 
   // mixed-precision IP operands: BF16, K-major, row strides padded to multiples of 8.  The exact
   // Fock-like diagonal d (diag_ip) is left out of them and applied in FP64 by the epilogue.

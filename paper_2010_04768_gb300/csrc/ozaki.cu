@@ -297,4 +297,48 @@ int gemm_f64_emulated(cudaStream_t st, long long M, long long N, long long K, do
   return s;
 }
 
+int gemm_f64_emulated_pre(cudaStream_t st, const EmuOperand &A, long long N, const double *B, IMap bk, IMap bn,
+                          double alpha, double beta, double *C, IMap cm, IMap cn, int P) {
+  const long long M = A.rows, K = A.K, S = A.S;
+  if (M <= 0 || N <= 0) return GFCC_OK;
+  GFCC_TRY(check_extent(B, 0, imap_max(bk, K) + imap_max(bn, N), "emulated contraction operand B"));
+  GFCC_TRY(check_extent(C, 0, imap_max(cm, M) + imap_max(cn, N), "emulated contraction output C"));
+  const long long ld = (K + 7) / 8 * 8;
+  if (A.ld != ld) {
+    set_error("emulated contraction: the sliced operand's row stride %lld is not %lld", A.ld, ld);
+    return GFCC_ERR_ARG;
+  }
+  const long long budget = 12LL << 30;
+  const long long nk = (K + 63) / 64, nz = (nk + KCHUNK_BLOCKS - 1) / KCHUNK_BLOCKS;
+  const long long per_col = ld * 8 + S * ld * 2 + nz * M * 4 + M * 8;
+  long long nb = std::max<long long>(256, budget / std::max<long long>(per_col, 1));
+  nb = std::min(nb, N);
+  void *bg = nullptr, *bdig = nullptr, *w = nullptr;
+  int s = GFCC_OK;
+  if (dmalloc(&bg, sizeof(double) * nb * ld) != cudaSuccess || dmalloc(&bdig, emu_operand_bytes(nb, K, (int)S)) != cudaSuccess ||
+      dmalloc(&w, emu_gemm_work_bytes(M, nb, K)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("emulated contraction: cannot allocate its temporaries (M=%lld N-block=%lld K=%lld)", M, nb, K);
+    s = GFCC_ERR_OOM;
+  }
+  EmuOperand eb;
+  for (long long n0 = 0; n0 < N && s == GFCC_OK; n0 += nb) {
+    const long long cols = std::min(nb, N - n0);
+    gather_kernel<<<grid1d(cols * ld), 256, 0, st>>>(B, cols, K, ld, bn, bk, n0, static_cast<double *>(bg));
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) {
+      s = GFCC_ERR_CUDA;
+      break;
+    }
+    s = emu_slice(st, static_cast<double *>(bg), cols, K, ld, (int)S, bdig, eb);
+    if (s == GFCC_OK) s = emu_gemm(st, A, eb, P, alpha, beta, C, cm, cn, w, n0);
+  }
+  if (s == GFCC_OK && cudaStreamSynchronize(st) != cudaSuccess) {
+    set_error("emulated contraction failed: %s", cudaGetErrorString(cudaGetLastError()));
+    s = GFCC_ERR_CUDA;
+  }
+  for (void *q : {bg, bdig, w}) dfree(q);
+  return s;
+}
+
 }  // namespace gfcc

@@ -45,4 +45,9 @@ int gemm_f64_emulated(cudaStream_t st, long long M, long long N, long long K, do
                       IMap ak, const double *B, IMap bk, IMap bn, double beta, double *C, IMap cm, IMap cn, int S,
                       int P);
 
+// The same with A already split into digit planes (rows x K, K-major; emu_slice with S digits): only B
+// (given through its index maps, N columns) is gathered and split per call.
+int gemm_f64_emulated_pre(cudaStream_t st, const EmuOperand &A, long long N, const double *B, IMap bk, IMap bn,
+                          double alpha, double beta, double *C, IMap cm, IMap cn, int P);
+
 }  // namespace gfcc

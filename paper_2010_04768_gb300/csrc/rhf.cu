@@ -24,9 +24,17 @@
 
 #include "ctx.cuh"
 #include "kernels.cuh"
+#include "ozaki.cuh"
 #include "sigma.cuh"
 
 namespace gfcc {
+
+// Contractions of at least this many flops run on the FP64-accurate digit-plane path when the
+// context's emulation option is on (the ring sums and the oooo term at useful sizes; the narrow ones
+// stay on the FP64 units); the digit planes of the ring matrices are cut once at setup with the
+// digit count and pair level of the setup's emulated contractions
+constexpr double RHF_EMULATE_MIN_FLOPS = 1e9;
+constexpr int RHF_EMU_DIGITS = 8, RHF_EMU_LEVEL = 9;
 
 namespace {
 
@@ -343,6 +351,25 @@ int build_hbar_rhf(gfcc_ctx *c, const double *d_fock, const double *d_chol) {
   GFCC_LAUNCH_CHECK();
   rhf_fold_kernel<<<cdiv(ov, 128), 128, 0, st>>>(c->rM2, o, v, c->Foo, c->Fvv, -1.0, 1.0);
   GFCC_LAUNCH_CHECK();
+  // digit planes of the three ring matrices, sliced once here for the digit-plane operator (when the
+  // three together take at most a quarter of the free device memory)
+  {
+    const long long eb = emu_operand_bytes(ov, ov, RHF_EMU_DIGITS);
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      cudaGetLastError();
+      fr = 0;
+    }
+    if (3.0 * (double)eb <= 0.25 * (double)fr) {
+      gfcc::EmuOperand *ops[3] = {&c->rM1e, &c->rM2e, &c->rM3e};
+      double *mats[3] = {c->rM1, c->rM2, c->rM3};
+      for (int k = 0; k < 3; k++) {
+        double *mem;
+        GFCC_TRY(dev_alloc(c, &mem, eb / 8 + 1));
+        GFCC_TRY(emu_slice(st, mats[k], ov, ov, ov, RHF_EMU_DIGITS, mem, *ops[k]));
+      }
+    }
+  }
 
   // ---- [(i,j,a)][e | m] = [-t_ij^ea | -W_maij]
   {
@@ -384,11 +411,6 @@ int build_hbar_rhf(gfcc_ctx *c, const double *d_fock, const double *d_chol) {
   return GFCC_OK;
 }
 
-// Contractions of at least this many flops run on the FP64-accurate digit-plane path when the
-// context's emulation option is on (the ring sums and the oooo term at useful sizes; the narrow ones
-// stay on the FP64 units)
-constexpr double RHF_EMULATE_MIN_FLOPS = 1e9;
-
 namespace {
 struct EmulateScope {
   bool prev_big;
@@ -425,15 +447,21 @@ int apply_ip_rhf(gfcc_ctx *c, const SysBatch &b, double *work) {
   GFCC_TRY(gemm_f64(st, oo, v * C2, oo, 1.0, c->Woooo, imap1(1), imap1(oo), r2u, imap1(v * C2), imap1(1), 1.0, S2,
                     imap1(v * C2), imap1(1)));
   {
-    PhaseTimer tr(c, PH_RING, 3.0 * 2.0 * (double)ov * (double)ov * (double)(o * C2));
+    const double rflops = 2.0 * (double)ov * (double)ov * (double)(o * C2);
+    PhaseTimer tr(c, PH_RING, 3.0 * rflops);
+    // the ring matrix k times the B operand (maps bk, bn) into S2 (maps cm, cn): from its digit
+    // planes cut at setup when the operator runs on digit planes, else through gemm_f64
+    auto ring = [&](const double *Mk, const EmuOperand &Ek, IMap bk, IMap bn, IMap cm, IMap cn) -> int {
+      if (c->rhf_emulate && Ek.dig != nullptr && rflops >= RHF_EMULATE_MIN_FLOPS)
+        return gemm_f64_emulated_pre(st, Ek, o * C2, r2u, bk, bn, 1.0, 1.0, S2, cm, cn, RHF_EMU_LEVEL);
+      return gemm_f64(st, ov, o * C2, ov, 1.0, Mk, imap1(ov), imap1(1), r2u, bk, bn, 1.0, S2, cm, cn);
+    };
     // + M1[(i,a)][(m,e)] r[m][j][e]
-    GFCC_TRY(gemm_f64(st, ov, o * C2, ov, 1.0, c->rM1, imap1(ov), imap1(1), r2u, imap2(v, C2, ov * C2),
-                      imap2(C2, 1, v * C2), 1.0, S2, imap2(v, C2, ov * C2), imap2(C2, 1, v * C2)));
+    GFCC_TRY(ring(c->rM1, c->rM1e, imap2(v, C2, ov * C2), imap2(C2, 1, v * C2), imap2(v, C2, ov * C2),
+                  imap2(C2, 1, v * C2)));
     // + M2[(j,a)][(m,e)] r[i][m][e] + M3[(j,a)][(m,e)] r[m][i][e]
-    GFCC_TRY(gemm_f64(st, ov, o * C2, ov, 1.0, c->rM2, imap1(ov), imap1(1), r2u, imap1(C2), imap2(C2, 1, ov * C2), 1.0,
-                      S2, imap1(C2), imap2(C2, 1, ov * C2)));
-    GFCC_TRY(gemm_f64(st, ov, o * C2, ov, 1.0, c->rM3, imap1(ov), imap1(1), r2u, imap2(v, C2, ov * C2),
-                      imap2(C2, 1, v * C2), 1.0, S2, imap1(C2), imap2(C2, 1, ov * C2)));
+    GFCC_TRY(ring(c->rM2, c->rM2e, imap1(C2), imap2(C2, 1, ov * C2), imap1(C2), imap2(C2, 1, ov * C2)));
+    GFCC_TRY(ring(c->rM3, c->rM3e, imap2(v, C2, ov * C2), imap2(C2, 1, v * C2), imap1(C2), imap2(C2, 1, ov * C2)));
   }
   // S1 = U1 [r1u; r2u]
   GFCC_TRY(gemm_f64(st, o, C2, o + o2v, 1.0, c->rU1, imap1(o + o2v), imap1(1), r1u, imap1(C2), imap1(1), 0.0, S1,
