@@ -151,16 +151,13 @@ void set_error(const char *fmt, ...) {
 namespace {
 
 // ---------------------------------------------------------------- input checks (device)
-__device__ __forceinline__ void atomic_max_abs(unsigned long long *dst, double v) {
-  // |v| as IEEE bits orders like an unsigned integer (NaN sorts above +inf)
-  const unsigned long long bits = __double_as_longlong(fabs(v)) & 0x7fffffffffffffffULL;
-  atomicMax(dst, bits);
-}
-
 // out[0] = max |x|; out[1] = max |x - sign * x^P| over the permutation given by (swap01, swap23) of a 4-index tensor
+// (per-thread maxima of the |value| bit patterns, which order like unsigned integers with NaN above
+// +inf, reduced over the warp, one atomic per warp and quantity; launched with whole warps)
 __global__ void symmetry_kernel(const double *x, long long d0, long long d1, long long d2, long long d3, int swap01,
                                 int swap23, double sign, unsigned long long *out) {
   const long long tot = d0 * d1 * d2 * d3;
+  unsigned long long m0 = 0, m1 = 0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     long long r = t;
     const long long k3 = r % d3; r /= d3;
@@ -172,8 +169,16 @@ __global__ void symmetry_kernel(const double *x, long long d0, long long d1, lon
     if (swap23) { p2 = k3; p3 = k2; }
     const double a = x[t];
     const double b = x[((p0 * d1 + p1) * d2 + p2) * d3 + p3];
-    atomic_max_abs(out, a);
-    atomic_max_abs(out + 1, a - sign * b);
+    m0 = max(m0, (unsigned long long)__double_as_longlong(fabs(a)) & 0x7fffffffffffffffULL);
+    m1 = max(m1, (unsigned long long)__double_as_longlong(fabs(a - sign * b)) & 0x7fffffffffffffffULL);
+  }
+  for (int w = 16; w > 0; w >>= 1) {
+    m0 = max(m0, __shfl_xor_sync(0xffffffffu, m0, w));
+    m1 = max(m1, __shfl_xor_sync(0xffffffffu, m1, w));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out, m0);
+    atomicMax(out + 1, m1);
   }
 }
 
