@@ -420,8 +420,14 @@ def run_reference(args, world, rank):
         seconds = res["seconds"] * args.steps
     else:
         problem = wl.problem()
-        res = cpu_baseline(wl, spec, problem, max_columns=max(1, args.steps))
-        seconds = res["seconds"]
+        if wl.closed_shell:
+            # the closed-shell oracle; each step one column (the frequency of timed step 1)
+            cols = [cpu_baseline_closed_shell(wl, problem) for _ in range(max(1, args.steps))]
+            seconds = sum(c["seconds"] for c in cols)
+            res = dict(cols[0], value=len(cols) / seconds)
+        else:
+            res = cpu_baseline(wl, spec, problem, max_columns=max(1, args.steps))
+            seconds = res["seconds"]
     line = {"metric": "converged G(omega) columns/sec", "value": res["value"], "unit": "columns/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * seconds / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
