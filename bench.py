@@ -407,7 +407,7 @@ def run_reference(args, world, rank):
                                   "d2h_bytes_per_step": 0}}), flush=True)
         return 0
     wl = workload(spec["base"])
-    if wl.name == "c60":
+    if wl.name.startswith("c60") and not wl.closed_shell:
         mo = MediumOracle()
         for _ in range(args.warmup):
             mo.warm()
@@ -800,7 +800,7 @@ def main():
         line["sampled_row_check"] = row_check
     if not args.no_cpu_baseline:
         try:
-            if wl.name == "c60":
+            if wl.name.startswith("c60") and not wl.closed_shell:
                 cb = cpu_baseline_extrapolated(wl, plain["iterations_per_column"] if plain else None)
             elif wl.closed_shell:
                 cb = cpu_baseline_closed_shell(wl, problem)
